@@ -1,0 +1,55 @@
+/*
+ * gpo.h -- FP64 CPU oracle for the split-step Crank-Nicolson propagator of the
+ * time-dependent Gross-Pitaevskii equation
+ *     i dphi/dt = [ -lap/2 + V(r) + g |phi|^2 ] phi
+ * (paper: "Solution method" of the program summary -- split-step Crank-Nicolson,
+ * imaginary- and real-time propagation; "Nature of problem" -- 1d, 2d, 3d,
+ * fully anisotropic Cartesian traps).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that the
+ * CUDA path is checked against.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * or constant with the CUDA library.
+ *
+ * The paper names the method but prints none of its formulas, so every
+ * discretisation detail below is a reading of the method; the readings are
+ * listed where each function is defined.
+ *
+ * Layout: complex interleaved (re, im) doubles, x fastest:
+ *     idx = i + nx * (j + ny * k).
+ */
+#ifndef GPO_H
+#define GPO_H
+#include <complex.h>
+
+typedef struct {
+  int dim;            /* 1, 2 or 3 */
+  int n[3];           /* points per axis (trailing entries ignored) */
+  double dx[3];       /* grid spacing per axis */
+  double dt;          /* time step (imaginary-time step in imag mode) */
+  double nkl[3];      /* trap frequencies nu, kappa, lambda */
+  double g;           /* nonlinearity */
+  const double* V;    /* NULL: harmonic trap; else full potential on the grid */
+} gpo_problem;
+
+long gpo_npoints(const gpo_problem* p);
+void gpo_coords(int n, double dx, double* x);
+void gpo_potential(const gpo_problem* p, double* V);
+void gpo_simpson_weights(int n, double dx, double* w);
+
+void gpo_phase(const gpo_problem* p, int imag, double complex* phi);
+void gpo_sweep(const gpo_problem* p, int imag, int axis, double sign, double complex* phi);
+void gpo_step(const gpo_problem* p, int imag, double complex* phi);
+void gpo_run(const gpo_problem* p, int imag, long nsteps, double complex* phi);
+
+double gpo_norm(const gpo_problem* p, const double complex* phi);
+void gpo_observables(const gpo_problem* p, const double complex* phi, double out[7], double* density);
+
+double gpo_adjoint_real(const gpo_problem* p, long nsteps, const double complex* phi0,
+                        const double complex* target, double complex* phiT,
+                        double* dJdV, double* dJdg);
+void gpo_adjoint_phase(const gpo_problem* p, const double complex* phi_in,
+                       double complex* lam, double* dJdV, double* dJdg);
+
+int gpo_num_threads(void);
+#endif
