@@ -1,0 +1,370 @@
+"""Benchmark of the split-step Crank-Nicolson GP propagator on GB300.
+
+Workload (default): the 3d imaginary-time anisotropic trap -- 128^3 grid,
+dx = 0.1, dt = 1e-3, V = (nu^2 x^2 + kappa^2 y^2 + lambda^2 z^2)/2 with
+nu, kappa, lambda = 1, 1.4, 1.8, g = 50, seeded-noise Gaussian initial state.
+One bench step = ``--inner`` imaginary-time steps (renormalised every step)
+followed by one evaluation of the observables (norm, energy, mu, rms), i.e.
+one pass of the whole hot path.  The metric is grid-point-steps per second.
+
+Two forms are timed: the plain FP64 path and the chosen FP32 form (FP32 state
+and sweeps, FP64 norm/energy/mu reductions and renormalisation).  ``value`` is
+the FP32 form's throughput; its mu error is measured against the FP64 path
+over the full 5000-step job (the FP64 path itself is held to the CPU oracle
+by the parity tests).
+
+The state (16.8 MB FP32, 33.5 MB FP64) fits in the 129 MB L2, so L2 is
+flushed (a 256 MB write) before every timed bench step; within a bench step
+the state stays resident across time steps, as it does in a real run.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "name": "imag3d_128: 3d imaginary-time anisotropic trap, 128^3, dx=0.1, dt=1e-3, "
+            "nu,kappa,lambda=1,1.4,1.8, g=50, 5000-step job",
+    "dim": 3, "n": [128, 128, 128], "dx": [0.1, 0.1, 0.1], "dt": 1e-3,
+    "nkl": [1.0, 1.4, 1.8], "g": 50.0, "seed": 1710, "job_steps": 5000,
+}
+METRIC = "3d split-step CN grid-point-steps/s: FP32/batched vs FP64 at fixed mu error"
+UNIT = "grid-point-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", type=int, default=100, help="time steps per bench step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mu-check", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1709_04423_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from a committed ncu capture, if the kernels have
+    not changed since it was taken (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    r = rec.get(kernel_key)
+    if not r or r.get("src_hash") != src_hash():
+        return None
+    return r.get("bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_rate(target_s=10.0, max_steps=40):
+    """Oracle (FP64, C, OpenMP over lines) on the host cores: imaginary-time
+    steps of the same workload, as many as fit in about target_s seconds."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1709_04423_gb300 import inputs
+    w = WORKLOAD
+    gr = O.Grid(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"])
+    phi = inputs.gaussian_state(w["dim"], w["n"], w["dx"], w["nkl"], seed=w["seed"], noise=1e-3)
+    t0 = time.perf_counter()
+    phi = O.run(gr, phi, True, 1)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(max_steps, int(target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    phi = O.run(gr, phi, True, k)
+    dt = time.perf_counter() - t0
+    np_ = int(np.prod(w["n"]))
+    return {"value": k * np_ / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{k} imaginary-time steps of the 128^3 workload (FP64, OpenMP over lines)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    import numpy as np
+
+    from paper_1709_04423_gb300 import inputs
+    w = WORKLOAD
+    gr = O.Grid(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"])
+    phi = inputs.gaussian_state(w["dim"], w["n"], w["dx"], w["nkl"], seed=w["seed"], noise=1e-3)
+    np_ = int(np.prod(w["n"]))
+    per = 2  # imaginary-time steps of the oracle per bench step
+    for _ in range(args.warmup):
+        phi = O.run(gr, phi, True, per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi = O.run(gr, phi, True, per)
+        O.observables(gr, phi)
+    dt = time.perf_counter() - t0
+    value = args.steps * per * np_ / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "inner_steps_per_step": per, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{per} imaginary-time steps + observables of the 128^3 workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1709_04423_gb300 import build as B
+    B.build()
+    from paper_1709_04423_gb300 import gpe, inputs
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOAD
+    np_ = int(np.prod(w["n"]))
+    phi0 = inputs.gaussian_state(w["dim"], w["n"], w["dx"], w["nkl"], seed=w["seed"], noise=1e-3)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def make(prec):
+        with torch.cuda.stream(stream):
+            p = gpe.Propagator(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"], precision=prec,
+                               stream=stream)
+            p.set_state(torch.tensor(phi0, device="cuda"))
+        return p
+
+    results = {}
+    # ---- mu accuracy of the FP32 form over the full job (untimed)
+    mu = {}
+    if not args.no_mu_check:
+        for prec in ("f64", "f32"):
+            p = make(prec)
+            with torch.cuda.stream(stream):
+                p.step_imag(w["job_steps"])
+                mu[prec] = p.observables()
+            p.close()
+    # ---- timed forms
+    for prec in ("f64", "f32"):
+        p = make(prec)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                p.step_imag(args.inner)
+                p.observables()
+            barrier()
+            l0 = gpe.gp_kernel_launches()
+            with ClockSampler(local) as clk:
+                for s in range(args.steps):
+                    flush.fill_(float(s))                 # evict the state from L2
+                    ev[s][0].record(stream)
+                    p.step_imag(args.inner)
+                    p.observables()
+                    ev[s][1].record(stream)
+                barrier()
+            launches = gpe.gp_kernel_launches() - l0
+            ms = [a.elapsed_time(b) for a, b in ev]
+            total_s = max_over_ranks(sum(ms) / 1e3)
+            # per-kernel durations, same state and sizes, right after the timed region
+            kms = p.time_sweeps(True, 64)
+            ob = p.observables()
+        p.close()
+        results[prec] = {"total_s": total_s, "ms": ms, "launches": launches, "clocks": clk.summary(),
+                         "kernel_ms": kms, "obs": ob}
+    # ---- end to end through the public API with host buffers (FP32 form)
+    e2e = None
+    p = make("f32")
+    host = torch.tensor(phi0.astype(np.complex64)).pin_memory()
+    hnp = host.numpy()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            p.set_state(hnp)
+            p.step_imag(args.inner)
+            p.observables()
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            p.set_state(hnp)                       # H2D of the state from pinned host memory
+            p.step_imag(args.inner)
+            ob = p.observables()                   # D2H of the observables
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+    p.close()
+    e2e = {"value": world * args.steps * args.inner * np_ / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(hnp.nbytes), "d2h_bytes_per_step": 7 * 8}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+
+    def roofline(prec):
+        r = results[prec]
+        kms = r["kernel_ms"]
+        axis = max(range(3), key=lambda d: kms[d])
+        esize = 16 if prec == "f64" else 8
+        algo = 2 * esize * np_                      # one read + one write of the state
+        achieved = algo / (kms[axis] * 1e-3) / 1e9
+        key = f"sweep_axis{axis}_{prec}_imag_128cube"
+        tr = traffic_record(key)
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": tr, "kernel": key,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                "kernel_ms": kms}
+
+    forms = {}
+    for prec in ("f64", "f32"):
+        r = results[prec]
+        v = world * args.steps * args.inner * np_ / r["total_s"]
+        forms[prec] = {"value": v, "ms_per_step": 1e3 * r["total_s"] / args.steps,
+                       "mu": r["obs"]["mu"], "roofline": roofline(prec)}
+    mu_err = abs(mu["f32"]["mu"] - mu["f64"]["mu"]) if mu else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_rate()
+    head = forms["f32"]
+    r32 = results["f32"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 state+sweeps, f64 reductions",
+        "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
+        "config": {"workload": w["name"], "global_batch": 1, "inner_steps_per_step": args.inner,
+                   "points": np_, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": head["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+        "forms": {
+            "f64": {"value": forms["f64"]["value"], "ms_per_step": forms["f64"]["ms_per_step"],
+                    "roofline": forms["f64"]["roofline"], "gpu_launches": results["f64"]["launches"],
+                    "clocks": results["f64"]["clocks"]},
+            "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": forms["f32"]["value"] / forms["f64"]["value"],
+                    "mu_err_vs_f64_full_job": mu_err,
+                    "mu_f32": mu["f32"]["mu"] if mu else None, "mu_f64": mu["f64"]["mu"] if mu else None},
+        },
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

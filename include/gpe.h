@@ -1,0 +1,150 @@
+/*
+ * gpe.h -- C ABI of the GB300 split-step Crank-Nicolson propagator for the
+ * time-dependent Gross-Pitaevskii (GP) equation
+ *
+ *     i d(phi)/dt = [ -lap/2 + V(r) + g |phi|^2 ] phi
+ *
+ * in imaginary time (stationary states) and real time (dynamics) on 1d, 2d and
+ * 3d Cartesian grids.  The paper's "Solution method" names the scheme:
+ * split-step Crank-Nicolson with imaginary- and real-time propagation; its
+ * "Nature of problem" gives the 1d/2d/3d fully anisotropic traps, and its
+ * abstract and "Summary of revisions" list the outputs: energy, chemical
+ * potential, root-mean-square sizes and densities.
+ *
+ * Discrete scheme (the paper prints no formula; these are the readings the
+ * library implements):
+ *   grid       x_i = -n dx/2 + i dx, i = 0..n-1 per axis;
+ *   potential  V = (nu^2 x^2 + kappa^2 y^2 + lambda^2 z^2)/2, or a user array;
+ *   one step   N, then L_x, L_y, L_z (Lie splitting, full dt each), where
+ *              N:   phi <- exp(-i dt (V + g|phi|^2)) phi      (real time)
+ *                   phi <- exp(-dt (V + g|phi|^2)) phi        (imaginary time)
+ *              L_d: Crank-Nicolson along axis d with Dirichlet ends held at 0:
+ *                   -r u[k-1] + (1+2r) u[k] - r u[k+1]
+ *                        = r p[k-1] + (1-2r) p[k] + r p[k+1],  k = 1..n-2,
+ *                   r = i dt/(4 dx^2) (real) or dt/(4 dx^2) (imaginary);
+ *   imaginary time renormalises phi <- phi/sqrt(Norm) after every step, with
+ *   Norm the composite-Simpson integral of |phi|^2 (Simpson on the first n
+ *   points for odd n, the first n-1 for even n; tensor product across axes).
+ *
+ * Memory layout of every grid array: x fastest, idx = i + nx*(j + ny*k).
+ * States are complex, interleaved (re, im), in the handle's precision:
+ * double2 for GP_F64, float2 for GP_F32.  Potentials and densities are double.
+ *
+ * Errors: every call returns GP_OK (0) or a negative code; gp_last_error()
+ * returns a thread-local message for the last failure.  No call aborts or
+ * throws.  Arguments are validated on the host before anything is launched.
+ *
+ * Streams: a handle is bound to the CUDA stream given at creation (NULL means
+ * the legacy default stream).  Work is enqueued in order on that stream; calls
+ * that return host data synchronise it.  Internally the library runs on its
+ * own non-blocking stream joined to the caller's stream by events, so that it
+ * can replay step loops as CUDA graphs.
+ *
+ * Ownership: the handle owns the state, coefficients and scratch memory, all
+ * allocated at creation and freed by gp_destroy.  Caller buffers are only read
+ * or written during the call (host buffers) or in stream order (device
+ * buffers); the library keeps no pointer to them.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GP_OK = 0,
+  GP_ERR_INVALID = -1,   /* bad argument (size, spacing, NaN, NULL, ...) */
+  GP_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  GP_ERR_NONFINITE = -3, /* a reduction found NaN or Inf in the state */
+  GP_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
+  GP_ERR_STATE = -5      /* call not valid in the handle's current state */
+};
+
+typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision;
+
+typedef struct gp_handle gp_handle;
+
+/* Observables of psi = phi/sqrt(norm):
+ *   norm   = Simpson integral of |phi|^2 (of the stored state),
+ *   energy = int[ 1/2 sum_d |d_d psi|^2 + V|psi|^2 + g/2 |psi|^4 ],
+ *   mu     = int[ 1/2 sum_d |d_d psi|^2 + V|psi|^2 + g   |psi|^4 ],
+ *   rms[d] = sqrt(int x_d^2 |psi|^2) (0 for absent axes), rms_r = sqrt(sum rms^2).
+ * Derivatives: 4th-order central differences for 2 <= i <= n-3, 2nd-order at
+ * i = 1 and n-2, zero at the end points.  All sums are accumulated in FP64. */
+typedef struct {
+  double norm, energy, mu, rms[3], rms_r;
+} gp_obs;
+
+/* Creates a propagator.
+ *   dim      1, 2 or 3.
+ *   n        points per axis, n[d] >= 3 for d < dim (entries >= dim ignored);
+ *            at most 2^31-1 points in total.
+ *   dx       grid spacing per axis, > 0.
+ *   dt       time step, finite and != 0 (the same dt serves imaginary time).
+ *   nkl      trap frequencies nu, kappa, lambda of the harmonic potential.
+ *   g        nonlinearity, finite.
+ *   prec     GP_F64 or GP_F32 (FP32 state and sweeps; norm, energy, mu and
+ *            the renormalisation factor are still computed in FP64).
+ *   stream   cudaStream_t to order work on (NULL = legacy default stream).
+ * The state starts at zero: call gp_set_state before stepping. */
+int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double dt,
+            const double nkl[3], double g, gp_precision prec, void* stream);
+
+/* Copies a state in (interleaved re, im, in the handle's precision, npoints
+ * values).  on_device != 0: psi is a device pointer read in stream order. */
+int gp_set_state(gp_handle* h, const void* psi, int on_device);
+
+/* Copies the state out in the handle's precision.  With on_device == 0 the
+ * call synchronises the stream. */
+int gp_get_state(gp_handle* h, void* psi, int on_device);
+
+/* Replaces the harmonic trap by a potential array (double, npoints values);
+ * V == NULL restores the harmonic trap. */
+int gp_set_potential(gp_handle* h, const double* V, int on_device);
+
+/* Changes the nonlinearity (e.g. the quench g -> 2g before real-time runs). */
+int gp_set_g(gp_handle* h, double g);
+
+/* Changes the time step and recomputes the elimination coefficients. */
+int gp_set_dt(gp_handle* h, double dt);
+
+/* Runs nsteps >= 0 imaginary-time steps, renormalising after each one.
+ * Asynchronous: enqueued on the handle's stream. */
+int gp_step_imag(gp_handle* h, long nsteps);
+
+/* Runs nsteps >= 0 real-time steps.  Asynchronous. */
+int gp_step_real(gp_handle* h, long nsteps);
+
+/* Computes the observables of the current state; density (optional, may be
+ * NULL) receives |phi|^2 as npoints doubles, on the device if
+ * density_on_device != 0.  Synchronises the stream.  Returns GP_ERR_NONFINITE
+ * if the state holds NaN or Inf. */
+int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device);
+
+/* Instrumentation: runs nsteps steps (imaginary time if imag != 0) launched
+ * one by one, with CUDA events on the library's stream around every sweep
+ * kernel, and stores the mean duration in milliseconds of the sweep along
+ * axis d in ms_per_launch[d] (d < 3; 0 for absent axes).  The state advances
+ * exactly as with gp_step_imag / gp_step_real.  0 <= nsteps <= 4096.
+ * Synchronises the stream. */
+int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch);
+
+/* Grid queries. */
+long gp_npoints(const gp_handle* h);
+int gp_precision_of(const gp_handle* h);
+
+/* Frees the handle and everything it owns (NULL is a no-op). */
+int gp_destroy(gp_handle* h);
+
+/* Thread-local message for the last error ("" if none). */
+const char* gp_last_error(void);
+
+/* Number of kernels this library has launched in this process (graph
+ * replays count every kernel node); for instrumentation. */
+unsigned long long gp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPE_H */

@@ -1,0 +1,106 @@
+// gpe_common.cuh -- shared device helpers of the GB300 split-step
+// Crank-Nicolson GP library: complex types, line geometry, FP64 block
+// reductions with a deterministic last-block finish.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+template <typename T> struct C2;
+template <> struct C2<double> { using type = double2; };
+template <> struct C2<float> { using type = float2; };
+template <typename T> using c2_t = typename C2<T>::type;
+
+template <typename T> __device__ __forceinline__ c2_t<T> mk(T x, T y) { c2_t<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Geometry of the lines of one sweep.  Line L of axis 0 starts at L*nx
+// (L = j + ny*k); of axis 1 at (L % nx) + (L / nx)*nx*ny (L = i + nx*k); of
+// axis 2 at L (L = i + nx*j).  Consecutive L of axes 1 and 2 are
+// neighbouring x positions, so a warp of consecutive lines reads whole rows.
+struct LineGeom {
+  int axis;
+  int n;        // points along the line
+  long stride;  // element distance between consecutive points
+  long nlines;
+  int nx, ny, nz;
+};
+
+__device__ __forceinline__ long line_base(const LineGeom& g, long L) {
+  if (g.axis == 0) return L * g.nx;
+  if (g.axis == 1) return (L % g.nx) + (L / g.nx) * (long)g.nx * g.ny;
+  return L;
+}
+
+// The two transverse indices (a, b) of line L: axis 0 -> (j, k), axis 1 ->
+// (i, k), axis 2 -> (i, j).
+__device__ __forceinline__ void line_transverse(const LineGeom& g, long L, int& a, int& b) {
+  if (g.axis == 0) { a = (int)(L % g.ny); b = (int)(L / g.ny); }
+  else { a = (int)(L % g.nx); b = (int)(L / g.nx); }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums K per-thread doubles over the block; thread 0 gets the totals.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* >= 32*K */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) smem[warp * K + q] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = lane < nw ? smem[lane * K + q] : 0.0;
+      v[q] = warp_sum(s);
+    }
+  }
+}
+
+// Writes the block's K totals to partials[blockIdx.x*K + q]; the last block to
+// finish sums all partials in block order (deterministic) and returns true
+// with the totals in tot[] (valid in thread 0 of that block only).  The
+// counter is reset for the next launch.
+template <int K>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials, unsigned int* counter,
+                                              double (&tot)[K], double* smem) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) partials[(long)blockIdx.x * K + q] = v[q];
+    __threadfence();
+    unsigned int done = atomicAdd(counter, 1u);
+    is_last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  // fixed-order sum: thread t takes blocks t, t+blockDim, ...; then the block tree
+  double acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] += __ldcg(&partials[(long)b * K + q]);
+  }
+  block_sum<K>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) tot[q] = acc[q];
+    *counter = 0u;
+  }
+  return true;
+}
+
+}  // namespace gpe

@@ -1,0 +1,266 @@
+"""Python binding of the GB300 split-step Crank-Nicolson GP library.
+
+Argument marshalling only: every step of the propagator runs in the CUDA
+kernels of ``libgpe.so`` behind the C ABI of ``include/gpe.h``.  The
+functions ``gp_*`` mirror the C entry points one to one (same names, same
+argument order); :class:`Propagator` is a small convenience wrapper that owns a
+handle and exchanges states as torch tensors (device memory and streams come
+from PyTorch).  There is no CPU fallback: if the library is missing or cannot
+be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpe.so")
+
+GP_OK = 0
+GP_ERR_INVALID = -1
+GP_ERR_CUDA = -2
+GP_ERR_NONFINITE = -3
+GP_ERR_TIMEOUT = -4
+GP_ERR_STATE = -5
+GP_F64 = 0
+GP_F32 = 1
+
+# every entry point declared in include/gpe.h
+ABI_SYMBOLS = (
+    "gp_init", "gp_set_state", "gp_get_state", "gp_set_potential", "gp_set_g", "gp_set_dt",
+    "gp_step_imag", "gp_step_real", "gp_observables", "gp_npoints", "gp_precision_of",
+    "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps",
+)
+
+
+class GPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class GpObs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("energy", ctypes.c_double), ("mu", ctypes.c_double),
+                ("rms", ctypes.c_double * 3), ("rms_r", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgpe.so (raises if it is absent: build it with build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgpe.so is not built ({path}); run paper_1709_04423_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    I, D, L = ctypes.c_int, ctypes.c_double, ctypes.c_long
+    lib.gp_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
+                            ctypes.POINTER(D), D, I, _vp]
+    lib.gp_set_state.argtypes = [_vp, _vp, I]
+    lib.gp_get_state.argtypes = [_vp, _vp, I]
+    lib.gp_set_potential.argtypes = [_vp, _vp, I]
+    lib.gp_set_g.argtypes = [_vp, D]
+    lib.gp_set_dt.argtypes = [_vp, D]
+    lib.gp_step_imag.argtypes = [_vp, L]
+    lib.gp_step_real.argtypes = [_vp, L]
+    lib.gp_observables.argtypes = [_vp, ctypes.POINTER(GpObs), _vp, I]
+    lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
+    lib.gp_npoints.argtypes = [_vp]
+    lib.gp_npoints.restype = L
+    lib.gp_precision_of.argtypes = [_vp]
+    lib.gp_destroy.argtypes = [_vp]
+    lib.gp_last_error.restype = ctypes.c_char_p
+    lib.gp_kernel_launches.restype = ctypes.c_ulonglong
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != GP_OK:
+        raise GPError(rc, load().gp_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+# ----------------------------------------------------------------- raw ABI
+
+def gp_init(dim, n, dx, dt, nkl, g, prec=GP_F64, stream=None):
+    h = _vp()
+    n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n)))[:3])
+    dx3 = (ctypes.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx)))[:3])
+    nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
+    _check(load().gp_init(ctypes.byref(h), int(dim), n3, dx3, float(dt), nkl3, float(g), int(prec),
+                          stream))
+    return h
+
+
+def gp_set_state(h, psi_ptr, on_device):
+    return _check(load().gp_set_state(h, psi_ptr, int(on_device)))
+
+
+def gp_get_state(h, psi_ptr, on_device):
+    return _check(load().gp_get_state(h, psi_ptr, int(on_device)))
+
+
+def gp_set_potential(h, V_ptr, on_device):
+    return _check(load().gp_set_potential(h, V_ptr, int(on_device)))
+
+
+def gp_set_g(h, g):
+    return _check(load().gp_set_g(h, float(g)))
+
+
+def gp_set_dt(h, dt):
+    return _check(load().gp_set_dt(h, float(dt)))
+
+
+def gp_step_imag(h, nsteps):
+    return _check(load().gp_step_imag(h, int(nsteps)))
+
+
+def gp_step_real(h, nsteps):
+    return _check(load().gp_step_real(h, int(nsteps)))
+
+
+def gp_observables(h, density_ptr=None, density_on_device=0):
+    out = GpObs()
+    _check(load().gp_observables(h, ctypes.byref(out), density_ptr, int(density_on_device)))
+    return out
+
+
+def gp_time_sweeps(h, imag, nsteps):
+    """Mean per-launch duration (ms) of each axis' sweep kernel over nsteps steps."""
+    ms = (ctypes.c_double * 3)()
+    _check(load().gp_time_sweeps(h, int(bool(imag)), int(nsteps), ms))
+    return list(ms)
+
+
+def gp_npoints(h):
+    return int(load().gp_npoints(h))
+
+
+def gp_precision_of(h):
+    return int(load().gp_precision_of(h))
+
+
+def gp_destroy(h):
+    return _check(load().gp_destroy(h))
+
+
+def gp_last_error():
+    return load().gp_last_error().decode()
+
+
+def gp_kernel_launches():
+    return int(load().gp_kernel_launches())
+
+
+# ----------------------------------------------------------------- wrapper
+
+def obs_dict(o: GpObs):
+    return {"norm": o.norm, "energy": o.energy, "mu": o.mu, "rms_x": o.rms[0], "rms_y": o.rms[1],
+            "rms_z": o.rms[2], "rms_r": o.rms_r}
+
+
+class Propagator:
+    """One GP problem on the current CUDA device.
+
+    ``precision``: ``"f64"`` (plain FP64) or ``"f32"`` (FP32 state and sweeps,
+    FP64 reductions and renormalisation).  States are complex tensors of shape
+    (nz, ny, nx) truncated to ``dim`` (x fastest).
+    """
+
+    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, precision="f64", stream=None):
+        import torch
+        self.torch = torch
+        self.dim = int(dim)
+        self.n = list(n)[: self.dim]
+        self.shape = tuple(reversed(self.n))
+        self.precision = precision
+        self.ctype = torch.complex128 if precision == "f64" else torch.complex64
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.h = gp_init(dim, n, dx, dt, nkl, g, GP_F64 if precision == "f64" else GP_F32,
+                         stream.cuda_stream)
+
+    def close(self):
+        if self.h is not None:
+            gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, psi):
+        torch = self.torch
+        if isinstance(psi, np.ndarray):
+            a = np.ascontiguousarray(psi.reshape(self.shape),
+                                     dtype=np.complex128 if self.precision == "f64" else np.complex64)
+            gp_set_state(self.h, a.ctypes.data, 0)
+            return
+        t = psi.reshape(self.shape).to(dtype=self.ctype).contiguous()
+        on_dev = t.is_cuda
+        gp_set_state(self.h, t.data_ptr(), 1 if on_dev else 0)
+
+    def get_state(self, device=True):
+        torch = self.torch
+        if device:
+            out = torch.empty(self.shape, dtype=self.ctype, device="cuda")
+            gp_get_state(self.h, out.data_ptr(), 1)
+            return out
+        out = np.empty(self.shape, dtype=np.complex128 if self.precision == "f64" else np.complex64)
+        gp_get_state(self.h, out.ctypes.data, 0)
+        return out
+
+    def set_potential(self, V):
+        if V is None:
+            gp_set_potential(self.h, None, 0)
+            return
+        if isinstance(V, np.ndarray):
+            a = np.ascontiguousarray(V.reshape(self.shape), dtype=np.float64)
+            gp_set_potential(self.h, a.ctypes.data, 0)
+            return
+        t = V.reshape(self.shape).to(dtype=self.torch.float64).contiguous()
+        gp_set_potential(self.h, t.data_ptr(), 1 if t.is_cuda else 0)
+
+    def set_g(self, g):
+        gp_set_g(self.h, g)
+
+    def set_dt(self, dt):
+        gp_set_dt(self.h, dt)
+
+    def step_imag(self, nsteps):
+        gp_step_imag(self.h, nsteps)
+
+    def step_real(self, nsteps):
+        gp_step_real(self.h, nsteps)
+
+    def time_sweeps(self, imag, nsteps):
+        return gp_time_sweeps(self.h, imag, nsteps)
+
+    def observables(self, density=False):
+        den = None
+        if density:
+            den = self.torch.empty(self.shape, dtype=self.torch.float64, device="cuda")
+        o = gp_observables(self.h, den.data_ptr() if den is not None else None, 1 if den is not None else 0)
+        d = obs_dict(o)
+        if density:
+            d["density"] = den
+        return d

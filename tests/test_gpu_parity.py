@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs are seeded and synthetic (trapped Gaussian condensate plus noise,
+harmonic traps, Gaussian-bump potentials).  Tolerances: the FP64 path must
+match the oracle to a relative L2 error <= 1e-12 on phi after 1000 steps and
+to 1e-10 on mu; single steps are compared element by element.  The FP32 form
+is held to |d mu| <= 1e-6 and a relative L2 error that FP32 rounding allows.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1709_04423_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_1709_04423_gb300 import gpe
+    gpe.load()
+    assert torch.cuda.is_available()
+    return gpe
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def make(G, dim, n, dx, dt, nkl, g, prec="f64"):
+    p = G.Propagator(dim, n, dx, dt, nkl, g, precision=prec)
+    gr = O.Grid(dim, n, dx, dt, nkl, g)
+    return p, gr
+
+
+CASES = [
+    (1, [17], [0.3]),
+    (1, [256], [0.05]),
+    (2, [33, 20], [0.25, 0.3]),
+    (2, [64, 48], [0.2, 0.2]),
+    (3, [17, 12, 9], [0.4, 0.45, 0.5]),
+    (3, [40, 33, 24], [0.25, 0.3, 0.35]),
+]
+
+
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("dim,n,dx", CASES)
+def test_one_step_elementwise_f64(G, dim, n, dx, imag):
+    nkl = [1.0, 1.4, 1.8][:dim]
+    p, gr = make(G, dim, n, dx, 2e-3, nkl, 12.0)
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=1709 + dim, noise=1e-3)
+    p.set_state(phi0)
+    (p.step_imag if imag else p.step_real)(1)
+    got = p.get_state(device=False)
+    ref = O.step(gr, phi0, imag)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    p.close()
+
+
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("dim,n,dx", [CASES[2], CASES[5]])
+def test_1000_steps_f64(G, dim, n, dx, imag):
+    nkl = [1.0, 1.4, 1.8][:dim]
+    dt = 1e-3 if imag else 2e-4
+    p, gr = make(G, dim, n, dx, dt, nkl, 20.0)
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=7, noise=1e-3)
+    p.set_state(phi0)
+    (p.step_imag if imag else p.step_real)(1000)
+    got = p.get_state(device=False)
+    ref = O.run(gr, phi0, imag, 1000)
+    assert rel_l2(got, ref) <= 1e-12
+    ob, obr = p.observables(), O.observables(gr, ref)
+    assert abs(ob["mu"] - obr["mu"]) <= 1e-10
+    assert abs(ob["energy"] - obr["energy"]) <= 1e-10
+    for k in ("norm", "rms_x", "rms_y", "rms_z", "rms_r"):
+        assert abs(ob[k] - obr[k]) <= 1e-11 * max(1.0, abs(obr[k]))
+    p.close()
+
+
+def test_1d_ground_state_workload_f64(G):
+    """1d imaginary time: N = 256, dx = 0.05 on [-6.4, 6.4), dt = 1e-4,
+    V = x^2/2, g = 10, 20000 steps, Gaussian plus 1e-3 seeded noise."""
+    n, dx, dt, g = [256], [0.05], 1e-4, 10.0
+    p, gr = make(G, 1, n, dx, dt, [1.0], g)
+    phi0 = I.gaussian_state(1, n, dx, [1.0], seed=1709, noise=1e-3)
+    p.set_state(phi0)
+    p.step_imag(20000)
+    got = p.get_state(device=False)
+    ref = O.run(gr, phi0, True, 20000)
+    assert rel_l2(got, ref) <= 1e-12
+    ob = p.observables(density=True)
+    obr = O.observables(gr, ref, density=True)
+    assert abs(ob["mu"] - obr["mu"]) <= 1e-10
+    assert np.max(np.abs(ob["density"].cpu().numpy() - obr["density"])) <= 1e-12 * obr["density"].max()
+    p.close()
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_fp32_form_mu_error(G, imag):
+    dim, n, dx = 3, [40, 33, 24], [0.25, 0.3, 0.35]
+    nkl = [1.0, 1.4, 1.8]
+    dt = 1e-3 if imag else 2e-4
+    p, gr = make(G, dim, n, dx, dt, nkl, 20.0, prec="f32")
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=7, noise=1e-3)
+    p.set_state(phi0)
+    (p.step_imag if imag else p.step_real)(1000)
+    got = p.get_state(device=False).astype(np.complex128)
+    ref = O.run(gr, phi0, imag, 1000)
+    assert rel_l2(got, ref) <= (2e-5 if imag else 1e-4)
+    ob, obr = p.observables(), O.observables(gr, ref)
+    assert abs(ob["mu"] - obr["mu"]) <= 1e-6 * max(1.0, abs(obr["mu"]))
+    p.close()
+
+
+def test_observables_random_state_f64(G):
+    dim, n, dx = 3, [21, 18, 16], [0.3, 0.3, 0.3]
+    p, gr = make(G, dim, n, dx, 1e-3, [1.0, 1.2, 1.5], 9.0)
+    u = I.uniform(99, 2 * gr.npoints).reshape((2,) + gr.shape)
+    phi = (u[0] - 0.5) + 1j * (u[1] - 0.5)
+    p.set_state(phi)
+    ob = p.observables()
+    obr = O.observables(gr, phi)
+    for k in O.OBS_KEYS:
+        assert ob[k] == pytest.approx(obr[k], rel=1e-12, abs=1e-14)
+    p.close()
+
+
+def test_user_potential_and_quench(G):
+    dim, n, dx = 2, [48, 40], [0.25, 0.25]
+    nkl = [1.0, 1.3]
+    p, gr = make(G, dim, n, dx, 5e-4, nkl, 10.0)
+    dV, _ = I.gaussian_bumps(dim, n, dx, seed=1713)
+    V = O.potential(gr) + dV
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=3)
+    p.set_state(phi0)
+    p.set_potential(V)
+    p.step_real(50)
+    p.set_g(25.0)
+    p.step_real(50)
+    p.set_dt(2.5e-4)
+    p.step_imag(40)
+    grV = gr.with_(V=V)
+    ref = O.run(grV, phi0, False, 50)
+    ref = O.run(grV.with_(g=25.0), ref, False, 50)
+    ref = O.run(grV.with_(g=25.0, dt=2.5e-4), ref, True, 40)
+    got = p.get_state(device=False)
+    assert rel_l2(got, ref) <= 1e-12
+    ob, obr = p.observables(), O.observables(grV.with_(g=25.0), ref)
+    assert abs(ob["mu"] - obr["mu"]) <= 1e-10
+    p.set_potential(None)   # back to the harmonic trap
+    p.step_real(5)
+    ref = O.run(gr.with_(g=25.0, dt=2.5e-4), ref, False, 5)
+    assert rel_l2(p.get_state(device=False), ref) <= 1e-12
+    p.close()
+
+
+def test_device_state_roundtrip_and_stream(G):
+    import torch
+    dim, n, dx = 3, [20, 16, 12], [0.3, 0.3, 0.3]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = G.Propagator(dim, n, dx, 1e-3, [1, 1, 1], 5.0, precision="f64", stream=s)
+        phi0 = torch.tensor(I.gaussian_state(dim, n, dx, [1, 1, 1], seed=5), device="cuda")
+        p.set_state(phi0)
+        p.step_imag(37)
+        out = p.get_state(device=True)
+    s.synchronize()
+    gr = O.Grid(dim, n, dx, 1e-3, [1, 1, 1], 5.0)
+    ref = O.run(gr, phi0.cpu().numpy(), True, 37)
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-13
+    p.close()
+
+
+def test_nonfinite_state_is_reported(G):
+    p, gr = make(G, 2, [16, 16], [0.3, 0.3], 1e-3, [1, 1], 1.0)
+    phi = I.gaussian_state(2, [16, 16], [0.3, 0.3], [1, 1])
+    phi[5, 7] = np.nan
+    p.set_state(phi)
+    with pytest.raises(G.GPError) as e:
+        p.observables()
+    assert e.value.code == G.GP_ERR_NONFINITE
+    p.close()
+
+
+def test_zero_steps_and_graph_boundaries(G):
+    """Step counts around the graph block size give the same result as one-by-one."""
+    dim, n, dx = 2, [24, 20], [0.3, 0.3]
+    phi0 = I.gaussian_state(dim, n, dx, [1, 1], seed=11)
+    res = []
+    for chunks in ([0, 33], [1] * 33, [31, 2], [32, 1]):
+        p, gr = make(G, dim, n, dx, 1e-3, [1, 1], 4.0)
+        p.set_state(phi0)
+        for c in chunks:
+            p.step_imag(c)
+        res.append(p.get_state(device=False))
+        p.close()
+    for r in res[1:]:
+        assert rel_l2(r, res[0]) <= 1e-14
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_full_size_128cube_two_steps(G, imag):
+    """3d 128^3 anisotropic trap (dx = 0.1, nu, kappa, lambda = 1, 1.4, 1.8,
+    g = 50), the size the benchmark runs: two steps against the oracle."""
+    n, dx, nkl = [128] * 3, [0.1] * 3, [1.0, 1.4, 1.8]
+    for prec in ("f64", "f32"):
+        p, gr = make(G, 3, n, dx, 1e-3, nkl, 50.0, prec=prec)
+        phi0 = I.gaussian_state(3, n, dx, nkl, seed=1710, noise=1e-3)
+        p.set_state(phi0)
+        (p.step_imag if imag else p.step_real)(2)
+        got = p.get_state(device=False).astype(np.complex128)
+        ref = O.run(gr, phi0, imag, 2)
+        assert rel_l2(got, ref) <= (1e-14 if prec == "f64" else 2e-6)
+        p.close()
