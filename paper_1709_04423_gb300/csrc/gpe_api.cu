@@ -2,106 +2,103 @@
 // (declared and documented in include/gpe.h).
 //
 // Host side of the library: argument validation, device memory owned by the
-// handle, the time-invariant elimination coefficients, the per-step launch
-// sequence (N fused into the x sweep, then the y and z sweeps, with the
-// imaginary-time norm fused into the last sweep), CUDA-graph replay of step
-// blocks, and the observables reduction.
+// handle, the time-invariant elimination coefficients (Thomas factors of the
+// Crank-Nicolson systems and the segment products the segmented sweeps use),
+// the choice of kernel shapes, and the observables reduction.  The per-step
+// launch sequence lives in gpe_step.cuh.
 #include <cuda_runtime.h>
 
-#include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <complex>
-#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "gpe.h"
-#include "gpe_obs.cuh"
-#include "gpe_sweep.cuh"
+#include "gpe_internal.h"
 
-using gpe::c2_t;
 using cd = std::complex<double>;
 
-namespace {
+namespace gpe {
 
 thread_local std::string g_err;
 std::atomic<unsigned long long> g_launches{0};
 
-constexpr int kSweepThreads = 128;
-constexpr int kObsThreads = 256;
-constexpr int kGraphSteps = 16;  // steps per captured graph (even: keeps the norm-slot parity)
-
-int fail(int code, const std::string& msg) {
-  g_err = msg;
-  return code;
-}
-
-#define GP_CUDA(call)                                                                  \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return fail(GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
-  } while (0)
-
-}  // namespace
-
-struct gp_handle {
-  int dim = 0;
-  int n[3] = {1, 1, 1};
-  double dx[3] = {1, 1, 1};
-  double dt = 0, g = 0;
-  double nkl[3] = {1, 1, 1};
-  int prec = GP_F64;
-  long np = 0;
-  size_t esize = 0;  // bytes per complex value
-  cudaStream_t user = nullptr, work = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  void* psi = nullptr;
-  double* Vd = nullptr;      // user potential (FP64), or nullptr for the trap
-  void* Vt = nullptr;        // same potential in the state precision
-  double* Vbuf = nullptr;    // storage behind Vd
-  float* Vbuf32 = nullptr;   // storage behind Vt for the FP32 form
-  void* vt[3] = {nullptr, nullptr, nullptr};        // nu_d^2 x^2/2 per axis, state precision
-  double* vd[3] = {nullptr, nullptr, nullptr};      // same in FP64
-  double* cdx[3] = {nullptr, nullptr, nullptr};     // coordinates
-  double* wd[3] = {nullptr, nullptr, nullptr};      // Simpson weights
-  void* cm[2][3] = {{nullptr}};   // [imag][axis] m_k
-  void* ccp[2][3] = {{nullptr}};  // [imag][axis] c'_k
-  double* scale = nullptr;   // [2] renormalisation slots
-  double* partials = nullptr;
-  unsigned int* counter = nullptr;
-  double* obs_out = nullptr;  // [8]
-  double* obs_host = nullptr; // pinned [8]
-  double* dens_scratch = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  std::vector<void*> allocs;
-};
-
-namespace {
-
 int dev_alloc(gp_handle* h, void** p, size_t bytes) {
-  GP_CUDA(cudaMalloc(p, bytes < 16 ? 16 : bytes));
+  const size_t b = bytes < 16 ? 16 : bytes;
+  GP_CUDA(cudaMalloc(p, b));
   h->allocs.push_back(*p);
-  GP_CUDA(cudaMemsetAsync(*p, 0, bytes < 16 ? 16 : bytes, h->work));
+  GP_CUDA(cudaMemsetAsync(*p, 0, b, h->work));
   return GP_OK;
 }
 
-int axis_len(const gp_handle* h, int d) { return d < h->dim ? h->n[d] : 1; }
+int join_in(gp_handle* h) {
+  GP_CUDA(cudaEventRecord(h->ev_in, h->user));
+  GP_CUDA(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+  return GP_OK;
+}
 
-// Thomas factors of one axis: m_k = 1/(b - a c'_{k-1}), c'_k = a m_k, k = 1..n-2,
-// with a = -r, b = 1 + 2r, r = beta (imaginary time) or i beta (real time).
-void thomas_factors(int n, double beta, bool imag, std::vector<cd>& m, std::vector<cd>& cp) {
-  m.assign(n, cd(0, 0));
-  cp.assign(n, cd(0, 0));
+int join_out(gp_handle* h) {
+  GP_CUDA(cudaEventRecord(h->ev_out, h->work));
+  GP_CUDA(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+  return GP_OK;
+}
+
+void drop_graphs(gp_handle* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
+}
+
+namespace {
+
+// Crank-Nicolson system (1 + A) with A = r T along one axis: a = -r (off
+// diagonals), b = 1 + 2r, r = i beta (real time) or beta (imaginary time),
+// beta = dt/(4 dx^2).  Thomas factors m_k = 1/(b - a c'_{k-1}), c'_k = a m_k
+// for the interior k = 1..n-2, and alpha_k = r m_k (= -c'_k).
+struct AxisFactors {
+  std::vector<cd> m, cp, alpha;
+};
+
+AxisFactors thomas_factors(int n, double beta, bool imag) {
+  AxisFactors f;
+  f.m.assign(n, cd(0, 0));
+  f.cp.assign(n, cd(0, 0));
+  f.alpha.assign(n, cd(0, 0));
   const cd r = imag ? cd(beta, 0) : cd(0, beta);
   const cd a = -r, b = 1.0 + 2.0 * r;
   cd cprev(0, 0);
   for (int k = 1; k <= n - 2; ++k) {
     const cd den = b - a * cprev;
-    m[k] = 1.0 / den;
-    cp[k] = a * m[k];
-    cprev = cp[k];
+    f.m[k] = 1.0 / den;
+    f.cp[k] = a * f.m[k];
+    f.alpha[k] = r * f.m[k];
+    cprev = f.cp[k];
+  }
+  return f;
+}
+
+// Segment products for segments of `seg` interior points starting at k = 1:
+// gf[k] = prod_{i=start..k} alpha_i, gb[k] = prod_{i=k..end} alpha_i.
+void segment_products(const std::vector<cd>& alpha, int n, int seg, std::vector<cd>& gf, std::vector<cd>& gb) {
+  const int M = n - 2;
+  gf.assign(n, cd(0, 0));
+  gb.assign(n, cd(0, 0));
+  for (int k0 = 1; k0 <= M; k0 += seg) {
+    const int k1 = std::min(M, k0 + seg - 1);
+    cd acc(1, 0);
+    for (int k = k0; k <= k1; ++k) {
+      acc *= alpha[k];
+      gf[k] = acc;
+    }
+    acc = cd(1, 0);
+    for (int k = k1; k >= k0; --k) {
+      acc *= alpha[k];
+      gb[k] = acc;
+    }
   }
 }
 
@@ -126,206 +123,76 @@ int upload_real(gp_handle* h, void* dst, const std::vector<double>& v) {
 }
 
 template <typename T>
-int upload_coefs(gp_handle* h) {
-  std::vector<cd> m, cp;
-  for (int imag = 0; imag < 2; ++imag)
+int upload_coefs_t(gp_handle* h) {
+  for (int mode = 0; mode < NUM_MODES; ++mode)
     for (int d = 0; d < h->dim; ++d) {
-      const double beta = h->dt / (4.0 * h->dx[d] * h->dx[d]);
-      thomas_factors(h->n[d], beta, imag != 0, m, cp);
-      int rc = upload_c2<T>(h, h->cm[imag][d], m);
+      const int n = h->n[d];
+      const double sign = mode == MODE_REAL_ADJ ? -1.0 : 1.0;
+      const double beta = sign * h->dt / (4.0 * h->dx[d] * h->dx[d]);
+      const AxisFactors f = thomas_factors(n, beta, mode == MODE_IMAG);
+      std::vector<cd> all((size_t)(1 + 2 * kNumSegs) * n);
+      std::copy(f.alpha.begin(), f.alpha.end(), all.begin());
+      std::vector<cd> gf, gb;
+      for (int s = 0; s < kNumSegs; ++s) {
+        segment_products(f.alpha, n, kSegs[s], gf, gb);
+        std::copy(gf.begin(), gf.end(), all.begin() + (size_t)(1 + 2 * s) * n);
+        std::copy(gb.begin(), gb.end(), all.begin() + (size_t)(2 + 2 * s) * n);
+      }
+      int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
-      rc = upload_c2<T>(h, h->ccp[imag][d], cp);
-      if (rc) return rc;
-    }
-  return GP_OK;
-}
-
-void drop_graphs(gp_handle* h) {
-  for (int i = 0; i < 2; ++i)
-    if (h->graph[i]) {
-      cudaGraphExecDestroy(h->graph[i]);
-      h->graph[i] = nullptr;
-    }
-}
-
-int join_in(gp_handle* h) {
-  GP_CUDA(cudaEventRecord(h->ev_in, h->user));
-  GP_CUDA(cudaStreamWaitEvent(h->work, h->ev_in, 0));
-  return GP_OK;
-}
-
-int join_out(gp_handle* h) {
-  GP_CUDA(cudaEventRecord(h->ev_out, h->work));
-  GP_CUDA(cudaStreamWaitEvent(h->user, h->ev_out, 0));
-  return GP_OK;
-}
-
-gpe::LineGeom geom_of(const gp_handle* h, int axis) {
-  gpe::LineGeom g;
-  g.axis = axis;
-  g.nx = axis_len(h, 0);
-  g.ny = axis_len(h, 1);
-  g.nz = axis_len(h, 2);
-  g.n = axis_len(h, axis);
-  g.stride = axis == 0 ? 1 : axis == 1 ? g.nx : (long)g.nx * g.ny;
-  g.nlines = h->np / g.n;
-  return g;
-}
-
-template <typename T, bool IMAG, bool FIRST, bool LAST>
-void launch_sweep(const gpe::SweepArgs<T>& a, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((a.geom.nlines + kSweepThreads - 1) / kSweepThreads);
-  gpe::cn_sweep_kernel<T, IMAG, FIRST, LAST><<<blocks, kSweepThreads, 0, s>>>(a);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-}
-
-// One step of parity `par`: N fused into the x sweep, then y and z; in
-// imaginary time the last sweep produces scale[1-par] from the norm and the
-// x sweep consumes scale[par].
-template <typename T>
-void enqueue_step(gp_handle* h, bool imag, int par, cudaEvent_t* ev = nullptr) {
-  for (int d = 0; d < h->dim; ++d) {
-    if (ev) cudaEventRecord(ev[2 * d], h->work);
-    gpe::SweepArgs<T> a;
-    std::memset(&a, 0, sizeof(a));
-    a.psi = (c2_t<T>*)h->psi;
-    a.geom = geom_of(h, d);
-    a.m = (const c2_t<T>*)h->cm[imag][d];
-    a.cp = (const c2_t<T>*)h->ccp[imag][d];
-    a.beta = (T)(h->dt / (4.0 * h->dx[d] * h->dx[d]));
-    a.V = (const T*)h->Vt;
-    a.vx = (const T*)h->vt[0];
-    a.vy = (const T*)h->vt[1];
-    a.vz = (const T*)h->vt[2];
-    a.dt = (T)h->dt;
-    a.g = (T)h->g;
-    a.scale_in = imag ? h->scale + par : nullptr;
-    a.w_axis = h->wd[d];
-    a.w_a = d == 0 ? h->wd[1] : h->wd[0];
-    a.w_b = d == 2 ? h->wd[1] : h->wd[2];
-    a.partials = h->partials;
-    a.counter = h->counter;
-    a.scale_out = h->scale + (1 - par);
-    const bool first = d == 0, last = d == h->dim - 1;
-    if (imag) {
-      if (first && last) launch_sweep<T, true, true, true>(a, h->work);
-      else if (first) launch_sweep<T, true, true, false>(a, h->work);
-      else if (last) launch_sweep<T, true, false, true>(a, h->work);
-      else launch_sweep<T, true, false, false>(a, h->work);
-    } else {
-      if (first) launch_sweep<T, false, true, false>(a, h->work);
-      else launch_sweep<T, false, false, false>(a, h->work);
-    }
-    if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
-  }
-}
-
-// Eager steps with an event pair around every sweep launch (recorded on the
-// library's stream, read once at the end); returns the mean duration of each
-// axis' sweep kernel in ms_out[axis].
-template <typename T>
-int time_steps(gp_handle* h, bool imag, long nsteps, double* ms_out) {
-  std::vector<cudaEvent_t> ev((size_t)nsteps * 2 * h->dim);
-  for (auto& e : ev) GP_CUDA(cudaEventCreate(&e));
-  int rc = join_in(h);
-  if (imag && !rc) {
-    gpe::set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-  }
-  for (long t = 0; t < nsteps && !rc; ++t)
-    enqueue_step<T>(h, imag, (int)(t & 1), ev.data() + (size_t)t * 2 * h->dim);
-  if (imag && !rc && nsteps > 0) {
-    const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-    gpe::scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->scale + (nsteps & 1));
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-  }
-  cudaError_t e = cudaStreamSynchronize(h->work);
-  if (!rc && e != cudaSuccess) rc = fail(GP_ERR_CUDA, std::string("gp_time_sweeps: ") + cudaGetErrorString(e));
-  double acc[3] = {0, 0, 0};
-  for (long t = 0; t < nsteps && !rc; ++t)
-    for (int d = 0; d < h->dim; ++d) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[(size_t)t * 2 * h->dim + 2 * d], ev[(size_t)t * 2 * h->dim + 2 * d + 1]);
-      acc[d] += ms;
-    }
-  for (auto& ee : ev) cudaEventDestroy(ee);
-  if (rc) return rc;
-  for (int d = 0; d < 3; ++d) ms_out[d] = (d < h->dim && nsteps > 0) ? acc[d] / nsteps : 0.0;
-  GP_CUDA(cudaGetLastError());
-  return join_out(h);
-}
-
-template <typename T>
-int run_steps(gp_handle* h, bool imag, long nsteps) {
-  if (nsteps == 0) return GP_OK;
-  int rc = join_in(h);
-  if (rc) return rc;
-  if (imag) {
-    gpe::set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-  }
-  long t = 0;
-  if (nsteps >= 2 * kGraphSteps) {
-    cudaGraphExec_t& ge = h->graph[imag ? 1 : 0];
-    if (!ge) {
-      cudaGraph_t graph;
-      GP_CUDA(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
-      const unsigned long long before = g_launches.load();
-      for (int s = 0; s < kGraphSteps; ++s) enqueue_step<T>(h, imag, s & 1);
-      g_launches.store(before);  // capture launches nothing
-      GP_CUDA(cudaStreamEndCapture(h->work, &graph));
-      cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) {
-        ge = nullptr;
-        return fail(GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      if (mode < 2) {
+        if ((rc = upload_c2<T>(h, h->cm[mode == MODE_IMAG][d], f.m))) return rc;
+        if ((rc = upload_c2<T>(h, h->ccp[mode == MODE_IMAG][d], f.cp))) return rc;
       }
     }
-    for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
-      GP_CUDA(cudaGraphLaunch(ge, h->work));
-      g_launches.fetch_add((unsigned long long)kGraphSteps * h->dim, std::memory_order_relaxed);
-    }
-  }
-  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, (int)(t & 1));
-  if (imag) {
-    const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-    gpe::scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->scale + (nsteps & 1));
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-  }
-  GP_CUDA(cudaGetLastError());
-  return join_out(h);
-}
-
-template <typename T>
-int run_observables(gp_handle* h, double* dens_dev) {
-  gpe::ObsArgs<T> a;
-  std::memset(&a, 0, sizeof(a));
-  a.psi = (const c2_t<T>*)h->psi;
-  a.dim = h->dim;
-  a.nx = axis_len(h, 0);
-  a.ny = axis_len(h, 1);
-  a.nz = axis_len(h, 2);
-  a.hx = h->dx[0];
-  a.hy = h->dx[1];
-  a.hz = h->dx[2];
-  a.V = h->Vd;
-  a.vx = h->vd[0]; a.vy = h->vd[1]; a.vz = h->vd[2];
-  a.cx = h->cdx[0]; a.cy = h->cdx[1]; a.cz = h->cdx[2];
-  a.wx = h->wd[0]; a.wy = h->wd[1]; a.wz = h->wd[2];
-  a.density = dens_dev;
-  a.partials = h->partials;
-  a.counter = h->counter;
-  a.out = h->obs_out;
-  const int blocks = (int)std::min<long>((h->np + kObsThreads - 1) / kObsThreads, 152L * 16);
-  gpe::observables_kernel<T><<<blocks, kObsThreads, 0, h->work>>>(a);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  GP_CUDA(cudaGetLastError());
   return GP_OK;
 }
 
-bool is_finite_value(double v) { return std::isfinite(v); }
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : dflt;
+}
+
+// Kernel shapes.  x lines: one warp per line with seg_x interior points per
+// lane (32 * seg_x >= n - 2, seg_x <= 16).  y/z lines: 32 lines per block and
+// at most 16 segments of seg_c points; keep_c keeps the input segment in
+// registers when it fits (FP32 seg <= 16, FP64 seg <= 8).  Longer lines use
+// the thread-per-line kernel (shape 0).  GPE_SEG_X / GPE_SEG_YZ / GPE_KEEP
+// override the defaults for tuning.
+void choose_shapes(gp_handle* h) {
+  const int M0 = h->n[0] - 2;
+  int sx = 0;
+  for (int s : {1, 2, 4, 8, 16})
+    if (32 * s >= M0) { sx = s; break; }
+  sx = env_int("GPE_SEG_X", sx);
+  if (sx > 0 && (seg_index(sx) < 0 || sx > 16 || 32 * sx < M0)) sx = 0;
+  h->seg_x = sx;
+  int Mc = 0;
+  for (int d = 1; d < h->dim; ++d) Mc = std::max(Mc, h->n[d] - 2);
+  const bool f64 = h->prec == GP_F64;
+  int sc = 0;
+  for (int s : {8, 16, 32})
+    if ((Mc + s - 1) / s <= 16) { sc = s; break; }
+  if (!f64 && sc == 8 && (Mc + 15) / 16 <= 16) sc = 16;
+  sc = env_int("GPE_SEG_YZ", sc);
+  if (sc > 0 && (seg_index(sc) < 0 || sc < 4 || (Mc + sc - 1) / sc > 16)) sc = 0;
+  int keep = f64 ? (sc <= 8) : (sc <= 16);
+  keep = env_int("GPE_KEEP", keep);
+  if (keep && sc > 16) keep = 0;
+  if (!keep && sc == 4) keep = 1;
+  h->seg_c = sc;
+  h->keep_c = keep;
+}
 
 }  // namespace
+
+int upload_coefs(gp_handle* h) {
+  return h->prec == GP_F64 ? upload_coefs_t<double>(h) : upload_coefs_t<float>(h);
+}
+
+}  // namespace gpe
+
+using namespace gpe;
 
 extern "C" {
 
@@ -413,22 +280,28 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     if ((rc = dev_alloc(h, (void**)&h->vd[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->cdx[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->wd[d], nd * sizeof(double)))) return bail(rc);
+    if ((rc = dev_alloc(h, &h->wt[d], nd * tsz))) return bail(rc);
     rc = prec == GP_F64 ? upload_real<double>(h, h->vt[d], v) : upload_real<float>(h, h->vt[d], v);
+    if (rc) return bail(rc);
+    rc = prec == GP_F64 ? upload_real<double>(h, h->wt[d], w) : upload_real<float>(h, h->wt[d], w);
     if (rc) return bail(rc);
     if ((rc = upload_real<double>(h, h->vd[d], v))) return bail(rc);
     if ((rc = upload_real<double>(h, h->cdx[d], x))) return bail(rc);
     if ((rc = upload_real<double>(h, h->wd[d], w))) return bail(rc);
   }
-  for (int imag = 0; imag < 2; ++imag)
-    for (int d = 0; d < dim; ++d) {
-      if ((rc = dev_alloc(h, &h->cm[imag][d], (size_t)h->n[d] * h->esize))) return bail(rc);
-      if ((rc = dev_alloc(h, &h->ccp[imag][d], (size_t)h->n[d] * h->esize))) return bail(rc);
+  for (int d = 0; d < dim; ++d) {
+    for (int mode = 0; mode < NUM_MODES; ++mode)
+      if ((rc = dev_alloc(h, &h->coef[mode][d], (size_t)(1 + 2 * kNumSegs) * h->n[d] * h->esize))) return bail(rc);
+    for (int im = 0; im < 2; ++im) {
+      if ((rc = dev_alloc(h, &h->cm[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
+      if ((rc = dev_alloc(h, &h->ccp[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
     }
-  rc = prec == GP_F64 ? upload_coefs<double>(h) : upload_coefs<float>(h);
-  if (rc) return bail(rc);
+  }
+  if ((rc = upload_coefs(h))) return bail(rc);
+  choose_shapes(h);
   // reduction scratch: enough partial slots for any sweep or observables grid
   long maxblocks = 152L * 16;
-  for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, (h->np / h->n[d] + kSweepThreads - 1) / kSweepThreads);
+  for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, h->np / h->n[d] / 4 + 1);
   if ((rc = dev_alloc(h, (void**)&h->partials, (size_t)maxblocks * 8 * sizeof(double)))) return bail(rc);
   if ((rc = dev_alloc(h, (void**)&h->counter, 64))) return bail(rc);
   if ((rc = dev_alloc(h, (void**)&h->scale, 2 * sizeof(double)))) return bail(rc);
@@ -488,9 +361,7 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
   if (h->prec == GP_F64) {
     h->Vt = h->Vbuf;
   } else {
-    const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-    gpe::to_float_kernel<<<blocks, 256, 0, h->work>>>(h->Vbuf32, h->Vbuf, h->np);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    to_float(h, h->Vbuf32, h->Vbuf, h->np);
     h->Vt = h->Vbuf32;
   }
   GP_CUDA(cudaGetLastError());
@@ -514,28 +385,27 @@ int gp_set_dt(gp_handle* h, double dt) {
   if (rc) return rc;
   drop_graphs(h);
   h->dt = dt;
-  rc = h->prec == GP_F64 ? upload_coefs<double>(h) : upload_coefs<float>(h);
-  if (rc) return rc;
+  if ((rc = upload_coefs(h))) return rc;
   return join_out(h);
 }
 
 int gp_step_imag(gp_handle* h, long nsteps) {
   if (!h) return fail(GP_ERR_INVALID, "gp_step_imag: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_step_imag: nsteps < 0");
-  return h->prec == GP_F64 ? run_steps<double>(h, true, nsteps) : run_steps<float>(h, true, nsteps);
+  return h->prec == GP_F64 ? run_steps_f64(h, true, nsteps) : run_steps_f32(h, true, nsteps);
 }
 
 int gp_step_real(gp_handle* h, long nsteps) {
   if (!h) return fail(GP_ERR_INVALID, "gp_step_real: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_step_real: nsteps < 0");
-  return h->prec == GP_F64 ? run_steps<double>(h, false, nsteps) : run_steps<float>(h, false, nsteps);
+  return h->prec == GP_F64 ? run_steps_f64(h, false, nsteps) : run_steps_f32(h, false, nsteps);
 }
 
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch) {
   if (!h || !ms_per_launch) return fail(GP_ERR_INVALID, "gp_time_sweeps: NULL argument");
   if (nsteps < 0 || nsteps > 4096) return fail(GP_ERR_INVALID, "gp_time_sweeps: nsteps must be in [0, 4096]");
-  return h->prec == GP_F64 ? time_steps<double>(h, imag != 0, nsteps, ms_per_launch)
-                           : time_steps<float>(h, imag != 0, nsteps, ms_per_launch);
+  return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms_per_launch)
+                           : time_steps_f32(h, imag != 0, nsteps, ms_per_launch);
 }
 
 int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device) {
@@ -555,7 +425,7 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
       ddev = h->dens_scratch;
     }
   }
-  rc = h->prec == GP_F64 ? run_observables<double>(h, ddev) : run_observables<float>(h, ddev);
+  rc = h->prec == GP_F64 ? run_observables_f64(h, ddev) : run_observables_f32(h, ddev);
   if (rc) return rc;
   GP_CUDA(cudaMemcpyAsync(h->obs_host, h->obs_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->work));
   if (density && !density_on_device)
@@ -575,7 +445,7 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
   }
   out->rms_r = std::sqrt(r2);
   for (int q = 0; q < 7; ++q)
-    if (!is_finite_value(S[q])) return fail(GP_ERR_NONFINITE, "gp_observables: the state holds NaN or Inf");
+    if (!std::isfinite(S[q])) return fail(GP_ERR_NONFINITE, "gp_observables: the state holds NaN or Inf");
   return GP_OK;
 }
 

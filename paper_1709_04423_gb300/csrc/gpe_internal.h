@@ -1,0 +1,104 @@
+// gpe_internal.h -- host-side internals shared by the translation units of
+// libgpe.so: the handle layout, error helpers, stream joins and the
+// per-precision step launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "gpe.h"
+
+namespace gpe {
+
+extern thread_local std::string g_err;
+extern std::atomic<unsigned long long> g_launches;
+
+inline int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define GP_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::gpe::fail(GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Segment lengths for which segment-product tables are kept.
+constexpr int kNumSegs = 6;
+constexpr int kSegs[kNumSegs] = {1, 2, 4, 8, 16, 32};
+inline int seg_index(int seg) {
+  for (int i = 0; i < kNumSegs; ++i)
+    if (kSegs[i] == seg) return i;
+  return -1;
+}
+
+// Coefficient modes: real-time step, imaginary-time step, and the real-time
+// step with dt -> -dt (the conjugate-transposed sweep used by the adjoint).
+enum { MODE_REAL = 0, MODE_IMAG = 1, MODE_REAL_ADJ = 2, NUM_MODES = 3 };
+
+}  // namespace gpe
+
+struct gp_handle {
+  int dim = 0;
+  int n[3] = {1, 1, 1};
+  double dx[3] = {1, 1, 1};
+  double dt = 0, g = 0;
+  double nkl[3] = {1, 1, 1};
+  int prec = GP_F64;
+  long np = 0;
+  size_t esize = 0;  // bytes per complex value
+  cudaStream_t user = nullptr, work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void* psi = nullptr;
+  double* Vd = nullptr;      // user potential (FP64), or nullptr for the trap
+  void* Vt = nullptr;        // same potential in the state precision
+  double* Vbuf = nullptr;    // storage behind Vd
+  float* Vbuf32 = nullptr;   // storage behind Vt for the FP32 form
+  void* vt[3] = {nullptr, nullptr, nullptr};     // nu_d^2 x^2/2 per axis, state precision
+  double* vd[3] = {nullptr, nullptr, nullptr};   // same in FP64
+  double* cdx[3] = {nullptr, nullptr, nullptr};  // coordinates
+  double* wd[3] = {nullptr, nullptr, nullptr};   // Simpson weights
+  void* wt[3] = {nullptr, nullptr, nullptr};     // Simpson weights, state precision
+  // per (mode, axis): [0] alpha_k, [1 + 2 s] forward and [2 + 2 s] backward
+  // segment products for segment length kSegs[s]; each n complex values
+  void* coef[gpe::NUM_MODES][3] = {{nullptr}};
+  // legacy thread-per-line factors (m_k, c'_k) per (imag, axis), used when a
+  // line is too long for the segmented kernels
+  void* cm[2][3] = {{nullptr}};
+  void* ccp[2][3] = {{nullptr}};
+  int seg_x = 0, seg_c = 0, keep_c = 1;  // kernel shapes (0 = thread-per-line kernel)
+  double* scale = nullptr;   // [2] renormalisation slots
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  double* obs_out = nullptr;  // [8]
+  double* obs_host = nullptr; // pinned [8]
+  double* dens_scratch = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+};
+
+namespace gpe {
+
+int dev_alloc(gp_handle* h, void** p, size_t bytes);
+int join_in(gp_handle* h);
+int join_out(gp_handle* h);
+inline int axis_len(const gp_handle* h, int d) { return d < h->dim ? h->n[d] : 1; }
+void drop_graphs(gp_handle* h);
+int upload_coefs(gp_handle* h);
+
+// per-precision entry points (gpe_step_f32.cu / gpe_step_f64.cu)
+int run_steps_f32(gp_handle* h, bool imag, long nsteps);
+int run_steps_f64(gp_handle* h, bool imag, long nsteps);
+int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out);
+int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out);
+int run_observables_f32(gp_handle* h, double* dens_dev);
+int run_observables_f64(gp_handle* h, double* dens_dev);
+void to_float(gp_handle* h, float* dst, const double* src, long n);
+
+}  // namespace gpe

@@ -1,0 +1,284 @@
+// gpe_step.cuh -- per-step launch sequence of the split-step propagator,
+// instantiated once per state precision (gpe_step_f32.cu, gpe_step_f64.cu).
+//
+// One step = N fused into the x sweep, then the y sweep, then the z sweep; in
+// imaginary time the last sweep also produces the next renormalisation factor
+// from the Simpson norm, consumed by the next step's x sweep (two device
+// slots, alternating with the step parity), and a final kernel applies the
+// last factor.  Step blocks of kGraphSteps steps are captured once into a CUDA
+// graph and replayed.
+#pragma once
+#include <algorithm>
+#include <cstring>
+
+#include "gpe_internal.h"
+#include "gpe_obs.cuh"
+#include "gpe_sweep.cuh"
+#include "gpe_sweep2.cuh"
+
+namespace gpe {
+
+constexpr int kLegacyThreads = 128;
+constexpr int kXWarps = 4;
+constexpr int kObsThreads = 256;
+constexpr int kGraphSteps = 16;  // even: keeps the renormalisation-slot parity
+
+inline LineGeom geom_of(const gp_handle* h, int axis) {
+  LineGeom g;
+  g.axis = axis;
+  g.nx = axis_len(h, 0);
+  g.ny = axis_len(h, 1);
+  g.nz = axis_len(h, 2);
+  g.n = axis_len(h, axis);
+  g.stride = axis == 0 ? 1 : axis == 1 ? g.nx : (long)g.nx * g.ny;
+  g.nlines = h->np / g.n;
+  return g;
+}
+
+template <typename T>
+inline const c2_t<T>* coef_ptr(const gp_handle* h, int mode, int axis, int slot) {
+  return (const c2_t<T>*)h->coef[mode][axis] + (size_t)slot * h->n[axis];
+}
+
+// ---- segmented x sweep
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+void launch_x(const Sweep2Args<T>& a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((a.geom.nlines + kXWarps - 1) / kXWarps);
+  xsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * kXWarps, 0, s>>>(a);
+  count_launch();
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST>
+void launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+  switch (seg) {
+    case 1: launch_x<T, IMAG, FIRST, LAST, 1>(a, s); break;
+    case 2: launch_x<T, IMAG, FIRST, LAST, 2>(a, s); break;
+    case 4: launch_x<T, IMAG, FIRST, LAST, 4>(a, s); break;
+    case 8: launch_x<T, IMAG, FIRST, LAST, 8>(a, s); break;
+    default: launch_x<T, IMAG, FIRST, LAST, 16>(a, s); break;
+  }
+}
+
+// ---- segmented y/z sweep
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
+void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
+  const int M = a.geom.n - 2;
+  const int nseg = (M + SEG - 1) / SEG;
+  const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
+  colsweep_kernel<T, IMAG, LAST, SEG, KEEP><<<blocks, 32 * nseg, 0, s>>>(a);
+  count_launch();
+}
+
+template <typename T, bool IMAG, bool LAST>
+void launch_c_seg(int seg, bool keep, const Sweep2Args<T>& a, cudaStream_t s) {
+  if (keep) {
+    switch (seg) {
+      case 4: launch_c<T, IMAG, LAST, 4, true>(a, s); break;
+      case 8: launch_c<T, IMAG, LAST, 8, true>(a, s); break;
+      default: launch_c<T, IMAG, LAST, 16, true>(a, s); break;
+    }
+  } else {
+    switch (seg) {
+      case 8: launch_c<T, IMAG, LAST, 8, false>(a, s); break;
+      case 16: launch_c<T, IMAG, LAST, 16, false>(a, s); break;
+      default: launch_c<T, IMAG, LAST, 32, false>(a, s); break;
+    }
+  }
+}
+
+// ---- thread-per-line fallback (lines longer than the segmented kernels take)
+template <typename T, bool IMAG, bool FIRST, bool LAST>
+void launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((a.geom.nlines + kLegacyThreads - 1) / kLegacyThreads);
+  cn_sweep_kernel<T, IMAG, FIRST, LAST><<<blocks, kLegacyThreads, 0, s>>>(a);
+  count_launch();
+}
+
+template <typename T>
+void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
+  const bool first = d == 0, last = d == h->dim - 1;
+  const int mode = imag ? MODE_IMAG : MODE_REAL;
+  const int seg = d == 0 ? h->seg_x : h->seg_c;
+  if (seg > 0) {
+    Sweep2Args<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = (c2_t<T>*)h->psi;
+    a.geom = geom_of(h, d);
+    const int si = seg_index(seg);
+    a.alpha = coef_ptr<T>(h, mode, d, 0);
+    a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
+    a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
+    a.V = (const T*)h->Vt;
+    a.vx = (const T*)h->vt[0];
+    a.vy = (const T*)h->vt[1];
+    a.vz = (const T*)h->vt[2];
+    a.dt = (T)h->dt;
+    a.g = (T)h->g;
+    a.scale_in = imag ? h->scale + par : nullptr;
+    a.w_axis = (const T*)h->wt[d];
+    a.w_a = d == 0 ? h->wd[1] : h->wd[0];
+    a.w_b = d == 2 ? h->wd[1] : h->wd[2];
+    a.partials = h->partials;
+    a.counter = h->counter;
+    a.scale_out = h->scale + (1 - par);
+    if (d == 0) {
+      if (imag) {
+        if (last) launch_x_seg<T, true, true, true>(seg, a, h->work);
+        else launch_x_seg<T, true, true, false>(seg, a, h->work);
+      } else {
+        launch_x_seg<T, false, true, false>(seg, a, h->work);
+      }
+    } else {
+      const bool keep = h->keep_c != 0;
+      if (imag) {
+        if (last) launch_c_seg<T, true, true>(seg, keep, a, h->work);
+        else launch_c_seg<T, true, false>(seg, keep, a, h->work);
+      } else {
+        launch_c_seg<T, false, false>(seg, keep, a, h->work);
+      }
+    }
+    return;
+  }
+  SweepArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.psi = (c2_t<T>*)h->psi;
+  a.geom = geom_of(h, d);
+  a.m = (const c2_t<T>*)h->cm[imag][d];
+  a.cp = (const c2_t<T>*)h->ccp[imag][d];
+  a.beta = (T)(h->dt / (4.0 * h->dx[d] * h->dx[d]));
+  a.V = (const T*)h->Vt;
+  a.vx = (const T*)h->vt[0];
+  a.vy = (const T*)h->vt[1];
+  a.vz = (const T*)h->vt[2];
+  a.dt = (T)h->dt;
+  a.g = (T)h->g;
+  a.scale_in = imag ? h->scale + par : nullptr;
+  a.w_axis = h->wd[d];
+  a.w_a = d == 0 ? h->wd[1] : h->wd[0];
+  a.w_b = d == 2 ? h->wd[1] : h->wd[2];
+  a.partials = h->partials;
+  a.counter = h->counter;
+  a.scale_out = h->scale + (1 - par);
+  if (imag) {
+    if (first && last) launch_legacy<T, true, true, true>(a, h->work);
+    else if (first) launch_legacy<T, true, true, false>(a, h->work);
+    else if (last) launch_legacy<T, true, false, true>(a, h->work);
+    else launch_legacy<T, true, false, false>(a, h->work);
+  } else {
+    if (first) launch_legacy<T, false, true, false>(a, h->work);
+    else launch_legacy<T, false, false, false>(a, h->work);
+  }
+}
+
+template <typename T>
+void enqueue_step(gp_handle* h, bool imag, int par, cudaEvent_t* ev = nullptr) {
+  for (int d = 0; d < h->dim; ++d) {
+    if (ev) cudaEventRecord(ev[2 * d], h->work);
+    enqueue_sweep<T>(h, imag, par, d);
+    if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
+  }
+}
+
+template <typename T>
+void enqueue_finish_imag(gp_handle* h, long nsteps) {
+  const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
+  scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->scale + (nsteps & 1));
+  count_launch();
+}
+
+template <typename T>
+int run_steps_t(gp_handle* h, bool imag, long nsteps) {
+  if (nsteps == 0) return GP_OK;
+  int rc = join_in(h);
+  if (rc) return rc;
+  if (imag) {
+    set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
+    count_launch();
+  }
+  long t = 0;
+  if (nsteps >= 2 * kGraphSteps) {
+    cudaGraphExec_t& ge = h->graph[imag ? 1 : 0];
+    if (!ge) {
+      cudaGraph_t graph;
+      GP_CUDA(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
+      const unsigned long long before = g_launches.load();
+      for (int s = 0; s < kGraphSteps; ++s) enqueue_step<T>(h, imag, s & 1);
+      g_launches.store(before);  // capturing launches nothing
+      GP_CUDA(cudaStreamEndCapture(h->work, &graph));
+      cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        ge = nullptr;
+        return fail(GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
+      GP_CUDA(cudaGraphLaunch(ge, h->work));
+      count_launch((unsigned long long)kGraphSteps * h->dim);
+    }
+  }
+  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, (int)(t & 1));
+  if (imag) enqueue_finish_imag<T>(h, nsteps);
+  GP_CUDA(cudaGetLastError());
+  return join_out(h);
+}
+
+// Eager steps with an event pair around every sweep launch (recorded on the
+// library's stream, read once at the end); returns the mean duration of each
+// axis' sweep kernel in ms_out[axis].
+template <typename T>
+int time_steps_t(gp_handle* h, bool imag, long nsteps, double* ms_out) {
+  std::vector<cudaEvent_t> ev((size_t)nsteps * 2 * h->dim);
+  for (auto& e : ev) GP_CUDA(cudaEventCreate(&e));
+  int rc = join_in(h);
+  if (imag && !rc) {
+    set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
+    count_launch();
+  }
+  for (long t = 0; t < nsteps && !rc; ++t)
+    enqueue_step<T>(h, imag, (int)(t & 1), ev.data() + (size_t)t * 2 * h->dim);
+  if (imag && !rc && nsteps > 0) enqueue_finish_imag<T>(h, nsteps);
+  cudaError_t e = cudaStreamSynchronize(h->work);
+  if (!rc && e != cudaSuccess) rc = fail(GP_ERR_CUDA, std::string("gp_time_sweeps: ") + cudaGetErrorString(e));
+  double acc[3] = {0, 0, 0};
+  for (long t = 0; t < nsteps && !rc; ++t)
+    for (int d = 0; d < h->dim; ++d) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[(size_t)t * 2 * h->dim + 2 * d], ev[(size_t)t * 2 * h->dim + 2 * d + 1]);
+      acc[d] += ms;
+    }
+  for (auto& ee : ev) cudaEventDestroy(ee);
+  if (rc) return rc;
+  for (int d = 0; d < 3; ++d) ms_out[d] = (d < h->dim && nsteps > 0) ? acc[d] / nsteps : 0.0;
+  GP_CUDA(cudaGetLastError());
+  return join_out(h);
+}
+
+template <typename T>
+int run_observables_t(gp_handle* h, double* dens_dev) {
+  ObsArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.psi = (const c2_t<T>*)h->psi;
+  a.dim = h->dim;
+  a.nx = axis_len(h, 0);
+  a.ny = axis_len(h, 1);
+  a.nz = axis_len(h, 2);
+  a.hx = h->dx[0];
+  a.hy = h->dx[1];
+  a.hz = h->dx[2];
+  a.V = h->Vd;
+  a.vx = h->vd[0]; a.vy = h->vd[1]; a.vz = h->vd[2];
+  a.cx = h->cdx[0]; a.cy = h->cdx[1]; a.cz = h->cdx[2];
+  a.wx = h->wd[0]; a.wy = h->wd[1]; a.wz = h->wd[2];
+  a.density = dens_dev;
+  a.partials = h->partials;
+  a.counter = h->counter;
+  a.out = h->obs_out;
+  const int blocks = (int)std::min<long>((h->np + kObsThreads - 1) / kObsThreads, 152L * 16);
+  observables_kernel<T><<<blocks, kObsThreads, 0, h->work>>>(a);
+  count_launch();
+  GP_CUDA(cudaGetLastError());
+  return GP_OK;
+}
+
+}  // namespace gpe

@@ -1,0 +1,22 @@
+// gpe_step_f32.cu -- instantiates the step launchers for the float state.
+#include "gpe_step.cuh"
+
+namespace gpe {
+
+int run_steps_f32(gp_handle* h, bool imag, long nsteps) { return run_steps_t<float>(h, imag, nsteps); }
+
+int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out) {
+  return time_steps_t<float>(h, imag, nsteps, ms_out);
+}
+
+int run_observables_f32(gp_handle* h, double* dens_dev) { return run_observables_t<float>(h, dens_dev); }
+
+}  // namespace gpe
+
+namespace gpe {
+void to_float(gp_handle* h, float* dst, const double* src, long n) {
+  const int blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
+  to_float_kernel<<<blocks, 256, 0, h->work>>>(dst, src, n);
+  count_launch();
+}
+}  // namespace gpe

@@ -1,0 +1,14 @@
+// gpe_step_f64.cu -- instantiates the step launchers for the double state.
+#include "gpe_step.cuh"
+
+namespace gpe {
+
+int run_steps_f64(gp_handle* h, bool imag, long nsteps) { return run_steps_t<double>(h, imag, nsteps); }
+
+int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out) {
+  return time_steps_t<double>(h, imag, nsteps, ms_out);
+}
+
+int run_observables_f64(gp_handle* h, double* dens_dev) { return run_observables_t<double>(h, dens_dev); }
+
+}  // namespace gpe

@@ -159,9 +159,9 @@ __global__ void scale_kernel(c2_t<T>* psi, long np, const double* scale) {
   }
 }
 
-__global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
+static __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
 
-__global__ void to_float_kernel(float* dst, const double* src, long n) {
+static __global__ void to_float_kernel(float* dst, const double* src, long n) {
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
     dst[q] = (float)src[q];
 }

@@ -213,3 +213,45 @@ def test_full_size_128cube_two_steps(G, imag):
         ref = O.run(gr, phi0, imag, 2)
         assert rel_l2(got, ref) <= (1e-14 if prec == "f64" else 2e-6)
         p.close()
+
+
+SHAPES = [
+    {"GPE_SEG_X": "0", "GPE_SEG_YZ": "0"},                      # thread-per-line kernels
+    {"GPE_SEG_X": "2", "GPE_SEG_YZ": "4", "GPE_KEEP": "1"},
+    {"GPE_SEG_X": "8", "GPE_SEG_YZ": "8", "GPE_KEEP": "1"},
+    {"GPE_SEG_X": "16", "GPE_SEG_YZ": "16", "GPE_KEEP": "0"},
+    {"GPE_SEG_YZ": "32", "GPE_KEEP": "0"},
+]
+
+
+@pytest.mark.parametrize("env", SHAPES, ids=lambda e: "-".join(f"{k[4:]}{v}" for k, v in e.items()))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_every_kernel_shape_matches_oracle(G, monkeypatch, env, prec):
+    """All line-segment shapes the autotuner may pick (and the thread-per-line
+    kernels kept for long lines) give the oracle's result."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    dim, n, dx = 3, [40, 33, 24], [0.25, 0.3, 0.35]
+    nkl = [1.0, 1.4, 1.8]
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=17, noise=1e-3)
+    for imag in (True, False):
+        dt = 1e-3 if imag else 2e-4
+        p, gr = make(G, dim, n, dx, dt, nkl, 20.0, prec=prec)
+        p.set_state(phi0)
+        (p.step_imag if imag else p.step_real)(40)
+        got = p.get_state(device=False).astype(np.complex128)
+        ref = O.run(gr, phi0, imag, 40)
+        assert rel_l2(got, ref) <= (1e-13 if prec == "f64" else 3e-6), (imag, rel_l2(got, ref))
+        p.close()
+
+
+def test_long_lines_use_fallback_kernels(G):
+    """Lines longer than the segmented kernels take (n = 600 along x and y)."""
+    dim, n, dx = 2, [600, 530], [0.05, 0.05]
+    p, gr = make(G, dim, n, dx, 5e-4, [1.0, 1.2], 5.0)
+    phi0 = I.gaussian_state(dim, n, dx, [1.0, 1.2], seed=23)
+    p.set_state(phi0)
+    p.step_real(3)
+    ref = O.run(gr, phi0, False, 3)
+    assert rel_l2(p.get_state(device=False), ref) <= 1e-13
+    p.close()
