@@ -138,8 +138,38 @@ int upload_coefs_t(gp_handle* h) {
         std::copy(gf.begin(), gf.end(), all.begin() + (size_t)(1 + 2 * s) * n);
         std::copy(gb.begin(), gb.end(), all.begin() + (size_t)(2 + 2 * s) * n);
       }
+      // carry tables for the segment scans: with A_q the product of alpha over
+      // segment q, Pf[q][t] = prod_{q<r<=t} A_r (q <= t) and
+      // Pb[q][t] = prod_{t<=r<q} A_r (q >= t), 16 x 16 per segment length
+      std::vector<cd> tabs((size_t)kNumSegs * 2 * 256, cd(0, 0));
+      const int M = n - 2;
+      for (int si = 0; si < kNumSegs; ++si) {
+        const int sg = kSegs[si];
+        cd Aseg[16];
+        for (int q = 0; q < 16; ++q) {
+          cd acc(1, 0);
+          for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) acc *= f.alpha[k];
+          Aseg[q] = acc;
+        }
+        cd* Pf = tabs.data() + (size_t)si * 512;
+        cd* Pb = Pf + 256;
+        for (int q = 0; q < 16; ++q)
+          for (int t = 0; t < 16; ++t) {
+            cd acc(1, 0);
+            if (q <= t) {
+              for (int r = q + 1; r <= t; ++r) acc *= Aseg[r];
+              Pf[q * 16 + t] = acc;
+            }
+            acc = cd(1, 0);
+            if (q >= t) {
+              for (int r = t; r < q; ++r) acc *= Aseg[r];
+              Pb[q * 16 + t] = acc;
+            }
+          }
+      }
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
+      if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;
       if (mode < 2) {
         if ((rc = upload_c2<T>(h, h->cm[mode == MODE_IMAG][d], f.m))) return rc;
         if ((rc = upload_c2<T>(h, h->ccp[mode == MODE_IMAG][d], f.cp))) return rc;
@@ -153,35 +183,41 @@ int env_int(const char* name, int dflt) {
   return v ? std::atoi(v) : dflt;
 }
 
-// Kernel shapes.  x lines: one warp per line with seg_x interior points per
-// lane (32 * seg_x >= n - 2, seg_x <= 16).  y/z lines: 32 lines per block and
-// at most 16 segments of seg_c points; keep_c keeps the input segment in
-// registers when it fits (FP32 seg <= 16, FP64 seg <= 8).  Longer lines use
-// the thread-per-line kernel (shape 0).  GPE_SEG_X / GPE_SEG_YZ / GPE_KEEP
-// override the defaults for tuning.
+// Kernel shapes.  y/z lines: 32 lines per block, one warp per segment, at
+// most 16 segments: seg = smallest of 4, 8, 16, 32 with ceil((n-2)/seg) <= 16.
+// x lines in 2d/3d: the shared-memory tile kernel with the same rule; the 1d
+// line: one warp per line with 32 * seg_x >= n - 2.  Lines longer than 514
+// points use the thread-per-line kernel (shape 0).  GPE_SEG_X, GPE_SEG_YZ and
+// GPE_TILE_X override the defaults (used by the autotuner and the shape tests).
+int tile_seg(int M) {
+  for (int s : {4, 8, 16, 32})
+    if ((M + s - 1) / s <= 16) return s;
+  return 0;
+}
+
 void choose_shapes(gp_handle* h) {
   const int M0 = h->n[0] - 2;
+  h->tile_x = env_int("GPE_TILE_X", h->dim > 1 ? 1 : 0) != 0;
   int sx = 0;
-  for (int s : {1, 2, 4, 8, 16})
-    if (32 * s >= M0) { sx = s; break; }
+  if (h->tile_x) {
+    sx = tile_seg(M0);
+  } else {
+    for (int s : {1, 2, 4, 8, 16})
+      if (32 * s >= M0) { sx = s; break; }
+  }
   sx = env_int("GPE_SEG_X", sx);
-  if (sx > 0 && (seg_index(sx) < 0 || sx > 16 || 32 * sx < M0)) sx = 0;
+  if (h->tile_x) {
+    if (sx < 4 || sx > 32 || seg_index(sx) < 0 || (M0 + sx - 1) / sx > 16) sx = 0;
+  } else if (sx > 0 && (seg_index(sx) < 0 || sx > 16 || 32 * sx < M0)) {
+    sx = 0;
+  }
+  if (sx == 0) h->tile_x = false;
   h->seg_x = sx;
   int Mc = 0;
   for (int d = 1; d < h->dim; ++d) Mc = std::max(Mc, h->n[d] - 2);
-  const bool f64 = h->prec == GP_F64;
-  int sc = 0;
-  for (int s : {8, 16, 32})
-    if ((Mc + s - 1) / s <= 16) { sc = s; break; }
-  if (!f64 && sc == 8 && (Mc + 15) / 16 <= 16) sc = 16;
-  sc = env_int("GPE_SEG_YZ", sc);
+  int sc = env_int("GPE_SEG_YZ", tile_seg(Mc));
   if (sc > 0 && (seg_index(sc) < 0 || sc < 4 || (Mc + sc - 1) / sc > 16)) sc = 0;
-  int keep = f64 ? (sc <= 8) : (sc <= 16);
-  keep = env_int("GPE_KEEP", keep);
-  if (keep && sc > 16) keep = 0;
-  if (!keep && sc == 4) keep = 1;
   h->seg_c = sc;
-  h->keep_c = keep;
 }
 
 }  // namespace
@@ -290,8 +326,10 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     if ((rc = upload_real<double>(h, h->wd[d], w))) return bail(rc);
   }
   for (int d = 0; d < dim; ++d) {
-    for (int mode = 0; mode < NUM_MODES; ++mode)
+    for (int mode = 0; mode < NUM_MODES; ++mode) {
       if ((rc = dev_alloc(h, &h->coef[mode][d], (size_t)(1 + 2 * kNumSegs) * h->n[d] * h->esize))) return bail(rc);
+      if ((rc = dev_alloc(h, &h->ctab[mode][d], (size_t)kNumSegs * 512 * h->esize))) return bail(rc);
+    }
     for (int im = 0; im < 2; ++im) {
       if ((rc = dev_alloc(h, &h->cm[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
       if ((rc = dev_alloc(h, &h->ccp[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);

@@ -68,11 +68,17 @@ struct gp_handle {
   // per (mode, axis): [0] alpha_k, [1 + 2 s] forward and [2 + 2 s] backward
   // segment products for segment length kSegs[s]; each n complex values
   void* coef[gpe::NUM_MODES][3] = {{nullptr}};
+  // per (mode, axis): for each segment length, the carry tables Pf and Pb
+  // (16 x 16 complex each) of the segment scans
+  void* ctab[gpe::NUM_MODES][3] = {{nullptr}};
   // legacy thread-per-line factors (m_k, c'_k) per (imag, axis), used when a
   // line is too long for the segmented kernels
   void* cm[2][3] = {{nullptr}};
   void* ccp[2][3] = {{nullptr}};
-  int seg_x = 0, seg_c = 0, keep_c = 1;  // kernel shapes (0 = thread-per-line kernel)
+  // kernel shapes: segment length per x / y,z lines (0 = thread-per-line
+  // kernel) and whether the x lines are staged through a shared-memory tile
+  int seg_x = 0, seg_c = 0;
+  bool tile_x = false;
   double* scale = nullptr;   // [2] renormalisation slots
   double* partials = nullptr;
   unsigned int* counter = nullptr;

@@ -59,30 +59,51 @@ void launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
   }
 }
 
-// ---- segmented y/z sweep
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
+// ---- segmented y/z sweep (registers, coefficients in shared memory)
+template <typename T, bool IMAG, bool LAST, int SEG>
 void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
-  colsweep_kernel<T, IMAG, LAST, SEG, KEEP><<<blocks, 32 * nseg, 0, s>>>(a);
+  const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
+  colsweep_kernel<T, IMAG, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
 }
 
 template <typename T, bool IMAG, bool LAST>
-void launch_c_seg(int seg, bool keep, const Sweep2Args<T>& a, cudaStream_t s) {
-  if (keep) {
-    switch (seg) {
-      case 4: launch_c<T, IMAG, LAST, 4, true>(a, s); break;
-      case 8: launch_c<T, IMAG, LAST, 8, true>(a, s); break;
-      default: launch_c<T, IMAG, LAST, 16, true>(a, s); break;
-    }
-  } else {
-    switch (seg) {
-      case 8: launch_c<T, IMAG, LAST, 8, false>(a, s); break;
-      case 16: launch_c<T, IMAG, LAST, 16, false>(a, s); break;
-      default: launch_c<T, IMAG, LAST, 32, false>(a, s); break;
-    }
+void launch_c_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+  switch (seg) {
+    case 4: launch_c<T, IMAG, LAST, 4>(a, s); break;
+    case 8: launch_c<T, IMAG, LAST, 8>(a, s); break;
+    case 16: launch_c<T, IMAG, LAST, 16>(a, s); break;
+    default: launch_c<T, IMAG, LAST, 32>(a, s); break;
+  }
+}
+
+// ---- shared-memory tile x sweep
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+void launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
+  const int M = a.geom.n - 2;
+  const int nseg = (M + SEG - 1) / SEG;
+  const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
+  const size_t smem = (size_t)a.geom.n * (kTilePitch + 3) * sizeof(c2_t<T>) + 512 * sizeof(c2_t<T>);
+  static bool attr_set = false;  // one opt-in per instantiation
+  if (!attr_set) {
+    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
+  tsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
+  count_launch();
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST>
+void launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+  switch (seg) {
+    case 4: launch_t<T, IMAG, FIRST, LAST, 4>(a, s); break;
+    case 8: launch_t<T, IMAG, FIRST, LAST, 8>(a, s); break;
+    case 16: launch_t<T, IMAG, FIRST, LAST, 16>(a, s); break;
+    default: launch_t<T, IMAG, FIRST, LAST, 32>(a, s); break;
   }
 }
 
@@ -108,6 +129,7 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
     a.alpha = coef_ptr<T>(h, mode, d, 0);
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
+    a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
     a.V = (const T*)h->Vt;
     a.vx = (const T*)h->vt[0];
     a.vy = (const T*)h->vt[1];
@@ -121,7 +143,14 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
     a.partials = h->partials;
     a.counter = h->counter;
     a.scale_out = h->scale + (1 - par);
-    if (d == 0) {
+    if (d == 0 && h->tile_x) {
+      if (imag) {
+        if (last) launch_t_seg<T, true, true, true>(seg, a, h->work);
+        else launch_t_seg<T, true, true, false>(seg, a, h->work);
+      } else {
+        launch_t_seg<T, false, true, false>(seg, a, h->work);
+      }
+    } else if (d == 0) {
       if (imag) {
         if (last) launch_x_seg<T, true, true, true>(seg, a, h->work);
         else launch_x_seg<T, true, true, false>(seg, a, h->work);
@@ -129,12 +158,11 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
         launch_x_seg<T, false, true, false>(seg, a, h->work);
       }
     } else {
-      const bool keep = h->keep_c != 0;
       if (imag) {
-        if (last) launch_c_seg<T, true, true>(seg, keep, a, h->work);
-        else launch_c_seg<T, true, false>(seg, keep, a, h->work);
+        if (last) launch_c_seg<T, true, true>(seg, a, h->work);
+        else launch_c_seg<T, true, false>(seg, a, h->work);
       } else {
-        launch_c_seg<T, false, false>(seg, keep, a, h->work);
+        launch_c_seg<T, false, false>(seg, a, h->work);
       }
     }
     return;

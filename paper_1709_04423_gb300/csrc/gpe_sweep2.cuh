@@ -18,25 +18,28 @@
 //
 // Both recurrences are linear with time-invariant coefficients, so a line is
 // split into segments of SEG points, each run by its own thread with a zero
-// carry-in; the true carries follow from the segment products
+// carry-in.  With the precomputed segment products
 //     Gf_k = prod_{i=start..k} alpha_i,   Gb_k = prod_{i=k..end} alpha_i,
-// (precomputed on the host) by a scan over segments:
-//     e_k = e^_k + Gf_k E_{s-1},  E_s = e^_end + Gf_end E_{s-1},
-//     z_k = z^_k + Gb_k Z_{s+1},  Z_s = z^_start + Gb_start Z_{s+1}.
-// The result is the exact elimination, reassociated.  Everything a thread
-// needs stays in registers: one read and one write of the state per point.
+// and A_q = the product over all of segment q, the true values are
+//     e_k = e^_k + Gf_k E_{s-1},   E_t = sum_{q<=t} (prod_{q<r<=t} A_r) e^_end(q),
+//     z_k = z^_k + Gb_k Z_{s+1},   Z_t = sum_{q>=t} (prod_{t<=r<q} A_r) z^_start(q),
+// where the products over segments are host-precomputed 16 x 16 tables, so
+// every thread forms its own carry-in as a short dot product (no serial scan
+// across segments).  The result is the exact elimination, reassociated.
 //
-// Two mappings:
-//  * x lines (contiguous): one warp per line, lane = segment; carries move by
-//    warp shuffles (Kogge-Stone affine scan).  FIRST fuses the sub-step N
-//    (and the pending imaginary-time renormalisation) into the load.
-//  * y/z lines (strided): lane = line, warp = segment, so every load and store
-//    of a warp is a contiguous row of 32 neighbouring lines; carries pass
-//    through shared memory.
+// Three mappings:
+//  * y/z lines (strided): lane = line (32 neighbouring lines per block, so
+//    every warp load and store is one contiguous row), warp = segment; the
+//    segment lives in registers.
+//  * x lines in 2d/3d: a tile of 32 lines x n points is loaded row-wise with
+//    coalesced accesses and transposed into shared memory (pitch 33), the
+//    sub-step N and the pending renormalisation are applied on the way in
+//    (FIRST), the segments are solved as above, and the tile is written back.
+//  * x line in 1d: one warp per line, lane = segment, carries by shuffles.
 // LAST (imaginary time) accumulates the Simpson-weighted norm of the output:
-// each thread sums its own SEG points in the state precision, and everything
-// from there on (the line weight, warp, block and grid sums) is FP64; the
-// last block stores the next step's factor 1/sqrt(norm).
+// each thread sums its own points in the state precision, everything from
+// there on (line weights, warp, block and grid sums) is FP64; the last block
+// stores the next step's factor 1/sqrt(norm).
 #pragma once
 #include "gpe_common.cuh"
 
@@ -49,13 +52,14 @@ struct Sweep2Args {
   const c2_t<T>* alpha;  // [n] alpha_k = r m_k (imaginary time: real part only)
   const c2_t<T>* gf;     // [n] forward segment products for this SEG
   const c2_t<T>* gb;     // [n] backward segment products for this SEG
+  const c2_t<T>* ptab;   // [2][16][16] carry tables Pf, Pb for this SEG
   // sub-step N (FIRST)
   const T* V;            // full potential or nullptr (separable harmonic trap)
   const T* vx; const T* vy; const T* vz;
   T dt, g;
   const double* scale_in;
   // norm (LAST)
-  const T* w_axis;     // Simpson weights along the line, state precision
+  const T* w_axis;       // Simpson weights along the line, state precision
   const double* w_a; const double* w_b;
   double* partials;
   unsigned int* counter;
@@ -104,11 +108,11 @@ __device__ __forceinline__ c2_t<T> shfl_down2(c2_t<T> v, int o) {
   return mk<T>(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
 }
 
-// Segment-local forward/backward passes over SEG registers.  k0 = first
-// interior index of the segment; points with k > M are padding (zero).
+// Segment-local passes over SEG registers.  k0 = first interior index of the
+// segment; points with k > M are padding (p = 0 there).
 template <typename T, bool IMAG, int SEG>
-__device__ __forceinline__ void local_forward(c2_t<T> (&p)[SEG], c2_t<T> (&e)[SEG], c2_t<T> pl, c2_t<T> pr,
-                                              const c2_t<T>* __restrict__ alpha, int k0, int M) {
+__device__ __forceinline__ void local_forward(const c2_t<T> (&p)[SEG], c2_t<T> (&e)[SEG], c2_t<T> pl, c2_t<T> pr,
+                                              const c2_t<T>* alpha, int k0, int M) {
   c2_t<T> prev = mk<T>(0, 0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
@@ -119,46 +123,255 @@ __device__ __forceinline__ void local_forward(c2_t<T> (&p)[SEG], c2_t<T> (&e)[SE
     const c2_t<T> t = mk<T>(prev.x - T(2) * (left.x + right.x) + T(4) * p[j].x,
                             prev.y - T(2) * (left.y + right.y) + T(4) * p[j].y);
     c2_t<T> v = mk<T>(0, 0);
-    if (k <= M) v = cf_mul<T, IMAG>(__ldg(&alpha[k]), t);
+    if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
     e[j] = v;
     prev = v;
   }
 }
 
 template <typename T, bool IMAG, int SEG>
-__device__ __forceinline__ void local_backward(c2_t<T> (&e)[SEG], const c2_t<T>* __restrict__ alpha, int k0, int M) {
+__device__ __forceinline__ void local_backward(c2_t<T> (&e)[SEG], const c2_t<T>* alpha, int k0, int M) {
   c2_t<T> next = mk<T>(0, 0);
 #pragma unroll
   for (int j = SEG - 1; j >= 0; --j) {
     const int k = k0 + j;
-    if (k <= M) next = cf_fma<T, IMAG>(__ldg(&alpha[k]), next, e[j]);
+    if (k <= M) next = cf_fma<T, IMAG>(alpha[k], next, e[j]);
     else next = mk<T>(0, 0);
     e[j] = next;
   }
 }
 
-// ---------------------------------------------------------------- x sweep
-// One warp per line; lane j owns interior points k = 1 + j*SEG .. (j+1)*SEG.
+// Shared-memory coefficient copy: alpha, gf, gb [n each] then Pf, Pb [512].
+template <typename T>
+__device__ __forceinline__ void load_coefs(const Sweep2Args<T>& A, c2_t<T>* sc, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    sc[k] = A.alpha[k];
+    sc[n + k] = A.gf[k];
+    sc[2 * n + k] = A.gb[k];
+  }
+  for (int q = threadIdx.x; q < 512; q += blockDim.x) sc[3 * n + q] = A.ptab[q];
+}
+
+// Solves the segment of thread (lane, warp s) of a block whose lines run one
+// per lane and whose segments run one per warp.  On entry p holds the
+// segment (zero beyond M) and pl/pr its outer neighbours; on exit z holds the
+// increment z_k.  Two block barriers; every thread of the block must call it.
+template <typename T, bool IMAG, int SEG>
+__device__ __forceinline__ void seg_solve(const c2_t<T> (&p)[SEG], c2_t<T> pl, c2_t<T> pr, c2_t<T> (&z)[SEG],
+                                          const c2_t<T>* sc, int n, c2_t<T> (*cf)[33], c2_t<T> (*cb)[33],
+                                          int s, int nseg, int lane) {
+  using c2 = c2_t<T>;
+  const int M = n - 2, k0 = 1 + s * SEG;
+  const c2* al = sc;
+  const c2* gf = sc + n;
+  const c2* gb = sc + 2 * n;
+  const c2* Pf = sc + 3 * n;
+  const c2* Pb = Pf + 256;
+  local_forward<T, IMAG, SEG>(p, z, pl, pr, al, k0, M);
+  {
+    c2 Bend = z[SEG - 1];
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) if (k0 + j == M) Bend = z[j];
+    cf[s][lane] = Bend;
+  }
+  __syncthreads();
+  c2 Ein = mk<T>(0, 0);
+  for (int q = 0; q < s; ++q) Ein = cf_fma<T, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    if (k <= M) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
+  }
+  local_backward<T, IMAG, SEG>(z, al, k0, M);
+  cb[s][lane] = z[0];
+  __syncthreads();
+  c2 Zin = mk<T>(0, 0);
+  for (int q = s + 1; q < nseg; ++q) Zin = cf_fma<T, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    if (k <= M) z[j] = cf_fma<T, IMAG>(gb[k], Zin, z[j]);
+  }
+}
+
+__device__ __forceinline__ int line_base32(const LineGeom& g, int L) {
+  if (g.axis == 0) return L * g.nx;
+  if (g.axis == 1) return (L % g.nx) + (L / g.nx) * g.nx * g.ny;
+  return L;
+}
+
+template <bool LAST>
+__device__ __forceinline__ void finish_norm(double nacc, double* partials, unsigned int* counter,
+                                            double* scale_out, double* red_smem) {
+  if (LAST) {
+    double v[1] = {nacc}, tot[1];
+    block_sum<1>(v, red_smem);
+    if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0) *scale_out = 1.0 / sqrt(tot[0]);
+  }
+}
+
+// ---------------------------------------------------------------- y/z sweep
+// blockDim.x = 32 * nseg, nseg = ceil((n-2)/SEG) <= 16; dynamic shared memory
+// holds the coefficients (3n + 512 complex values).
+template <typename T, bool IMAG, bool LAST, int SEG>
+__global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
+  using c2 = c2_t<T>;
+  extern __shared__ __align__(16) unsigned char csmem_raw[];
+  c2* sc = reinterpret_cast<c2*>(csmem_raw);
+  __shared__ c2 cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  const LineGeom& G = A.geom;
+  const int n = G.n, M = n - 2;
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nseg = blockDim.x >> 5;
+  const int L = blockIdx.x * 32 + lane;
+  const bool active = L < G.nlines;
+  const int st = (int)G.stride;
+  const int k0 = 1 + s * SEG;
+  load_coefs<T>(A, sc, n);
+  c2* line = A.psi + (active ? line_base32(G, L) : 0);
+  c2 p[SEG];
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    p[j] = (active && k <= M) ? line[k * st] : mk<T>(0, 0);
+  }
+  const c2 pl = (active && k0 - 1 >= 1) ? line[(k0 - 1) * st] : mk<T>(0, 0);
+  const c2 pr = (active && k0 + SEG <= M) ? line[(k0 + SEG) * st] : mk<T>(0, 0);
+  __syncthreads();  // coefficients
+  c2 z[SEG];
+  seg_solve<T, IMAG, SEG>(p, pl, pr, z, sc, n, cf, cb, s, nseg, lane);
+  double nacc = 0.0;
+  if (active) {
+    const T* w = A.w_axis;
+    T tacc = T(0);
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      const int k = k0 + j;
+      if (k <= M) {
+        const c2 u = mk<T>(p[j].x - z[j].x, p[j].y - z[j].y);
+        line[k * st] = u;
+        if (LAST) tacc += w[k] * (u.x * u.x + u.y * u.y);
+      }
+    }
+    if (s == 0) {
+      line[0] = mk<T>(0, 0);
+      line[(n - 1) * st] = mk<T>(0, 0);
+    }
+    if (LAST) nacc = (double)tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);  // FP64 from here on
+  }
+  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
+}
+
+// ---------------------------------------------------------------- x sweep (2d/3d)
+// Tile of 32 x lines in shared memory, transposed ([point][line], pitch 33).
+// blockDim.x = 32 * nseg; dynamic shared memory: coefficients (3n + 512)
+// then the tile (33 n) complex values.
+constexpr int kTilePitch = 33;
+
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+__global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
+  using c2 = c2_t<T>;
+  extern __shared__ __align__(16) unsigned char tsmem_raw[];
+  const LineGeom& G = A.geom;
+  const int n = G.n, M = n - 2;
+  c2* sc = reinterpret_cast<c2*>(tsmem_raw);
+  c2* tile = sc + 3 * n + 512;
+  __shared__ c2 cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nseg = blockDim.x >> 5;
+  const int L0 = blockIdx.x * 32;
+  const int nl = min(32, (int)G.nlines - L0);
+  load_coefs<T>(A, sc, n);
+  T scl = T(1);
+  if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
+  // ---- load: warp w takes lines w, w + nseg, ...; lane takes points lane, lane + 32, ...
+  const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
+  for (int c = s; c < 32; c += nseg) {
+    const bool line_ok = c < nl;
+    const int gbase = (L0 + c) * G.nx;
+    c2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int k = q * 32 + lane;
+      v[q] = (q < per_line && line_ok && k >= 1 && k <= M) ? A.psi[gbase + k] : mk<T>(0, 0);
+    }
+    T vline = T(0);
+    if (FIRST && line_ok && !A.V) {
+      const int L = L0 + c;
+      vline = A.vy[L % G.ny] + A.vz[L / G.ny];
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int k = q * 32 + lane;
+      if (q >= per_line || k >= n) continue;
+      c2 w = v[q];
+      if (FIRST && line_ok && k >= 1 && k <= M) {
+        w.x *= scl; w.y *= scl;
+        const T Vk = A.V ? A.V[gbase + k] : A.vx[k] + vline;
+        w = phase_N<T, IMAG>(w, Vk, A.dt, A.g);
+      }
+      tile[k * kTilePitch + c] = w;
+    }
+  }
+  __syncthreads();
+  // ---- segments: lane = line, warp = segment
+  const int k0 = 1 + s * SEG;
+  c2 p[SEG];
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    p[j] = k <= M ? tile[k * kTilePitch + lane] : mk<T>(0, 0);
+  }
+  const c2 pl = tile[(k0 - 1) * kTilePitch + lane];
+  const c2 pr = (k0 + SEG <= M) ? tile[(k0 + SEG) * kTilePitch + lane] : mk<T>(0, 0);
+  c2 z[SEG];
+  seg_solve<T, IMAG, SEG>(p, pl, pr, z, sc, n, cf, cb, s, nseg, lane);
+  T tacc = T(0);
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    if (k <= M) {
+      const c2 u = mk<T>(p[j].x - z[j].x, p[j].y - z[j].y);
+      tile[k * kTilePitch + lane] = u;
+      if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
+    }
+  }
+  double nacc = 0.0;
+  if (LAST && lane < nl) {
+    const int L = L0 + lane;
+    nacc = (double)tacc * (A.w_a[L % G.ny] * A.w_b[L / G.ny]);  // FP64 from here on
+  }
+  __syncthreads();
+  // ---- store (tile end points are zero)
+  for (int c = s; c < nl; c += nseg) {
+    const int gbase = (L0 + c) * G.nx;
+    for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
+  }
+  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
+}
+
+// ---------------------------------------------------------------- x sweep (1d)
+// One warp per line; lane j owns interior points k = 1 + j*SEG .. (j+1)*SEG;
+// carries by a Kogge-Stone affine scan over shuffles.
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
 __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
   using c2 = c2_t<T>;
   __shared__ double red_smem[32];
   const LineGeom& G = A.geom;
   const int lane = threadIdx.x & 31;
-  const long L = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int L = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const bool active = L < G.nlines;  // warp-uniform
   double nacc = 0.0;
   if (active) {
     const int M = G.n - 2;
-    const long base = L * (long)G.nx;
+    const int base = L * G.nx;
     c2* line = A.psi + base;
     const int k0 = 1 + lane * SEG;
-    int ta, tb;
-    line_transverse(G, L, ta, tb);
-    T vline = T(0), sc = T(1);
+    const int ta = L % G.ny, tb = L / G.ny;
+    T vline = T(0), scl = T(1);
     if (FIRST) {
       if (A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
-      if (A.scale_in) sc = (T)(*A.scale_in);
+      if (A.scale_in) scl = (T)(*A.scale_in);
     }
     c2 p[SEG], e[SEG];
 #pragma unroll
@@ -168,28 +381,23 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
       if (k <= M) {
         v = line[k];
         if (FIRST) {
-          v.x *= sc; v.y *= sc;
+          v.x *= scl; v.y *= scl;
           const T Vk = A.V ? A.V[base + k] : (A.vx[k] + vline);
           v = phase_N<T, IMAG>(v, Vk, A.dt, A.g);
         }
       }
       p[j] = v;
     }
-    // halo from the neighbouring lanes (zero at the Dirichlet ends)
     c2 pl = shfl_up2<T>(p[SEG - 1], 1);
     c2 pr = shfl_down2<T>(p[0], 1);
     if (lane == 0) pl = mk<T>(0, 0);
     if (lane == 31) pr = mk<T>(0, 0);
     local_forward<T, IMAG, SEG>(p, e, pl, pr, A.alpha, k0, M);
-    // forward carries: C_j = e^_end(j) + P_j C_{j-1}
     const int kend = k0 + SEG - 1;
     c2 Pm = (k0 <= M) ? __ldg(&A.gf[min(kend, M)]) : mk<T>(1, 0);
     c2 Bc = e[SEG - 1];
-    if (k0 <= M && kend > M) {
-      // ragged last segment: its end value sits at index M - k0
 #pragma unroll
-      for (int j = 0; j < SEG; ++j) if (k0 + j == M) Bc = e[j];
-    }
+    for (int j = 0; j < SEG; ++j) if (k0 + j == M) Bc = e[j];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const c2 Pp = shfl_up2<T>(Pm, o), Bp = shfl_up2<T>(Bc, o);
@@ -206,7 +414,6 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
       if (k <= M) e[j] = cf_fma<T, IMAG>(__ldg(&A.gf[k]), Ein, e[j]);
     }
     local_backward<T, IMAG, SEG>(e, A.alpha, k0, M);
-    // backward carries: D_j = z^_start(j) + Q_j D_{j+1}
     c2 Qm = (k0 <= M) ? __ldg(&A.gb[k0]) : mk<T>(1, 0);
     c2 Dc = e[0];
 #pragma unroll
@@ -219,7 +426,7 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
     }
     c2 Zin = shfl_down2<T>(Dc, 1);
     if (lane == 31) Zin = mk<T>(0, 0);
-    T tacc = T(0);  // this thread's few points, in the state precision
+    T tacc = T(0);
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
@@ -234,127 +441,7 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
     if (lane == 31) line[G.n - 1] = mk<T>(0, 0);
     if (LAST) nacc = (double)tacc * (A.w_a[ta] * A.w_b[tb]);  // FP64 from here on
   }
-  if (LAST) {
-    double v[1] = {nacc}, tot[1];
-    block_sum<1>(v, red_smem);
-    if (grid_sum_last<1>(v, A.partials, A.counter, tot, red_smem) && threadIdx.x == 0)
-      *A.scale_out = 1.0 / sqrt(tot[0]);
-  }
-}
-
-// ---------------------------------------------------------------- y/z sweep
-// Lane = line (32 consecutive lines per block), warp s = segment of SEG points;
-// blockDim.x = 32 * nseg with nseg <= 16.  KEEP holds the input segment in
-// registers for the final u = p - z; otherwise the forward pass streams the
-// loads and the final pass reads p again (from L2), halving register use.
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
-__global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
-  using c2 = c2_t<T>;
-  __shared__ c2 carry[16][33];
-  __shared__ double red_smem[32];
-  const LineGeom& G = A.geom;
-  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nseg = blockDim.x >> 5;
-  const long L = (long)blockIdx.x * 32 + lane;
-  const bool active = L < G.nlines;
-  const int M = G.n - 2;
-  const long st = G.stride;
-  const int k0 = 1 + s * SEG;
-  const long base = active ? line_base(G, L) : 0;
-  c2* line = A.psi + base;
-  auto ld = [&](int k) -> c2 { return (active && k >= 1 && k <= M) ? line[(long)k * st] : mk<T>(0, 0); };
-  c2 e[SEG];
-  c2 p[KEEP ? SEG : 1];
-  if constexpr (KEEP) {
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) p[j] = ld(k0 + j);
-    local_forward<T, IMAG, SEG>(p, e, ld(k0 - 1), ld(k0 + SEG), A.alpha, k0, M);
-  } else {
-    c2 pm = ld(k0 - 1), pc = ld(k0), prev = mk<T>(0, 0);
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      const int k = k0 + j;
-      const c2 pn = ld(k + 1);
-      const c2 t = mk<T>(prev.x - T(2) * (pm.x + pn.x) + T(4) * pc.x,
-                         prev.y - T(2) * (pm.y + pn.y) + T(4) * pc.y);
-      c2 v = mk<T>(0, 0);
-      if (k <= M) v = cf_mul<T, IMAG>(__ldg(&A.alpha[k]), t);
-      e[j] = v;
-      prev = v;
-      pm = pc;
-      pc = pn;
-    }
-  }
-  // segment end value -> shared; one warp runs the carry recurrence
-  {
-    c2 Bc = e[SEG - 1];
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) if (k0 + j == M) Bc = e[j];
-    carry[s][lane] = Bc;
-  }
-  __syncthreads();
-  if (s == 0) {
-    c2 C = mk<T>(0, 0);
-    for (int q = 0; q < nseg; ++q) {
-      const int kq0 = 1 + q * SEG;
-      if (kq0 > M) break;
-      const c2 Pq = __ldg(&A.gf[min(kq0 + SEG - 1, M)]);
-      C = cf_fma<T, IMAG>(Pq, C, carry[q][lane]);
-      carry[q][lane] = C;  // E_q
-    }
-  }
-  __syncthreads();
-  const c2 Ein = (s > 0) ? carry[s - 1][lane] : mk<T>(0, 0);
-#pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    if (k <= M) e[j] = cf_fma<T, IMAG>(__ldg(&A.gf[k]), Ein, e[j]);
-  }
-  local_backward<T, IMAG, SEG>(e, A.alpha, k0, M);
-  __syncthreads();  // every warp has read its E before the slots are reused
-  carry[s][lane] = e[0];
-  __syncthreads();
-  if (s == 0) {
-    c2 D = mk<T>(0, 0);
-    for (int q = nseg - 1; q >= 0; --q) {
-      const int kq0 = 1 + q * SEG;
-      if (kq0 > M) continue;
-      const c2 Qq = __ldg(&A.gb[kq0]);
-      D = cf_fma<T, IMAG>(Qq, D, carry[q][lane]);
-      carry[q][lane] = D;  // Z_q
-    }
-  }
-  __syncthreads();
-  const c2 Zin = (s + 1 < nseg && k0 + SEG <= M) ? carry[s + 1][lane] : mk<T>(0, 0);
-  double nacc = 0.0;
-  if (active) {
-    int ta = 0, tb = 0;
-    if (LAST) line_transverse(G, L, ta, tb);
-    T tacc = T(0);  // this thread's few points, in the state precision
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      const int k = k0 + j;
-      if (k <= M) {
-        const c2 z = cf_fma<T, IMAG>(__ldg(&A.gb[k]), Zin, e[j]);
-        c2 pk;
-        if constexpr (KEEP) pk = p[j];
-        else pk = __ldcg(&line[(long)k * st]);
-        const c2 u = mk<T>(pk.x - z.x, pk.y - z.y);
-        line[(long)k * st] = u;
-        if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
-      }
-    }
-    if (s == 0) {
-      line[0] = mk<T>(0, 0);
-      line[(long)(G.n - 1) * st] = mk<T>(0, 0);
-    }
-    if (LAST) nacc = (double)tacc * (A.w_a[ta] * A.w_b[tb]);  // FP64 from here on
-  }
-  if (LAST) {
-    double v[1] = {nacc}, tot[1];
-    block_sum<1>(v, red_smem);
-    if (grid_sum_last<1>(v, A.partials, A.counter, tot, red_smem) && threadIdx.x == 0)
-      *A.scale_out = 1.0 / sqrt(tot[0]);
-  }
+  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
 }
 
 }  // namespace gpe

@@ -216,15 +216,17 @@ def test_full_size_128cube_two_steps(G, imag):
 
 
 SHAPES = [
-    {"GPE_SEG_X": "0", "GPE_SEG_YZ": "0"},                      # thread-per-line kernels
-    {"GPE_SEG_X": "2", "GPE_SEG_YZ": "4", "GPE_KEEP": "1"},
-    {"GPE_SEG_X": "8", "GPE_SEG_YZ": "8", "GPE_KEEP": "1"},
-    {"GPE_SEG_X": "16", "GPE_SEG_YZ": "16", "GPE_KEEP": "0"},
-    {"GPE_SEG_YZ": "32", "GPE_KEEP": "0"},
+    {"GPE_SEG_X": "0", "GPE_SEG_YZ": "0"},                     # thread-per-line kernels
+    {"GPE_TILE_X": "0"},                                       # warp-per-line x sweep
+    {"GPE_TILE_X": "0", "GPE_SEG_X": "2", "GPE_SEG_YZ": "16"},
+    {},                                                        # default shapes
+    {"GPE_SEG_X": "4", "GPE_SEG_YZ": "4"},
+    {"GPE_SEG_X": "16", "GPE_SEG_YZ": "8"},
+    {"GPE_SEG_X": "32", "GPE_SEG_YZ": "32"},
 ]
 
 
-@pytest.mark.parametrize("env", SHAPES, ids=lambda e: "-".join(f"{k[4:]}{v}" for k, v in e.items()))
+@pytest.mark.parametrize("env", SHAPES, ids=lambda e: "-".join(f"{k[4:]}{v}" for k, v in e.items()) or "default")
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_every_kernel_shape_matches_oracle(G, monkeypatch, env, prec):
     """All line-segment shapes the autotuner may pick (and the thread-per-line
