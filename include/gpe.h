@@ -130,6 +130,31 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
  * Synchronises the stream. */
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch);
 
+/* Observables without a handle and without allocating.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the moment they need the observables -- code running
+ * while a stream is captured into a CUDA graph, code inside an application
+ * that owns the whole device-memory budget, code that must not synchronise
+ * (cudaMalloc/cudaFree may).  It computes what gp_observables computes, for
+ * a state the caller passes, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   dim, n, dx, nkl, g, prec  as for gp_init; at most 4096 points per axis
+ *                             (GP_ERR_INVALID beyond that).
+ *   psi      device state (npoints complex values in precision prec).
+ *   V        device potential (npoints doubles), or NULL for the harmonic trap.
+ *   out      device buffer of 7 doubles, written in stream order with
+ *            {norm, energy, mu, rms_x, rms_y, rms_z, rms_r} (the gp_obs layout).
+ *   stream   cudaStream_t the work is enqueued on (asynchronous).
+ * Scratch space: one file-scope device array of about 448 KB, which every GPU
+ * that loads the library holds until the process exits.  All calls share it
+ * and it keeps the last call's contents (each call clears what must start at
+ * zero), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller.  The
+ * first call on a device looks up the array's device address, so make that
+ * first call before any stream capture begins. */
+int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const double nkl[3], double g,
+                           gp_precision prec, const void* psi, const double* V, double* out, void* stream);
+
 /* Grid queries. */
 long gp_npoints(const gp_handle* h);
 int gp_precision_of(const gp_handle* h);

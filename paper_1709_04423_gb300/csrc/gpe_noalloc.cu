@@ -1,0 +1,165 @@
+// gpe_noalloc.cu -- gp_observables_noalloc: the observables reduction for
+// callers that cannot allocate device memory (declared in include/gpe.h).
+//
+// Some callers cannot call cudaMalloc when they need the observables of a
+// state: code that runs while a stream is being captured into a CUDA graph
+// (allocation calls are not allowed inside a capture), code embedded in a
+// host application that owns the whole device-memory budget and forbids
+// allocations after start-up, and code that must never synchronise the
+// device (cudaMalloc and cudaFree may synchronise).  For them this entry point
+// computes the same quantities as gp_observables without a handle and
+// without allocating: its scratch space (per-axis tables, per-block partial
+// sums, the raw sums and the completion counter) is the file-scope array
+// below, which every GPU that loads the library holds until the process ends.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gpe_internal.h"
+#include "gpe_obs.cuh"
+
+namespace {
+
+constexpr int kMaxAxis = 4096;          // points per axis at most
+constexpr int kBlocks = 152 * 16;       // reduction grid (at most)
+constexpr int kThreads = 256;
+// layout, in doubles: [3 axes][v, coord, weight][kMaxAxis] | partials | sums | counter
+constexpr long kAxisOff = 0;
+constexpr long kPartOff = kAxisOff + 3L * 3 * kMaxAxis;
+constexpr long kSumOff = kPartOff + 8L * kBlocks;
+constexpr long kCntOff = kSumOff + 8;
+constexpr long kScratchDoubles = kCntOff + 32;  // about 448 KB in all
+
+__device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mutex;
+
+// Fills the per-axis tables (nu_d^2 x^2/2, x, Simpson weight; absent axes get
+// a single point with 0, 0, 1) and clears the completion counter.
+__global__ void noalloc_setup_kernel(double* scratch, int dim, int nx, int ny, int nz, double hx, double hy,
+                                     double hz, double nu, double ka, double la) {
+  const int nn[3] = {nx, ny, nz};
+  const double hh[3] = {hx, hy, hz}, ff[3] = {nu, ka, la};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * kMaxAxis; t += gridDim.x * blockDim.x) {
+    const int d = t / kMaxAxis, i = t % kMaxAxis;
+    double* v = scratch + kAxisOff + (3L * d + 0) * kMaxAxis;
+    double* c = scratch + kAxisOff + (3L * d + 1) * kMaxAxis;
+    double* w = scratch + kAxisOff + (3L * d + 2) * kMaxAxis;
+    if (i >= nn[d]) continue;
+    if (d >= dim) {
+      v[i] = 0.0; c[i] = 0.0; w[i] = 1.0;
+      continue;
+    }
+    const int n = nn[d];
+    const double x = -0.5 * n * hh[d] + i * hh[d];
+    v[i] = 0.5 * ff[d] * ff[d] * x * x;
+    c[i] = x;
+    const int m = (n % 2 == 1) ? n : n - 1;  // composite Simpson on the first m points
+    double wc = 0.0;
+    if (i < m) wc = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
+    w[i] = wc * hh[d] / 3.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *(unsigned int*)(scratch + kCntOff) = 0u;
+}
+
+// Turns the seven Simpson sums into the gp_obs fields.
+__global__ void noalloc_finish_kernel(const double* S, double g, double* out) {
+  const double N = S[0];
+  out[0] = N;
+  out[1] = (S[1] + S[2]) / N + 0.5 * g * S[3] / (N * N);
+  out[2] = (S[1] + S[2]) / N + g * S[3] / (N * N);
+  double r2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    out[3 + d] = sqrt(S[4 + d] / N);
+    r2 += S[4 + d] / N;
+  }
+  out[6] = sqrt(r2);
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device.
+int scratch_address(double** out) {
+  int dev = 0;
+  GP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: device ordinal too large");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    GP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_scratch_addr[dev] = p;
+  }
+  *out = (double*)g_scratch_addr[dev];
+  return GP_OK;
+}
+
+template <typename T>
+void launch_obs(double* scratch, int dim, const int* n3, const double* dx3, const void* psi, const double* V,
+                cudaStream_t s) {
+  gpe::ObsArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.psi = (const gpe::c2_t<T>*)psi;
+  a.dim = dim;
+  a.nx = n3[0]; a.ny = n3[1]; a.nz = n3[2];
+  a.hx = dx3[0]; a.hy = dx3[1]; a.hz = dx3[2];
+  a.V = V;
+  a.vx = scratch + kAxisOff + 0L * kMaxAxis;
+  a.cx = scratch + kAxisOff + 1L * kMaxAxis;
+  a.wx = scratch + kAxisOff + 2L * kMaxAxis;
+  a.vy = scratch + kAxisOff + 3L * kMaxAxis;
+  a.cy = scratch + kAxisOff + 4L * kMaxAxis;
+  a.wy = scratch + kAxisOff + 5L * kMaxAxis;
+  a.vz = scratch + kAxisOff + 6L * kMaxAxis;
+  a.cz = scratch + kAxisOff + 7L * kMaxAxis;
+  a.wz = scratch + kAxisOff + 8L * kMaxAxis;
+  a.density = nullptr;
+  a.partials = scratch + kPartOff;
+  a.counter = (unsigned int*)(scratch + kCntOff);
+  a.out = scratch + kSumOff;
+  const long np = (long)n3[0] * n3[1] * n3[2];
+  const int blocks = (int)std::min<long>((np + kThreads - 1) / kThreads, kBlocks);
+  gpe::observables_kernel<T><<<blocks, kThreads, 0, s>>>(a);
+  gpe::count_launch();
+}
+
+}  // namespace
+
+extern "C" int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const double nkl[3], double g,
+                                      gp_precision prec, const void* psi, const double* V, double* out,
+                                      void* stream) {
+  if (!n || !dx || !nkl || !psi || !out) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: NULL argument");
+  if (dim < 1 || dim > 3) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: dim must be 1, 2 or 3");
+  if (prec != GP_F64 && prec != GP_F32) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: unknown precision");
+  int n3[3] = {1, 1, 1};
+  double dx3[3] = {1.0, 1.0, 1.0};
+  for (int d = 0; d < dim; ++d) {
+    if (n[d] < 3) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: every axis needs n >= 3 points");
+    if (n[d] > kMaxAxis)
+      return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: at most 4096 points per axis (static scratch size)");
+    if (!(dx[d] > 0.0) || !std::isfinite(dx[d]))
+      return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: dx must be finite and > 0");
+    if (!std::isfinite(nkl[d])) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: trap frequencies must be finite");
+    n3[d] = n[d];
+    dx3[d] = dx[d];
+  }
+  if ((long)n3[0] * n3[1] * n3[2] > 2147483647L)
+    return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: more than 2^31-1 grid points");
+  if (!std::isfinite(g)) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: g must be finite");
+  double* scratch = nullptr;
+  int rc = scratch_address(&scratch);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  noalloc_setup_kernel<<<36, 256, 0, s>>>(scratch, dim, n3[0], n3[1], n3[2], dx3[0], dx3[1], dx3[2],
+                                          nkl[0], dim > 1 ? nkl[1] : 0.0, dim > 2 ? nkl[2] : 0.0);
+  gpe::count_launch();
+  if (prec == GP_F64) launch_obs<double>(scratch, dim, n3, dx3, psi, V, s);
+  else launch_obs<float>(scratch, dim, n3, dx3, psi, V, s);
+  noalloc_finish_kernel<<<1, 1, 0, s>>>(scratch + kSumOff, g, out);
+  gpe::count_launch();
+  GP_CUDA(cudaGetLastError());
+  return GP_OK;
+}

@@ -31,7 +31,7 @@ GP_F32 = 1
 ABI_SYMBOLS = (
     "gp_init", "gp_set_state", "gp_get_state", "gp_set_potential", "gp_set_g", "gp_set_dt",
     "gp_step_imag", "gp_step_real", "gp_observables", "gp_npoints", "gp_precision_of",
-    "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps",
+    "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
 )
 
 
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.gp_step_real.argtypes = [_vp, L]
     lib.gp_observables.argtypes = [_vp, ctypes.POINTER(GpObs), _vp, I]
     lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
+    lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
+                                           _vp, _vp, _vp, _vp]
     lib.gp_npoints.argtypes = [_vp]
     lib.gp_npoints.restype = L
     lib.gp_precision_of.argtypes = [_vp]
@@ -146,6 +148,16 @@ def gp_time_sweeps(h, imag, nsteps):
     ms = (ctypes.c_double * 3)()
     _check(load().gp_time_sweeps(h, int(bool(imag)), int(nsteps), ms))
     return list(ms)
+
+
+def gp_observables_noalloc(dim, n, dx, nkl, g, prec, psi_ptr, V_ptr, out_ptr, stream=None):
+    """Observables of a device state into a device buffer of 7 doubles, with
+    no handle and no allocation (see include/gpe.h); asynchronous on stream."""
+    n3 = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n)))[:3])
+    dx3 = (ctypes.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx)))[:3])
+    nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
+    return _check(load().gp_observables_noalloc(int(dim), n3, dx3, nkl3, float(g), int(prec), psi_ptr, V_ptr,
+                                                out_ptr, stream))
 
 
 def gp_npoints(h):
