@@ -138,8 +138,8 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
     a.g = (T)h->g;
     a.scale_in = imag ? h->scale + par : nullptr;
     a.w_axis = (const T*)h->wt[d];
-    a.w_a = d == 0 ? h->wd[1] : h->wd[0];
-    a.w_b = d == 2 ? h->wd[1] : h->wd[2];
+    a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
+    a.w_b = (const T*)(d == 2 ? h->wt[1] : h->wt[2]);
     a.partials = h->partials;
     a.counter = h->counter;
     a.scale_out = h->scale + (1 - par);

@@ -37,9 +37,12 @@
 //    (FIRST), the segments are solved as above, and the tile is written back.
 //  * x line in 1d: one warp per line, lane = segment, carries by shuffles.
 // LAST (imaginary time) accumulates the Simpson-weighted norm of the output:
-// each thread sums its own points in the state precision, everything from
-// there on (line weights, warp, block and grid sums) is FP64; the last block
-// stores the next step's factor 1/sqrt(norm).
+// each thread and then each block sums in the state precision, the per-block
+// totals are summed over the grid in FP64 in a fixed order, and the last block
+// stores the next step's factor 1/sqrt(norm).  (FP64 per point would cost more
+// than the whole sweep on this part, whose FP64 rate is 1/70 of FP32; the
+// factor only rescales the state, and the observables recompute the norm in
+// FP64 from scratch.)
 #pragma once
 #include "gpe_common.cuh"
 
@@ -60,7 +63,7 @@ struct Sweep2Args {
   const double* scale_in;
   // norm (LAST)
   const T* w_axis;       // Simpson weights along the line, state precision
-  const double* w_a; const double* w_b;
+  const T* w_a; const T* w_b;  // weights of the two transverse indices, state precision
   double* partials;
   unsigned int* counter;
   double* scale_out;
@@ -200,12 +203,27 @@ __device__ __forceinline__ int line_base32(const LineGeom& g, int L) {
   return L;
 }
 
-template <bool LAST>
-__device__ __forceinline__ void finish_norm(double nacc, double* partials, unsigned int* counter,
-                                            double* scale_out, double* red_smem) {
+// Norm of the block's output: the per-thread values (in the state
+// precision) are summed over the block in the state precision -- a tree of at
+// most log2(blockDim) levels -- and the per-block totals over the grid in FP64
+// (fixed order, last block); the result sets the next renormalisation factor.
+template <typename T, bool LAST>
+__device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned int* counter, double* scale_out,
+                                            double* red_smem) {
   if (LAST) {
-    double v[1] = {nacc}, tot[1];
-    block_sum<1>(v, red_smem);
+    __shared__ T tred[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tval += __shfl_xor_sync(0xffffffffu, tval, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) tred[warp] = tval;
+    __syncthreads();
+    double v[1] = {0.0}, tot[1];
+    if (warp == 0) {
+      T b = lane < nw ? tred[lane] : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+      v[0] = (double)b;  // FP64 from here on
+    }
     if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0) *scale_out = 1.0 / sqrt(tot[0]);
   }
 }
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
   __syncthreads();  // coefficients
   c2 z[SEG];
   seg_solve<T, IMAG, SEG>(p, pl, pr, z, sc, n, cf, cb, s, nseg, lane);
-  double nacc = 0.0;
+  T nval = T(0);
   if (active) {
     const T* w = A.w_axis;
     T tacc = T(0);
@@ -257,9 +275,9 @@ __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
       line[0] = mk<T>(0, 0);
       line[(n - 1) * st] = mk<T>(0, 0);
     }
-    if (LAST) nacc = (double)tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);  // FP64 from here on
+    if (LAST) nval = tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
   }
-  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
 // ---------------------------------------------------------------- x sweep (2d/3d)
@@ -289,28 +307,30 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
   for (int c = s; c < 32; c += nseg) {
     const bool line_ok = c < nl;
     const int gbase = (L0 + c) * G.nx;
-    c2 v[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int k = q * 32 + lane;
-      v[q] = (q < per_line && line_ok && k >= 1 && k <= M) ? A.psi[gbase + k] : mk<T>(0, 0);
-    }
     T vline = T(0);
     if (FIRST && line_ok && !A.V) {
       const int L = L0 + c;
       vline = A.vy[L % G.ny] + A.vz[L / G.ny];
     }
+    for (int q0 = 0; q0 < per_line; q0 += 4) {
+      c2 v[4];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int k = q * 32 + lane;
-      if (q >= per_line || k >= n) continue;
-      c2 w = v[q];
-      if (FIRST && line_ok && k >= 1 && k <= M) {
-        w.x *= scl; w.y *= scl;
-        const T Vk = A.V ? A.V[gbase + k] : A.vx[k] + vline;
-        w = phase_N<T, IMAG>(w, Vk, A.dt, A.g);
+      for (int i = 0; i < 4; ++i) {
+        const int k = (q0 + i) * 32 + lane;
+        v[i] = (line_ok && k >= 1 && k <= M) ? A.psi[gbase + k] : mk<T>(0, 0);
       }
-      tile[k * kTilePitch + c] = w;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = (q0 + i) * 32 + lane;
+        if (k >= n) break;
+        c2 w = v[i];
+        if (FIRST && line_ok && k >= 1 && k <= M) {
+          w.x *= scl; w.y *= scl;
+          const T Vk = A.V ? A.V[gbase + k] : A.vx[k] + vline;
+          w = phase_N<T, IMAG>(w, Vk, A.dt, A.g);
+        }
+        tile[k * kTilePitch + c] = w;
+      }
     }
   }
   __syncthreads();
@@ -336,10 +356,10 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
       if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
     }
   }
-  double nacc = 0.0;
+  T nval = T(0);
   if (LAST && lane < nl) {
     const int L = L0 + lane;
-    nacc = (double)tacc * (A.w_a[L % G.ny] * A.w_b[L / G.ny]);  // FP64 from here on
+    nval = tacc * (A.w_a[L % G.ny] * A.w_b[L / G.ny]);
   }
   __syncthreads();
   // ---- store (tile end points are zero)
@@ -347,7 +367,7 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
     const int gbase = (L0 + c) * G.nx;
     for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
   }
-  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
 // ---------------------------------------------------------------- x sweep (1d)
@@ -361,7 +381,7 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
   const int lane = threadIdx.x & 31;
   const int L = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const bool active = L < G.nlines;  // warp-uniform
-  double nacc = 0.0;
+  T nval = T(0);
   if (active) {
     const int M = G.n - 2;
     const int base = L * G.nx;
@@ -439,9 +459,9 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
     }
     if (lane == 0) line[0] = mk<T>(0, 0);
     if (lane == 31) line[G.n - 1] = mk<T>(0, 0);
-    if (LAST) nacc = (double)tacc * (A.w_a[ta] * A.w_b[tb]);  // FP64 from here on
+    if (LAST) nval = tacc * (A.w_a[ta] * A.w_b[tb]);
   }
-  finish_norm<LAST>(nacc, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
 }  // namespace gpe
