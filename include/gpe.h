@@ -130,6 +130,37 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
  * Synchronises the stream. */
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch);
 
+/* ---- Batched form: many independent 2d real-time runs stepped together.
+ * Each run r has its own grid (n[2r] x n[2r+1] points, spacing dx[2r],
+ * dx[2r+1]), harmonic trap (nu = nkl[2r], kappa = nkl[2r+1]) and nonlinearity
+ * g[r]; all runs share dt.  One batch step advances every run by one
+ * split-step Crank-Nicolson step with the same discretisation as gp_step_real
+ * (a run in a batch gives the same result as the same run in its own handle).
+ * Runs are stored back to back: run r starts at element gp_batch_offset(r).
+ * Limits: 1 <= nruns <= 65536, 3 <= n <= 514 per axis, < 2^31 points in all. */
+typedef struct gp_batch gp_batch;
+
+int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, double dt, const double* nkl,
+                  const double* g, gp_precision prec, void* stream);
+
+/* Copies run `run`'s state in or out (run = -1: all runs, back to back), in
+ * the batch's precision; host copies synchronise the stream. */
+int gp_batch_set_state(gp_batch* b, int run, const void* psi, int on_device);
+int gp_batch_get_state(gp_batch* b, int run, void* psi, int on_device);
+
+/* Runs nsteps >= 0 real-time steps of every run.  Asynchronous. */
+int gp_batch_step_real(gp_batch* b, long nsteps);
+
+/* Observables of every run (out has nruns entries; rms[2] = 0).  FP64
+ * reductions.  Synchronises the stream; GP_ERR_NONFINITE on NaN/Inf. */
+int gp_batch_observables(gp_batch* b, gp_obs* out);
+
+/* Element offset of run `run` in the back-to-back state, or -1. */
+long gp_batch_offset(const gp_batch* b, int run);
+
+/* Frees the batch (NULL is a no-op). */
+int gp_batch_destroy(gp_batch* b);
+
 /* Observables without a handle and without allocating.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at the moment they need the observables -- code running

@@ -53,16 +53,10 @@ void drop_graphs(gp_handle* h) {
     }
 }
 
-namespace {
-
 // Crank-Nicolson system (1 + A) with A = r T along one axis: a = -r (off
 // diagonals), b = 1 + 2r, r = i beta (real time) or beta (imaginary time),
 // beta = dt/(4 dx^2).  Thomas factors m_k = 1/(b - a c'_{k-1}), c'_k = a m_k
 // for the interior k = 1..n-2, and alpha_k = r m_k (= -c'_k).
-struct AxisFactors {
-  std::vector<cd> m, cp, alpha;
-};
-
 AxisFactors thomas_factors(int n, double beta, bool imag) {
   AxisFactors f;
   f.m.assign(n, cd(0, 0));
@@ -102,6 +96,38 @@ void segment_products(const std::vector<cd>& alpha, int n, int seg, std::vector<
   }
 }
 
+// Carry tables of the segment scans for segment length sg: with A_q the
+// product of alpha over segment q, Pf[q][t] = prod_{q<r<=t} A_r (q <= t) and
+// Pb[q][t] = prod_{t<=r<q} A_r (q >= t); 16 x 16 each, Pf then Pb.
+void carry_tables(const std::vector<cd>& alpha, int n, int sg, cd* out /* 512 */) {
+  const int M = n - 2;
+  cd Aseg[16];
+  for (int q = 0; q < 16; ++q) {
+    cd acc(1, 0);
+    for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) acc *= alpha[k];
+    Aseg[q] = acc;
+  }
+  cd* Pf = out;
+  cd* Pb = out + 256;
+  for (int q = 0; q < 16; ++q)
+    for (int t = 0; t < 16; ++t) {
+      cd acc(1, 0);
+      Pf[q * 16 + t] = cd(0, 0);
+      Pb[q * 16 + t] = cd(0, 0);
+      if (q <= t) {
+        for (int r = q + 1; r <= t; ++r) acc *= Aseg[r];
+        Pf[q * 16 + t] = acc;
+      }
+      acc = cd(1, 0);
+      if (q >= t) {
+        for (int r = t; r < q; ++r) acc *= Aseg[r];
+        Pb[q * 16 + t] = acc;
+      }
+    }
+}
+
+namespace {
+
 template <typename T>
 int upload_c2(gp_handle* h, void* dst, const std::vector<cd>& v) {
   std::vector<T> tmp(2 * v.size());
@@ -138,35 +164,8 @@ int upload_coefs_t(gp_handle* h) {
         std::copy(gf.begin(), gf.end(), all.begin() + (size_t)(1 + 2 * s) * n);
         std::copy(gb.begin(), gb.end(), all.begin() + (size_t)(2 + 2 * s) * n);
       }
-      // carry tables for the segment scans: with A_q the product of alpha over
-      // segment q, Pf[q][t] = prod_{q<r<=t} A_r (q <= t) and
-      // Pb[q][t] = prod_{t<=r<q} A_r (q >= t), 16 x 16 per segment length
-      std::vector<cd> tabs((size_t)kNumSegs * 2 * 256, cd(0, 0));
-      const int M = n - 2;
-      for (int si = 0; si < kNumSegs; ++si) {
-        const int sg = kSegs[si];
-        cd Aseg[16];
-        for (int q = 0; q < 16; ++q) {
-          cd acc(1, 0);
-          for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) acc *= f.alpha[k];
-          Aseg[q] = acc;
-        }
-        cd* Pf = tabs.data() + (size_t)si * 512;
-        cd* Pb = Pf + 256;
-        for (int q = 0; q < 16; ++q)
-          for (int t = 0; t < 16; ++t) {
-            cd acc(1, 0);
-            if (q <= t) {
-              for (int r = q + 1; r <= t; ++r) acc *= Aseg[r];
-              Pf[q * 16 + t] = acc;
-            }
-            acc = cd(1, 0);
-            if (q >= t) {
-              for (int r = t; r < q; ++r) acc *= Aseg[r];
-              Pb[q * 16 + t] = acc;
-            }
-          }
-      }
+      std::vector<cd> tabs((size_t)kNumSegs * 512, cd(0, 0));
+      for (int si = 0; si < kNumSegs; ++si) carry_tables(f.alpha, n, kSegs[si], tabs.data() + (size_t)si * 512);
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
       if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;
@@ -183,6 +182,8 @@ int env_int(const char* name, int dflt) {
   return v ? std::atoi(v) : dflt;
 }
 
+}  // namespace
+
 // Kernel shapes.  y/z lines: 32 lines per block, one warp per segment, at
 // most 16 segments: seg = smallest of 4, 8, 16, 32 with ceil((n-2)/seg) <= 16.
 // x lines in 2d/3d: the shared-memory tile kernel with the same rule; the 1d
@@ -195,9 +196,13 @@ int tile_seg(int M) {
   return 0;
 }
 
+namespace {
+
 void choose_shapes(gp_handle* h) {
   const int M0 = h->n[0] - 2;
-  h->tile_x = env_int("GPE_TILE_X", h->dim > 1 ? 1 : 0) != 0;
+  // the x tile needs (36 n + 512) complex values of shared memory (<= 200 KB)
+  const bool tile_fits = (36L * h->n[0] + 512) * (long)h->esize <= 200L * 1024;
+  h->tile_x = env_int("GPE_TILE_X", h->dim > 1 && tile_fits ? 1 : 0) != 0 && tile_fits;
   int sx = 0;
   if (h->tile_x) {
     sx = tile_seg(M0);

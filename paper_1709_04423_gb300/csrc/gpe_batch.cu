@@ -1,0 +1,633 @@
+// gpe_batch.cu -- many independent 2d real-time runs of uneven size stepped
+// together (the batched form; declared in include/gpe.h).
+//
+// Every run is its own split-step Crank-Nicolson problem ("Solution method" of
+// the paper) with its own grid, trap and nonlinearity; they share dt.  One
+// time step of the whole batch is one launch of the x sweep (sub-step N fused
+// into the load) and one launch of the y sweep per segment-length class --
+// runs are grouped by the segment length their line length needs (n <= 66,
+// <= 130, <= 258, <= 514 points, plus FP64 x lines too long for the shared
+// tile) -- and each block takes one (run, tile) work item from a table, so
+// uneven runs share the launch without padding.  The
+// kernels are the single-grid bodies of gpe_sweep2.cuh driven by a per-run
+// descriptor table, so a run in a batch takes exactly the same arithmetic as
+// the same run alone.  Step blocks are captured once into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gpe_internal.h"
+#include "gpe_obs.cuh"
+#include "gpe_sweep2.cuh"
+
+using cd = std::complex<double>;
+
+namespace gpe {
+
+template <typename T>
+struct BatchRun {
+  c2_t<T>* psi;
+  int nx, ny;
+  const c2_t<T>* coef[2];  // per axis: alpha | gf | gb (3 n values) for the run's segment length
+  const c2_t<T>* ptab[2];  // per axis: carry tables (512 values)
+  const T* vx; const T* vy; const T* vz0;  // nu^2 x^2/2, kappa^2 y^2/2, a single 0
+  T g;
+};
+
+struct BatchItem {
+  int run, L0;
+};
+
+template <typename T, int SEG>
+__global__ void __launch_bounds__(512) batch_x_kernel(const BatchRun<T>* __restrict__ runs,
+                                                      const BatchItem* __restrict__ items, T dt) {
+  extern __shared__ __align__(16) unsigned char bsmem_raw[];
+  __shared__ c2_t<T> cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  const BatchItem it = items[blockIdx.x];
+  const BatchRun<T>& R = runs[it.run];
+  Sweep2Args<T> A;
+  memset(&A, 0, sizeof(A));
+  A.psi = R.psi;
+  A.geom.axis = 0;
+  A.geom.n = R.nx;
+  A.geom.stride = 1;
+  A.geom.nlines = R.ny;
+  A.geom.nx = R.nx;
+  A.geom.ny = R.ny;
+  A.geom.nz = 1;
+  A.alpha = R.coef[0];
+  A.gf = R.coef[0] + R.nx;
+  A.gb = R.coef[0] + 2 * R.nx;
+  A.ptab = R.ptab[0];
+  A.vx = R.vx;
+  A.vy = R.vy;
+  A.vz = R.vz0;
+  A.dt = dt;
+  A.g = R.g;
+  tsweep_body<T, false, true, false, SEG>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
+}
+
+// x lines whose shared-memory tile would not fit (FP64, n > 333): one warp
+// per line, 4 lines per block; the item's L0 is the block's first line.
+template <typename T, int SEG>
+__global__ void __launch_bounds__(128) batch_xw_kernel(const BatchRun<T>* __restrict__ runs,
+                                                       const BatchItem* __restrict__ items, T dt) {
+  __shared__ double red_smem[32];
+  const BatchItem it = items[blockIdx.x];
+  const BatchRun<T>& R = runs[it.run];
+  Sweep2Args<T> A;
+  memset(&A, 0, sizeof(A));
+  A.psi = R.psi;
+  A.geom.axis = 0;
+  A.geom.n = R.nx;
+  A.geom.stride = 1;
+  A.geom.nlines = R.ny;
+  A.geom.nx = R.nx;
+  A.geom.ny = R.ny;
+  A.geom.nz = 1;
+  A.alpha = R.coef[0];
+  A.gf = R.coef[0] + R.nx;
+  A.gb = R.coef[0] + 2 * R.nx;
+  A.vx = R.vx;
+  A.vy = R.vy;
+  A.vz = R.vz0;
+  A.dt = dt;
+  A.g = R.g;
+  xsweep_body<T, false, true, false, SEG>(A, it.L0 + (threadIdx.x >> 5), red_smem);
+}
+
+template <typename T, int SEG>
+__global__ void __launch_bounds__(512) batch_y_kernel(const BatchRun<T>* __restrict__ runs,
+                                                      const BatchItem* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char bsmem_raw[];
+  __shared__ c2_t<T> cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  const BatchItem it = items[blockIdx.x];
+  const BatchRun<T>& R = runs[it.run];
+  Sweep2Args<T> A;
+  memset(&A, 0, sizeof(A));
+  A.psi = R.psi;
+  A.geom.axis = 1;
+  A.geom.n = R.ny;
+  A.geom.stride = R.nx;
+  A.geom.nlines = R.nx;
+  A.geom.nx = R.nx;
+  A.geom.ny = R.ny;
+  A.geom.nz = 1;
+  A.alpha = R.coef[1];
+  A.gf = R.coef[1] + R.ny;
+  A.gb = R.coef[1] + 2 * R.ny;
+  A.ptab = R.ptab[1];
+  colsweep_body<T, false, false, SEG>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
+}
+
+// Segment-length classes: a line of n points goes to the first class whose
+// segment length gives at most 16 segments (the rule the single-grid handle
+// uses), so a run in a batch takes the same arithmetic as alone.  x lines
+// whose tile does not fit in shared memory form a fifth class, run one warp
+// per line (segment length = the smallest power of two >= (n-2)/32).
+constexpr int kNumClasses = 5;
+constexpr int kClassSegs[4] = {4, 8, 16, 32};
+constexpr int kBatchGraphSteps = 16;
+
+}  // namespace gpe
+
+struct gp_batch {
+  int nruns = 0, prec = GP_F64;
+  size_t esize = 0;
+  double dt = 0;
+  std::vector<int> n;        // [nruns][2]
+  std::vector<double> dx;    // [nruns][2]
+  std::vector<double> nk;    // [nruns][2]
+  std::vector<double> g;     // [nruns]
+  std::vector<long> off;     // element offset of each run's state
+  long total = 0;
+  cudaStream_t user = nullptr, work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void* psi = nullptr;
+  void* runs_d = nullptr;
+  void* items_d[2][5] = {{nullptr}};  // [axis][class]
+  int nitems[2][5] = {{0}};
+  int class_n[2][5] = {{0}};          // longest line of the class
+  int warp_seg = 16;                  // segment length of the warp-per-line class
+  std::string launch_err;             // first failed launch of the current call
+  // FP64 observables: per-run tables
+  std::vector<double*> vd, cdx, wd;   // [nruns][2] device arrays
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  double* obs_out = nullptr;
+  double* obs_host = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace gpe {
+namespace {
+
+int b_alloc(gp_batch* b, void** p, size_t bytes) {
+  const size_t sz = bytes < 16 ? 16 : bytes;
+  GP_CUDA(cudaMalloc(p, sz));
+  b->allocs.push_back(*p);
+  GP_CUDA(cudaMemsetAsync(*p, 0, sz, b->work));
+  return GP_OK;
+}
+
+template <typename T>
+int b_upload(gp_batch* b, void* dst, const std::vector<T>& v) {
+  GP_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->work));
+  GP_CUDA(cudaStreamSynchronize(b->work));
+  return GP_OK;
+}
+
+bool x_tile_fits(int n, size_t esize) { return (36L * n + 512) * (long)esize <= 200L * 1024; }
+
+// class of a line of n points along axis a; class 4 = warp-per-line x lines
+int class_of(int n, int a, size_t esize) {
+  if (a == 0 && !x_tile_fits(n, esize)) return 4;
+  const int M = n - 2;
+  for (int c = 0; c < 4; ++c)
+    if ((M + kClassSegs[c] - 1) / kClassSegs[c] <= 16) return c;
+  return -1;
+}
+
+int warp_seg_of(int n) {
+  for (int s : {1, 2, 4, 8, 16})
+    if (32 * s >= n - 2) return s;
+  return 16;
+}
+
+template <typename T>
+int build_tables(gp_batch* b) {
+  const int R = b->nruns;
+  // one segment length for every warp-per-line x line: enough for the longest
+  int nwarp = 0;
+  for (int r = 0; r < R; ++r)
+    if (class_of(b->n[2 * r], 0, b->esize) == 4) nwarp = std::max(nwarp, b->n[2 * r]);
+  b->warp_seg = nwarp ? warp_seg_of(nwarp) : 16;
+  // coefficients: per run per axis 3n (alpha | gf | gb) + 512 carry tables
+  std::vector<size_t> coff(2 * R), poff(2 * R);
+  size_t ctot = 0;
+  for (int r = 0; r < R; ++r)
+    for (int a = 0; a < 2; ++a) {
+      coff[2 * r + a] = ctot;
+      ctot += 3 * (size_t)b->n[2 * r + a];
+      poff[2 * r + a] = ctot;
+      ctot += 512;
+    }
+  std::vector<T> cbuf(2 * ctot, T(0));
+  size_t vtot = 0;
+  std::vector<size_t> voff(2 * R);
+  for (int r = 0; r < R; ++r)
+    for (int a = 0; a < 2; ++a) {
+      voff[2 * r + a] = vtot;
+      vtot += b->n[2 * r + a];
+    }
+  std::vector<T> vbuf(vtot + 1, T(0));  // last entry: the shared 0 for the absent z axis
+  for (int r = 0; r < R; ++r)
+    for (int a = 0; a < 2; ++a) {
+      const int n = b->n[2 * r + a];
+      const double h = b->dx[2 * r + a];
+      const AxisFactors f = thomas_factors(n, b->dt / (4.0 * h * h), false);
+      const int cls = class_of(n, a, b->esize);
+      const int seg = cls == 4 ? b->warp_seg : kClassSegs[cls];
+      std::vector<cd> gf, gb;
+      segment_products(f.alpha, n, seg, gf, gb);
+      cd tabs[512];
+      carry_tables(f.alpha, n, seg, tabs);
+      T* c = cbuf.data() + 2 * coff[2 * r + a];
+      for (int k = 0; k < n; ++k) {
+        c[2 * k] = (T)f.alpha[k].real(); c[2 * k + 1] = (T)f.alpha[k].imag();
+        c[2 * (n + k)] = (T)gf[k].real(); c[2 * (n + k) + 1] = (T)gf[k].imag();
+        c[2 * (2 * n + k)] = (T)gb[k].real(); c[2 * (2 * n + k) + 1] = (T)gb[k].imag();
+      }
+      T* pt = cbuf.data() + 2 * poff[2 * r + a];
+      for (int q = 0; q < 512; ++q) { pt[2 * q] = (T)tabs[q].real(); pt[2 * q + 1] = (T)tabs[q].imag(); }
+      const double w = b->nk[2 * r + a];
+      for (int i = 0; i < n; ++i) {
+        const double x = -0.5 * n * h + i * h;
+        vbuf[voff[2 * r + a] + i] = (T)(0.5 * w * w * x * x);
+      }
+    }
+  void *cdev = nullptr, *vdev = nullptr;
+  int rc;
+  if ((rc = b_alloc(b, &cdev, cbuf.size() * sizeof(T)))) return rc;
+  if ((rc = b_upload<T>(b, cdev, cbuf))) return rc;
+  if ((rc = b_alloc(b, &vdev, vbuf.size() * sizeof(T)))) return rc;
+  if ((rc = b_upload<T>(b, vdev, vbuf))) return rc;
+  std::vector<BatchRun<T>> runs(R);
+  for (int r = 0; r < R; ++r) {
+    BatchRun<T>& q = runs[r];
+    q.psi = (c2_t<T>*)b->psi + b->off[r];
+    q.nx = b->n[2 * r];
+    q.ny = b->n[2 * r + 1];
+    for (int a = 0; a < 2; ++a) {
+      q.coef[a] = (const c2_t<T>*)cdev + coff[2 * r + a];
+      q.ptab[a] = (const c2_t<T>*)cdev + poff[2 * r + a];
+    }
+    q.vx = (const T*)vdev + voff[2 * r];
+    q.vy = (const T*)vdev + voff[2 * r + 1];
+    q.vz0 = (const T*)vdev + vtot;
+    q.g = (T)b->g[r];
+  }
+  if ((rc = b_alloc(b, &b->runs_d, R * sizeof(BatchRun<T>)))) return rc;
+  GP_CUDA(cudaMemcpyAsync(b->runs_d, runs.data(), R * sizeof(BatchRun<T>), cudaMemcpyHostToDevice, b->work));
+  GP_CUDA(cudaStreamSynchronize(b->work));
+  // work items per axis and class: (run, first line of a 32-line tile)
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < kNumClasses; ++c) {
+      std::vector<BatchItem> items;
+      int nmax = 0;
+      const int step = c == 4 ? 4 : 32;         // lines per block
+      for (int r = 0; r < R; ++r) {
+        const int n = b->n[2 * r + a];          // line length along axis a
+        const int nl = b->n[2 * r + (1 - a)];   // number of lines
+        if (class_of(n, a, b->esize) != c) continue;
+        nmax = std::max(nmax, n);
+        for (int L0 = 0; L0 < nl; L0 += step) items.push_back({r, L0});
+      }
+      b->nitems[a][c] = (int)items.size();
+      b->class_n[a][c] = nmax;
+      if (items.empty()) continue;
+      if ((rc = b_alloc(b, &b->items_d[a][c], items.size() * sizeof(BatchItem)))) return rc;
+      GP_CUDA(cudaMemcpyAsync(b->items_d[a][c], items.data(), items.size() * sizeof(BatchItem),
+                              cudaMemcpyHostToDevice, b->work));
+      GP_CUDA(cudaStreamSynchronize(b->work));
+    }
+  return GP_OK;
+}
+
+template <typename T, int SEG>
+void launch_batch_warp(gp_batch* b) {
+  const auto* runs = (const BatchRun<T>*)b->runs_d;
+  const auto* items = (const BatchItem*)b->items_d[0][4];
+  batch_xw_kernel<T, SEG><<<b->nitems[0][4], 128, 0, b->work>>>(runs, items, (T)b->dt);
+  count_launch();
+}
+
+template <typename T, int SEG>
+void launch_batch_class(gp_batch* b, int a, int c) {
+  const int n = b->class_n[a][c];
+  const int threads = 32 * ((n - 2 + SEG - 1) / SEG);
+  const auto* runs = (const BatchRun<T>*)b->runs_d;
+  const auto* items = (const BatchItem*)b->items_d[a][c];
+  if (a == 0) {
+    const size_t smem = (size_t)(36 * n + 512) * sizeof(c2_t<T>);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(batch_x_kernel<T, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    batch_x_kernel<T, SEG><<<b->nitems[a][c], threads, smem, b->work>>>(runs, items, (T)b->dt);
+  } else {
+    const size_t smem = (size_t)(3 * n + 512) * sizeof(c2_t<T>);
+    static bool attr = false;  // static + dynamic shared memory can pass 48 KB
+    if (!attr) {
+      cudaFuncSetAttribute(batch_y_kernel<T, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      attr = true;
+    }
+    batch_y_kernel<T, SEG><<<b->nitems[a][c], threads, smem, b->work>>>(runs, items);
+  }
+  count_launch();
+}
+
+void note_launch(gp_batch* b, int a, int c) {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess && b->launch_err.empty())
+    b->launch_err = std::string("batch sweep axis ") + std::to_string(a) + " class " + std::to_string(c) +
+                    " (longest line " + std::to_string(b->class_n[a][c]) + ", " + std::to_string(b->nitems[a][c]) +
+                    " blocks): " + cudaGetErrorString(e);
+}
+
+template <typename T>
+void enqueue_batch_step(gp_batch* b) {
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < kNumClasses; ++c) {
+      if (!b->nitems[a][c]) continue;
+      struct Note {
+        gp_batch* b; int a, c;
+        ~Note() { note_launch(b, a, c); }
+      } note{b, a, c};
+      switch (c) {
+        case 0: launch_batch_class<T, 4>(b, a, c); break;
+        case 1: launch_batch_class<T, 8>(b, a, c); break;
+        case 2: launch_batch_class<T, 16>(b, a, c); break;
+        case 3: launch_batch_class<T, 32>(b, a, c); break;
+        default:
+          switch (b->warp_seg) {
+            case 1: launch_batch_warp<T, 1>(b); break;
+            case 2: launch_batch_warp<T, 2>(b); break;
+            case 4: launch_batch_warp<T, 4>(b); break;
+            case 8: launch_batch_warp<T, 8>(b); break;
+            default: launch_batch_warp<T, 16>(b); break;
+          }
+      }
+    }
+}
+
+int launches_per_step(const gp_batch* b) {
+  int k = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < kNumClasses; ++c) k += b->nitems[a][c] > 0;
+  return k;
+}
+
+int b_join_in(gp_batch* b) {
+  GP_CUDA(cudaEventRecord(b->ev_in, b->user));
+  GP_CUDA(cudaStreamWaitEvent(b->work, b->ev_in, 0));
+  return GP_OK;
+}
+
+int b_join_out(gp_batch* b) {
+  GP_CUDA(cudaEventRecord(b->ev_out, b->work));
+  GP_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return GP_OK;
+}
+
+template <typename T>
+int batch_steps(gp_batch* b, long nsteps) {
+  if (nsteps == 0) return GP_OK;
+  int rc = b_join_in(b);
+  if (rc) return rc;
+  b->launch_err.clear();
+  long t = 0;
+  if (nsteps >= 2 * kBatchGraphSteps) {
+    if (!b->graph) {
+      cudaGraph_t graph;
+      GP_CUDA(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
+      const unsigned long long before = g_launches.load();
+      for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step<T>(b);
+      g_launches.store(before);
+      const cudaError_t ce = cudaStreamEndCapture(b->work, &graph);
+      if (ce != cudaSuccess)
+        return fail(GP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce) +
+                                     (b->launch_err.empty() ? "" : "; " + b->launch_err));
+      cudaError_t e = cudaGraphInstantiate(&b->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(GP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    for (; nsteps - t >= kBatchGraphSteps; t += kBatchGraphSteps) {
+      GP_CUDA(cudaGraphLaunch(b->graph, b->work));
+      count_launch((unsigned long long)kBatchGraphSteps * launches_per_step(b));
+    }
+  }
+  for (; t < nsteps; ++t) enqueue_batch_step<T>(b);
+  if (!b->launch_err.empty()) return fail(GP_ERR_CUDA, b->launch_err);
+  GP_CUDA(cudaGetLastError());
+  return b_join_out(b);
+}
+
+template <typename T>
+int batch_observables(gp_batch* b) {
+  for (int r = 0; r < b->nruns; ++r) {
+    ObsArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = (const c2_t<T>*)b->psi + b->off[r];
+    a.dim = 2;
+    a.nx = b->n[2 * r];
+    a.ny = b->n[2 * r + 1];
+    a.nz = 1;
+    a.hx = b->dx[2 * r];
+    a.hy = b->dx[2 * r + 1];
+    a.hz = 1.0;
+    a.vx = b->vd[2 * r]; a.vy = b->vd[2 * r + 1];
+    a.cx = b->cdx[2 * r]; a.cy = b->cdx[2 * r + 1];
+    a.wx = b->wd[2 * r]; a.wy = b->wd[2 * r + 1];
+    // absent z axis: single point with v = c = 0, w = 1 (the last three slots of obs_out's tail)
+    a.vz = b->obs_out + 8L * b->nruns;
+    a.cz = b->obs_out + 8L * b->nruns;
+    a.wz = b->obs_out + 8L * b->nruns + 1;
+    a.partials = b->partials;
+    a.counter = b->counter;
+    a.out = b->obs_out + 8L * r;
+    const long np = (long)a.nx * a.ny;
+    const int blocks = (int)std::min<long>((np + 255) / 256, 152L * 16);
+    observables_kernel<T><<<blocks, 256, 0, b->work>>>(a);
+    count_launch();
+  }
+  GP_CUDA(cudaGetLastError());
+  return GP_OK;
+}
+
+}  // namespace
+}  // namespace gpe
+
+using namespace gpe;
+
+extern "C" {
+
+int gp_batch_destroy(gp_batch* b) {
+  if (!b) return GP_OK;
+  if (b->work) cudaStreamSynchronize(b->work);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->obs_host) cudaFreeHost(b->obs_host);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->work) cudaStreamDestroy(b->work);
+  delete b;
+  return GP_OK;
+}
+
+int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, double dt, const double* nkl,
+                  const double* g, gp_precision prec, void* stream) {
+  g_err.clear();
+  if (!out || !n || !dx || !nkl || !g) return fail(GP_ERR_INVALID, "gp_batch_init: NULL argument");
+  *out = nullptr;
+  if (nruns < 1 || nruns > 65536) return fail(GP_ERR_INVALID, "gp_batch_init: nruns must be in [1, 65536]");
+  if (prec != GP_F64 && prec != GP_F32) return fail(GP_ERR_INVALID, "gp_batch_init: unknown precision");
+  if (!std::isfinite(dt) || dt == 0.0) return fail(GP_ERR_INVALID, "gp_batch_init: dt must be finite and nonzero");
+  long total = 0;
+  for (int r = 0; r < nruns; ++r) {
+    for (int a = 0; a < 2; ++a) {
+      const int na = n[2 * r + a];
+      if (na < 3 || na > 514) return fail(GP_ERR_INVALID, "gp_batch_init: every axis needs 3 <= n <= 514 points");
+      if (!(dx[2 * r + a] > 0.0) || !std::isfinite(dx[2 * r + a]))
+        return fail(GP_ERR_INVALID, "gp_batch_init: dx must be finite and > 0");
+      if (!std::isfinite(nkl[2 * r + a])) return fail(GP_ERR_INVALID, "gp_batch_init: trap frequencies must be finite");
+    }
+    if (!std::isfinite(g[r])) return fail(GP_ERR_INVALID, "gp_batch_init: g must be finite");
+    total += (long)n[2 * r] * n[2 * r + 1];
+    if (total > 2147483647L) return fail(GP_ERR_INVALID, "gp_batch_init: more than 2^31-1 points in all");
+  }
+  gp_batch* b = new gp_batch();
+  b->nruns = nruns;
+  b->prec = prec;
+  b->esize = prec == GP_F64 ? sizeof(double2) : sizeof(float2);
+  b->dt = dt;
+  b->n.assign(n, n + 2 * nruns);
+  b->dx.assign(dx, dx + 2 * nruns);
+  b->nk.assign(nkl, nkl + 2 * nruns);
+  b->g.assign(g, g + nruns);
+  b->off.resize(nruns);
+  long acc = 0;
+  for (int r = 0; r < nruns; ++r) {
+    b->off[r] = acc;
+    acc += (long)n[2 * r] * n[2 * r + 1];
+  }
+  b->total = acc;
+  b->user = (cudaStream_t)stream;
+  auto bail = [&](int code) { gp_batch_destroy(b); return code; };
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->obs_host, 8 * sizeof(double) * nruns);
+    if (e != cudaSuccess) return bail(fail(GP_ERR_CUDA, std::string("gp_batch_init: ") + cudaGetErrorString(e)));
+  }
+  int rc;
+  if ((rc = b_alloc(b, &b->psi, (size_t)acc * b->esize))) return bail(rc);
+  rc = prec == GP_F64 ? build_tables<double>(b) : build_tables<float>(b);
+  if (rc) return bail(rc);
+  // FP64 tables of the observables, per run and axis
+  b->vd.resize(2 * nruns);
+  b->cdx.resize(2 * nruns);
+  b->wd.resize(2 * nruns);
+  for (int r = 0; r < nruns; ++r)
+    for (int a = 0; a < 2; ++a) {
+      const int na = n[2 * r + a];
+      const double h = dx[2 * r + a], w = nkl[2 * r + a];
+      std::vector<double> x(na), v(na), wt(na);
+      const int m = (na % 2 == 1) ? na : na - 1;
+      for (int i = 0; i < na; ++i) {
+        x[i] = -0.5 * na * h + i * h;
+        v[i] = 0.5 * w * w * x[i] * x[i];
+        double c = 0.0;
+        if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
+        wt[i] = c * h / 3.0;
+      }
+      void *pv, *pc, *pw;
+      if ((rc = b_alloc(b, &pv, na * sizeof(double))) || (rc = b_upload<double>(b, pv, v))) return bail(rc);
+      if ((rc = b_alloc(b, &pc, na * sizeof(double))) || (rc = b_upload<double>(b, pc, x))) return bail(rc);
+      if ((rc = b_alloc(b, &pw, na * sizeof(double))) || (rc = b_upload<double>(b, pw, wt))) return bail(rc);
+      b->vd[2 * r + a] = (double*)pv;
+      b->cdx[2 * r + a] = (double*)pc;
+      b->wd[2 * r + a] = (double*)pw;
+    }
+  if ((rc = b_alloc(b, (void**)&b->partials, 152L * 16 * 8 * sizeof(double)))) return bail(rc);
+  if ((rc = b_alloc(b, (void**)&b->counter, 64))) return bail(rc);
+  if ((rc = b_alloc(b, (void**)&b->obs_out, (8L * nruns + 8) * sizeof(double)))) return bail(rc);
+  {
+    // the absent z axis of the observables: v = c = 0 (slot 0), w = 1 (slot 1)
+    const double zw[2] = {0.0, 1.0};
+    cudaError_t e = cudaMemcpyAsync(b->obs_out + 8L * nruns, zw, sizeof(zw), cudaMemcpyHostToDevice, b->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->work);
+    if (e != cudaSuccess) return bail(fail(GP_ERR_CUDA, std::string("gp_batch_init: ") + cudaGetErrorString(e)));
+  }
+  *out = b;
+  return GP_OK;
+}
+
+long gp_batch_offset(const gp_batch* b, int run) {
+  if (!b || run < 0 || run >= b->nruns) return -1;
+  return b->off[run];
+}
+
+int gp_batch_set_state(gp_batch* b, int run, const void* psi, int on_device) {
+  if (!b || !psi) return fail(GP_ERR_INVALID, "gp_batch_set_state: NULL argument");
+  if (run < -1 || run >= b->nruns) return fail(GP_ERR_INVALID, "gp_batch_set_state: run out of range");
+  int rc = b_join_in(b);
+  if (rc) return rc;
+  const long off = run < 0 ? 0 : b->off[run];
+  const long cnt = run < 0 ? b->total : (long)b->n[2 * run] * b->n[2 * run + 1];
+  GP_CUDA(cudaMemcpyAsync((char*)b->psi + off * b->esize, psi, (size_t)cnt * b->esize,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->work));
+  if (!on_device) GP_CUDA(cudaStreamSynchronize(b->work));
+  return b_join_out(b);
+}
+
+int gp_batch_get_state(gp_batch* b, int run, void* psi, int on_device) {
+  if (!b || !psi) return fail(GP_ERR_INVALID, "gp_batch_get_state: NULL argument");
+  if (run < -1 || run >= b->nruns) return fail(GP_ERR_INVALID, "gp_batch_get_state: run out of range");
+  int rc = b_join_in(b);
+  if (rc) return rc;
+  const long off = run < 0 ? 0 : b->off[run];
+  const long cnt = run < 0 ? b->total : (long)b->n[2 * run] * b->n[2 * run + 1];
+  GP_CUDA(cudaMemcpyAsync(psi, (const char*)b->psi + off * b->esize, (size_t)cnt * b->esize,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->work));
+  if (!on_device) GP_CUDA(cudaStreamSynchronize(b->work));
+  return b_join_out(b);
+}
+
+int gp_batch_step_real(gp_batch* b, long nsteps) {
+  if (!b) return fail(GP_ERR_INVALID, "gp_batch_step_real: NULL handle");
+  if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_batch_step_real: nsteps < 0");
+  return b->prec == GP_F64 ? batch_steps<double>(b, nsteps) : batch_steps<float>(b, nsteps);
+}
+
+int gp_batch_observables(gp_batch* b, gp_obs* out) {
+  if (!b || !out) return fail(GP_ERR_INVALID, "gp_batch_observables: NULL argument");
+  int rc = b_join_in(b);
+  if (rc) return rc;
+  rc = b->prec == GP_F64 ? batch_observables<double>(b) : batch_observables<float>(b);
+  if (rc) return rc;
+  GP_CUDA(cudaMemcpyAsync(b->obs_host, b->obs_out, 8 * sizeof(double) * b->nruns, cudaMemcpyDeviceToHost, b->work));
+  GP_CUDA(cudaStreamSynchronize(b->work));
+  if ((rc = b_join_out(b))) return rc;
+  bool finite = true;
+  for (int r = 0; r < b->nruns; ++r) {
+    const double* S = b->obs_host + 8L * r;
+    const double N = S[0];
+    gp_obs& o = out[r];
+    o.norm = N;
+    o.energy = (S[1] + S[2]) / N + 0.5 * b->g[r] * S[3] / (N * N);
+    o.mu = (S[1] + S[2]) / N + b->g[r] * S[3] / (N * N);
+    o.rms[0] = std::sqrt(S[4] / N);
+    o.rms[1] = std::sqrt(S[5] / N);
+    o.rms[2] = 0.0;
+    o.rms_r = std::sqrt((S[4] + S[5]) / N);
+    for (int q = 0; q < 7; ++q) finite = finite && std::isfinite(S[q]);
+  }
+  if (!finite) return fail(GP_ERR_NONFINITE, "gp_batch_observables: a state holds NaN or Inf");
+  return GP_OK;
+}
+
+}  // extern "C"

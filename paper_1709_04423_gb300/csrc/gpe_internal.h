@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <complex>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,18 @@ struct gp_handle {
 };
 
 namespace gpe {
+
+// Thomas factors of one axis (m_k, c'_k, alpha_k = r m_k for k = 1..n-2) of
+// the Crank-Nicolson system with beta = dt/(4 dx^2) (signed), imaginary or
+// real time; segment products and carry tables for a segment length.
+struct AxisFactors {
+  std::vector<std::complex<double>> m, cp, alpha;
+};
+AxisFactors thomas_factors(int n, double beta, bool imag);
+void segment_products(const std::vector<std::complex<double>>& alpha, int n, int seg,
+                      std::vector<std::complex<double>>& gf, std::vector<std::complex<double>>& gb);
+void carry_tables(const std::vector<std::complex<double>>& alpha, int n, int sg, std::complex<double>* out);
+int tile_seg(int M);
 
 int dev_alloc(gp_handle* h, void** p, size_t bytes);
 int join_in(gp_handle* h);

@@ -66,6 +66,12 @@ void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
   const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
+  static bool attr_set = false;  // static + dynamic shared memory can pass 48 KB
+  if (!attr_set) {
+    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         64 * 1024);
+    attr_set = true;
+  }
   colsweep_kernel<T, IMAG, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
 }

@@ -155,14 +155,33 @@ __device__ __forceinline__ void load_coefs(const Sweep2Args<T>& A, c2_t<T>* sc, 
   for (int q = threadIdx.x; q < 512; q += blockDim.x) sc[3 * n + q] = A.ptab[q];
 }
 
-// Solves the segment of thread (lane, warp s) of a block whose lines run one
-// per lane and whose segments run one per warp.  On entry p holds the
-// segment (zero beyond M) and pl/pr its outer neighbours; on exit z holds the
-// increment z_k.  Two block barriers; every thread of the block must call it.
+// Forward pass over a segment whose points are fetched one at a time by
+// getp(k) (0 outside 1..M), so the input segment need not sit in registers.
+template <typename T, bool IMAG, int SEG, typename GetP>
+__device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], const c2_t<T>* alpha, int k0, int M) {
+  using c2 = c2_t<T>;
+  c2 pm = getp(k0 - 1), pc = getp(k0), prev = mk<T>(0, 0);
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int k = k0 + j;
+    const c2 pn = getp(k + 1);
+    const c2 t = mk<T>(prev.x - T(2) * (pm.x + pn.x) + T(4) * pc.x, prev.y - T(2) * (pm.y + pn.y) + T(4) * pc.y);
+    c2 v = mk<T>(0, 0);
+    if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
+    e[j] = v;
+    prev = v;
+    pm = pc;
+    pc = pn;
+  }
+}
+
+// Completes the segment of thread (lane, warp s) of a block whose lines run
+// one per lane and whose segments run one per warp: on entry z holds the
+// segment-local forward values e^ (zero carry-in); on exit the increment z_k.
+// Two block barriers; every thread of the block must call it.
 template <typename T, bool IMAG, int SEG>
-__device__ __forceinline__ void seg_solve(const c2_t<T> (&p)[SEG], c2_t<T> pl, c2_t<T> pr, c2_t<T> (&z)[SEG],
-                                          const c2_t<T>* sc, int n, c2_t<T> (*cf)[33], c2_t<T> (*cb)[33],
-                                          int s, int nseg, int lane) {
+__device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc, int n, c2_t<T> (*cf)[33],
+                                            c2_t<T> (*cb)[33], int s, int nseg, int lane) {
   using c2 = c2_t<T>;
   const int M = n - 2, k0 = 1 + s * SEG;
   const c2* al = sc;
@@ -170,7 +189,6 @@ __device__ __forceinline__ void seg_solve(const c2_t<T> (&p)[SEG], c2_t<T> pl, c
   const c2* gb = sc + 2 * n;
   const c2* Pf = sc + 3 * n;
   const c2* Pb = Pf + 256;
-  local_forward<T, IMAG, SEG>(p, z, pl, pr, al, k0, M);
   {
     c2 Bend = z[SEG - 1];
 #pragma unroll
@@ -229,35 +247,48 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
 }
 
 // ---------------------------------------------------------------- y/z sweep
-// blockDim.x = 32 * nseg, nseg = ceil((n-2)/SEG) <= 16; dynamic shared memory
-// holds the coefficients (3n + 512 complex values).
+// blockDim.x >= 32 * nseg, nseg = ceil((n-2)/SEG) <= 16, blockDim.x <= 512;
+// dynamic shared memory holds the coefficients (3n + 512 complex values).
+// Body shared with the batched kernels: lines L0 .. L0+31 of the grid
+// described by A; nseg = ceil((n-2)/SEG) warps take part, the other warps of
+// the block (if any) only join the barriers.
 template <typename T, bool IMAG, bool LAST, int SEG>
-__global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
+__device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
+                                              c2_t<T> (*cb)[33], double* red_smem) {
   using c2 = c2_t<T>;
-  extern __shared__ __align__(16) unsigned char csmem_raw[];
-  c2* sc = reinterpret_cast<c2*>(csmem_raw);
-  __shared__ c2 cf[16][33], cb[16][33];
-  __shared__ double red_smem[32];
   const LineGeom& G = A.geom;
   const int n = G.n, M = n - 2;
-  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nseg = blockDim.x >> 5;
-  const int L = blockIdx.x * 32 + lane;
-  const bool active = L < G.nlines;
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+  const int nseg = (M + SEG - 1) / SEG;
+  const bool seg_ok = s < nseg;
+  const int L = L0 + lane;
+  const bool active = L < G.nlines && seg_ok;
   const int st = (int)G.stride;
   const int k0 = 1 + s * SEG;
   load_coefs<T>(A, sc, n);
   c2* line = A.psi + (active ? line_base32(G, L) : 0);
-  c2 p[SEG];
+  // keep the input segment in registers when it is small; otherwise stream it
+  // in the forward pass and read it again (from L2) for u = p - z
+  constexpr bool KEEP = SEG * sizeof(T) <= 64;
+  c2 p[KEEP ? SEG : 1];
+  if constexpr (KEEP) {
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    p[j] = (active && k <= M) ? line[k * st] : mk<T>(0, 0);
+    for (int j = 0; j < SEG; ++j) {
+      const int k = k0 + j;
+      p[j] = (active && k <= M) ? line[k * st] : mk<T>(0, 0);
+    }
   }
-  const c2 pl = (active && k0 - 1 >= 1) ? line[(k0 - 1) * st] : mk<T>(0, 0);
-  const c2 pr = (active && k0 + SEG <= M) ? line[(k0 + SEG) * st] : mk<T>(0, 0);
   __syncthreads();  // coefficients
   c2 z[SEG];
-  seg_solve<T, IMAG, SEG>(p, pl, pr, z, sc, n, cf, cb, s, nseg, lane);
+  if constexpr (KEEP) {
+    const c2 pl = (active && k0 - 1 >= 1) ? line[(k0 - 1) * st] : mk<T>(0, 0);
+    const c2 pr = (active && k0 + SEG <= M) ? line[(k0 + SEG) * st] : mk<T>(0, 0);
+    local_forward<T, IMAG, SEG>(p, z, pl, pr, sc, k0, M);
+  } else {
+    stream_forward<T, IMAG, SEG>(
+        [&](int k) { return (active && k >= 1 && k <= M) ? line[k * st] : mk<T>(0, 0); }, z, sc, k0, M);
+  }
+  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
   T nval = T(0);
   if (active) {
     const T* w = A.w_axis;
@@ -266,7 +297,10 @@ __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
       if (k <= M) {
-        const c2 u = mk<T>(p[j].x - z[j].x, p[j].y - z[j].y);
+        c2 pk;
+        if constexpr (KEEP) pk = p[j];
+        else pk = __ldcg(&line[k * st]);
+        const c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
         line[k * st] = u;
         if (LAST) tacc += w[k] * (u.x * u.x + u.y * u.y);
       }
@@ -280,31 +314,38 @@ __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
   finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
+template <typename T, bool IMAG, bool LAST, int SEG>
+__global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
+  extern __shared__ __align__(16) unsigned char csmem_raw[];
+  __shared__ c2_t<T> cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  colsweep_body<T, IMAG, LAST, SEG>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb, red_smem);
+}
+
 // ---------------------------------------------------------------- x sweep (2d/3d)
 // Tile of 32 x lines in shared memory, transposed ([point][line], pitch 33).
-// blockDim.x = 32 * nseg; dynamic shared memory: coefficients (3n + 512)
-// then the tile (33 n) complex values.
+// blockDim.x >= 32 * nseg (<= 512); dynamic shared memory: coefficients
+// (3n + 512) then the tile (33 n) complex values.
 constexpr int kTilePitch = 33;
 
+// Body shared with the batched kernels: x lines L0 .. L0+31; sc points to
+// 3n + 512 + 33n complex values of shared memory.
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-__global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
+__device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
+                                            c2_t<T> (*cb)[33], double* red_smem) {
   using c2 = c2_t<T>;
-  extern __shared__ __align__(16) unsigned char tsmem_raw[];
   const LineGeom& G = A.geom;
   const int n = G.n, M = n - 2;
-  c2* sc = reinterpret_cast<c2*>(tsmem_raw);
   c2* tile = sc + 3 * n + 512;
-  __shared__ c2 cf[16][33], cb[16][33];
-  __shared__ double red_smem[32];
-  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nseg = blockDim.x >> 5;
-  const int L0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nseg = (M + SEG - 1) / SEG;
   const int nl = min(32, (int)G.nlines - L0);
   load_coefs<T>(A, sc, n);
   T scl = T(1);
   if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
-  // ---- load: warp w takes lines w, w + nseg, ...; lane takes points lane, lane + 32, ...
+  // ---- load: warp w takes lines w, w + nwarps, ...; lane takes points lane, lane + 32, ...
   const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
-  for (int c = s; c < 32; c += nseg) {
+  for (int c = s; c < 32; c += nwarps) {
     const bool line_ok = c < nl;
     const int gbase = (L0 + c) * G.nx;
     T vline = T(0);
@@ -334,24 +375,19 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
     }
   }
   __syncthreads();
-  // ---- segments: lane = line, warp = segment
+  // ---- segments: lane = line, warp = segment; the input stays in the tile
   const int k0 = 1 + s * SEG;
-  c2 p[SEG];
-#pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    p[j] = k <= M ? tile[k * kTilePitch + lane] : mk<T>(0, 0);
-  }
-  const c2 pl = tile[(k0 - 1) * kTilePitch + lane];
-  const c2 pr = (k0 + SEG <= M) ? tile[(k0 + SEG) * kTilePitch + lane] : mk<T>(0, 0);
   c2 z[SEG];
-  seg_solve<T, IMAG, SEG>(p, pl, pr, z, sc, n, cf, cb, s, nseg, lane);
+  stream_forward<T, IMAG, SEG>([&](int k) { return (k >= 1 && k <= M) ? tile[k * kTilePitch + lane] : mk<T>(0, 0); },
+                               z, sc, k0, M);
+  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
   T tacc = T(0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
     if (k <= M) {
-      const c2 u = mk<T>(p[j].x - z[j].x, p[j].y - z[j].y);
+      const c2 pk = tile[k * kTilePitch + lane];
+      const c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
       tile[k * kTilePitch + lane] = u;
       if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
     }
@@ -363,23 +399,31 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
   }
   __syncthreads();
   // ---- store (tile end points are zero)
-  for (int c = s; c < nl; c += nseg) {
+  for (int c = s; c < nl; c += nwarps) {
     const int gbase = (L0 + c) * G.nx;
     for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
   }
   finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+__global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
+  extern __shared__ __align__(16) unsigned char tsmem_raw[];
+  __shared__ c2_t<T> cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  tsweep_body<T, IMAG, FIRST, LAST, SEG>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(tsmem_raw), cf, cb,
+                                         red_smem);
+}
+
 // ---------------------------------------------------------------- x sweep (1d)
 // One warp per line; lane j owns interior points k = 1 + j*SEG .. (j+1)*SEG;
 // carries by a Kogge-Stone affine scan over shuffles.
+// Body shared with the batched kernels: each warp takes line L.
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-__global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
+__device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, double* red_smem) {
   using c2 = c2_t<T>;
-  __shared__ double red_smem[32];
   const LineGeom& G = A.geom;
   const int lane = threadIdx.x & 31;
-  const int L = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const bool active = L < G.nlines;  // warp-uniform
   T nval = T(0);
   if (active) {
@@ -462,6 +506,12 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
     if (LAST) nval = tacc * (A.w_a[ta] * A.w_b[tb]);
   }
   finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+__global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
+  __shared__ double red_smem[32];
+  xsweep_body<T, IMAG, FIRST, LAST, SEG>(A, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), red_smem);
 }
 
 }  // namespace gpe

@@ -32,6 +32,8 @@ ABI_SYMBOLS = (
     "gp_init", "gp_set_state", "gp_get_state", "gp_set_potential", "gp_set_g", "gp_set_dt",
     "gp_step_imag", "gp_step_real", "gp_observables", "gp_npoints", "gp_precision_of",
     "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
+    "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
+    "gp_batch_offset", "gp_batch_destroy",
 )
 
 
@@ -72,6 +74,15 @@ def load(path: str = LIB_PATH):
     lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
+    lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
+                                  ctypes.POINTER(D), ctypes.POINTER(D), I, _vp]
+    lib.gp_batch_set_state.argtypes = [_vp, I, _vp, I]
+    lib.gp_batch_get_state.argtypes = [_vp, I, _vp, I]
+    lib.gp_batch_step_real.argtypes = [_vp, L]
+    lib.gp_batch_observables.argtypes = [_vp, ctypes.POINTER(GpObs)]
+    lib.gp_batch_offset.argtypes = [_vp, I]
+    lib.gp_batch_offset.restype = L
+    lib.gp_batch_destroy.argtypes = [_vp]
     lib.gp_npoints.argtypes = [_vp]
     lib.gp_npoints.restype = L
     lib.gp_precision_of.argtypes = [_vp]
@@ -158,6 +169,43 @@ def gp_observables_noalloc(dim, n, dx, nkl, g, prec, psi_ptr, V_ptr, out_ptr, st
     nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
     return _check(load().gp_observables_noalloc(int(dim), n3, dx3, nkl3, float(g), int(prec), psi_ptr, V_ptr,
                                                 out_ptr, stream))
+
+
+def gp_batch_init(nruns, n, dx, dt, nkl, g, prec=GP_F32, stream=None):
+    """n, dx, nkl: sequences of (x, y) pairs per run; g: one value per run."""
+    b = _vp()
+    na = (ctypes.c_int * (2 * nruns))(*[int(v) for pair in n for v in pair])
+    dxa = (ctypes.c_double * (2 * nruns))(*[float(v) for pair in dx for v in pair])
+    nka = (ctypes.c_double * (2 * nruns))(*[float(v) for pair in nkl for v in pair])
+    ga = (ctypes.c_double * nruns)(*[float(v) for v in g])
+    _check(load().gp_batch_init(ctypes.byref(b), int(nruns), na, dxa, float(dt), nka, ga, int(prec), stream))
+    return b
+
+
+def gp_batch_set_state(b, run, psi_ptr, on_device):
+    return _check(load().gp_batch_set_state(b, int(run), psi_ptr, int(on_device)))
+
+
+def gp_batch_get_state(b, run, psi_ptr, on_device):
+    return _check(load().gp_batch_get_state(b, int(run), psi_ptr, int(on_device)))
+
+
+def gp_batch_step_real(b, nsteps):
+    return _check(load().gp_batch_step_real(b, int(nsteps)))
+
+
+def gp_batch_observables(b, nruns):
+    out = (GpObs * nruns)()
+    _check(load().gp_batch_observables(b, out))
+    return [obs_dict(o) for o in out]
+
+
+def gp_batch_offset(b, run):
+    return int(load().gp_batch_offset(b, int(run)))
+
+
+def gp_batch_destroy(b):
+    return _check(load().gp_batch_destroy(b))
 
 
 def gp_npoints(h):
@@ -276,3 +324,68 @@ class Propagator:
         if density:
             d["density"] = den
         return d
+
+
+class Batch:
+    """Independent 2d real-time runs stepped together (see gp_batch_init).
+
+    ``sizes``: list of (nx, ny); ``dx``, ``nkl``: lists of (x, y) pairs; ``g``:
+    list of floats.  States are exchanged per run as (ny, nx) complex tensors.
+    """
+
+    def __init__(self, sizes, dx, dt, nkl, g, precision="f32", stream=None):
+        import torch
+        self.torch = torch
+        self.sizes = [tuple(int(v) for v in s) for s in sizes]
+        self.nruns = len(self.sizes)
+        self.precision = precision
+        self.ctype = torch.complex128 if precision == "f64" else torch.complex64
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.b = gp_batch_init(self.nruns, self.sizes, dx, dt, nkl, g,
+                               GP_F64 if precision == "f64" else GP_F32, stream.cuda_stream)
+
+    def close(self):
+        if self.b is not None:
+            gp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, run, psi):
+        nx, ny = self.sizes[run]
+        if isinstance(psi, np.ndarray):
+            a = np.ascontiguousarray(psi.reshape(ny, nx),
+                                     dtype=np.complex128 if self.precision == "f64" else np.complex64)
+            gp_batch_set_state(self.b, run, a.ctypes.data, 0)
+            return
+        t = psi.reshape(ny, nx).to(dtype=self.ctype).contiguous()
+        gp_batch_set_state(self.b, run, t.data_ptr(), 1 if t.is_cuda else 0)
+
+    def set_all(self, flat):
+        """All runs at once from a flat (back-to-back) device tensor or host array."""
+        if isinstance(flat, np.ndarray):
+            gp_batch_set_state(self.b, -1, flat.ctypes.data, 0)
+        else:
+            gp_batch_set_state(self.b, -1, flat.data_ptr(), 1 if flat.is_cuda else 0)
+
+    def get_state(self, run, device=False):
+        nx, ny = self.sizes[run]
+        if device:
+            out = self.torch.empty((ny, nx), dtype=self.ctype, device="cuda")
+            gp_batch_get_state(self.b, run, out.data_ptr(), 1)
+            return out
+        out = np.empty((ny, nx), dtype=np.complex128 if self.precision == "f64" else np.complex64)
+        gp_batch_get_state(self.b, run, out.ctypes.data, 0)
+        return out
+
+    def step_real(self, nsteps):
+        gp_batch_step_real(self.b, nsteps)
+
+    def observables(self):
+        return gp_batch_observables(self.b, self.nruns)

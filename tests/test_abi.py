@@ -68,3 +68,16 @@ def test_init_without_gpu_fails_loudly(lib):
     rc, h = _init(lib)
     assert rc == gpe.GP_ERR_CUDA
     assert "cuda" in lib.gp_last_error().decode().lower()
+
+
+def test_batch_init_rejects_bad_arguments(lib):
+    def init(n, dx=(0.1, 0.1), nk=(1.0, 1.0), g=1.0, nruns=1, dt=1e-3):
+        b = ctypes.c_void_p()
+        na = (ctypes.c_int * 2)(*n)
+        return lib.gp_batch_init(ctypes.byref(b), nruns, na, (ctypes.c_double * 2)(*dx), dt,
+                                 (ctypes.c_double * 2)(*nk), (ctypes.c_double * 1)(g), 1, None), b
+    for kw in (dict(n=(2, 8)), dict(n=(8, 515)), dict(n=(8, 8), dx=(0.0, 0.1)), dict(n=(8, 8), g=float("nan")),
+               dict(n=(8, 8), nruns=0), dict(n=(8, 8), dt=0.0)):
+        rc, b = init(**kw)
+        assert rc == gpe.GP_ERR_INVALID, kw
+        assert not b.value
