@@ -130,6 +130,33 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
  * Synchronises the stream. */
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch);
 
+/* ---- Differentiation form: adjoint of real-time propagation.
+ * Objective J(phi(T)) of the state after nsteps real-time steps; gradients
+ * with respect to the potential values V (per grid point), g and phi(0).
+ * Convention: the adjoint of a complex state is lambda = dJ/dRe(phi) +
+ * i dJ/dIm(phi) (torch.autograd's convention for complex tensors), with the
+ * real inner product <a, b> = Re sum conj(a) b.  The reverse step applies the
+ * Crank-Nicolson sweeps with dt -> -dt in the order z, y, x (the conjugate
+ * transposes of the forward sweeps) and then the adjoint of N at the step's
+ * input p: with u = exp(-i th) p, th = dt (V + g|p|^2), s = Im(conj(lam) u):
+ *     lam <- exp(i th) lam + 2 g dt s p,  dJ/dV += dt s,  dJ/dg += dt sum s|p|^2.
+ *
+ * gp_adjoint_forward: runs nsteps >= 1 real-time steps from the current state
+ * (which becomes phi(T), as with gp_step_real), keeping the state every
+ * ckpt_every steps in library memory (ceil(nsteps/ckpt_every) + ckpt_every
+ * states).  Lines must have at most 514 points.
+ * gp_adjoint_backward: given lambda(T) (npoints complex values in the handle's
+ * precision, host or device), recomputes each checkpoint segment and runs the
+ * reverse steps.  Writes dJdV (npoints doubles, host or device per flag; may be
+ * NULL), *dJdg (may be NULL) and lambda(0) (device buffer in the handle's
+ * precision; may be NULL).  FP64 accumulation of dJ/dV and dJ/dg.  Returns
+ * GP_ERR_STATE if no forward was recorded or dt or the potential changed
+ * since; g may be changed in between (the forward's g is used).  The handle's
+ * state is left as phi(T).  Synchronises the stream. */
+int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every);
+int gp_adjoint_backward(gp_handle* h, const void* lambda_T, int lambda_on_device, double* dJdV, int dJdV_on_device,
+                        double* dJdg, void* lambda_0);
+
 /* ---- Batched form: many independent 2d real-time runs stepped together.
  * Each run r has its own grid (n[2r] x n[2r+1] points, spacing dx[2r],
  * dx[2r+1]), harmonic trap (nu = nkl[2r], kappa = nkl[2r+1]) and nonlinearity

@@ -382,6 +382,7 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
   int rc = join_in(h);
   if (rc) return rc;
   drop_graphs(h);
+  ++h->pot_version;
   if (!V) {
     h->Vd = nullptr;
     h->Vt = nullptr;
@@ -449,6 +450,82 @@ int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch) {
   if (nsteps < 0 || nsteps > 4096) return fail(GP_ERR_INVALID, "gp_time_sweeps: nsteps must be in [0, 4096]");
   return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms_per_launch)
                            : time_steps_f32(h, imag != 0, nsteps, ms_per_launch);
+}
+
+namespace {
+
+// (Re)allocates a buffer of `count` states when the current one is smaller.
+int ensure_states(gp_handle* h, void** buf, long* cap, long count) {
+  if (*cap >= count && *buf) return GP_OK;
+  if (*buf) {
+    cudaStreamSynchronize(h->work);
+    cudaFree(*buf);
+    for (auto& p : h->allocs)
+      if (p == *buf) p = nullptr;
+    *buf = nullptr;
+    *cap = 0;
+  }
+  int rc = dev_alloc(h, buf, (size_t)count * h->np * h->esize);
+  if (rc) return rc;
+  *cap = count;
+  return GP_OK;
+}
+
+}  // namespace
+
+int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_adjoint_forward: NULL handle");
+  if (nsteps < 1 || ckpt_every < 1) return fail(GP_ERR_INVALID, "gp_adjoint_forward: need nsteps >= 1, ckpt_every >= 1");
+  if (h->seg_x == 0 || (h->dim > 1 && h->seg_c == 0))
+    return fail(GP_ERR_INVALID, "gp_adjoint_forward: lines longer than 514 points are not supported");
+  const int K = (int)std::min<long>(ckpt_every, nsteps);
+  const long nck = (nsteps + K - 1) / K;
+  int rc;
+  if ((rc = ensure_states(h, &h->adj_ckpt, &h->adj_ckpt_cap, nck))) return rc;
+  if ((rc = ensure_states(h, &h->adj_traj, &h->adj_traj_cap, K))) return rc;
+  if (!h->adj_lam) {
+    if ((rc = dev_alloc(h, &h->adj_lam, (size_t)h->np * h->esize))) return rc;
+    void* p = nullptr;
+    if ((rc = dev_alloc(h, &p, (size_t)h->np * sizeof(double)))) return rc;
+    h->adj_dJdV = (double*)p;
+    if ((rc = dev_alloc(h, &p, 16))) return rc;
+    h->adj_dJdg = (double*)p;
+  }
+  h->adj_nsteps = -1;
+  rc = h->prec == GP_F64 ? adjoint_forward_f64(h, nsteps, K) : adjoint_forward_f32(h, nsteps, K);
+  if (rc) return rc;
+  h->adj_nsteps = nsteps;
+  h->adj_K = K;
+  h->adj_g = h->g;
+  h->adj_dt = h->dt;
+  h->adj_pot_version = h->pot_version;
+  return GP_OK;
+}
+
+int gp_adjoint_backward(gp_handle* h, const void* lambda_T, int lambda_on_device, double* dJdV, int dJdV_on_device,
+                        double* dJdg, void* lambda_0) {
+  if (!h || !lambda_T) return fail(GP_ERR_INVALID, "gp_adjoint_backward: NULL argument");
+  if (h->adj_nsteps < 1) return fail(GP_ERR_STATE, "gp_adjoint_backward: no gp_adjoint_forward recorded");
+  if (h->dt != h->adj_dt || h->pot_version != h->adj_pot_version)
+    return fail(GP_ERR_STATE, "gp_adjoint_backward: dt or the potential changed since gp_adjoint_forward");
+  int rc = join_in(h);
+  if (rc) return rc;
+  GP_CUDA(cudaMemcpyAsync(h->adj_lam, lambda_T, (size_t)h->np * h->esize,
+                          lambda_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
+  if (!lambda_on_device) GP_CUDA(cudaStreamSynchronize(h->work));
+  if ((rc = join_out(h))) return rc;
+  double* ddev = (dJdV && dJdV_on_device) ? dJdV : nullptr;
+  rc = h->prec == GP_F64 ? adjoint_backward_f64(h, ddev, lambda_0) : adjoint_backward_f32(h, ddev, lambda_0);
+  if (rc) return rc;
+  if ((rc = join_in(h))) return rc;
+  if (dJdV && !dJdV_on_device)
+    GP_CUDA(cudaMemcpyAsync(dJdV, h->adj_dJdV, (size_t)h->np * sizeof(double), cudaMemcpyDeviceToHost, h->work));
+  GP_CUDA(cudaMemcpyAsync(h->obs_host, h->adj_dJdg, sizeof(double), cudaMemcpyDeviceToHost, h->work));
+  GP_CUDA(cudaStreamSynchronize(h->work));
+  if ((rc = join_out(h))) return rc;
+  if (dJdg) *dJdg = h->obs_host[0];
+  if (!std::isfinite(h->obs_host[0])) return fail(GP_ERR_NONFINITE, "gp_adjoint_backward: non-finite gradient");
+  return GP_OK;
 }
 
 int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device) {

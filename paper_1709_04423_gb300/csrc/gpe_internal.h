@@ -87,6 +87,19 @@ struct gp_handle {
   double* obs_host = nullptr; // pinned [8]
   double* dens_scratch = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // adjoint: checkpoints of the last gp_adjoint_forward and scratch
+  long adj_nsteps = -1;       // -1: no forward recorded
+  long pot_version = 0;       // bumped by gp_set_potential
+  long adj_pot_version = 0;
+  int adj_K = 0;
+  double adj_g = 0, adj_dt = 0;
+  void* adj_ckpt = nullptr;   // ceil(nsteps / K) states
+  long adj_ckpt_cap = 0;      // states the buffer holds
+  void* adj_traj = nullptr;   // K states
+  long adj_traj_cap = 0;
+  void* adj_lam = nullptr;    // one state
+  double* adj_dJdV = nullptr; // npoints doubles
+  double* adj_dJdg = nullptr; // one double
   std::vector<void*> allocs;
 };
 
@@ -119,5 +132,9 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out);
 int run_observables_f32(gp_handle* h, double* dens_dev);
 int run_observables_f64(gp_handle* h, double* dens_dev);
 void to_float(gp_handle* h, float* dst, const double* src, long n);
+int adjoint_forward_f32(gp_handle* h, long nsteps, int K);
+int adjoint_forward_f64(gp_handle* h, long nsteps, int K);
+int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev);
+int adjoint_backward_f64(gp_handle* h, double* dJdV_dev, void* lam0_dev);
 
 }  // namespace gpe

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "gpe_adjoint.cuh"
 #include "gpe_internal.h"
 #include "gpe_obs.cuh"
 #include "gpe_sweep.cuh"
@@ -122,7 +123,7 @@ void launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
+void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nullptr) {
   const bool first = d == 0, last = d == h->dim - 1;
   const int mode = imag ? MODE_IMAG : MODE_REAL;
   const int seg = d == 0 ? h->seg_x : h->seg_c;
@@ -130,6 +131,7 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
     Sweep2Args<T> a;
     std::memset(&a, 0, sizeof(a));
     a.psi = (c2_t<T>*)h->psi;
+    a.src = d == 0 ? (const c2_t<T>*)src : nullptr;
     a.geom = geom_of(h, d);
     const int si = seg_index(seg);
     a.alpha = coef_ptr<T>(h, mode, d, 0);
@@ -204,11 +206,13 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d) {
   }
 }
 
+// One step; with src != nullptr the x sweep reads the step's input from src
+// (segmented kernels only) and every sweep writes h->psi.
 template <typename T>
-void enqueue_step(gp_handle* h, bool imag, int par, cudaEvent_t* ev = nullptr) {
+void enqueue_step(gp_handle* h, bool imag, int par, cudaEvent_t* ev = nullptr, const void* src = nullptr) {
   for (int d = 0; d < h->dim; ++d) {
     if (ev) cudaEventRecord(ev[2 * d], h->work);
-    enqueue_sweep<T>(h, imag, par, d);
+    enqueue_sweep<T>(h, imag, par, d, src);
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
 }
@@ -313,6 +317,109 @@ int run_observables_t(gp_handle* h, double* dens_dev) {
   count_launch();
   GP_CUDA(cudaGetLastError());
   return GP_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+// Sweep of the adjoint state along axis d with the dt -> -dt coefficients
+// (the conjugate-transposed Crank-Nicolson map).
+template <typename T>
+void enqueue_adj_sweep(gp_handle* h, int d) {
+  Sweep2Args<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.psi = (c2_t<T>*)h->adj_lam;
+  a.geom = geom_of(h, d);
+  const int seg = d == 0 ? h->seg_x : h->seg_c;
+  const int si = seg_index(seg);
+  a.alpha = coef_ptr<T>(h, MODE_REAL_ADJ, d, 0);
+  a.gf = coef_ptr<T>(h, MODE_REAL_ADJ, d, 1 + 2 * si);
+  a.gb = coef_ptr<T>(h, MODE_REAL_ADJ, d, 2 + 2 * si);
+  a.ptab = (const c2_t<T>*)h->ctab[MODE_REAL_ADJ][d] + (size_t)si * 512;
+  if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work);
+  else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work);
+  else launch_c_seg<T, false, false>(seg, a, h->work);
+}
+
+template <typename T>
+void enqueue_adj_phase(gp_handle* h, const void* phi) {
+  AdjPhaseArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.phi = (const c2_t<T>*)phi;
+  a.lam = (c2_t<T>*)h->adj_lam;
+  a.np = h->np;
+  a.nx = axis_len(h, 0);
+  a.ny = axis_len(h, 1);
+  a.V = (const T*)h->Vt;
+  a.vx = (const T*)h->vt[0];
+  a.vy = (const T*)h->vt[1];
+  a.vz = (const T*)h->vt[2];
+  a.dt = (T)h->adj_dt;
+  a.g = (T)h->adj_g;
+  a.dJdV = h->adj_dJdV;
+  a.partials = h->partials;
+  a.counter = h->counter;
+  a.dJdg = h->adj_dJdg;
+  const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 16);
+  adjoint_phase_kernel<T><<<blocks, 256, 0, h->work>>>(a);
+  count_launch();
+}
+
+// Forward run of nsteps real-time steps from the current state, keeping the
+// state at steps 0, K, 2K, ... (buffers sized by the caller of this function).
+template <typename T>
+int adjoint_forward_t(gp_handle* h, long nsteps, int K) {
+  const long nck = (nsteps + K - 1) / K;
+  for (long c = 0; c < nck; ++c) {
+    int rc = join_in(h);
+    if (rc) return rc;
+    GP_CUDA(cudaMemcpyAsync((char*)h->adj_ckpt + (size_t)c * h->np * h->esize, h->psi, (size_t)h->np * h->esize,
+                            cudaMemcpyDeviceToDevice, h->work));
+    if ((rc = join_out(h))) return rc;
+    if ((rc = run_steps_t<T>(h, false, std::min<long>(K, nsteps - c * K)))) return rc;
+  }
+  return GP_OK;
+}
+
+// Reverse pass: h->adj_lam holds lambda(T) on entry and lambda(0) on exit;
+// h->adj_dJdV (when dJdV_dev is null) or dJdV_dev receives dJ/dV, h->adj_dJdg
+// dJ/dg.  Each checkpoint segment is recomputed forward into the trajectory
+// buffer (the x sweep reads step j and writes step j+1), then walked back.
+template <typename T>
+int adjoint_backward_t(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
+  const long nsteps = h->adj_nsteps;
+  const int K = h->adj_K;
+  const long nck = (nsteps + K - 1) / K;
+  const size_t sbytes = (size_t)h->np * h->esize;
+  double* dJdV_keep = h->adj_dJdV;
+  if (dJdV_dev) h->adj_dJdV = dJdV_dev;
+  int rc = join_in(h);
+  if (rc) return rc;
+  GP_CUDA(cudaMemsetAsync(h->adj_dJdV, 0, (size_t)h->np * sizeof(double), h->work));
+  GP_CUDA(cudaMemsetAsync(h->adj_dJdg, 0, sizeof(double), h->work));
+  void* psi_saved = h->psi;
+  const double g_now = h->g, dt_now = h->dt;
+  h->g = h->adj_g;  // the forward's g and dt drive the recomputation
+  h->dt = h->adj_dt;
+  for (long c = nck - 1; c >= 0; --c) {
+    const long t0 = c * K;
+    const int len = (int)std::min<long>(K, nsteps - t0);
+    char* traj = (char*)h->adj_traj;
+    cudaMemcpyAsync(traj, (const char*)h->adj_ckpt + (size_t)c * sbytes, sbytes, cudaMemcpyDeviceToDevice, h->work);
+    for (int j = 0; j + 1 < len; ++j) {
+      h->psi = traj + (size_t)(j + 1) * sbytes;
+      enqueue_step<T>(h, false, 0, nullptr, traj + (size_t)j * sbytes);
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      for (int d = h->dim - 1; d >= 0; --d) enqueue_adj_sweep<T>(h, d);
+      enqueue_adj_phase<T>(h, traj + (size_t)j * sbytes);
+    }
+  }
+  h->psi = psi_saved;
+  h->g = g_now;
+  h->dt = dt_now;
+  h->adj_dJdV = dJdV_keep;
+  if (lam0_dev) cudaMemcpyAsync(lam0_dev, h->adj_lam, sbytes, cudaMemcpyDeviceToDevice, h->work);
+  GP_CUDA(cudaGetLastError());
+  return join_out(h);
 }
 
 }  // namespace gpe

@@ -11,6 +11,12 @@ int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out) {
 
 int run_observables_f32(gp_handle* h, double* dens_dev) { return run_observables_t<float>(h, dens_dev); }
 
+int adjoint_forward_f32(gp_handle* h, long nsteps, int K) { return adjoint_forward_t<float>(h, nsteps, K); }
+
+int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
+  return adjoint_backward_t<float>(h, dJdV_dev, lam0_dev);
+}
+
 }  // namespace gpe
 
 namespace gpe {

@@ -11,4 +11,10 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out) {
 
 int run_observables_f64(gp_handle* h, double* dens_dev) { return run_observables_t<double>(h, dens_dev); }
 
+int adjoint_forward_f64(gp_handle* h, long nsteps, int K) { return adjoint_forward_t<double>(h, nsteps, K); }
+
+int adjoint_backward_f64(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
+  return adjoint_backward_t<double>(h, dJdV_dev, lam0_dev);
+}
+
 }  // namespace gpe

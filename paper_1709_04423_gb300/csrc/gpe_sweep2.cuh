@@ -50,7 +50,8 @@ namespace gpe {
 
 template <typename T>
 struct Sweep2Args {
-  c2_t<T>* psi;
+  c2_t<T>* psi;          // lines are written here
+  const c2_t<T>* src;    // and read from here (x sweeps; nullptr = psi)
   LineGeom geom;
   const c2_t<T>* alpha;  // [n] alpha_k = r m_k (imaginary time: real part only)
   const c2_t<T>* gf;     // [n] forward segment products for this SEG
@@ -353,12 +354,13 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
       const int L = L0 + c;
       vline = A.vy[L % G.ny] + A.vz[L / G.ny];
     }
+    const c2* in = A.src ? A.src : A.psi;
     for (int q0 = 0; q0 < per_line; q0 += 4) {
       c2 v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = (q0 + i) * 32 + lane;
-        v[i] = (line_ok && k >= 1 && k <= M) ? A.psi[gbase + k] : mk<T>(0, 0);
+        v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -437,13 +439,14 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       if (A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
       if (A.scale_in) scl = (T)(*A.scale_in);
     }
+    const c2* in = (A.src ? A.src : A.psi) + base;
     c2 p[SEG], e[SEG];
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
       c2 v = mk<T>(0, 0);
       if (k <= M) {
-        v = line[k];
+        v = in[k];
         if (FIRST) {
           v.x *= scl; v.y *= scl;
           const T Vk = A.V ? A.V[base + k] : (A.vx[k] + vline);

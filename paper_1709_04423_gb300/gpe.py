@@ -33,7 +33,7 @@ ABI_SYMBOLS = (
     "gp_step_imag", "gp_step_real", "gp_observables", "gp_npoints", "gp_precision_of",
     "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
-    "gp_batch_offset", "gp_batch_destroy",
+    "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
 )
 
 
@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
     lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
+    lib.gp_adjoint_forward.argtypes = [_vp, L, I]
+    lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
     lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
                                   ctypes.POINTER(D), ctypes.POINTER(D), I, _vp]
     lib.gp_batch_set_state.argtypes = [_vp, I, _vp, I]
@@ -169,6 +171,18 @@ def gp_observables_noalloc(dim, n, dx, nkl, g, prec, psi_ptr, V_ptr, out_ptr, st
     nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
     return _check(load().gp_observables_noalloc(int(dim), n3, dx3, nkl3, float(g), int(prec), psi_ptr, V_ptr,
                                                 out_ptr, stream))
+
+
+def gp_adjoint_forward(h, nsteps, ckpt_every):
+    return _check(load().gp_adjoint_forward(h, int(nsteps), int(ckpt_every)))
+
+
+def gp_adjoint_backward(h, lam_ptr, lam_on_device, dJdV_ptr=None, dJdV_on_device=1, lam0_ptr=None):
+    """Returns dJ/dg; writes dJ/dV and lambda(0) where pointers are given."""
+    dJdg = ctypes.c_double(0.0)
+    _check(load().gp_adjoint_backward(h, lam_ptr, int(lam_on_device), dJdV_ptr, int(dJdV_on_device),
+                                      ctypes.byref(dJdg), lam0_ptr))
+    return float(dJdg.value)
 
 
 def gp_batch_init(nruns, n, dx, dt, nkl, g, prec=GP_F32, stream=None):
@@ -389,3 +403,53 @@ class Batch:
 
     def observables(self):
         return gp_batch_observables(self.b, self.nruns)
+
+
+def real_time_evolution(prop, phi0, V, g, nsteps, ckpt_every):
+    """Differentiable real-time propagation: phi(T) from phi(0), with gradients
+    flowing to phi0 (complex tensor), V (real FP64 tensor: the full potential on
+    the grid) and g (0-dim real tensor).  ``prop`` is a Propagator that this
+    call owns until the backward pass has run; the forward pass keeps a
+    checkpoint every ``ckpt_every`` steps and the backward pass recomputes
+    between checkpoints (gp_adjoint_forward / gp_adjoint_backward)."""
+    return _RealTimeEvolution.apply(phi0, V, g, prop, int(nsteps), int(ckpt_every))
+
+
+def _make_function():
+    import torch
+
+    class RealTimeEvolution(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi0, V, g, prop, nsteps, ckpt_every):
+            prop.set_potential(V.detach().to(torch.float64).contiguous())
+            prop.set_g(float(g))
+            prop.set_state(phi0.detach())
+            gp_adjoint_forward(prop.h, nsteps, ckpt_every)
+            ctx.prop = prop
+            ctx.V_dtype, ctx.g_dtype = V.dtype, g.dtype
+            return prop.get_state(device=True)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            prop = ctx.prop
+            lam = grad_out.to(prop.ctype).contiguous()
+            dJdV = torch.empty(prop.shape, dtype=torch.float64, device="cuda")
+            lam0 = torch.empty_like(lam)
+            dJdg = gp_adjoint_backward(prop.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1, lam0.data_ptr())
+            return (lam0, dJdV.to(ctx.V_dtype), torch.tensor(dJdg, dtype=ctx.g_dtype, device="cuda"),
+                    None, None, None)
+
+    return RealTimeEvolution
+
+
+class _Lazy:
+    def __init__(self):
+        self.fn = None
+
+    def apply(self, *args):
+        if self.fn is None:
+            self.fn = _make_function()
+        return self.fn.apply(*args)
+
+
+_RealTimeEvolution = _Lazy()
