@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=100, help="time steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mu-check", action="store_true")
+    ap.add_argument("--no-quench", action="store_true", help="skip the 256^3 real-time form")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
+    ap.add_argument("--quench-imag-steps", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -325,6 +328,91 @@ def run_ours(args):
                       "gpu_launches": blaunch}
     bmu_err = max(abs(a - b_) for a, b_ in zip(bmu["f32"], bmu["f64"])) if bmu else None
 
+    # ---- 3d real-time quench at 256^3 (dx = 0.08, dt = 2e-4, isotropic trap):
+    # imaginary-time ground state at g = 20, then real time at g = 40.  The
+    # state (134 MB FP32, 268 MB FP64) is larger than L2, so these sweeps run
+    # from HBM; timed per kernel like the headline form.
+    qres = {}
+    if not args.no_quench:
+        qn, qdx = [256] * 3, [0.08] * 3
+        qnp = 256 ** 3
+        qphi = torch.tensor(inputs.gaussian_state(3, qn, qdx, [1.0] * 3, seed=1711, noise=1e-3), device="cuda")
+        for prec in ("f64", "f32"):
+            with torch.cuda.stream(stream):
+                q = gpe.Propagator(3, qn, qdx, 1e-3, [1.0] * 3, 20.0, precision=prec, stream=stream)
+                q.set_state(qphi)
+                q.step_imag(args.quench_imag_steps)
+                q.set_dt(2e-4)
+                q.set_g(40.0)
+                ob0 = q.observables()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                for _ in range(args.warmup):
+                    q.step_real(args.inner)
+                barrier()
+                for s_ in range(args.steps):
+                    ev[s_][0].record(stream)
+                    q.step_real(args.inner)
+                    q.observables()
+                    ev[s_][1].record(stream)
+                barrier()
+                qt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
+                kms = q.time_sweeps(False, 16)
+                ob1 = q.observables()
+                q.close()
+            esize = 16 if prec == "f64" else 8
+            axis = max(range(3), key=lambda d: kms[d])
+            ach = 2 * esize * qnp / (kms[axis] * 1e-3) / 1e9
+            qres[prec] = {"value": world * args.steps * args.inner * qnp / qt, "ms_per_step": 1e3 * qt / args.steps,
+                          "kernel_ms": kms, "dominant_sweep_axis": axis, "achieved_gbs": ach,
+                          "frac_of_measured_hbm": ach / float(measured_peaks()[0]["hbm_gbs"]),
+                          "energy_drift_rel": abs(ob1["energy"] / ob0["energy"] - 1),
+                          "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1)}
+
+    # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V
+    # and g at 128^3 (dx = 0.1, dt = 5e-4, 1000 steps, g = 30, isotropic trap +
+    # 8 Gaussian bumps, checkpoints every 50 steps); FP32 forward, FP64
+    # accumulation of the gradients.  One timed unit = forward + backward.
+    ares = {}
+    if not args.no_adjoint:
+        an, adx = [128] * 3, [0.1] * 3
+        anp = 128 ** 3
+        dV, _bp = inputs.gaussian_bumps(3, an, adx, seed=1713, count=8, amp=0.5, center=3.0)
+        xs = inputs.axis_coords(128, 0.1)
+        harm = 0.5 * (xs[:, None, None] ** 2 + xs[None, :, None] ** 2 + xs[None, None, :] ** 2)
+        AV = torch.tensor(harm + dV, device="cuda")
+        aphi = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3), device="cuda")
+        atgt = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3, shift=(0.5, 0.0, 0.0)), device="cuda")
+        for prec in ("f32",):
+            with torch.cuda.stream(stream):
+                q = gpe.Propagator(3, an, adx, 5e-4, [1.0] * 3, 30.0, precision=prec, stream=stream)
+                q.set_potential(AV)
+                times = []
+                for rep in range(1 + 2):
+                    q.set_state(aphi)
+                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                    barrier()
+                    e0.record(stream)
+                    gpe.gp_adjoint_forward(q.h, 1000, 50)
+                    e1.record(stream)
+                    phiT = q.get_state(device=True).to(torch.complex128)
+                    c = torch.sum(torch.conj(atgt) * phiT) * 1e-3
+                    lam = (2 * c * atgt * 1e-3).to(q.ctype).contiguous()
+                    dJdV = torch.empty(tuple(an), dtype=torch.float64, device="cuda")
+                    e_b = torch.cuda.Event(enable_timing=True)
+                    e_b.record(stream)
+                    dJdg = gpe.gp_adjoint_backward(q.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1)
+                    e2.record(stream)
+                    barrier()
+                    if rep:
+                        times.append((e0.elapsed_time(e1), e_b.elapsed_time(e2)))
+                q.close()
+            tf = sum(t[0] for t in times) / len(times)
+            tb = sum(t[1] for t in times) / len(times)
+            ares[prec] = {"forward_ms": tf, "backward_ms": tb,
+                          "value": world * 1000 * anp / ((tf + tb) * 1e-3),
+                          "backward_over_forward": tb / tf, "dJdg": dJdg}
+
     # ---- end to end through the public API with host buffers (FP32 form)
     e2e = None
     p = make("f32")
@@ -400,6 +488,16 @@ def run_ours(args):
             "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": forms["f32"]["value"] / forms["f64"]["value"],
                     "mu_err_vs_f64_full_job": mu_err,
                     "mu_f32": mu["f32"]["mu"] if mu else None, "mu_f64": mu["f64"]["mu"] if mu else None},
+            "quench256": ({"workload": "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, imaginary-time "
+                                       f"ground state at g=20 ({args.quench_imag_steps} steps) then g=40; L2 not flushed "
+                                       "(state larger than L2)",
+                           "f64": qres.get("f64"), "f32": qres.get("f32"),
+                           "speedup_f32_vs_f64": qres["f32"]["value"] / qres["f64"]["value"]} if qres else None),
+            "adjoint": ({"workload": "gradient of |<phi_target|phi(T)>|^2 w.r.t. V (per grid value) and g: 128^3, "
+                                     "dx=0.1, dt=5e-4, 1000 real-time steps, g=30, isotropic trap + 8 Gaussian bumps "
+                                     "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "
+                                     "point-steps/s; FP32 forward, FP64 gradient accumulation",
+                         "f32": ares.get("f32")} if ares else None),
             "batched": {"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
                                     "(SplitMix64 seed 1712), dx=0.1, dt=5e-4, g~U[0,50], nu=1, kappa~U[1,2], "
                                     "g=0 trap ground state quenched; one launch per sweep and segment class, "
