@@ -231,6 +231,31 @@ int upload_coefs(gp_handle* h) {
   return h->prec == GP_F64 ? upload_coefs_t<double>(h) : upload_coefs_t<float>(h);
 }
 
+// Per-axis potential factors of the sub-step N for the current dt (absent
+// axes: a single factor 1); and, with a user potential, the per-point ones.
+int upload_factors(gp_handle* h) {
+  for (int d = 0; d < 3; ++d) {
+    const int nd = axis_len(h, d);
+    std::vector<cd> fr(nd, cd(1, 0)), fi(nd, cd(1, 0));
+    if (d < h->dim)
+      for (int i = 0; i < nd; ++i) {
+        const double x = -0.5 * nd * h->dx[d] + i * h->dx[d];
+        const double v = 0.5 * h->nkl[d] * h->nkl[d] * x * x;
+        fr[i] = cd(std::cos(h->dt * v), -std::sin(h->dt * v));
+        fi[i] = cd(std::exp(-h->dt * v), 0.0);
+      }
+    int rc = h->prec == GP_F64 ? upload_c2<double>(h, h->fac[0][d], fr) : upload_c2<float>(h, h->fac[0][d], fr);
+    if (rc) return rc;
+    rc = h->prec == GP_F64 ? upload_c2<double>(h, h->fac[1][d], fi) : upload_c2<float>(h, h->fac[1][d], fi);
+    if (rc) return rc;
+  }
+  if (h->Vd) {
+    potential_factors(h);
+    GP_CUDA(cudaGetLastError());
+  }
+  return GP_OK;
+}
+
 }  // namespace gpe
 
 using namespace gpe;
@@ -318,6 +343,8 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
       }
     }
     if ((rc = dev_alloc(h, &h->vt[d], nd * tsz))) return bail(rc);
+    if ((rc = dev_alloc(h, &h->fac[0][d], nd * h->esize))) return bail(rc);
+    if ((rc = dev_alloc(h, &h->fac[1][d], nd * h->esize))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->vd[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->cdx[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->wd[d], nd * sizeof(double)))) return bail(rc);
@@ -341,6 +368,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     }
   }
   if ((rc = upload_coefs(h))) return bail(rc);
+  if ((rc = upload_factors(h))) return bail(rc);
   choose_shapes(h);
   // reduction scratch: enough partial slots for any sweep or observables grid
   long maxblocks = 152L * 16;
@@ -398,6 +426,8 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
       if ((rc = dev_alloc(h, &p, (size_t)h->np * sizeof(float)))) return rc;
       h->Vbuf32 = (float*)p;
     }
+    if ((rc = dev_alloc(h, &h->fV[0], (size_t)h->np * h->esize))) return rc;
+    if ((rc = dev_alloc(h, &h->fV[1], (size_t)h->np * h->esize))) return rc;
   }
   GP_CUDA(cudaMemcpyAsync(h->Vbuf, V, (size_t)h->np * sizeof(double),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
@@ -408,6 +438,7 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
     to_float(h, h->Vbuf32, h->Vbuf, h->np);
     h->Vt = h->Vbuf32;
   }
+  potential_factors(h);
   GP_CUDA(cudaGetLastError());
   if (!on_device) GP_CUDA(cudaStreamSynchronize(h->work));
   return join_out(h);
@@ -430,6 +461,7 @@ int gp_set_dt(gp_handle* h, double dt) {
   drop_graphs(h);
   h->dt = dt;
   if ((rc = upload_coefs(h))) return rc;
+  if ((rc = upload_factors(h))) return rc;
   return join_out(h);
 }
 

@@ -35,7 +35,9 @@ struct BatchRun {
   int nx, ny;
   const c2_t<T>* coef[2];  // per axis: alpha | gf | gb (3 n values) for the run's segment length
   const c2_t<T>* ptab[2];  // per axis: carry tables (512 values)
-  const T* vx; const T* vy; const T* vz0;  // nu^2 x^2/2, kappa^2 y^2/2, a single 0
+  const c2_t<T>* fx; const c2_t<T>* fy; const c2_t<T>* fz1;  // exp(-i dt v(x)), exp(-i dt v(y)), a single 1 (FP64)
+  T dtg;                                                   // dt g (FP64)
+  const T* vx; const T* vy; const T* vz0;                  // nu^2 x^2/2, kappa^2 y^2/2, a single 0 (FP32)
   T g;
 };
 
@@ -65,6 +67,10 @@ __global__ void __launch_bounds__(512) batch_x_kernel(const BatchRun<T>* __restr
   A.gf = R.coef[0] + R.nx;
   A.gb = R.coef[0] + 2 * R.nx;
   A.ptab = R.ptab[0];
+  A.fx = R.fx;
+  A.fy = R.fy;
+  A.fz = R.fz1;
+  A.dtg = R.dtg;
   A.vx = R.vx;
   A.vy = R.vy;
   A.vz = R.vz0;
@@ -94,6 +100,10 @@ __global__ void __launch_bounds__(128) batch_xw_kernel(const BatchRun<T>* __rest
   A.alpha = R.coef[0];
   A.gf = R.coef[0] + R.nx;
   A.gb = R.coef[0] + 2 * R.nx;
+  A.fx = R.fx;
+  A.fy = R.fy;
+  A.fz = R.fz1;
+  A.dtg = R.dtg;
   A.vx = R.vx;
   A.vy = R.vy;
   A.vz = R.vz0;
@@ -228,7 +238,9 @@ int build_tables(gp_batch* b) {
       voff[2 * r + a] = vtot;
       vtot += b->n[2 * r + a];
     }
-  std::vector<T> vbuf(vtot + 1, T(0));  // last entry: the shared 0 for the absent z axis
+  std::vector<T> vbuf(2 * (vtot + 1), T(0));  // complex factors; last entry: the shared 1 for the absent z axis
+  vbuf[2 * vtot] = T(1);
+  std::vector<T> pbuf(vtot + 1, T(0));        // potentials; last entry: the shared 0 for the absent z axis
   for (int r = 0; r < R; ++r)
     for (int a = 0; a < 2; ++a) {
       const int n = b->n[2 * r + a];
@@ -251,11 +263,16 @@ int build_tables(gp_batch* b) {
       const double w = b->nk[2 * r + a];
       for (int i = 0; i < n; ++i) {
         const double x = -0.5 * n * h + i * h;
-        vbuf[voff[2 * r + a] + i] = (T)(0.5 * w * w * x * x);
+        const double v = 0.5 * w * w * x * x;
+        vbuf[2 * (voff[2 * r + a] + i)] = (T)std::cos(b->dt * v);
+        vbuf[2 * (voff[2 * r + a] + i) + 1] = (T)(-std::sin(b->dt * v));
+        pbuf[voff[2 * r + a] + i] = (T)v;
       }
     }
-  void *cdev = nullptr, *vdev = nullptr;
+  void *cdev = nullptr, *vdev = nullptr, *pdev = nullptr;
   int rc;
+  if ((rc = b_alloc(b, &pdev, pbuf.size() * sizeof(T)))) return rc;
+  if ((rc = b_upload<T>(b, pdev, pbuf))) return rc;
   if ((rc = b_alloc(b, &cdev, cbuf.size() * sizeof(T)))) return rc;
   if ((rc = b_upload<T>(b, cdev, cbuf))) return rc;
   if ((rc = b_alloc(b, &vdev, vbuf.size() * sizeof(T)))) return rc;
@@ -270,9 +287,13 @@ int build_tables(gp_batch* b) {
       q.coef[a] = (const c2_t<T>*)cdev + coff[2 * r + a];
       q.ptab[a] = (const c2_t<T>*)cdev + poff[2 * r + a];
     }
-    q.vx = (const T*)vdev + voff[2 * r];
-    q.vy = (const T*)vdev + voff[2 * r + 1];
-    q.vz0 = (const T*)vdev + vtot;
+    q.fx = (const c2_t<T>*)vdev + voff[2 * r];
+    q.fy = (const c2_t<T>*)vdev + voff[2 * r + 1];
+    q.fz1 = (const c2_t<T>*)vdev + vtot;
+    q.dtg = (T)(b->dt * b->g[r]);
+    q.vx = (const T*)pdev + voff[2 * r];
+    q.vy = (const T*)pdev + voff[2 * r + 1];
+    q.vz0 = (const T*)pdev + vtot;
     q.g = (T)b->g[r];
   }
   if ((rc = b_alloc(b, &b->runs_d, R * sizeof(BatchRun<T>)))) return rc;

@@ -62,6 +62,11 @@ struct gp_handle {
   double* Vbuf = nullptr;    // storage behind Vd
   float* Vbuf32 = nullptr;   // storage behind Vt for the FP32 form
   void* vt[3] = {nullptr, nullptr, nullptr};     // nu_d^2 x^2/2 per axis, state precision
+  // potential factors of the sub-step N, state precision, complex:
+  // fac[0][d][i] = exp(-i dt v_d(x_i)), fac[1][d][i] = exp(-dt v_d(x_i)) (real);
+  // with a user potential fV[0][q] = exp(-i dt V_q), fV[1][q] = exp(-dt V_q)
+  void* fac[2][3] = {{nullptr}};
+  void* fV[2] = {nullptr, nullptr};
   double* vd[3] = {nullptr, nullptr, nullptr};   // same in FP64
   double* cdx[3] = {nullptr, nullptr, nullptr};  // coordinates
   double* wd[3] = {nullptr, nullptr, nullptr};   // Simpson weights
@@ -123,6 +128,7 @@ int join_out(gp_handle* h);
 inline int axis_len(const gp_handle* h, int d) { return d < h->dim ? h->n[d] : 1; }
 void drop_graphs(gp_handle* h);
 int upload_coefs(gp_handle* h);
+int upload_factors(gp_handle* h);
 
 // per-precision entry points (gpe_step_f32.cu / gpe_step_f64.cu)
 int run_steps_f32(gp_handle* h, bool imag, long nsteps);
@@ -132,6 +138,7 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out);
 int run_observables_f32(gp_handle* h, double* dens_dev);
 int run_observables_f64(gp_handle* h, double* dens_dev);
 void to_float(gp_handle* h, float* dst, const double* src, long n);
+void potential_factors(gp_handle* h);  // fV from the FP64 potential (state precision)
 int adjoint_forward_f32(gp_handle* h, long nsteps, int K);
 int adjoint_forward_f64(gp_handle* h, long nsteps, int K);
 int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev);

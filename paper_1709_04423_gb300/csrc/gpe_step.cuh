@@ -138,6 +138,12 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
+    const int fm = imag ? 1 : 0;
+    a.fV = h->Vd ? (const c2_t<T>*)h->fV[fm] : nullptr;
+    a.fx = (const c2_t<T>*)h->fac[fm][0];
+    a.fy = (const c2_t<T>*)h->fac[fm][1];
+    a.fz = (const c2_t<T>*)h->fac[fm][2];
+    a.dtg = (T)(h->dt * h->g);
     a.V = (const T*)h->Vt;
     a.vx = (const T*)h->vt[0];
     a.vy = (const T*)h->vt[1];

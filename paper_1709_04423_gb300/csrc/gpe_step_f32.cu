@@ -20,6 +20,17 @@ int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
 }  // namespace gpe
 
 namespace gpe {
+void potential_factors(gp_handle* h) {
+  const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
+  if (h->prec == GP_F64)
+    potential_factor_kernel<double><<<blocks, 256, 0, h->work>>>((double2*)h->fV[0], (double2*)h->fV[1], h->Vbuf,
+                                                                h->dt, h->np);
+  else
+    potential_factor_kernel<float><<<blocks, 256, 0, h->work>>>((float2*)h->fV[0], (float2*)h->fV[1], h->Vbuf,
+                                                               h->dt, h->np);
+  count_launch();
+}
+
 void to_float(gp_handle* h, float* dst, const double* src, long n) {
   const int blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
   to_float_kernel<<<blocks, 256, 0, h->work>>>(dst, src, n);

@@ -161,6 +161,17 @@ __global__ void scale_kernel(c2_t<T>* psi, long np, const double* scale) {
 
 static __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
 
+// exp(-i dt V) and exp(-dt V) per point, evaluated in FP64 and stored in T
+template <typename T>
+__global__ void potential_factor_kernel(c2_t<T>* fr, c2_t<T>* fi, const double* V, double dt, long n) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(dt * V[q], &s, &c);
+    fr[q] = mk<T>((T)c, (T)(-s));
+    fi[q] = mk<T>((T)exp(-dt * V[q]), T(0));
+  }
+}
+
 static __global__ void to_float_kernel(float* dst, const double* src, long n) {
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
     dst[q] = (float)src[q];

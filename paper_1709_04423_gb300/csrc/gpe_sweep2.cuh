@@ -57,8 +57,17 @@ struct Sweep2Args {
   const c2_t<T>* gf;     // [n] forward segment products for this SEG
   const c2_t<T>* gb;     // [n] backward segment products for this SEG
   const c2_t<T>* ptab;   // [2][16][16] carry tables Pf, Pb for this SEG
-  // sub-step N (FIRST)
-  const T* V;            // full potential or nullptr (separable harmonic trap)
+  // sub-step N (FIRST).  FP64 state: exp(-i dt V) (real time) or exp(-dt V)
+  // (imaginary time, real part only) as a per-point factor array fV, or for
+  // the separable harmonic trap as per-axis factors fx[i] fy[j] fz[k], and
+  // dtg = dt g for the nonlinear part.  FP32 state: the potential V (array) or
+  // vx[i] + vy[j] + vz[k], and dt, g: the phase angle is formed per point,
+  // because FP32-rounded factors would be applied identically every step and
+  // their |F| - 1 ~ 1e-7 would add up step after step.
+  const c2_t<T>* fV;
+  const c2_t<T>* fx; const c2_t<T>* fy; const c2_t<T>* fz;
+  T dtg;
+  const T* V;
   const T* vx; const T* vy; const T* vz;
   T dt, g;
   const double* scale_in;
@@ -70,18 +79,63 @@ struct Sweep2Args {
   double* scale_out;
 };
 
+// Sub-step N at one point: p <- F exp(-i a) p (real time) or F exp(-a) p
+// (imaginary time), where F = exp(-i dt V) or exp(-dt V) is the precomputed
+// potential factor and a = dt g |p|^2.  For |a| < 1/8 the exponential of the
+// nonlinear part is its Taylor series (sin to a^11, cos to a^12, exp to
+// a^13): the first omitted term is below 1.2e-21 relative, far under FP64
+// rounding; larger |a| takes the library sincos/exp.
 template <typename T, bool IMAG>
-__device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, T V, T dt, T g) {
-  const T dens = p.x * p.x + p.y * p.y;
-  const T th = dt * (V + g * dens);
+__device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
+  const T a = dtg * (p.x * p.x + p.y * p.y);
+  if (IMAG) {
+    T e;
+    if (fabs(a) < T(0.125)) {
+      const T m = -a;
+      e = T(1) + m * (T(1) + m * (T(1.0 / 2) + m * (T(1.0 / 6) + m * (T(1.0 / 24) + m * (T(1.0 / 120) +
+          m * (T(1.0 / 720) + m * (T(1.0 / 5040) + m * (T(1.0 / 40320) + m * (T(1.0 / 362880) +
+          m * (T(1.0 / 3628800) + m * (T(1.0 / 39916800) + m * (T(1.0 / 479001600) + m * T(1.0 / 6227020800.0)))))))))))));
+    } else {
+      e = exp(-a);
+    }
+    const T f = F.x * e;
+    return mk<T>(f * p.x, f * p.y);
+  } else {
+    T sn, cs;
+    if (fabs(a) < T(0.125)) {
+      const T a2 = a * a;
+      sn = a * (T(1) + a2 * (T(-1.0 / 6) + a2 * (T(1.0 / 120) + a2 * (T(-1.0 / 5040) + a2 * (T(1.0 / 362880) +
+               a2 * T(-1.0 / 39916800))))));
+      cs = T(1) + a2 * (T(-1.0 / 2) + a2 * (T(1.0 / 24) + a2 * (T(-1.0 / 720) + a2 * (T(1.0 / 40320) +
+               a2 * (T(-1.0 / 3628800) + a2 * T(1.0 / 479001600))))));
+    } else {
+      sincos(a, &sn, &cs);
+    }
+    // w = F exp(-i a) = (cs F.x + sn F.y) + i (cs F.y - sn F.x); return w p
+    const c2_t<T> w = mk<T>(cs * F.x + sn * F.y, cs * F.y - sn * F.x);
+    return mk<T>(w.x * p.x - w.y * p.y, w.x * p.y + w.y * p.x);
+  }
+}
+
+// FP32 state: p <- exp(-i th) p or exp(-th) p with th = dt (V + g |p|^2)
+// formed per point (library sincos / exp of the state precision).
+template <typename T, bool IMAG>
+__device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
+  const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
   if (IMAG) {
     const T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
-  } else {
-    T s, c;
-    sincos(th, &s, &c);
-    return mk<T>(c * p.x + s * p.y, c * p.y - s * p.x);  // exp(-i th) p
   }
+  T s, c;
+  sincos(th, &s, &c);
+  return mk<T>(c * p.x + s * p.y, c * p.y - s * p.x);
+}
+
+// product of two potential factors (real in imaginary time)
+template <typename T, bool IMAG>
+__device__ __forceinline__ c2_t<T> fac_mul(c2_t<T> a, c2_t<T> b) {
+  if (IMAG) return mk<T>(a.x * b.x, T(0));
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
 // a * b for the coefficient type: complex in real time, real in imaginary time
@@ -349,10 +403,13 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   for (int c = s; c < 32; c += nwarps) {
     const bool line_ok = c < nl;
     const int gbase = (L0 + c) * G.nx;
+    constexpr bool kFactors = sizeof(T) == 8;  // FP64: precomputed potential factors
+    c2 fline = mk<T>(1, 0);
     T vline = T(0);
-    if (FIRST && line_ok && !A.V) {
+    if (FIRST && line_ok) {
       const int L = L0 + c;
-      vline = A.vy[L % G.ny] + A.vz[L / G.ny];
+      if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[L % G.ny], A.fz[L / G.ny]);
+      if (!kFactors && !A.V) vline = A.vy[L % G.ny] + A.vz[L / G.ny];
     }
     const c2* in = A.src ? A.src : A.psi;
     for (int q0 = 0; q0 < per_line; q0 += 4) {
@@ -369,8 +426,12 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
         c2 w = v[i];
         if (FIRST && line_ok && k >= 1 && k <= M) {
           w.x *= scl; w.y *= scl;
-          const T Vk = A.V ? A.V[gbase + k] : A.vx[k] + vline;
-          w = phase_N<T, IMAG>(w, Vk, A.dt, A.g);
+          if (kFactors) {
+            const c2 F = A.fV ? A.fV[gbase + k] : fac_mul<T, IMAG>(A.fx[k], fline);
+            w = phase_N<T, IMAG>(w, F, A.dtg);
+          } else {
+            w = phase_direct<T, IMAG>(w, A.V ? A.V[gbase + k] : A.vx[k] + vline, A.dt, A.g);
+          }
         }
         tile[k * kTilePitch + c] = w;
       }
@@ -434,9 +495,12 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     c2* line = A.psi + base;
     const int k0 = 1 + lane * SEG;
     const int ta = L % G.ny, tb = L / G.ny;
+    constexpr bool kFactors = sizeof(T) == 8;  // FP64: precomputed potential factors
+    c2 fline = mk<T>(1, 0);
     T vline = T(0), scl = T(1);
     if (FIRST) {
-      if (A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
+      if (kFactors && A.fV == nullptr) fline = fac_mul<T, IMAG>(A.fy[ta], A.fz[tb]);
+      if (!kFactors && A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
       if (A.scale_in) scl = (T)(*A.scale_in);
     }
     const c2* in = (A.src ? A.src : A.psi) + base;
@@ -449,8 +513,12 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
         v = in[k];
         if (FIRST) {
           v.x *= scl; v.y *= scl;
-          const T Vk = A.V ? A.V[base + k] : (A.vx[k] + vline);
-          v = phase_N<T, IMAG>(v, Vk, A.dt, A.g);
+          if (kFactors) {
+            const c2 F = A.fV ? A.fV[base + k] : fac_mul<T, IMAG>(A.fx[k], fline);
+            v = phase_N<T, IMAG>(v, F, A.dtg);
+          } else {
+            v = phase_direct<T, IMAG>(v, A.V ? A.V[base + k] : A.vx[k] + vline, A.dt, A.g);
+          }
         }
       }
       p[j] = v;
