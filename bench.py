@@ -238,6 +238,7 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             p = gpe.Propagator(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"], precision=prec,
                                stream=stream)
+            p.autotune(imag=True, cache=False)   # kernel shapes for this grid (untimed)
             p.set_state(torch.tensor(phi0, device="cuda"))
         return p
 
@@ -276,9 +277,10 @@ def run_ours(args):
             # per-kernel durations, same state and sizes, right after the timed region
             kms = p.time_sweeps(True, 64)
             ob = p.observables()
+            shp = p.shapes()
         p.close()
         results[prec] = {"total_s": total_s, "ms": ms, "launches": launches, "clocks": clk.summary(),
-                         "kernel_ms": kms, "obs": ob}
+                         "kernel_ms": kms, "obs": ob, "shapes": shp}
     # ---- batched form: 64 independent 2d real-time runs (sizes from
     # {128..512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1, kappa ~ U[1, 2]),
     # each from its g = 0 trap ground state (an interaction quench)
@@ -344,6 +346,7 @@ def run_ours(args):
                 q.step_imag(args.quench_imag_steps)
                 q.set_dt(2e-4)
                 q.set_g(40.0)
+                q.autotune(imag=False, cache=False)
                 ob0 = q.observables()
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(args.steps)]

@@ -213,6 +213,23 @@ int gp_batch_destroy(gp_batch* b);
 int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const double nkl[3], double g,
                            gp_precision prec, const void* psi, const double* V, double* out, void* stream);
 
+/* ---- Kernel shapes and the autotuner.
+ * A handle's sweeps run with a segment length per line (seg_x for x lines,
+ * seg_c for y/z lines: 1..32, a power of two) and, for x lines in 2d/3d, an
+ * optional shared-memory tile (tile_x); shape 0 means the thread-per-line
+ * kernels used for lines longer than 514 points.  Defaults are set by
+ * gp_init.  gp_autotune times every valid shape of the x sweep and of the y/z
+ * sweeps on this handle's grid (2 warm-up + nsteps timed steps each, imaginary
+ * time if imag != 0; 1 <= nsteps <= 256), keeps the fastest, restores the
+ * state, and remembers the result for this process (a later call for the same
+ * grid, precision and mode applies it without timing unless best_ms != NULL,
+ * which receives the best mean x-sweep and y+z-sweep times in ms).  Uses one
+ * temporary state-sized device buffer.  gp_set_shapes applies shapes (e.g.
+ * from a cache file); GP_ERR_INVALID if they do not fit the grid. */
+int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms);
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c);
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c);
+
 /* Grid queries. */
 long gp_npoints(const gp_handle* h);
 int gp_precision_of(const gp_handle* h);

@@ -9,7 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <complex>
 #include <cstdlib>
 #include <cstring>
@@ -558,6 +562,130 @@ int gp_adjoint_backward(gp_handle* h, const void* lambda_T, int lambda_on_device
   if (dJdg) *dJdg = h->obs_host[0];
   if (!std::isfinite(h->obs_host[0])) return fail(GP_ERR_NONFINITE, "gp_adjoint_backward: non-finite gradient");
   return GP_OK;
+}
+
+namespace {
+
+bool shapes_valid(const gp_handle* h, int tile_x, int seg_x, int seg_c) {
+  const int M0 = h->n[0] - 2;
+  int Mc = 0;
+  for (int d = 1; d < h->dim; ++d) Mc = std::max(Mc, h->n[d] - 2);
+  if (seg_x != 0) {
+    if (seg_index(seg_x) < 0) return false;
+    if (tile_x) {
+      if (h->dim < 2 || seg_x < 4 || (M0 + seg_x - 1) / seg_x > 16) return false;
+      if ((36L * h->n[0] + 512) * (long)h->esize > 200L * 1024) return false;
+    } else if (seg_x > 16 || 32 * seg_x < M0) {
+      return false;
+    }
+  } else if (tile_x) {
+    return false;
+  }
+  if (h->dim > 1 && seg_c != 0 && (seg_index(seg_c) < 0 || seg_c < 4 || (Mc + seg_c - 1) / seg_c > 16)) return false;
+  if (h->dim == 1 && seg_c != 0 && (seg_index(seg_c) < 0 || seg_c < 4)) return false;
+  return true;
+}
+
+struct TuneKey {
+  int dim, n0, n1, n2, prec, imag;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dim, n0, n1, n2, prec, imag) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.imag);
+  }
+};
+std::map<TuneKey, std::array<int, 3>> g_tuned;  // process-wide results
+std::mutex g_tune_mutex;
+
+}  // namespace
+
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
+  if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
+  drop_graphs(h);
+  h->tile_x = tile_x != 0;
+  h->seg_x = seg_x;
+  h->seg_c = seg_c;
+  return GP_OK;
+}
+
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_get_shapes: NULL handle");
+  if (tile_x) *tile_x = h->tile_x ? 1 : 0;
+  if (seg_x) *seg_x = h->seg_x;
+  if (seg_c) *seg_c = h->seg_c;
+  return GP_OK;
+}
+
+int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_autotune: NULL handle");
+  if (nsteps < 1 || nsteps > 256) return fail(GP_ERR_INVALID, "gp_autotune: nsteps must be in [1, 256]");
+  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], h->prec, imag != 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end() && !best_ms) return gp_set_shapes(h, it->second[0], it->second[1], it->second[2]);
+  }
+  // candidate shapes for the x sweep and for the y/z sweeps (timed separately)
+  std::vector<std::array<int, 2>> xs;  // (tile, seg)
+  for (int sg : {4, 8, 16, 32})
+    if (shapes_valid(h, 1, sg, h->seg_c)) xs.push_back({1, sg});
+  for (int sg : {1, 2, 4, 8, 16})
+    if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg}); break; }
+  std::vector<int> cs;
+  if (h->dim > 1)
+    for (int sg : {4, 8, 16, 32})
+      if (shapes_valid(h, h->tile_x, h->seg_x, sg)) cs.push_back(sg);
+  const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c;
+  void* saved = nullptr;
+  GP_CUDA(cudaMalloc(&saved, (size_t)h->np * h->esize));
+  int rc = join_in(h);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(saved, h->psi, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
+    if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  auto time_shape = [&](int t, int sx, int sc, double* ms3) -> int {
+    h->tile_x = t != 0;
+    h->seg_x = sx;
+    h->seg_c = sc;
+    double warm[3];
+    int r = h->prec == GP_F64 ? time_steps_f64(h, imag != 0, 2, warm) : time_steps_f32(h, imag != 0, 2, warm);
+    if (r) return r;
+    return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms3) : time_steps_f32(h, imag != 0, nsteps, ms3);
+  };
+  double bx = 1e30, bc = 1e30;
+  int best_t = keep_t, best_x = keep_x, best_c = keep_c;
+  for (const auto& c : xs) {
+    if (rc) break;
+    double ms[3];
+    rc = time_shape(c[0], c[1], keep_c, ms);
+    if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; }
+  }
+  for (int sc : cs) {
+    if (rc) break;
+    double ms[3];
+    rc = time_shape(best_t, best_x, sc, ms);
+    const double t = ms[1] + ms[2];
+    if (!rc && t < bc) { bc = t; best_c = sc; }
+  }
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(h->psi, saved, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->work);
+    if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(saved);
+  if (rc) {
+    h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c;
+    return rc;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = {best_t, best_x, best_c};
+  }
+  if (best_ms) {
+    best_ms[0] = xs.empty() ? 0.0 : bx;
+    best_ms[1] = cs.empty() ? 0.0 : bc;
+  }
+  if ((rc = gp_set_shapes(h, best_t, best_x, best_c))) return rc;
+  return join_out(h);
 }
 
 int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device) {

@@ -34,6 +34,7 @@ ABI_SYMBOLS = (
     "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
+    "gp_autotune", "gp_set_shapes", "gp_get_shapes",
 )
 
 
@@ -74,6 +75,9 @@ def load(path: str = LIB_PATH):
     lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
+    lib.gp_autotune.argtypes = [_vp, I, I, ctypes.POINTER(D)]
+    lib.gp_set_shapes.argtypes = [_vp, I, I, I]
+    lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
     lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
@@ -171,6 +175,27 @@ def gp_observables_noalloc(dim, n, dx, nkl, g, prec, psi_ptr, V_ptr, out_ptr, st
     nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
     return _check(load().gp_observables_noalloc(int(dim), n3, dx3, nkl3, float(g), int(prec), psi_ptr, V_ptr,
                                                 out_ptr, stream))
+
+
+def gp_autotune(h, imag, nsteps=8, timings=False):
+    """Times the valid kernel shapes and keeps the fastest; with timings=True
+    returns (best x-sweep ms, best y+z-sweep ms)."""
+    if timings:
+        ms = (ctypes.c_double * 2)()
+        _check(load().gp_autotune(h, int(bool(imag)), int(nsteps), ms))
+        return float(ms[0]), float(ms[1])
+    _check(load().gp_autotune(h, int(bool(imag)), int(nsteps), None))
+    return None
+
+
+def gp_set_shapes(h, tile_x, seg_x, seg_c):
+    return _check(load().gp_set_shapes(h, int(tile_x), int(seg_x), int(seg_c)))
+
+
+def gp_get_shapes(h):
+    t, x, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().gp_get_shapes(h, ctypes.byref(t), ctypes.byref(x), ctypes.byref(c)))
+    return {"tile_x": t.value, "seg_x": x.value, "seg_c": c.value}
 
 
 def gp_adjoint_forward(h, nsteps, ckpt_every):
@@ -328,6 +353,45 @@ class Propagator:
 
     def time_sweeps(self, imag, nsteps):
         return gp_time_sweeps(self.h, imag, nsteps)
+
+    def shapes(self):
+        return gp_get_shapes(self.h)
+
+    def autotune(self, imag, nsteps=8, cache=True):
+        """Picks the fastest kernel shapes for this grid (see gp_autotune).
+        With ``cache`` the result is kept in a JSON file keyed by GPU name,
+        grid, precision and mode ($GPE_TUNE_CACHE, default
+        ~/.cache/gpe_gb300/shapes.json), so later processes skip the timing."""
+        import json
+        import torch
+        path = os.environ.get("GPE_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gpe_gb300",
+                                                             "shapes.json"))
+        key = "|".join([torch.cuda.get_device_name(), "x".join(map(str, self.n)), self.precision,
+                        "imag" if imag else "real"])
+        table = {}
+        if cache and os.path.exists(path):
+            try:
+                with open(path) as f:
+                    table = json.load(f)
+            except Exception:
+                table = {}
+        if cache and key in table:
+            s = table[key]
+            gp_set_shapes(self.h, s["tile_x"], s["seg_x"], s["seg_c"])
+            return s
+        gp_autotune(self.h, imag, nsteps)
+        s = gp_get_shapes(self.h)
+        if cache:
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                table[key] = s
+                tmp = path + f".tmp{os.getpid()}"
+                with open(tmp, "w") as f:
+                    json.dump(table, f, indent=1, sort_keys=True)
+                os.replace(tmp, path)
+            except OSError:
+                pass
+        return s
 
     def observables(self, density=False):
         den = None

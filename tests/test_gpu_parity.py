@@ -257,3 +257,26 @@ def test_long_lines_use_fallback_kernels(G):
     ref = O.run(gr, phi0, False, 3)
     assert rel_l2(p.get_state(device=False), ref) <= 1e-13
     p.close()
+
+
+def test_autotune_picks_valid_shapes_and_keeps_parity(G, tmp_path, monkeypatch):
+    import json
+    monkeypatch.setenv("GPE_TUNE_CACHE", str(tmp_path / "shapes.json"))
+    dim, n, dx = 3, [40, 33, 24], [0.25, 0.3, 0.35]
+    nkl = [1.0, 1.4, 1.8]
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=19, noise=1e-3)
+    for prec, tol in (("f64", 1e-13), ("f32", 3e-6)):
+        p, gr = make(G, dim, n, dx, 1e-3, nkl, 20.0, prec=prec)
+        s = p.autotune(imag=True, nsteps=2)
+        assert s == p.shapes()
+        table = json.load(open(tmp_path / "shapes.json"))
+        assert any(k.endswith(f"{prec}|imag") for k in table)
+        p.set_state(phi0)
+        p.step_imag(40)
+        assert rel_l2(p.get_state(device=False).astype(np.complex128), O.run(gr, phi0, True, 40)) <= tol
+        q, _ = make(G, dim, n, dx, 1e-3, nkl, 20.0, prec=prec)
+        assert q.autotune(imag=True) == s          # from the cache file, no timing
+        with pytest.raises(G.GPError):
+            G.gp_set_shapes(q.h, 1, 3, 8)         # 3 is not a segment length
+        p.close()
+        q.close()
