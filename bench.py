@@ -56,7 +56,25 @@ def parse():
     ap.add_argument("--no-quench", action="store_true", help="skip the 256^3 real-time form")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
+    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint"],
+                    help="time one form only (for profiling); the other forms are reported as null")
     return ap.parse_args()
+
+
+def replica_throughput(points_per_rank, seconds, device="cpu"):
+    """Whole-job throughput of independent replicas: the points all ranks
+    processed divided by the slowest rank's time (one process per GPU; no
+    collective on the data path, only this reduction of the timings)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return points_per_rank / seconds, seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    n = torch.tensor([float(points_per_rank)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()) / float(t.item()), float(t.item())
 
 
 def dist_env():
@@ -253,7 +271,7 @@ def run_ours(args):
                 mu[prec] = p.observables()
             p.close()
     # ---- timed forms
-    for prec in ("f64", "f32"):
+    for prec in (("f64", "f32") if not args.no_headline else ()):
         p = make(prec)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
@@ -273,14 +291,15 @@ def run_ours(args):
                 barrier()
             launches = gpe.gp_kernel_launches() - l0
             ms = [a.elapsed_time(b) for a, b in ev]
-            total_s = max_over_ranks(sum(ms) / 1e3)
+            # whole-job throughput over replicas: all ranks' points / slowest rank's time
+            value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
             # per-kernel durations, same state and sizes, right after the timed region
             kms = p.time_sweeps(True, 64)
             ob = p.observables()
             shp = p.shapes()
         p.close()
-        results[prec] = {"total_s": total_s, "ms": ms, "launches": launches, "clocks": clk.summary(),
-                         "kernel_ms": kms, "obs": ob, "shapes": shp}
+        results[prec] = {"total_s": total_s, "value": value, "ms": ms, "launches": launches,
+                         "clocks": clk.summary(), "kernel_ms": kms, "obs": ob, "shapes": shp}
     # ---- batched form: 64 independent 2d real-time runs (sizes from
     # {128..512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1, kappa ~ U[1, 2]),
     # each from its g = 0 trap ground state (an interaction quench)
@@ -301,7 +320,7 @@ def run_ours(args):
 
     bres = {}
     bmu = {}
-    for prec in ("f64", "f32"):
+    for prec in (("f64", "f32") if not args.no_batched else ()):
         bb = make_batch(prec)
         with torch.cuda.stream(stream):
             if not args.no_mu_check:
@@ -416,6 +435,15 @@ def run_ours(args):
                           "value": world * 1000 * anp / ((tf + tb) * 1e-3),
                           "backward_over_forward": tb / tf, "dJdg": dJdg}
 
+    if args.only and args.only != "headline":
+        # profiling run of a single form: report it and stop
+        if rank == 0:
+            print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
+                              "batched": bres or None}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
     # ---- end to end through the public API with host buffers (FP32 form)
     e2e = None
     p = make("f32")
@@ -462,7 +490,7 @@ def run_ours(args):
     forms = {}
     for prec in ("f64", "f32"):
         r = results[prec]
-        v = world * args.steps * args.inner * np_ / r["total_s"]
+        v = r["value"]
         forms[prec] = {"value": v, "ms_per_step": 1e3 * r["total_s"] / args.steps,
                        "mu": r["obs"]["mu"], "roofline": roofline(prec)}
     mu_err = abs(mu["f32"]["mu"] - mu["f64"]["mu"]) if mu else None
@@ -501,7 +529,7 @@ def run_ours(args):
                                      "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "
                                      "point-steps/s; FP32 forward, FP64 gradient accumulation",
                          "f32": ares.get("f32")} if ares else None),
-            "batched": {"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
+            "batched": ({"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
                                     "(SplitMix64 seed 1712), dx=0.1, dt=5e-4, g~U[0,50], nu=1, kappa~U[1,2], "
                                     "g=0 trap ground state quenched; one launch per sweep and segment class, "
                                     "graph-captured; L2 flushed before every timed step",
@@ -509,7 +537,7 @@ def run_ours(args):
                         "value_f32": bres["f32"]["value"], "value_f64": bres["f64"]["value"],
                         "speedup_f32_vs_f64": bres["f32"]["value"] / bres["f64"]["value"],
                         "ms_per_step_f32": bres["f32"]["ms_per_step"], "gpu_launches_f32": bres["f32"]["gpu_launches"],
-                        "max_abs_mu_diff_f32_vs_f64_after_400_steps": bmu_err},
+                        "max_abs_mu_diff_f32_vs_f64_after_400_steps": bmu_err} if bres else None),
         },
     }
     print(json.dumps(line), flush=True)
@@ -519,6 +547,16 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.only:
+        args.no_quench = args.only != "quench256"
+        args.no_adjoint = args.only != "adjoint"
+        args.no_batched = args.only != "batched"
+        args.no_headline = args.only != "headline"
+        if args.only != "headline":
+            args.no_cpu_baseline = True
+            args.no_mu_check = True
+    else:
+        args.no_headline = False
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -215,9 +215,10 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
 
 /* ---- Kernel shapes and the autotuner.
  * A handle's sweeps run with a segment length per line (seg_x for x lines,
- * seg_c for y/z lines: 1..32, a power of two) and, for x lines in 2d/3d, an
- * optional shared-memory tile (tile_x); shape 0 means the thread-per-line
- * kernels used for lines longer than 514 points.  Defaults are set by
+ * seg_c for y/z lines: 1..32, a power of two), for x lines in 2d/3d an
+ * optional shared-memory tile (tile_x), and for y/z lines whether the input
+ * segment is kept in registers (keep_c) or streamed and read again; shape 0
+ * means the thread-per-line kernels used for lines longer than 514 points.  Defaults are set by
  * gp_init.  gp_autotune times every valid shape of the x sweep and of the y/z
  * sweeps on this handle's grid (2 warm-up + nsteps timed steps each, imaginary
  * time if imag != 0; 1 <= nsteps <= 256), keeps the fastest, restores the
@@ -227,8 +228,8 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
  * temporary state-sized device buffer.  gp_set_shapes applies shapes (e.g.
  * from a cache file); GP_ERR_INVALID if they do not fit the grid. */
 int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms);
-int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c);
-int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c);
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int keep_c);
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* keep_c);
 
 /* Grid queries. */
 long gp_npoints(const gp_handle* h);

@@ -227,6 +227,7 @@ void choose_shapes(gp_handle* h) {
   int sc = env_int("GPE_SEG_YZ", tile_seg(Mc));
   if (sc > 0 && (seg_index(sc) < 0 || sc < 4 || (Mc + sc - 1) / sc > 16)) sc = 0;
   h->seg_c = sc;
+  h->keep_c = env_int("GPE_KEEP", 1) != 0;
 }
 
 }  // namespace
@@ -592,26 +593,28 @@ struct TuneKey {
     return std::tie(dim, n0, n1, n2, prec, imag) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.imag);
   }
 };
-std::map<TuneKey, std::array<int, 3>> g_tuned;  // process-wide results
+std::map<TuneKey, std::array<int, 4>> g_tuned;  // process-wide results
 std::mutex g_tune_mutex;
 
 }  // namespace
 
-int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c) {
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int keep_c) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
   drop_graphs(h);
   h->tile_x = tile_x != 0;
   h->seg_x = seg_x;
   h->seg_c = seg_c;
+  h->keep_c = keep_c != 0;
   return GP_OK;
 }
 
-int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c) {
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* keep_c) {
   if (!h) return fail(GP_ERR_INVALID, "gp_get_shapes: NULL handle");
   if (tile_x) *tile_x = h->tile_x ? 1 : 0;
   if (seg_x) *seg_x = h->seg_x;
   if (seg_c) *seg_c = h->seg_c;
+  if (keep_c) *keep_c = h->keep_c;
   return GP_OK;
 }
 
@@ -622,7 +625,9 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
-    if (it != g_tuned.end() && !best_ms) return gp_set_shapes(h, it->second[0], it->second[1], it->second[2]);
+    if (it != g_tuned.end() && !best_ms) {
+      return gp_set_shapes(h, it->second[0], it->second[1], it->second[2], it->second[3]);
+    }
   }
   // candidate shapes for the x sweep and for the y/z sweeps (timed separately)
   std::vector<std::array<int, 2>> xs;  // (tile, seg)
@@ -630,11 +635,14 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     if (shapes_valid(h, 1, sg, h->seg_c)) xs.push_back({1, sg});
   for (int sg : {1, 2, 4, 8, 16})
     if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg}); break; }
-  std::vector<int> cs;
+  std::vector<std::array<int, 2>> cs;  // (seg, keep input in registers)
   if (h->dim > 1)
     for (int sg : {4, 8, 16, 32})
-      if (shapes_valid(h, h->tile_x, h->seg_x, sg)) cs.push_back(sg);
-  const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c;
+      if (shapes_valid(h, h->tile_x, h->seg_x, sg)) {
+        if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1});
+        cs.push_back({sg, 0});
+      }
+  const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
   void* saved = nullptr;
   GP_CUDA(cudaMalloc(&saved, (size_t)h->np * h->esize));
   int rc = join_in(h);
@@ -642,29 +650,30 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     cudaError_t e = cudaMemcpyAsync(saved, h->psi, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
-  auto time_shape = [&](int t, int sx, int sc, double* ms3) -> int {
+  auto time_shape = [&](int t, int sx, int sc, int kc, double* ms3) -> int {
     h->tile_x = t != 0;
     h->seg_x = sx;
     h->seg_c = sc;
+    h->keep_c = kc;
     double warm[3];
     int r = h->prec == GP_F64 ? time_steps_f64(h, imag != 0, 2, warm) : time_steps_f32(h, imag != 0, 2, warm);
     if (r) return r;
     return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms3) : time_steps_f32(h, imag != 0, nsteps, ms3);
   };
   double bx = 1e30, bc = 1e30;
-  int best_t = keep_t, best_x = keep_x, best_c = keep_c;
+  int best_t = keep_t, best_x = keep_x, best_c = keep_c, best_k = keep_k;
   for (const auto& c : xs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(c[0], c[1], keep_c, ms);
+    rc = time_shape(c[0], c[1], keep_c, keep_k, ms);
     if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; }
   }
-  for (int sc : cs) {
+  for (const auto& c : cs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(best_t, best_x, sc, ms);
+    rc = time_shape(best_t, best_x, c[0], c[1], ms);
     const double t = ms[1] + ms[2];
-    if (!rc && t < bc) { bc = t; best_c = sc; }
+    if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; }
   }
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(h->psi, saved, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
@@ -673,18 +682,18 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   }
   cudaFree(saved);
   if (rc) {
-    h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c;
+    h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c; h->keep_c = keep_k;
     return rc;
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[key] = {best_t, best_x, best_c};
+    g_tuned[key] = {best_t, best_x, best_c, best_k};
   }
   if (best_ms) {
     best_ms[0] = xs.empty() ? 0.0 : bx;
     best_ms[1] = cs.empty() ? 0.0 : bc;
   }
-  if ((rc = gp_set_shapes(h, best_t, best_x, best_c))) return rc;
+  if ((rc = gp_set_shapes(h, best_t, best_x, best_c, best_k))) return rc;
   return join_out(h);
 }
 

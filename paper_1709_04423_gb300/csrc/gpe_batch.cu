@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(512) batch_y_kernel(const BatchRun<T>* __restr
   A.gf = R.coef[1] + R.ny;
   A.gb = R.coef[1] + 2 * R.ny;
   A.ptab = R.ptab[1];
-  colsweep_body<T, false, false, SEG>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
+  colsweep_body<T, false, false, SEG, (SEG * sizeof(T) <= 64)>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
 }
 
 // Segment-length classes: a line of n points goes to the first class whose

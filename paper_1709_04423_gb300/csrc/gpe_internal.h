@@ -85,6 +85,7 @@ struct gp_handle {
   // kernel) and whether the x lines are staged through a shared-memory tile
   int seg_x = 0, seg_c = 0;
   bool tile_x = false;
+  int keep_c = 1;  // y/z sweeps keep their input segment in registers (when short enough)
   double* scale = nullptr;   // [2] renormalisation slots
   double* partials = nullptr;
   unsigned int* counter = nullptr;

@@ -61,7 +61,7 @@ void launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
 }
 
 // ---- segmented y/z sweep (registers, coefficients in shared memory)
-template <typename T, bool IMAG, bool LAST, int SEG>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
 void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
@@ -69,21 +69,23 @@ void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
   static bool attr_set = false;  // static + dynamic shared memory can pass 48 KB
   if (!attr_set) {
-    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          64 * 1024);
     attr_set = true;
   }
-  colsweep_kernel<T, IMAG, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
+  colsweep_kernel<T, IMAG, LAST, SEG, KEEP><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
 }
 
+// keep = 1: input segment in registers (only for short segments); 0: streamed
 template <typename T, bool IMAG, bool LAST>
-void launch_c_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+void launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s) {
+  const bool k = keep && seg * (int)sizeof(T) <= 64;
   switch (seg) {
-    case 4: launch_c<T, IMAG, LAST, 4>(a, s); break;
-    case 8: launch_c<T, IMAG, LAST, 8>(a, s); break;
-    case 16: launch_c<T, IMAG, LAST, 16>(a, s); break;
-    default: launch_c<T, IMAG, LAST, 32>(a, s); break;
+    case 4: k ? launch_c<T, IMAG, LAST, 4, true>(a, s) : launch_c<T, IMAG, LAST, 4, false>(a, s); break;
+    case 8: k ? launch_c<T, IMAG, LAST, 8, true>(a, s) : launch_c<T, IMAG, LAST, 8, false>(a, s); break;
+    case 16: k ? launch_c<T, IMAG, LAST, 16, true>(a, s) : launch_c<T, IMAG, LAST, 16, false>(a, s); break;
+    default: launch_c<T, IMAG, LAST, 32, false>(a, s); break;
   }
 }
 
@@ -173,10 +175,10 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
       }
     } else {
       if (imag) {
-        if (last) launch_c_seg<T, true, true>(seg, a, h->work);
-        else launch_c_seg<T, true, false>(seg, a, h->work);
+        if (last) launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work);
+        else launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work);
       } else {
-        launch_c_seg<T, false, false>(seg, a, h->work);
+        launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
       }
     }
     return;
@@ -342,7 +344,7 @@ void enqueue_adj_sweep(gp_handle* h, int d) {
   a.ptab = (const c2_t<T>*)h->ctab[MODE_REAL_ADJ][d] + (size_t)si * 512;
   if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work);
   else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work);
-  else launch_c_seg<T, false, false>(seg, a, h->work);
+  else launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
 }
 
 template <typename T>

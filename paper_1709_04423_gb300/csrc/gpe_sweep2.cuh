@@ -307,7 +307,7 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
 // Body shared with the batched kernels: lines L0 .. L0+31 of the grid
 // described by A; nseg = ceil((n-2)/SEG) warps take part, the other warps of
 // the block (if any) only join the barriers.
-template <typename T, bool IMAG, bool LAST, int SEG>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP = (SEG * sizeof(T) <= 64)>
 __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
                                               c2_t<T> (*cb)[33], double* red_smem) {
   using c2 = c2_t<T>;
@@ -322,9 +322,9 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   const int k0 = 1 + s * SEG;
   load_coefs<T>(A, sc, n);
   c2* line = A.psi + (active ? line_base32(G, L) : 0);
-  // keep the input segment in registers when it is small; otherwise stream it
-  // in the forward pass and read it again (from L2) for u = p - z
-  constexpr bool KEEP = SEG * sizeof(T) <= 64;
+  // KEEP: the input segment stays in registers; otherwise it is streamed in
+  // the forward pass and read again (from L2) for u = p - z, which halves the
+  // registers per thread and doubles the blocks an SM can hold
   c2 p[KEEP ? SEG : 1];
   if constexpr (KEEP) {
 #pragma unroll
@@ -369,12 +369,13 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
 }
 
-template <typename T, bool IMAG, bool LAST, int SEG>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
 __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
   extern __shared__ __align__(16) unsigned char csmem_raw[];
   __shared__ c2_t<T> cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
-  colsweep_body<T, IMAG, LAST, SEG>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb, red_smem);
+  colsweep_body<T, IMAG, LAST, SEG, KEEP>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb,
+                                          red_smem);
 }
 
 // ---------------------------------------------------------------- x sweep (2d/3d)

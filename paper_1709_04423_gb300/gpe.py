@@ -76,8 +76,8 @@ def load(path: str = LIB_PATH):
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
     lib.gp_autotune.argtypes = [_vp, I, I, ctypes.POINTER(D)]
-    lib.gp_set_shapes.argtypes = [_vp, I, I, I]
-    lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.gp_set_shapes.argtypes = [_vp, I, I, I, I]
+    lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
     lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
@@ -188,14 +188,14 @@ def gp_autotune(h, imag, nsteps=8, timings=False):
     return None
 
 
-def gp_set_shapes(h, tile_x, seg_x, seg_c):
-    return _check(load().gp_set_shapes(h, int(tile_x), int(seg_x), int(seg_c)))
+def gp_set_shapes(h, tile_x, seg_x, seg_c, keep_c=1):
+    return _check(load().gp_set_shapes(h, int(tile_x), int(seg_x), int(seg_c), int(keep_c)))
 
 
 def gp_get_shapes(h):
-    t, x, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().gp_get_shapes(h, ctypes.byref(t), ctypes.byref(x), ctypes.byref(c)))
-    return {"tile_x": t.value, "seg_x": x.value, "seg_c": c.value}
+    t, x, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().gp_get_shapes(h, ctypes.byref(t), ctypes.byref(x), ctypes.byref(c), ctypes.byref(k)))
+    return {"tile_x": t.value, "seg_x": x.value, "seg_c": c.value, "keep_c": k.value}
 
 
 def gp_adjoint_forward(h, nsteps, ckpt_every):
@@ -377,7 +377,7 @@ class Propagator:
                 table = {}
         if cache and key in table:
             s = table[key]
-            gp_set_shapes(self.h, s["tile_x"], s["seg_x"], s["seg_c"])
+            gp_set_shapes(self.h, s["tile_x"], s["seg_x"], s["seg_c"], s.get("keep_c", 1))
             return s
         gp_autotune(self.h, imag, nsteps)
         s = gp_get_shapes(self.h)

@@ -223,6 +223,7 @@ SHAPES = [
     {"GPE_SEG_X": "4", "GPE_SEG_YZ": "4"},
     {"GPE_SEG_X": "16", "GPE_SEG_YZ": "8"},
     {"GPE_SEG_X": "32", "GPE_SEG_YZ": "32"},
+    {"GPE_SEG_YZ": "8", "GPE_KEEP": "0"},                      # y/z input streamed and re-read
 ]
 
 
@@ -277,6 +278,6 @@ def test_autotune_picks_valid_shapes_and_keeps_parity(G, tmp_path, monkeypatch):
         q, _ = make(G, dim, n, dx, 1e-3, nkl, 20.0, prec=prec)
         assert q.autotune(imag=True) == s          # from the cache file, no timing
         with pytest.raises(G.GPError):
-            G.gp_set_shapes(q.h, 1, 3, 8)         # 3 is not a segment length
+            G.gp_set_shapes(q.h, 1, 3, 8, 1)      # 3 is not a segment length
         p.close()
         q.close()
