@@ -216,9 +216,11 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
 /* ---- Kernel shapes and the autotuner.
  * A handle's sweeps run with a segment length per line (seg_x for x lines,
  * seg_c for y/z lines: 1..32, a power of two), for x lines in 2d/3d an
- * optional shared-memory tile (tile_x), and for y/z lines whether the input
- * segment is kept in registers (keep_c) or streamed and read again; shape 0
- * means the thread-per-line kernels used for lines longer than 514 points.  Defaults are set by
+ * optional shared-memory tile (tile_x); flags (GP_SHAPE_*) select whether the
+ * y/z input segment is kept in registers or streamed and read again, and
+ * whether the x and y/z sweeps run as persistent double-buffered kernels
+ * (possible where two 32-line tiles fit in shared memory); shape 0 means the
+ * thread-per-line kernels used for lines longer than 514 points.  Defaults are set by
  * gp_init.  gp_autotune times every valid shape of the x sweep and of the y/z
  * sweeps on this handle's grid (2 warm-up + nsteps timed steps each, imaginary
  * time if imag != 0; 1 <= nsteps <= 256), keeps the fastest, restores the
@@ -227,9 +229,14 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
  * which receives the best mean x-sweep and y+z-sweep times in ms).  Uses one
  * temporary state-sized device buffer.  gp_set_shapes applies shapes (e.g.
  * from a cache file); GP_ERR_INVALID if they do not fit the grid. */
+enum {
+  GP_SHAPE_KEEP_YZ = 1, /* y/z sweeps keep their input segment in registers */
+  GP_SHAPE_PIPE_X = 2,  /* x sweep: persistent double-buffered tile kernel (needs tile_x) */
+  GP_SHAPE_PIPE_YZ = 4  /* y/z sweeps: persistent double-buffered kernel */
+};
 int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms);
-int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int keep_c);
-int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* keep_c);
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags);
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* flags);
 
 /* Grid queries. */
 long gp_npoints(const gp_handle* h);

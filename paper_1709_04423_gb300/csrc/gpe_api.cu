@@ -194,6 +194,14 @@ int env_int(const char* name, int dflt) {
 // line: one warp per line with 32 * seg_x >= n - 2.  Lines longer than 514
 // points use the thread-per-line kernel (shape 0).  GPE_SEG_X, GPE_SEG_YZ and
 // GPE_TILE_X override the defaults (used by the autotuner and the shape tests).
+// two shared-memory stages of a 32-line tile plus the coefficient tables
+// (200 KB of dynamic shared memory leaves room for the kernel's static carry
+// buffers within the 227 KB a block may hold)
+bool pipe_fits(const gp_handle* h, int n, bool axis0) {
+  const long stage = axis0 ? 32L * (n + 1) : (long)n * 33;
+  return (3L * n + 512 + 2 * stage) * (long)h->esize <= 200L * 1024;
+}
+
 int tile_seg(int M) {
   for (int s : {4, 8, 16, 32})
     if ((M + s - 1) / s <= 16) return s;
@@ -228,6 +236,10 @@ void choose_shapes(gp_handle* h) {
   if (sc > 0 && (seg_index(sc) < 0 || sc < 4 || (Mc + sc - 1) / sc > 16)) sc = 0;
   h->seg_c = sc;
   h->keep_c = env_int("GPE_KEEP", 1) != 0;
+  int nmax = 0;
+  for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
+  h->pipe_x = env_int("GPE_PIPE", 0) != 0 && h->tile_x && pipe_fits(h, h->n[0], true);
+  h->pipe_c = env_int("GPE_PIPE", 0) != 0 && h->dim > 1 && sc > 0 && pipe_fits(h, nmax, false);
 }
 
 }  // namespace
@@ -598,23 +610,33 @@ std::mutex g_tune_mutex;
 
 }  // namespace
 
-int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int keep_c) {
+int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
+  const bool px = (flags & GP_SHAPE_PIPE_X) != 0, pc = (flags & GP_SHAPE_PIPE_YZ) != 0;
+  if (px && (!tile_x || seg_x == 0 || !pipe_fits(h, h->n[0], true)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: pipelined x sweep needs the x tile and two stages in shared memory");
+  int nmax = 0;
+  for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
+  if (pc && (h->dim < 2 || seg_c == 0 || !pipe_fits(h, nmax, false)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: pipelined y/z sweeps need two stages in shared memory");
   drop_graphs(h);
   h->tile_x = tile_x != 0;
   h->seg_x = seg_x;
   h->seg_c = seg_c;
-  h->keep_c = keep_c != 0;
+  h->keep_c = (flags & GP_SHAPE_KEEP_YZ) != 0;
+  h->pipe_x = px;
+  h->pipe_c = pc;
   return GP_OK;
 }
 
-int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* keep_c) {
+int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* flags) {
   if (!h) return fail(GP_ERR_INVALID, "gp_get_shapes: NULL handle");
   if (tile_x) *tile_x = h->tile_x ? 1 : 0;
   if (seg_x) *seg_x = h->seg_x;
   if (seg_c) *seg_c = h->seg_c;
-  if (keep_c) *keep_c = h->keep_c;
+  if (flags)
+    *flags = (h->keep_c ? GP_SHAPE_KEEP_YZ : 0) | (h->pipe_x ? GP_SHAPE_PIPE_X : 0) | (h->pipe_c ? GP_SHAPE_PIPE_YZ : 0);
   return GP_OK;
 }
 
@@ -630,19 +652,26 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     }
   }
   // candidate shapes for the x sweep and for the y/z sweeps (timed separately)
-  std::vector<std::array<int, 2>> xs;  // (tile, seg)
+  std::vector<std::array<int, 3>> xs;  // (tile, seg, pipelined)
   for (int sg : {4, 8, 16, 32})
-    if (shapes_valid(h, 1, sg, h->seg_c)) xs.push_back({1, sg});
+    if (shapes_valid(h, 1, sg, h->seg_c)) {
+      xs.push_back({1, sg, 0});
+      if (pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
+    }
   for (int sg : {1, 2, 4, 8, 16})
-    if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg}); break; }
-  std::vector<std::array<int, 2>> cs;  // (seg, keep input in registers)
+    if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }
+  std::vector<std::array<int, 3>> cs;  // (seg, keep input in registers, pipelined)
+  int nmax = 0;
+  for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
   if (h->dim > 1)
     for (int sg : {4, 8, 16, 32})
       if (shapes_valid(h, h->tile_x, h->seg_x, sg)) {
-        if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1});
-        cs.push_back({sg, 0});
+        if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1, 0});
+        cs.push_back({sg, 0, 0});
+        if (pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
       }
   const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
+  const bool keep_px = h->pipe_x, keep_pc = h->pipe_c;
   void* saved = nullptr;
   GP_CUDA(cudaMalloc(&saved, (size_t)h->np * h->esize));
   int rc = join_in(h);
@@ -650,30 +679,32 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     cudaError_t e = cudaMemcpyAsync(saved, h->psi, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
-  auto time_shape = [&](int t, int sx, int sc, int kc, double* ms3) -> int {
+  auto time_shape = [&](int t, int sx, int px, int sc, int kc, int pc, double* ms3) -> int {
     h->tile_x = t != 0;
     h->seg_x = sx;
+    h->pipe_x = px != 0;
     h->seg_c = sc;
     h->keep_c = kc;
+    h->pipe_c = pc != 0;
     double warm[3];
     int r = h->prec == GP_F64 ? time_steps_f64(h, imag != 0, 2, warm) : time_steps_f32(h, imag != 0, 2, warm);
     if (r) return r;
     return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms3) : time_steps_f32(h, imag != 0, nsteps, ms3);
   };
   double bx = 1e30, bc = 1e30;
-  int best_t = keep_t, best_x = keep_x, best_c = keep_c, best_k = keep_k;
+  int best_t = keep_t, best_x = keep_x, best_c = keep_c, best_k = keep_k, best_px = keep_px, best_pc = keep_pc;
   for (const auto& c : xs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(c[0], c[1], keep_c, keep_k, ms);
-    if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; }
+    rc = time_shape(c[0], c[1], c[2], keep_c, keep_k, keep_pc, ms);
+    if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; best_px = c[2]; }
   }
   for (const auto& c : cs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(best_t, best_x, c[0], c[1], ms);
+    rc = time_shape(best_t, best_x, best_px, c[0], c[1], c[2], ms);
     const double t = ms[1] + ms[2];
-    if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; }
+    if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; }
   }
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(h->psi, saved, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
@@ -681,19 +712,22 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
   cudaFree(saved);
+  const int best_flags = (best_k ? GP_SHAPE_KEEP_YZ : 0) | (best_px ? GP_SHAPE_PIPE_X : 0) |
+                         (best_pc ? GP_SHAPE_PIPE_YZ : 0);
   if (rc) {
     h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c; h->keep_c = keep_k;
+    h->pipe_x = keep_px; h->pipe_c = keep_pc;
     return rc;
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[key] = {best_t, best_x, best_c, best_k};
+    g_tuned[key] = {best_t, best_x, best_c, best_flags};
   }
   if (best_ms) {
     best_ms[0] = xs.empty() ? 0.0 : bx;
     best_ms[1] = cs.empty() ? 0.0 : bc;
   }
-  if ((rc = gp_set_shapes(h, best_t, best_x, best_c, best_k))) return rc;
+  if ((rc = gp_set_shapes(h, best_t, best_x, best_c, best_flags))) return rc;
   return join_out(h);
 }
 

@@ -86,6 +86,9 @@ struct gp_handle {
   int seg_x = 0, seg_c = 0;
   bool tile_x = false;
   int keep_c = 1;  // y/z sweeps keep their input segment in registers (when short enough)
+  // persistent double-buffered sweeps (x needs tile_x); only where two
+  // shared-memory stages of 32 lines fit
+  bool pipe_x = false, pipe_c = false;
   double* scale = nullptr;   // [2] renormalisation slots
   double* partials = nullptr;
   unsigned int* counter = nullptr;

@@ -116,6 +116,45 @@ void launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
   }
 }
 
+// ---- pipelined (persistent, double-buffered) sweeps
+template <typename T>
+inline size_t psweep_smem(int n, bool axis0) {
+  const size_t stage = axis0 ? 32 * (size_t)(n + 1) : (size_t)n * kTilePitch;
+  return (3 * (size_t)n + 512 + 2 * stage) * sizeof(c2_t<T>);
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool AXIS0>
+void launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
+  const int M = a.geom.n - 2;
+  const int nseg = (M + SEG - 1) / SEG;
+  const int ntiles = (int)((a.geom.nlines + 31) / 32);
+  const size_t smem = psweep_smem<T>(a.geom.n, AXIS0);
+  static size_t attr_set = 0;  // largest dynamic shared memory opted in so far (static + dynamic <= 227 KB)
+  if (smem > attr_set) {
+    cudaFuncSetAttribute(psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = smem;
+  }
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, 32 * nseg,
+                                                smem);
+  const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * std::max(1, sms)));
+  psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0><<<blocks, 32 * nseg, smem, s>>>(a);
+  count_launch();
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST, bool AXIS0>
+void launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+  switch (seg) {
+    case 4: launch_p<T, IMAG, FIRST, LAST, 4, AXIS0>(a, s); break;
+    case 8: launch_p<T, IMAG, FIRST, LAST, 8, AXIS0>(a, s); break;
+    case 16: launch_p<T, IMAG, FIRST, LAST, 16, AXIS0>(a, s); break;
+    default: launch_p<T, IMAG, FIRST, LAST, 32, AXIS0>(a, s); break;
+  }
+}
+
 // ---- thread-per-line fallback (lines longer than the segmented kernels take)
 template <typename T, bool IMAG, bool FIRST, bool LAST>
 void launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
@@ -159,7 +198,21 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     a.partials = h->partials;
     a.counter = h->counter;
     a.scale_out = h->scale + (1 - par);
-    if (d == 0 && h->tile_x) {
+    if (d == 0 && h->tile_x && h->pipe_x) {
+      if (imag) {
+        if (last) launch_p_seg<T, true, true, true, true>(seg, a, h->work);
+        else launch_p_seg<T, true, true, false, true>(seg, a, h->work);
+      } else {
+        launch_p_seg<T, false, true, false, true>(seg, a, h->work);
+      }
+    } else if (d > 0 && h->pipe_c) {
+      if (imag) {
+        if (last) launch_p_seg<T, true, false, true, false>(seg, a, h->work);
+        else launch_p_seg<T, true, false, false, false>(seg, a, h->work);
+      } else {
+        launch_p_seg<T, false, false, false, false>(seg, a, h->work);
+      }
+    } else if (d == 0 && h->tile_x) {
       if (imag) {
         if (last) launch_t_seg<T, true, true, true>(seg, a, h->work);
         else launch_t_seg<T, true, true, false>(seg, a, h->work);
@@ -342,8 +395,10 @@ void enqueue_adj_sweep(gp_handle* h, int d) {
   a.gf = coef_ptr<T>(h, MODE_REAL_ADJ, d, 1 + 2 * si);
   a.gb = coef_ptr<T>(h, MODE_REAL_ADJ, d, 2 + 2 * si);
   a.ptab = (const c2_t<T>*)h->ctab[MODE_REAL_ADJ][d] + (size_t)si * 512;
-  if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work);
+  if (d == 0 && h->tile_x && h->pipe_x) launch_p_seg<T, false, false, false, true>(seg, a, h->work);
+  else if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work);
   else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work);
+  else if (h->pipe_c) launch_p_seg<T, false, false, false, false>(seg, a, h->work);
   else launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
 }
 

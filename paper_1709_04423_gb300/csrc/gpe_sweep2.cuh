@@ -587,3 +587,167 @@ __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
 }
 
 }  // namespace gpe
+
+namespace gpe {
+
+// ---------------------------------------------------------------- pipelined sweep
+// Persistent blocks, each taking 32-line tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...; while one tile is solved the next is already on its way
+// into the second shared-memory stage (cp.async, zero-filled outside the
+// interior), so the memory system never waits for a block to finish its
+// arithmetic.  Tile layout per stage: y/z lines [point][line] with pitch 33,
+// x lines [line][point] with pitch n + 1 -- both conflict-free for the
+// lane = line reads of the solve.  The coefficient tables are loaded once per
+// block, the norm (LAST) is reduced once per block.  blockDim.x = 32 * nseg.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// async copy of one complex value (8 or 16 bytes); src_bytes = 0 zero-fills
+template <typename T>
+__device__ __forceinline__ void cp_async_c2(c2_t<T>* dst, const c2_t<T>* src, bool valid) {
+  const unsigned d = smem_u32(dst);
+  if constexpr (sizeof(c2_t<T>) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Issues the copies of tile `tile` into stage buffer `buf` (every thread its share).
+template <typename T, bool AXIS0>
+__device__ __forceinline__ void psweep_issue(const Sweep2Args<T>& A, int tile, c2_t<T>* buf, int pitch) {
+  const LineGeom& G = A.geom;
+  const int n = G.n, M = n - 2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int L0 = tile * 32;
+  const int nl = min(32, (int)G.nlines - L0);
+  const c2_t<T>* in = A.src ? A.src : A.psi;
+  if (AXIS0) {
+    for (int c = w; c < 32; c += nwarps) {
+      const bool lok = c < nl;
+      const int gbase = lok ? (L0 + c) * G.nx : 0;
+      for (int k = lane; k < n; k += 32) cp_async_c2<T>(buf + c * pitch + k, in + gbase + k, lok && k >= 1 && k <= M);
+    }
+  } else {
+    const bool lok = lane < nl;
+    const int base = lok ? line_base32(G, L0 + lane) : 0;
+    const int st = (int)G.stride;
+    for (int k = w; k < n; k += nwarps) cp_async_c2<T>(buf + k * kTilePitch + lane, in + base + k * st,
+                                                       lok && k >= 1 && k <= M);
+  }
+}
+
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool AXIS0>
+__global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
+  using c2 = c2_t<T>;
+  extern __shared__ __align__(16) unsigned char psmem_raw[];
+  __shared__ c2 cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  const LineGeom& G = A.geom;
+  const int n = G.n, M = n - 2;
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+  const int nseg = blockDim.x >> 5;
+  const int k0 = 1 + s * SEG;
+  const int pitch = AXIS0 ? n + 1 : kTilePitch;
+  const int stage_elems = AXIS0 ? 32 * (n + 1) : n * kTilePitch;
+  c2* sc = reinterpret_cast<c2*>(psmem_raw);
+  c2* stage[2] = {sc + 3 * n + 512, sc + 3 * n + 512 + stage_elems};
+  const int ntiles = (int)((G.nlines + 31) / 32);
+  load_coefs<T>(A, sc, n);
+  T scl = T(1);
+  if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
+  constexpr bool kFactors = sizeof(T) == 8;
+  T tval = T(0);
+  int it = 0;
+  if (blockIdx.x < ntiles) psweep_issue<T, AXIS0>(A, blockIdx.x, stage[0], pitch);
+  cp_async_commit();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    c2* buf = stage[it & 1];
+    const int next = tile + gridDim.x;
+    if (next < ntiles) psweep_issue<T, AXIS0>(A, next, stage[(it + 1) & 1], pitch);
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's group has landed (the newest may still be in flight)
+    __syncthreads();
+    const int L0 = tile * 32;
+    const int nl = min(32, (int)G.nlines - L0);
+    auto at = [&](int k) -> c2& { return AXIS0 ? buf[lane * pitch + k] : buf[k * kTilePitch + lane]; };
+    if (FIRST) {
+      // sub-step N (and the pending renormalisation) on this thread's own points
+      if (lane < nl) {
+        const int L = L0 + lane;
+        c2 fline = mk<T>(1, 0);
+        T vline = T(0);
+        if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[L % G.ny], A.fz[L / G.ny]);
+        if (!kFactors && !A.V) vline = A.vy[L % G.ny] + A.vz[L / G.ny];
+        const int gb = L * G.nx;
+#pragma unroll
+        for (int j = 0; j < SEG; ++j) {
+          const int k = k0 + j;
+          if (k <= M) {
+            c2 w = at(k);
+            w.x *= scl; w.y *= scl;
+            if (kFactors) {
+              const c2 F = A.fV ? A.fV[gb + k] : fac_mul<T, IMAG>(A.fx[k], fline);
+              w = phase_N<T, IMAG>(w, F, A.dtg);
+            } else {
+              w = phase_direct<T, IMAG>(w, A.V ? A.V[gb + k] : A.vx[k] + vline, A.dt, A.g);
+            }
+            at(k) = w;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    c2 z[SEG];
+    stream_forward<T, IMAG, SEG>([&](int k) { return (k >= 1 && k <= M) ? at(k) : mk<T>(0, 0); }, z, sc, k0, M);
+    seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
+    T tacc = T(0);
+    if (AXIS0) {
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        const int k = k0 + j;
+        if (k <= M) {
+          const c2 p = at(k);
+          const c2 u = mk<T>(p.x - z[j].x, p.y - z[j].y);
+          at(k) = u;
+          if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
+        }
+      }
+      __syncthreads();
+      // coalesced store of the tile: warp w takes lines w, w + nseg, ...
+      for (int c = s; c < nl; c += nseg) {
+        const int gbase = (L0 + c) * G.nx;
+        for (int k = lane; k < n; k += 32) A.psi[gbase + k] = buf[c * pitch + k];
+      }
+    } else if (lane < nl) {
+      c2* line = A.psi + line_base32(G, L0 + lane);
+      const int st = (int)G.stride;
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        const int k = k0 + j;
+        if (k <= M) {
+          const c2 p = at(k);
+          const c2 u = mk<T>(p.x - z[j].x, p.y - z[j].y);
+          line[k * st] = u;
+          if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
+        }
+      }
+      if (s == 0) {
+        line[0] = mk<T>(0, 0);
+        line[(n - 1) * st] = mk<T>(0, 0);
+      }
+    }
+    if (LAST && lane < nl) {
+      const int L = L0 + lane;
+      tval += AXIS0 ? tacc * (A.w_a[L % G.ny] * A.w_b[L / G.ny]) : tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
+    }
+    __syncthreads();  // the stage is refilled by the prefetch of the next iteration
+  }
+  cp_async_wait<0>();
+  finish_norm<T, LAST>(tval, A.partials, A.counter, A.scale_out, red_smem);
+}
+
+}  // namespace gpe

@@ -26,6 +26,9 @@ GP_ERR_TIMEOUT = -4
 GP_ERR_STATE = -5
 GP_F64 = 0
 GP_F32 = 1
+GP_SHAPE_KEEP_YZ = 1
+GP_SHAPE_PIPE_X = 2
+GP_SHAPE_PIPE_YZ = 4
 
 # every entry point declared in include/gpe.h
 ABI_SYMBOLS = (
@@ -188,14 +191,14 @@ def gp_autotune(h, imag, nsteps=8, timings=False):
     return None
 
 
-def gp_set_shapes(h, tile_x, seg_x, seg_c, keep_c=1):
-    return _check(load().gp_set_shapes(h, int(tile_x), int(seg_x), int(seg_c), int(keep_c)))
+def gp_set_shapes(h, tile_x, seg_x, seg_c, flags=GP_SHAPE_KEEP_YZ):
+    return _check(load().gp_set_shapes(h, int(tile_x), int(seg_x), int(seg_c), int(flags)))
 
 
 def gp_get_shapes(h):
     t, x, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().gp_get_shapes(h, ctypes.byref(t), ctypes.byref(x), ctypes.byref(c), ctypes.byref(k)))
-    return {"tile_x": t.value, "seg_x": x.value, "seg_c": c.value, "keep_c": k.value}
+    return {"tile_x": t.value, "seg_x": x.value, "seg_c": c.value, "flags": k.value}
 
 
 def gp_adjoint_forward(h, nsteps, ckpt_every):
@@ -377,7 +380,7 @@ class Propagator:
                 table = {}
         if cache and key in table:
             s = table[key]
-            gp_set_shapes(self.h, s["tile_x"], s["seg_x"], s["seg_c"], s.get("keep_c", 1))
+            gp_set_shapes(self.h, s["tile_x"], s["seg_x"], s["seg_c"], s.get("flags", GP_SHAPE_KEEP_YZ))
             return s
         gp_autotune(self.h, imag, nsteps)
         s = gp_get_shapes(self.h)

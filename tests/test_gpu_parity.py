@@ -224,6 +224,8 @@ SHAPES = [
     {"GPE_SEG_X": "16", "GPE_SEG_YZ": "8"},
     {"GPE_SEG_X": "32", "GPE_SEG_YZ": "32"},
     {"GPE_SEG_YZ": "8", "GPE_KEEP": "0"},                      # y/z input streamed and re-read
+    {"GPE_PIPE": "1"},                                         # persistent double-buffered sweeps
+    {"GPE_PIPE": "1", "GPE_SEG_X": "4", "GPE_SEG_YZ": "16"},
 ]
 
 
