@@ -28,7 +28,9 @@
  *
  * Memory layout of every grid array: x fastest, idx = i + nx*(j + ny*k).
  * States are complex, interleaved (re, im), in the handle's precision:
- * double2 for GP_F64, float2 for GP_F32.  Potentials and densities are double.
+ * double2 for GP_F64, float2 for GP_F32, and double2 (complex128) at the API
+ * for GP_DF64, whose device state is double-float.  Potentials and densities
+ * are double.
  *
  * Errors: every call returns GP_OK (0) or a negative code; gp_last_error()
  * returns a thread-local message for the last failure.  No call aborts or
@@ -61,7 +63,12 @@ enum {
   GP_ERR_STATE = -5      /* call not valid in the handle's current state */
 };
 
-typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision;
+/* GP_DF64: the state and the sweeps in double-float arithmetic (each real a
+ * pair of floats hi + lo, about 48 significant bits) on the FP32 pipes, for
+ * FP64-class results on parts whose FP64 rate is a small fraction of FP32;
+ * the potential factors are exact triple-float images of the FP64 ones, and
+ * the reductions are FP64. */
+typedef enum { GP_F64 = 0, GP_F32 = 1, GP_DF64 = 2 } gp_precision;
 
 typedef struct gp_handle gp_handle;
 
@@ -84,19 +91,22 @@ typedef struct {
  *   dt       time step, finite and != 0 (the same dt serves imaginary time).
  *   nkl      trap frequencies nu, kappa, lambda of the harmonic potential.
  *   g        nonlinearity, finite.
- *   prec     GP_F64 or GP_F32 (FP32 state and sweeps; norm, energy, mu and
- *            the renormalisation factor are still computed in FP64).
+ *   prec     GP_F64, GP_F32 (FP32 state and sweeps; norm, energy, mu and
+ *            the renormalisation factor are still computed in FP64) or
+ *            GP_DF64 (double-float state and sweeps; at most 514 points per
+ *            axis; no adjoint, no pipelined shapes, not in batches).
  *   stream   cudaStream_t to order work on (NULL = legacy default stream).
  * The state starts at zero: call gp_set_state before stepping. */
 int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double dt,
             const double nkl[3], double g, gp_precision prec, void* stream);
 
-/* Copies a state in (interleaved re, im, in the handle's precision, npoints
- * values).  on_device != 0: psi is a device pointer read in stream order. */
+/* Copies a state in (interleaved re, im, in the handle's precision -- double
+ * for GP_DF64 -- npoints values).  on_device != 0: psi is a device pointer
+ * read in stream order. */
 int gp_set_state(gp_handle* h, const void* psi, int on_device);
 
-/* Copies the state out in the handle's precision.  With on_device == 0 the
- * call synchronises the stream. */
+/* Copies the state out in the handle's precision (GP_DF64: rounded to
+ * double).  With on_device == 0 the call synchronises the stream. */
 int gp_get_state(gp_handle* h, void* psi, int on_device);
 
 /* Replaces the harmonic trap by a potential array (double, npoints values);

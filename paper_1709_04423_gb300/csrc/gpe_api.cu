@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "gpe_df.cuh"
 #include "gpe_internal.h"
 
 using cd = std::complex<double>;
@@ -238,19 +239,50 @@ void choose_shapes(gp_handle* h) {
   h->keep_c = env_int("GPE_KEEP", 1) != 0;
   int nmax = 0;
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
-  h->pipe_x = env_int("GPE_PIPE", 0) != 0 && h->tile_x && pipe_fits(h, h->n[0], true);
-  h->pipe_c = env_int("GPE_PIPE", 0) != 0 && h->dim > 1 && sc > 0 && pipe_fits(h, nmax, false);
+  const bool pipe = env_int("GPE_PIPE", 0) != 0 && h->prec != GP_DF64;
+  h->pipe_x = pipe && h->tile_x && pipe_fits(h, h->n[0], true);
+  h->pipe_c = pipe && h->dim > 1 && sc > 0 && pipe_fits(h, nmax, false);
 }
 
 }  // namespace
 
 int upload_coefs(gp_handle* h) {
+  if (h->prec == GP_DF64) return upload_coefs_t<df64>(h);
   return h->prec == GP_F64 ? upload_coefs_t<double>(h) : upload_coefs_t<float>(h);
 }
+
+// Step launchers of the handle's state precision.
+int run_steps_any(gp_handle* h, bool imag, long nsteps) {
+  if (h->prec == GP_DF64) return run_steps_df(h, imag, nsteps);
+  return h->prec == GP_F64 ? run_steps_f64(h, imag, nsteps) : run_steps_f32(h, imag, nsteps);
+}
+int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms) {
+  if (h->prec == GP_DF64) return time_steps_df(h, imag, nsteps, ms);
+  return h->prec == GP_F64 ? time_steps_f64(h, imag, nsteps, ms) : time_steps_f32(h, imag, nsteps, ms);
+}
+int run_observables_any(gp_handle* h, double* dens_dev) {
+  if (h->prec == GP_DF64) return run_observables_df(h, dens_dev);
+  return h->prec == GP_F64 ? run_observables_f64(h, dens_dev) : run_observables_f32(h, dens_dev);
+}
+
+namespace {
+// Host triple-float images of complex factors (exact splits of the doubles).
+int upload_tf(gp_handle* h, void* dst, const std::vector<cd>& v) {
+  std::vector<tf3c> tmp(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    tf_split(v[i].real(), tmp[i].re);
+    tf_split(v[i].imag(), tmp[i].im);
+  }
+  GP_CUDA(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(tf3c), cudaMemcpyHostToDevice, h->work));
+  GP_CUDA(cudaStreamSynchronize(h->work));
+  return GP_OK;
+}
+}  // namespace
 
 // Per-axis potential factors of the sub-step N for the current dt (absent
 // axes: a single factor 1); and, with a user potential, the per-point ones.
 int upload_factors(gp_handle* h) {
+  std::vector<cd> per_axis[2][3];
   for (int d = 0; d < 3; ++d) {
     const int nd = axis_len(h, d);
     std::vector<cd> fr(nd, cd(1, 0)), fi(nd, cd(1, 0));
@@ -261,10 +293,24 @@ int upload_factors(gp_handle* h) {
         fr[i] = cd(std::cos(h->dt * v), -std::sin(h->dt * v));
         fi[i] = cd(std::exp(-h->dt * v), 0.0);
       }
-    int rc = h->prec == GP_F64 ? upload_c2<double>(h, h->fac[0][d], fr) : upload_c2<float>(h, h->fac[0][d], fr);
+    const bool f64 = h->prec != GP_F32;  // the double-float form keeps FP64 factors too
+    int rc = f64 ? upload_c2<double>(h, h->fac[0][d], fr) : upload_c2<float>(h, h->fac[0][d], fr);
     if (rc) return rc;
-    rc = h->prec == GP_F64 ? upload_c2<double>(h, h->fac[1][d], fi) : upload_c2<float>(h, h->fac[1][d], fi);
+    rc = f64 ? upload_c2<double>(h, h->fac[1][d], fi) : upload_c2<float>(h, h->fac[1][d], fi);
     if (rc) return rc;
+    per_axis[0][d] = fr;
+    per_axis[1][d] = fi;
+  }
+  if (h->prec == GP_DF64) {
+    const int ny = axis_len(h, 1), nz = axis_len(h, 2);
+    for (int m = 0; m < 2; ++m) {
+      std::vector<cd> yz((size_t)ny * nz);
+      for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j) yz[(size_t)k * ny + j] = per_axis[m][1][j] * per_axis[m][2][k];
+      int rc = upload_tf(h, h->tfx[m], per_axis[m][0]);
+      if (rc) return rc;
+      if ((rc = upload_tf(h, h->tfyz[m], yz))) return rc;
+    }
   }
   if (h->Vd) {
     potential_factors(h);
@@ -306,7 +352,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
   if (!out || !n || !dx || !nkl) return fail(GP_ERR_INVALID, "gp_init: NULL argument");
   *out = nullptr;
   if (dim < 1 || dim > 3) return fail(GP_ERR_INVALID, "gp_init: dim must be 1, 2 or 3");
-  if (prec != GP_F64 && prec != GP_F32) return fail(GP_ERR_INVALID, "gp_init: unknown precision");
+  if (prec != GP_F64 && prec != GP_F32 && prec != GP_DF64) return fail(GP_ERR_INVALID, "gp_init: unknown precision");
   long np = 1;
   for (int d = 0; d < dim; ++d) {
     if (n[d] < 3) return fail(GP_ERR_INVALID, "gp_init: every axis needs n >= 3 points");
@@ -329,7 +375,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
   h->g = g;
   h->prec = prec;
   h->np = np;
-  h->esize = prec == GP_F64 ? sizeof(double2) : sizeof(float2);
+  h->esize = prec == GP_F64 ? sizeof(double2) : prec == GP_DF64 ? sizeof(df64x2) : sizeof(float2);
   h->user = (cudaStream_t)stream;
   int rc = GP_OK;
   auto bail = [&](int code) { gp_destroy(h); return code; };
@@ -341,7 +387,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->obs_host, 8 * sizeof(double));
     if (e != cudaSuccess) return bail(fail(GP_ERR_CUDA, std::string("gp_init: ") + cudaGetErrorString(e)));
   }
-  const size_t tsz = prec == GP_F64 ? sizeof(double) : sizeof(float);
+  const size_t tsz = prec == GP_F64 ? sizeof(double) : prec == GP_DF64 ? sizeof(df64) : sizeof(float);
   if ((rc = dev_alloc(h, &h->psi, (size_t)np * h->esize))) return bail(rc);
   for (int d = 0; d < 3; ++d) {
     const int nd = axis_len(h, d);
@@ -366,9 +412,13 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     if ((rc = dev_alloc(h, (void**)&h->cdx[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->wd[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, &h->wt[d], nd * tsz))) return bail(rc);
-    rc = prec == GP_F64 ? upload_real<double>(h, h->vt[d], v) : upload_real<float>(h, h->vt[d], v);
-    if (rc) return bail(rc);
-    rc = prec == GP_F64 ? upload_real<double>(h, h->wt[d], w) : upload_real<float>(h, h->wt[d], w);
+    if (prec == GP_DF64) {
+      rc = upload_real<df64>(h, h->vt[d], v);
+      if (!rc) rc = upload_real<df64>(h, h->wt[d], w);
+    } else {
+      rc = prec == GP_F64 ? upload_real<double>(h, h->vt[d], v) : upload_real<float>(h, h->vt[d], v);
+      if (!rc) rc = prec == GP_F64 ? upload_real<double>(h, h->wt[d], w) : upload_real<float>(h, h->wt[d], w);
+    }
     if (rc) return bail(rc);
     if ((rc = upload_real<double>(h, h->vd[d], v))) return bail(rc);
     if ((rc = upload_real<double>(h, h->cdx[d], x))) return bail(rc);
@@ -384,9 +434,19 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
       if ((rc = dev_alloc(h, &h->ccp[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
     }
   }
+  if (prec == GP_DF64) {
+    const long nyz = (long)axis_len(h, 1) * axis_len(h, 2);
+    for (int m = 0; m < 2; ++m) {
+      if ((rc = dev_alloc(h, &h->tfx[m], (size_t)h->n[0] * sizeof(tf3c)))) return bail(rc);
+      if ((rc = dev_alloc(h, &h->tfyz[m], (size_t)nyz * sizeof(tf3c)))) return bail(rc);
+    }
+    if ((rc = dev_alloc(h, &h->df_stage, (size_t)np * sizeof(double2)))) return bail(rc);
+  }
   if ((rc = upload_coefs(h))) return bail(rc);
   if ((rc = upload_factors(h))) return bail(rc);
   choose_shapes(h);
+  if (prec == GP_DF64 && (h->seg_x == 0 || (dim > 1 && h->seg_c == 0)))
+    return bail(fail(GP_ERR_INVALID, "gp_init: the double-float form takes at most 514 points per axis"));
   // reduction scratch: enough partial slots for any sweep or observables grid
   long maxblocks = 152L * 16;
   for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, h->np / h->n[d] / 4 + 1);
@@ -406,8 +466,18 @@ int gp_set_state(gp_handle* h, const void* psi, int on_device) {
   if (!h || !psi) return fail(GP_ERR_INVALID, "gp_set_state: NULL argument");
   int rc = join_in(h);
   if (rc) return rc;
-  GP_CUDA(cudaMemcpyAsync(h->psi, psi, (size_t)h->np * h->esize,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
+  if (h->prec == GP_DF64) {  // complex128 in, split on the device
+    const void* src = psi;
+    if (!on_device) {
+      GP_CUDA(cudaMemcpyAsync(h->df_stage, psi, (size_t)h->np * sizeof(double2), cudaMemcpyHostToDevice, h->work));
+      src = h->df_stage;
+    }
+    df_from_c128(h, src);
+    GP_CUDA(cudaGetLastError());
+  } else {
+    GP_CUDA(cudaMemcpyAsync(h->psi, psi, (size_t)h->np * h->esize,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
+  }
   if (!on_device) GP_CUDA(cudaStreamSynchronize(h->work));
   return join_out(h);
 }
@@ -416,8 +486,15 @@ int gp_get_state(gp_handle* h, void* psi, int on_device) {
   if (!h || !psi) return fail(GP_ERR_INVALID, "gp_get_state: NULL argument");
   int rc = join_in(h);
   if (rc) return rc;
-  GP_CUDA(cudaMemcpyAsync(psi, h->psi, (size_t)h->np * h->esize,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->work));
+  if (h->prec == GP_DF64) {  // rounded to complex128
+    df_to_c128(h, on_device ? psi : h->df_stage);
+    GP_CUDA(cudaGetLastError());
+    if (!on_device)
+      GP_CUDA(cudaMemcpyAsync(psi, h->df_stage, (size_t)h->np * sizeof(double2), cudaMemcpyDeviceToHost, h->work));
+  } else {
+    GP_CUDA(cudaMemcpyAsync(psi, h->psi, (size_t)h->np * h->esize,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->work));
+  }
   if (!on_device) GP_CUDA(cudaStreamSynchronize(h->work));
   return join_out(h);
 }
@@ -445,12 +522,18 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
     }
     if ((rc = dev_alloc(h, &h->fV[0], (size_t)h->np * h->esize))) return rc;
     if ((rc = dev_alloc(h, &h->fV[1], (size_t)h->np * h->esize))) return rc;
+    if (h->prec == GP_DF64) {
+      if ((rc = dev_alloc(h, &h->tfV[0], (size_t)h->np * sizeof(tf3c)))) return rc;
+      if ((rc = dev_alloc(h, &h->tfV[1], (size_t)h->np * sizeof(tf3c)))) return rc;
+    }
   }
   GP_CUDA(cudaMemcpyAsync(h->Vbuf, V, (size_t)h->np * sizeof(double),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
   h->Vd = h->Vbuf;
   if (h->prec == GP_F64) {
     h->Vt = h->Vbuf;
+  } else if (h->prec == GP_DF64) {
+    h->Vt = nullptr;  // the double-float sweeps read only the factors
   } else {
     to_float(h, h->Vbuf32, h->Vbuf, h->np);
     h->Vt = h->Vbuf32;
@@ -485,20 +568,19 @@ int gp_set_dt(gp_handle* h, double dt) {
 int gp_step_imag(gp_handle* h, long nsteps) {
   if (!h) return fail(GP_ERR_INVALID, "gp_step_imag: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_step_imag: nsteps < 0");
-  return h->prec == GP_F64 ? run_steps_f64(h, true, nsteps) : run_steps_f32(h, true, nsteps);
+  return run_steps_any(h, true, nsteps);
 }
 
 int gp_step_real(gp_handle* h, long nsteps) {
   if (!h) return fail(GP_ERR_INVALID, "gp_step_real: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_step_real: nsteps < 0");
-  return h->prec == GP_F64 ? run_steps_f64(h, false, nsteps) : run_steps_f32(h, false, nsteps);
+  return run_steps_any(h, false, nsteps);
 }
 
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch) {
   if (!h || !ms_per_launch) return fail(GP_ERR_INVALID, "gp_time_sweeps: NULL argument");
   if (nsteps < 0 || nsteps > 4096) return fail(GP_ERR_INVALID, "gp_time_sweeps: nsteps must be in [0, 4096]");
-  return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms_per_launch)
-                           : time_steps_f32(h, imag != 0, nsteps, ms_per_launch);
+  return time_steps_any(h, imag != 0, nsteps, ms_per_launch);
 }
 
 namespace {
@@ -527,6 +609,8 @@ int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every) {
   if (nsteps < 1 || ckpt_every < 1) return fail(GP_ERR_INVALID, "gp_adjoint_forward: need nsteps >= 1, ckpt_every >= 1");
   if (h->seg_x == 0 || (h->dim > 1 && h->seg_c == 0))
     return fail(GP_ERR_INVALID, "gp_adjoint_forward: lines longer than 514 points are not supported");
+  if (h->prec == GP_DF64)
+    return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint takes GP_F64 or GP_F32 states");
   const int K = (int)std::min<long>(ckpt_every, nsteps);
   const long nck = (nsteps + K - 1) / K;
   int rc;
@@ -614,6 +698,8 @@ int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
   const bool px = (flags & GP_SHAPE_PIPE_X) != 0, pc = (flags & GP_SHAPE_PIPE_YZ) != 0;
+  if ((px || pc) && h->prec == GP_DF64)
+    return fail(GP_ERR_INVALID, "gp_set_shapes: the pipelined sweeps take GP_F64 or GP_F32 states");
   if (px && (!tile_x || seg_x == 0 || !pipe_fits(h, h->n[0], true)))
     return fail(GP_ERR_INVALID, "gp_set_shapes: pipelined x sweep needs the x tile and two stages in shared memory");
   int nmax = 0;
@@ -656,7 +742,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   for (int sg : {4, 8, 16, 32})
     if (shapes_valid(h, 1, sg, h->seg_c)) {
       xs.push_back({1, sg, 0});
-      if (pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
+      if (h->prec != GP_DF64 && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
     }
   for (int sg : {1, 2, 4, 8, 16})
     if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }
@@ -668,7 +754,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
       if (shapes_valid(h, h->tile_x, h->seg_x, sg)) {
         if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1, 0});
         cs.push_back({sg, 0, 0});
-        if (pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
+        if (h->prec != GP_DF64 && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
       }
   const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
   const bool keep_px = h->pipe_x, keep_pc = h->pipe_c;
@@ -687,9 +773,9 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     h->keep_c = kc;
     h->pipe_c = pc != 0;
     double warm[3];
-    int r = h->prec == GP_F64 ? time_steps_f64(h, imag != 0, 2, warm) : time_steps_f32(h, imag != 0, 2, warm);
+    int r = time_steps_any(h, imag != 0, 2, warm);
     if (r) return r;
-    return h->prec == GP_F64 ? time_steps_f64(h, imag != 0, nsteps, ms3) : time_steps_f32(h, imag != 0, nsteps, ms3);
+    return time_steps_any(h, imag != 0, nsteps, ms3);
   };
   double bx = 1e30, bc = 1e30;
   int best_t = keep_t, best_x = keep_x, best_c = keep_c, best_k = keep_k, best_px = keep_px, best_pc = keep_pc;
@@ -748,7 +834,7 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
       ddev = h->dens_scratch;
     }
   }
-  rc = h->prec == GP_F64 ? run_observables_f64(h, ddev) : run_observables_f32(h, ddev);
+  rc = run_observables_any(h, ddev);
   if (rc) return rc;
   GP_CUDA(cudaMemcpyAsync(h->obs_host, h->obs_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->work));
   if (density && !density_on_device)

@@ -5,11 +5,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gpe_df.cuh"
+
 namespace gpe {
 
 template <typename T> struct C2;
 template <> struct C2<double> { using type = double2; };
 template <> struct C2<float> { using type = float2; };
+template <> struct C2<df64> { using type = df64x2; };
+template <typename T> struct is_df { static constexpr bool value = false; };
+template <> struct is_df<df64> { static constexpr bool value = true; };
 template <typename T> using c2_t = typename C2<T>::type;
 
 template <typename T> __device__ __forceinline__ c2_t<T> mk(T x, T y) { c2_t<T> r; r.x = x; r.y = y; return r; }

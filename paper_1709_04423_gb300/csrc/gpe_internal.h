@@ -67,6 +67,13 @@ struct gp_handle {
   // with a user potential fV[0][q] = exp(-i dt V_q), fV[1][q] = exp(-dt V_q)
   void* fac[2][3] = {{nullptr}};
   void* fV[2] = {nullptr, nullptr};
+  // double-float state: the factors as exact triple-floats (tf3c) -- per x
+  // index, per x line (fy[j] fz[k]) and, with a user potential, per point --
+  // and a complex128 staging buffer for the state exchange and observables
+  void* tfx[2] = {nullptr, nullptr};
+  void* tfyz[2] = {nullptr, nullptr};
+  void* tfV[2] = {nullptr, nullptr};
+  void* df_stage = nullptr;
   double* vd[3] = {nullptr, nullptr, nullptr};   // same in FP64
   double* cdx[3] = {nullptr, nullptr, nullptr};  // coordinates
   double* wd[3] = {nullptr, nullptr, nullptr};   // Simpson weights
@@ -135,6 +142,16 @@ int upload_coefs(gp_handle* h);
 int upload_factors(gp_handle* h);
 
 // per-precision entry points (gpe_step_f32.cu / gpe_step_f64.cu)
+int run_steps_any(gp_handle* h, bool imag, long nsteps);  // dispatch on h->prec
+int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms_out);
+int run_observables_any(gp_handle* h, double* dens_dev);
+int run_steps_df(gp_handle* h, bool imag, long nsteps);
+int time_steps_df(gp_handle* h, bool imag, long nsteps, double* ms_out);
+int run_observables_df(gp_handle* h, double* dens_dev);
+// double-float state <-> complex128 (device buffers, on the library stream)
+void df_from_c128(gp_handle* h, const void* src);
+void df_to_c128(gp_handle* h, void* dst);
+void tf_from_c128(gp_handle* h, void* dst, const void* src, long n);  // exact triple-float split
 int run_steps_f32(gp_handle* h, bool imag, long nsteps);
 int run_steps_f64(gp_handle* h, bool imag, long nsteps);
 int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out);

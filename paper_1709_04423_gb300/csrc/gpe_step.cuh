@@ -191,6 +191,11 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     a.vz = (const T*)h->vt[2];
     a.dt = (T)h->dt;
     a.g = (T)h->g;
+    if constexpr (is_df<T>::value) {
+      a.tfV = h->Vd ? (const tf3c*)h->tfV[fm] : nullptr;
+      a.tfx = (const tf3c*)h->tfx[fm];
+      a.tfyz = (const tf3c*)h->tfyz[fm];
+    }
     a.scale_in = imag ? h->scale + par : nullptr;
     a.w_axis = (const T*)h->wt[d];
     a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
@@ -198,21 +203,27 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     a.partials = h->partials;
     a.counter = h->counter;
     a.scale_out = h->scale + (1 - par);
-    if (d == 0 && h->tile_x && h->pipe_x) {
-      if (imag) {
-        if (last) launch_p_seg<T, true, true, true, true>(seg, a, h->work);
-        else launch_p_seg<T, true, true, false, true>(seg, a, h->work);
-      } else {
-        launch_p_seg<T, false, true, false, true>(seg, a, h->work);
+    if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
+      if (d == 0 && h->tile_x && h->pipe_x) {
+        if (imag) {
+          if (last) launch_p_seg<T, true, true, true, true>(seg, a, h->work);
+          else launch_p_seg<T, true, true, false, true>(seg, a, h->work);
+        } else {
+          launch_p_seg<T, false, true, false, true>(seg, a, h->work);
+        }
+        return;
       }
-    } else if (d > 0 && h->pipe_c) {
-      if (imag) {
-        if (last) launch_p_seg<T, true, false, true, false>(seg, a, h->work);
-        else launch_p_seg<T, true, false, false, false>(seg, a, h->work);
-      } else {
-        launch_p_seg<T, false, false, false, false>(seg, a, h->work);
+      if (d > 0 && h->pipe_c) {
+        if (imag) {
+          if (last) launch_p_seg<T, true, false, true, false>(seg, a, h->work);
+          else launch_p_seg<T, true, false, false, false>(seg, a, h->work);
+        } else {
+          launch_p_seg<T, false, false, false, false>(seg, a, h->work);
+        }
+        return;
       }
-    } else if (d == 0 && h->tile_x) {
+    }
+    if (d == 0 && h->tile_x) {
       if (imag) {
         if (last) launch_t_seg<T, true, true, true>(seg, a, h->work);
         else launch_t_seg<T, true, true, false>(seg, a, h->work);
@@ -236,6 +247,9 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     }
     return;
   }
+  if constexpr (is_df<T>::value) {
+    return;  // the double-float form needs the segmented kernels (checked at gp_init)
+  } else {
   SweepArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.psi = (c2_t<T>*)h->psi;
@@ -264,6 +278,7 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
   } else {
     if (first) launch_legacy<T, false, true, false>(a, h->work);
     else launch_legacy<T, false, false, false>(a, h->work);
+  }
   }
 }
 

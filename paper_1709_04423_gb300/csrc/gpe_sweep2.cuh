@@ -44,6 +44,8 @@
 // factor only rescales the state, and the observables recompute the norm in
 // FP64 from scratch.)
 #pragma once
+#include <type_traits>
+
 #include "gpe_common.cuh"
 
 namespace gpe {
@@ -70,6 +72,11 @@ struct Sweep2Args {
   const T* V;
   const T* vx; const T* vy; const T* vz;
   T dt, g;
+  // double-float state: the same factors as exact triple-floats, per point
+  // (tfV) or per x index (tfx) and per x line (tfyz = fy[j] fz[k], formed in FP64)
+  const tf3c* tfV;
+  const tf3c* tfx;
+  const tf3c* tfyz;
   const double* scale_in;
   // norm (LAST)
   const T* w_axis;       // Simpson weights along the line, state precision
@@ -131,6 +138,78 @@ __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
   return mk<T>(c * p.x + s * p.y, c * p.y - s * p.x);
 }
 
+// Double-float state: p <- exp(-i a) p (real time) or exp(-a) p (imaginary
+// time), a = dt g |p|^2, then the potential factors (exact triple-floats).
+// For |a| < 1/8 the exponential is its Taylor series; the terms of order a^6
+// and up (at most 5.3e-9 here) only need float accuracy for a 2^-50 total
+// and are summed in float, the leading ones in double-float.  Larger |a|
+// goes through FP64.
+template <bool IMAG>
+__device__ __forceinline__ df64x2 phase_df(df64x2 p, const Sweep2Args<df64>& A, long gidx, int k, int L) {
+  const df64 a = A.dtg * (p.x * p.x + p.y * p.y);
+  if (IMAG) {
+    df64 e;
+    if (fabsf(a.hi) < 0.125f) {
+      const df64 m = -a;
+      const float mf = m.hi;
+      const float te = 1.0f / 720 + mf * (1.0f / 5040 + mf * (1.0f / 40320 + mf * (1.0f / 362880 + mf * (1.0f / 3628800))));
+      constexpr df64 c5(1.0 / 120), c4(1.0 / 24), c3(1.0 / 6), c2(0.5), c1(1.0);
+      e = df_mulf(m, te) + c5;
+      e = m * e + c4;
+      e = m * e + c3;
+      e = m * e + c2;
+      e = m * e + c1;
+      e = m * e + c1;
+    } else {
+      e = df64(::exp(-(double)a));
+    }
+    p = df64x2{e * p.x, e * p.y};
+    if (A.tfV) {
+      const tf3c F = A.tfV[gidx];
+      p = df64x2{tf_mul(F.re, p.x), tf_mul(F.re, p.y)};
+    } else {
+      const tf3c Fx = A.tfx[k], Fl = A.tfyz[L];
+      p = df64x2{tf_mul(Fx.re, p.x), tf_mul(Fx.re, p.y)};
+      p = df64x2{tf_mul(Fl.re, p.x), tf_mul(Fl.re, p.y)};
+    }
+    return p;
+  } else {
+    df64 sn, cs;
+    if (fabsf(a.hi) < 0.125f) {
+      const df64 a2 = a * a;
+      const float q = a2.hi;
+      const float ts = -1.0f / 5040 + q * (1.0f / 362880 + q * (-1.0f / 39916800));
+      const float tc = -1.0f / 720 + q * (1.0f / 40320 + q * (-1.0f / 3628800 + q * (1.0f / 479001600)));
+      constexpr df64 s2(1.0 / 120), s1(-1.0 / 6), c2(1.0 / 24), c1(-0.5), one(1.0);
+      df64 S = df_mulf(a2, ts) + s2;
+      S = a2 * S + s1;
+      S = a2 * S + one;
+      sn = a * S;
+      df64 C = df_mulf(a2, tc) + c2;
+      C = a2 * C + c1;
+      cs = a2 * C + one;
+    } else {
+      double sd, cd;
+      ::sincos((double)a, &sd, &cd);
+      sn = df64(sd);
+      cs = df64(cd);
+    }
+    // exp(-i a) p = (cs px + sn py) + i (cs py - sn px)
+    p = df64x2{cs * p.x + sn * p.y, cs * p.y - sn * p.x};
+    auto cmul_tf = [](const tf3c& F, df64x2 v) {
+      // (Fr + i Fi)(vx + i vy) = (Fr vx - Fi vy) + i (Fr vy - Fi (-vx))
+      return df64x2{tf_dot2(F.re, v.x, F.im, v.y), tf_dot2(F.re, v.y, F.im, -v.x)};
+    };
+    if (A.tfV) {
+      p = cmul_tf(A.tfV[gidx], p);
+    } else {
+      p = cmul_tf(A.tfx[k], p);
+      p = cmul_tf(A.tfyz[L], p);
+    }
+    return p;
+  }
+}
+
 // product of two potential factors (real in imaginary time)
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> fac_mul(c2_t<T> a, c2_t<T> b) {
@@ -159,11 +238,11 @@ __device__ __forceinline__ c2_t<T> cf_cc(c2_t<T> a, c2_t<T> b) {
 
 template <typename T>
 __device__ __forceinline__ c2_t<T> shfl_up2(c2_t<T> v, int o) {
-  return mk<T>(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+  return mk<T>(shfl_up_t(v.x, o), shfl_up_t(v.y, o));
 }
 template <typename T>
 __device__ __forceinline__ c2_t<T> shfl_down2(c2_t<T> v, int o) {
-  return mk<T>(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+  return mk<T>(shfl_down_t(v.x, o), shfl_down_t(v.y, o));
 }
 
 // Segment-local passes over SEG registers.  k0 = first interior index of the
@@ -286,7 +365,7 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
   if (LAST) {
     __shared__ T tred[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tval += __shfl_xor_sync(0xffffffffu, tval, o);
+    for (int o = 16; o > 0; o >>= 1) tval += shfl_xor_t(tval, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) tred[warp] = tval;
     __syncthreads();
@@ -294,7 +373,7 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
     if (warp == 0) {
       T b = lane < nw ? tred[lane] : T(0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+      for (int o = 16; o > 0; o >>= 1) b += shfl_xor_t(b, o);
       v[0] = (double)b;  // FP64 from here on
     }
     if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0) *scale_out = 1.0 / sqrt(tot[0]);
@@ -404,10 +483,10 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   for (int c = s; c < 32; c += nwarps) {
     const bool line_ok = c < nl;
     const int gbase = (L0 + c) * G.nx;
-    constexpr bool kFactors = sizeof(T) == 8;  // FP64: precomputed potential factors
+    constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
     c2 fline = mk<T>(1, 0);
     T vline = T(0);
-    if (FIRST && line_ok) {
+    if (FIRST && line_ok && !is_df<T>::value) {
       const int L = L0 + c;
       if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[L % G.ny], A.fz[L / G.ny]);
       if (!kFactors && !A.V) vline = A.vy[L % G.ny] + A.vz[L / G.ny];
@@ -426,12 +505,17 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
         if (k >= n) break;
         c2 w = v[i];
         if (FIRST && line_ok && k >= 1 && k <= M) {
-          w.x *= scl; w.y *= scl;
-          if (kFactors) {
-            const c2 F = A.fV ? A.fV[gbase + k] : fac_mul<T, IMAG>(A.fx[k], fline);
-            w = phase_N<T, IMAG>(w, F, A.dtg);
+          if constexpr (is_df<T>::value) {
+            if (IMAG) { w.x *= scl; w.y *= scl; }
+            w = phase_df<IMAG>(w, A, gbase + k, k, L0 + c);
           } else {
-            w = phase_direct<T, IMAG>(w, A.V ? A.V[gbase + k] : A.vx[k] + vline, A.dt, A.g);
+            w.x *= scl; w.y *= scl;
+            if (kFactors) {
+              const c2 F = A.fV ? A.fV[gbase + k] : fac_mul<T, IMAG>(A.fx[k], fline);
+              w = phase_N<T, IMAG>(w, F, A.dtg);
+            } else {
+              w = phase_direct<T, IMAG>(w, A.V ? A.V[gbase + k] : A.vx[k] + vline, A.dt, A.g);
+            }
           }
         }
         tile[k * kTilePitch + c] = w;
@@ -496,12 +580,14 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     c2* line = A.psi + base;
     const int k0 = 1 + lane * SEG;
     const int ta = L % G.ny, tb = L / G.ny;
-    constexpr bool kFactors = sizeof(T) == 8;  // FP64: precomputed potential factors
+    constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
     c2 fline = mk<T>(1, 0);
     T vline = T(0), scl = T(1);
-    if (FIRST) {
+    if (FIRST && !is_df<T>::value) {
       if (kFactors && A.fV == nullptr) fline = fac_mul<T, IMAG>(A.fy[ta], A.fz[tb]);
       if (!kFactors && A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
+    }
+    if (FIRST) {
       if (A.scale_in) scl = (T)(*A.scale_in);
     }
     const c2* in = (A.src ? A.src : A.psi) + base;
@@ -512,7 +598,10 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       c2 v = mk<T>(0, 0);
       if (k <= M) {
         v = in[k];
-        if (FIRST) {
+        if constexpr (FIRST && is_df<T>::value) {
+          if (IMAG) { v.x *= scl; v.y *= scl; }
+          v = phase_df<IMAG>(v, A, base + k, k, L);
+        } else if constexpr (FIRST) {
           v.x *= scl; v.y *= scl;
           if (kFactors) {
             const c2 F = A.fV ? A.fV[base + k] : fac_mul<T, IMAG>(A.fx[k], fline);
@@ -659,7 +748,8 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
   load_coefs<T>(A, sc, n);
   T scl = T(1);
   if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
-  constexpr bool kFactors = sizeof(T) == 8;
+  constexpr bool kFactors = std::is_same<T, double>::value;
+  static_assert(!is_df<T>::value, "the pipelined sweeps take FP32 and FP64 states");
   T tval = T(0);
   int it = 0;
   if (blockIdx.x < ntiles) psweep_issue<T, AXIS0>(A, blockIdx.x, stage[0], pitch);

@@ -26,6 +26,8 @@ GP_ERR_TIMEOUT = -4
 GP_ERR_STATE = -5
 GP_F64 = 0
 GP_F32 = 1
+GP_DF64 = 2
+PRECISIONS = {"f64": GP_F64, "f32": GP_F32, "df64": GP_DF64}
 GP_SHAPE_KEEP_YZ = 1
 GP_SHAPE_PIPE_X = 2
 GP_SHAPE_PIPE_YZ = 4
@@ -280,9 +282,10 @@ def obs_dict(o: GpObs):
 class Propagator:
     """One GP problem on the current CUDA device.
 
-    ``precision``: ``"f64"`` (plain FP64) or ``"f32"`` (FP32 state and sweeps,
-    FP64 reductions and renormalisation).  States are complex tensors of shape
-    (nz, ny, nx) truncated to ``dim`` (x fastest).
+    ``precision``: ``"f64"`` (plain FP64), ``"f32"`` (FP32 state and sweeps,
+    FP64 reductions and renormalisation) or ``"df64"`` (double-float state and
+    sweeps on the FP32 pipes, exchanged as complex128).  States are complex
+    tensors of shape (nz, ny, nx) truncated to ``dim`` (x fastest).
     """
 
     def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, precision="f64", stream=None):
@@ -291,13 +294,15 @@ class Propagator:
         self.dim = int(dim)
         self.n = list(n)[: self.dim]
         self.shape = tuple(reversed(self.n))
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.precision = precision
-        self.ctype = torch.complex128 if precision == "f64" else torch.complex64
+        self.ctype = torch.complex64 if precision == "f32" else torch.complex128
+        self.npdtype = np.complex64 if precision == "f32" else np.complex128
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self.h = gp_init(dim, n, dx, dt, nkl, g, GP_F64 if precision == "f64" else GP_F32,
-                         stream.cuda_stream)
+        self.h = gp_init(dim, n, dx, dt, nkl, g, PRECISIONS[precision], stream.cuda_stream)
 
     def close(self):
         if self.h is not None:
@@ -313,8 +318,7 @@ class Propagator:
     def set_state(self, psi):
         torch = self.torch
         if isinstance(psi, np.ndarray):
-            a = np.ascontiguousarray(psi.reshape(self.shape),
-                                     dtype=np.complex128 if self.precision == "f64" else np.complex64)
+            a = np.ascontiguousarray(psi.reshape(self.shape), dtype=self.npdtype)
             gp_set_state(self.h, a.ctypes.data, 0)
             return
         t = psi.reshape(self.shape).to(dtype=self.ctype).contiguous()
@@ -327,7 +331,7 @@ class Propagator:
             out = torch.empty(self.shape, dtype=self.ctype, device="cuda")
             gp_get_state(self.h, out.data_ptr(), 1)
             return out
-        out = np.empty(self.shape, dtype=np.complex128 if self.precision == "f64" else np.complex64)
+        out = np.empty(self.shape, dtype=self.npdtype)
         gp_get_state(self.h, out.ctypes.data, 0)
         return out
 
@@ -419,6 +423,8 @@ class Batch:
         self.torch = torch
         self.sizes = [tuple(int(v) for v in s) for s in sizes]
         self.nruns = len(self.sizes)
+        if precision not in ("f64", "f32"):
+            raise ValueError("batched runs take precision 'f64' or 'f32'")
         self.precision = precision
         self.ctype = torch.complex128 if precision == "f64" else torch.complex64
         if stream is None:
