@@ -57,9 +57,14 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
+    ap.add_argument("--forms", default="f64,f32,df64",
+                    help="precision forms of the headline workload to time (the line needs f32; f64 for ratios)")
     ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint"],
                     help="time one form only (for profiling); the other forms are reported as null")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if "f32" not in args.forms.split(","):
+        ap.error("--forms must include f32 (the headline form)")
+    return args
 
 
 def replica_throughput(points_per_rank, seconds, device="cpu"):
@@ -263,15 +268,21 @@ def run_ours(args):
     results = {}
     # ---- mu accuracy of the FP32 form over the full job (untimed)
     mu = {}
+    forms_sel = [f for f in ("f64", "f32", "df64") if f in args.forms.split(",")]
+    mu_conv = {}
     if not args.no_mu_check:
-        for prec in ("f64", "f32"):
+        for prec in forms_sel:
             p = make(prec)
             with torch.cuda.stream(stream):
                 p.step_imag(w["job_steps"])
                 mu[prec] = p.observables()
+                # continued to 20000 steps: the state no longer changes (FP32: an
+                # exact fixed point of the rounded step), mu is the converged one
+                p.step_imag(20000 - w["job_steps"])
+                mu_conv[prec] = p.observables()
             p.close()
     # ---- timed forms
-    for prec in (("f64", "f32") if not args.no_headline else ()):
+    for prec in (forms_sel if not args.no_headline else ()):
         p = make(prec)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
@@ -281,6 +292,7 @@ def run_ours(args):
                 p.observables()
             barrier()
             l0 = gpe.gp_kernel_launches()
+            torch.cuda.nvtx.range_push(f"timed_{prec}")   # profilers can select the timed launches
             with ClockSampler(local) as clk:
                 for s in range(args.steps):
                     flush.fill_(float(s))                 # evict the state from L2
@@ -289,6 +301,7 @@ def run_ours(args):
                     p.observables()
                     ev[s][1].record(stream)
                 barrier()
+            torch.cuda.nvtx.range_pop()
             launches = gpe.gp_kernel_launches() - l0
             ms = [a.elapsed_time(b) for a, b in ev]
             # whole-job throughput over replicas: all ranks' points / slowest rank's time
@@ -358,7 +371,7 @@ def run_ours(args):
         qn, qdx = [256] * 3, [0.08] * 3
         qnp = 256 ** 3
         qphi = torch.tensor(inputs.gaussian_state(3, qn, qdx, [1.0] * 3, seed=1711, noise=1e-3), device="cuda")
-        for prec in ("f64", "f32"):
+        for prec in ("f64", "f32", "df64"):
             with torch.cuda.stream(stream):
                 q = gpe.Propagator(3, qn, qdx, 1e-3, [1.0] * 3, 20.0, precision=prec, stream=stream)
                 q.set_state(qphi)
@@ -382,7 +395,7 @@ def run_ours(args):
                 kms = q.time_sweeps(False, 16)
                 ob1 = q.observables()
                 q.close()
-            esize = 16 if prec == "f64" else 8
+            esize = 8 if prec == "f32" else 16
             axis = max(range(3), key=lambda d: kms[d])
             ach = 2 * esize * qnp / (kms[axis] * 1e-3) / 1e9
             qres[prec] = {"value": world * args.steps * args.inner * qnp / qt, "ms_per_step": 1e3 * qt / args.steps,
@@ -477,7 +490,7 @@ def run_ours(args):
         r = results[prec]
         kms = r["kernel_ms"]
         axis = max(range(3), key=lambda d: kms[d])
-        esize = 16 if prec == "f64" else 8
+        esize = 8 if prec == "f32" else 16
         algo = 2 * esize * np_                      # one read + one write of the state
         achieved = algo / (kms[axis] * 1e-3) / 1e9
         key = f"sweep_axis{axis}_{prec}_imag_128cube"
@@ -488,12 +501,19 @@ def run_ours(args):
                 "kernel_ms": kms}
 
     forms = {}
-    for prec in ("f64", "f32"):
+    for prec in forms_sel:
         r = results[prec]
         v = r["value"]
         forms[prec] = {"value": v, "ms_per_step": 1e3 * r["total_s"] / args.steps,
                        "mu": r["obs"]["mu"], "roofline": roofline(prec)}
-    mu_err = abs(mu["f32"]["mu"] - mu["f64"]["mu"]) if mu else None
+    mu_err = abs(mu["f32"]["mu"] - mu["f64"]["mu"]) if "f32" in mu and "f64" in mu else None
+    mu_err_df = abs(mu["df64"]["mu"] - mu["f64"]["mu"]) if "df64" in mu and "f64" in mu else None
+
+    def conv_err(prec):
+        return abs(mu_conv[prec]["mu"] - mu_conv["f64"]["mu"]) if prec in mu_conv and "f64" in mu_conv else None
+
+    def ratio(a, b):
+        return forms[a]["value"] / forms[b]["value"] if a in forms and b in forms else None
     cpu = None
     if not args.no_cpu_baseline:
         cpu = oracle_rate()
@@ -513,17 +533,25 @@ def run_ours(args):
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "forms": {
-            "f64": {"value": forms["f64"]["value"], "ms_per_step": forms["f64"]["ms_per_step"],
-                    "roofline": forms["f64"]["roofline"], "gpu_launches": results["f64"]["launches"],
-                    "clocks": results["f64"]["clocks"]},
-            "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": forms["f32"]["value"] / forms["f64"]["value"],
-                    "mu_err_vs_f64_full_job": mu_err,
-                    "mu_f32": mu["f32"]["mu"] if mu else None, "mu_f64": mu["f64"]["mu"] if mu else None},
+            "f64": ({"value": forms["f64"]["value"], "ms_per_step": forms["f64"]["ms_per_step"],
+                     "roofline": forms["f64"]["roofline"], "gpu_launches": results["f64"]["launches"],
+                     "clocks": results["f64"]["clocks"]} if "f64" in forms else None),
+            "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": ratio("f32", "f64"),
+                    "mu_err_vs_f64_full_job": mu_err, "mu_err_vs_f64_converged_20000_steps": conv_err("f32"),
+                    "mu_f32": mu["f32"]["mu"] if "f32" in mu else None,
+                    "mu_f64": mu["f64"]["mu"] if "f64" in mu else None},
+            "df64": ({"value": forms["df64"]["value"], "ms_per_step": forms["df64"]["ms_per_step"],
+                      "speedup_vs_f64": ratio("df64", "f64"),
+                      "mu_err_vs_f64_full_job": mu_err_df,
+                      "mu_err_vs_f64_converged_20000_steps": conv_err("df64"), "roofline": forms["df64"]["roofline"],
+                      "note": "double-float state and sweeps on the FP32 pipes (~48-bit), exact triple-float "
+                              "potential factors, FP64 reductions; FP32-ALU bound"} if "df64" in forms else None),
             "quench256": ({"workload": "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, imaginary-time "
                                        f"ground state at g=20 ({args.quench_imag_steps} steps) then g=40; L2 not flushed "
                                        "(state larger than L2)",
-                           "f64": qres.get("f64"), "f32": qres.get("f32"),
-                           "speedup_f32_vs_f64": qres["f32"]["value"] / qres["f64"]["value"]} if qres else None),
+                           "f64": qres.get("f64"), "f32": qres.get("f32"), "df64": qres.get("df64"),
+                           "speedup_f32_vs_f64": qres["f32"]["value"] / qres["f64"]["value"],
+                           "speedup_df64_vs_f64": qres["df64"]["value"] / qres["f64"]["value"]} if qres else None),
             "adjoint": ({"workload": "gradient of |<phi_target|phi(T)>|^2 w.r.t. V (per grid value) and g: 128^3, "
                                      "dx=0.1, dt=5e-4, 1000 real-time steps, g=30, isotropic trap + 8 Gaussian bumps "
                                      "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "

@@ -213,7 +213,7 @@ int gp_batch_destroy(gp_batch* b);
  *   out      device buffer of 7 doubles, written in stream order with
  *            {norm, energy, mu, rms_x, rms_y, rms_z, rms_r} (the gp_obs layout).
  *   stream   cudaStream_t the work is enqueued on (asynchronous).
- * Scratch space: one file-scope device array of about 448 KB, which every GPU
+ * Scratch space: one file-scope device array of about 600 KB, which every GPU
  * that loads the library holds until the process exits.  All calls share it
  * and it keeps the last call's contents (each call clears what must start at
  * zero), so calls that overlap on the GPU -- on different streams, or from

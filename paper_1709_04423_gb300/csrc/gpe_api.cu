@@ -391,7 +391,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
   if ((rc = dev_alloc(h, &h->psi, (size_t)np * h->esize))) return bail(rc);
   for (int d = 0; d < 3; ++d) {
     const int nd = axis_len(h, d);
-    std::vector<double> x(nd, 0.0), v(nd, 0.0), w(nd, 1.0);
+    std::vector<double> x(nd, 0.0), v(nd, 0.0), w(nd, 1.0), wc(nd, 1.0);
     if (d < dim) {
       for (int i = 0; i < nd; ++i) {
         x[i] = -0.5 * nd * dx[d] + i * dx[d];
@@ -402,8 +402,10 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
       for (int i = 0; i < nd; ++i) {
         double c = 0.0;
         if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
+        wc[i] = c;
         w[i] = c * dx[d] / 3.0;
       }
+      h->wscale *= dx[d] / 3.0;
     }
     if ((rc = dev_alloc(h, &h->vt[d], nd * tsz))) return bail(rc);
     if ((rc = dev_alloc(h, &h->fac[0][d], nd * h->esize))) return bail(rc);
@@ -412,12 +414,15 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     if ((rc = dev_alloc(h, (void**)&h->cdx[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->wd[d], nd * sizeof(double)))) return bail(rc);
     if ((rc = dev_alloc(h, &h->wt[d], nd * tsz))) return bail(rc);
+    if ((rc = dev_alloc(h, &h->ct[d], nd * tsz))) return bail(rc);
     if (prec == GP_DF64) {
       rc = upload_real<df64>(h, h->vt[d], v);
-      if (!rc) rc = upload_real<df64>(h, h->wt[d], w);
+      if (!rc) rc = upload_real<df64>(h, h->wt[d], wc);
+      if (!rc) rc = upload_real<df64>(h, h->ct[d], x);
     } else {
       rc = prec == GP_F64 ? upload_real<double>(h, h->vt[d], v) : upload_real<float>(h, h->vt[d], v);
-      if (!rc) rc = prec == GP_F64 ? upload_real<double>(h, h->wt[d], w) : upload_real<float>(h, h->wt[d], w);
+      if (!rc) rc = prec == GP_F64 ? upload_real<double>(h, h->wt[d], wc) : upload_real<float>(h, h->wt[d], wc);
+      if (!rc) rc = prec == GP_F64 ? upload_real<double>(h, h->ct[d], x) : upload_real<float>(h, h->ct[d], x);
     }
     if (rc) return bail(rc);
     if ((rc = upload_real<double>(h, h->vd[d], v))) return bail(rc);

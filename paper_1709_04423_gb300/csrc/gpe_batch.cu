@@ -168,7 +168,8 @@ struct gp_batch {
   int warp_seg = 16;                  // segment length of the warp-per-line class
   std::string launch_err;             // first failed launch of the current call
   // FP64 observables: per-run tables
-  std::vector<double*> vd, cdx, wd;   // [nruns][2] device arrays
+  std::vector<void*> vd, cdx, wd;     // [nruns][2] device arrays, observables' arithmetic type
+  void* ztab = nullptr;               // the absent z axis: v = c = 0 (slot 0), w = 1 (slot 1)
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   double* obs_out = nullptr;
@@ -459,19 +460,18 @@ int batch_observables(gp_batch* b) {
     a.hx = b->dx[2 * r];
     a.hy = b->dx[2 * r + 1];
     a.hz = 1.0;
-    a.vx = b->vd[2 * r]; a.vy = b->vd[2 * r + 1];
-    a.cx = b->cdx[2 * r]; a.cy = b->cdx[2 * r + 1];
-    a.wx = b->wd[2 * r]; a.wy = b->wd[2 * r + 1];
-    // absent z axis: single point with v = c = 0, w = 1 (the last three slots of obs_out's tail)
-    a.vz = b->obs_out + 8L * b->nruns;
-    a.cz = b->obs_out + 8L * b->nruns;
-    a.wz = b->obs_out + 8L * b->nruns + 1;
+    using R = obs_r<T>;
+    a.vx = (const R*)b->vd[2 * r]; a.vy = (const R*)b->vd[2 * r + 1];
+    a.cx = (const R*)b->cdx[2 * r]; a.cy = (const R*)b->cdx[2 * r + 1];
+    a.wx = (const R*)b->wd[2 * r]; a.wy = (const R*)b->wd[2 * r + 1];
+    a.vz = (const R*)b->ztab;
+    a.cz = (const R*)b->ztab;
+    a.wz = (const R*)b->ztab + 1;
+    a.wscale = b->dx[2 * r] * b->dx[2 * r + 1] / 9.0;  // the tables hold the Simpson coefficients
     a.partials = b->partials;
     a.counter = b->counter;
     a.out = b->obs_out + 8L * r;
-    const long np = (long)a.nx * a.ny;
-    const int blocks = (int)std::min<long>((np + 255) / 256, 152L * 16);
-    observables_kernel<T><<<blocks, 256, 0, b->work>>>(a);
+    launch_observables<T>(a, b->work);
     count_launch();
   }
   GP_CUDA(cudaGetLastError());
@@ -548,7 +548,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   if ((rc = b_alloc(b, &b->psi, (size_t)acc * b->esize))) return bail(rc);
   rc = prec == GP_F64 ? build_tables<double>(b) : build_tables<float>(b);
   if (rc) return bail(rc);
-  // FP64 tables of the observables, per run and axis
+  // tables of the observables, per run and axis, in their arithmetic type
   b->vd.resize(2 * nruns);
   b->cdx.resize(2 * nruns);
   b->wd.resize(2 * nruns);
@@ -563,26 +563,31 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
         v[i] = 0.5 * w * w * x[i] * x[i];
         double c = 0.0;
         if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
-        wt[i] = c * h / 3.0;
+        wt[i] = c;  // exact; the factor h/3 per axis is applied to the FP64 totals
       }
       void *pv, *pc, *pw;
-      if ((rc = b_alloc(b, &pv, na * sizeof(double))) || (rc = b_upload<double>(b, pv, v))) return bail(rc);
-      if ((rc = b_alloc(b, &pc, na * sizeof(double))) || (rc = b_upload<double>(b, pc, x))) return bail(rc);
-      if ((rc = b_alloc(b, &pw, na * sizeof(double))) || (rc = b_upload<double>(b, pw, wt))) return bail(rc);
-      b->vd[2 * r + a] = (double*)pv;
-      b->cdx[2 * r + a] = (double*)pc;
-      b->wd[2 * r + a] = (double*)pw;
+      const size_t rs = prec == GP_F64 ? sizeof(double) : sizeof(float);
+      auto up = [&](void* dst, const std::vector<double>& src) {
+        return prec == GP_F64 ? b_upload<double>(b, dst, src)
+                              : b_upload<float>(b, dst, std::vector<float>(src.begin(), src.end()));
+      };
+      if ((rc = b_alloc(b, &pv, na * rs)) || (rc = up(pv, v))) return bail(rc);
+      if ((rc = b_alloc(b, &pc, na * rs)) || (rc = up(pc, x))) return bail(rc);
+      if ((rc = b_alloc(b, &pw, na * rs)) || (rc = up(pw, wt))) return bail(rc);
+      b->vd[2 * r + a] = pv;
+      b->cdx[2 * r + a] = pc;
+      b->wd[2 * r + a] = pw;
     }
+  {
+    const std::vector<double> zw = {0.0, 1.0};
+    if ((rc = b_alloc(b, &b->ztab, 2 * sizeof(double)))) return bail(rc);
+    if ((rc = prec == GP_F64 ? b_upload<double>(b, b->ztab, zw)
+                             : b_upload<float>(b, b->ztab, std::vector<float>(zw.begin(), zw.end()))))
+      return bail(rc);
+  }
   if ((rc = b_alloc(b, (void**)&b->partials, 152L * 16 * 8 * sizeof(double)))) return bail(rc);
   if ((rc = b_alloc(b, (void**)&b->counter, 64))) return bail(rc);
   if ((rc = b_alloc(b, (void**)&b->obs_out, (8L * nruns + 8) * sizeof(double)))) return bail(rc);
-  {
-    // the absent z axis of the observables: v = c = 0 (slot 0), w = 1 (slot 1)
-    const double zw[2] = {0.0, 1.0};
-    cudaError_t e = cudaMemcpyAsync(b->obs_out + 8L * nruns, zw, sizeof(zw), cudaMemcpyHostToDevice, b->work);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->work);
-    if (e != cudaSuccess) return bail(fail(GP_ERR_CUDA, std::string("gp_batch_init: ") + cudaGetErrorString(e)));
-  }
   *out = b;
   return GP_OK;
 }

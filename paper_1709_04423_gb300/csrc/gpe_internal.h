@@ -78,6 +78,8 @@ struct gp_handle {
   double* cdx[3] = {nullptr, nullptr, nullptr};  // coordinates
   double* wd[3] = {nullptr, nullptr, nullptr};   // Simpson weights
   void* wt[3] = {nullptr, nullptr, nullptr};     // Simpson weights, state precision
+  void* ct[3] = {nullptr, nullptr, nullptr};     // coordinates, state precision (FP32 observables)
+  double wscale = 1.0;                           // prod_d dx_d/3: wt holds the Simpson coefficients
   // per (mode, axis): [0] alpha_k, [1 + 2 s] forward and [2 + 2 s] backward
   // segment products for segment length kSegs[s]; each n complex values
   void* coef[gpe::NUM_MODES][3] = {{nullptr}};

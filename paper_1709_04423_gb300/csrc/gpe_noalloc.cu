@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "gpe_internal.h"
 #include "gpe_obs.cuh"
@@ -25,13 +26,15 @@ namespace {
 
 constexpr int kMaxAxis = 4096;          // points per axis at most
 constexpr int kBlocks = 152 * 16;       // reduction grid (at most)
-constexpr int kThreads = 256;
-// layout, in doubles: [3 axes][v, coord, weight][kMaxAxis] | partials | sums | counter
+// layout, in doubles: [3 axes][v, coord, weight][kMaxAxis] | the same tables
+// as floats (FP32 states) | partials | sums | counter
 constexpr long kAxisOff = 0;
-constexpr long kPartOff = kAxisOff + 3L * 3 * kMaxAxis;
+constexpr long kAxisOffF = kAxisOff + 3L * 3 * kMaxAxis;
+constexpr long kPartOff = kAxisOffF + 3L * 3 * kMaxAxis / 2;
 constexpr long kSumOff = kPartOff + 8L * kBlocks;
 constexpr long kCntOff = kSumOff + 8;
-constexpr long kScratchDoubles = kCntOff + 32;  // about 448 KB in all
+constexpr long kScratchDoubles = kCntOff + 32;  // about 600 KB in all
+static_assert(kBlocks >= gpe::kObsBlocks, "partial slots for every block of the reduction");
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -50,9 +53,13 @@ __global__ void noalloc_setup_kernel(double* scratch, int dim, int nx, int ny, i
     double* v = scratch + kAxisOff + (3L * d + 0) * kMaxAxis;
     double* c = scratch + kAxisOff + (3L * d + 1) * kMaxAxis;
     double* w = scratch + kAxisOff + (3L * d + 2) * kMaxAxis;
+    float* vf = (float*)(scratch + kAxisOffF) + (3L * d + 0) * kMaxAxis;
+    float* cf = (float*)(scratch + kAxisOffF) + (3L * d + 1) * kMaxAxis;
+    float* wf = (float*)(scratch + kAxisOffF) + (3L * d + 2) * kMaxAxis;
     if (i >= nn[d]) continue;
     if (d >= dim) {
       v[i] = 0.0; c[i] = 0.0; w[i] = 1.0;
+      vf[i] = 0.f; cf[i] = 0.f; wf[i] = 1.f;
       continue;
     }
     const int n = nn[d];
@@ -63,6 +70,9 @@ __global__ void noalloc_setup_kernel(double* scratch, int dim, int nx, int ny, i
     double wc = 0.0;
     if (i < m) wc = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
     w[i] = wc * hh[d] / 3.0;
+    vf[i] = (float)v[i];
+    cf[i] = (float)c[i];
+    wf[i] = (float)wc;  // FP32 tables: the exact Simpson coefficient (factor applied to the totals)
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *(unsigned int*)(scratch + kCntOff) = 0u;
 }
@@ -107,22 +117,25 @@ void launch_obs(double* scratch, int dim, const int* n3, const double* dx3, cons
   a.nx = n3[0]; a.ny = n3[1]; a.nz = n3[2];
   a.hx = dx3[0]; a.hy = dx3[1]; a.hz = dx3[2];
   a.V = V;
-  a.vx = scratch + kAxisOff + 0L * kMaxAxis;
-  a.cx = scratch + kAxisOff + 1L * kMaxAxis;
-  a.wx = scratch + kAxisOff + 2L * kMaxAxis;
-  a.vy = scratch + kAxisOff + 3L * kMaxAxis;
-  a.cy = scratch + kAxisOff + 4L * kMaxAxis;
-  a.wy = scratch + kAxisOff + 5L * kMaxAxis;
-  a.vz = scratch + kAxisOff + 6L * kMaxAxis;
-  a.cz = scratch + kAxisOff + 7L * kMaxAxis;
-  a.wz = scratch + kAxisOff + 8L * kMaxAxis;
+  using R = gpe::obs_r<T>;
+  const R* tab = std::is_same<R, float>::value ? (const R*)(scratch + kAxisOffF) : (const R*)(scratch + kAxisOff);
+  a.vx = tab + 0L * kMaxAxis;
+  a.cx = tab + 1L * kMaxAxis;
+  a.wx = tab + 2L * kMaxAxis;
+  a.vy = tab + 3L * kMaxAxis;
+  a.cy = tab + 4L * kMaxAxis;
+  a.wy = tab + 5L * kMaxAxis;
+  a.vz = tab + 6L * kMaxAxis;
+  a.cz = tab + 7L * kMaxAxis;
+  a.wz = tab + 8L * kMaxAxis;
+  a.wscale = 1.0;
+  if (std::is_same<R, float>::value)
+    for (int d = 0; d < dim; ++d) a.wscale *= dx3[d] / 3.0;
   a.density = nullptr;
   a.partials = scratch + kPartOff;
   a.counter = (unsigned int*)(scratch + kCntOff);
   a.out = scratch + kSumOff;
-  const long np = (long)n3[0] * n3[1] * n3[2];
-  const int blocks = (int)std::min<long>((np + kThreads - 1) / kThreads, kBlocks);
-  gpe::observables_kernel<T><<<blocks, kThreads, 0, s>>>(a);
+  gpe::launch_observables<T>(a, s);
   gpe::count_launch();
 }
 

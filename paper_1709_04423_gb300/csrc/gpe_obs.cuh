@@ -8,7 +8,17 @@
 //   S2 = sum w V |phi|^2                     (potential)
 //   S3 = sum w |phi|^4                       (interaction)
 //   S4..S6 = sum w x_d^2 |phi|^2             (second moments)
-// all in FP64, whatever the state's precision; the host turns them into
+// The weights are either the FP64 Simpson weights or, for an FP32 state,
+// the exact Simpson coefficients (1, 2, 4) with the factor prod dx/3 applied
+// to the FP64 totals.
+// The per-point terms are formed in the arithmetic type R of the state (float
+// for an FP32 state, double otherwise) and summed per thread in R over the
+// thread's 10-100 points; the per-thread sums are then reduced over the
+// block (warp shuffles) and the grid (fixed order) in FP64.  FP32 rounding
+// of the terms is of the size of the FP32 state's own rounding and averages
+// out over the grid; an FP64 term per point would cost more than the
+// propagation steps themselves on a part whose FP64 rate is 1/70 of FP32.
+// The host turns the sums into
 // E = (S1+S2)/S0 + g/2 S3/S0^2, mu = (S1+S2)/S0 + g S3/S0^2, rms_d = sqrt(S_{4+d}/S0).
 // Derivatives: 4th-order central differences for 2 <= i <= n-3, 2nd-order at
 // i = 1, n-2, zero at the end points.  Optionally writes |phi|^2 (FP64).
@@ -17,76 +27,112 @@
 
 namespace gpe {
 
+// arithmetic type of the per-point terms
+template <typename T> struct ObsReal { using type = double; };
+template <> struct ObsReal<float> { using type = float; };
+template <typename T> using obs_r = typename ObsReal<T>::type;
+
 template <typename T>
 struct ObsArgs {
   const c2_t<T>* psi;
   int dim, nx, ny, nz;
   double hx, hy, hz;        // grid spacings
   const double* V;          // full potential or nullptr
-  const double* vx; const double* vy; const double* vz;  // separable trap terms
-  const double* cx; const double* cy; const double* cz;  // coordinates
-  const double* wx; const double* wy; const double* wz;  // Simpson weights
+  // per-axis tables in the arithmetic type: separable trap terms, coordinates,
+  // Simpson weights
+  const obs_r<T>* vx; const obs_r<T>* vy; const obs_r<T>* vz;
+  const obs_r<T>* cx; const obs_r<T>* cy; const obs_r<T>* cz;
+  const obs_r<T>* wx; const obs_r<T>* wy; const obs_r<T>* wz;
+  double wscale;            // factor of the FP64 totals (1, or prod dx/3 with coefficient weights)
   double* density;          // optional |phi|^2 output
   double* partials;
   unsigned int* counter;
   double* out;              // [7] sums
 };
 
-template <typename T>
-__device__ __forceinline__ double2 ld2(const c2_t<T>* p, long q) {
-  c2_t<T> v = p[q];
-  return make_double2((double)v.x, (double)v.y);
-}
-
-template <typename T>
-__device__ __forceinline__ double grad2_axis(const c2_t<T>* psi, long q, int i, int n, long s, double h) {
-  if (i == 0 || i == n - 1) return 0.0;
-  double2 d;
+// |d phi / d axis|^2 at point q (index i of n along the axis, stride s);
+// f1 = 1/(2h), f4 = 1/(12h)
+template <typename T, typename R>
+__device__ __forceinline__ R grad2_axis(const c2_t<T>* psi, long q, int i, int n, long s, R f1, R f4) {
+  if (i == 0 || i == n - 1) return R(0);
+  R dx, dy;
   if (i == 1 || i == n - 2) {
-    double2 a = ld2<T>(psi, q - s), b = ld2<T>(psi, q + s);
-    const double f = 1.0 / (2.0 * h);
-    d = make_double2((b.x - a.x) * f, (b.y - a.y) * f);
+    const c2_t<T> a = psi[q - s], b = psi[q + s];
+    dx = (R(b.x) - R(a.x)) * f1;
+    dy = (R(b.y) - R(a.y)) * f1;
   } else {
-    double2 a = ld2<T>(psi, q - 2 * s), b = ld2<T>(psi, q - s), c = ld2<T>(psi, q + s), e = ld2<T>(psi, q + 2 * s);
-    const double f = 1.0 / (12.0 * h);
-    d = make_double2((a.x - 8.0 * b.x + 8.0 * c.x - e.x) * f, (a.y - 8.0 * b.y + 8.0 * c.y - e.y) * f);
+    const c2_t<T> a = psi[q - 2 * s], b = psi[q - s], c = psi[q + s], e = psi[q + 2 * s];
+    dx = (R(a.x) - R(8) * R(b.x) + R(8) * R(c.x) - R(e.x)) * f4;
+    dy = (R(a.y) - R(8) * R(b.y) + R(8) * R(c.y) - R(e.y)) * f4;
   }
-  return d.x * d.x + d.y * d.y;
+  return dx * dx + dy * dy;
 }
 
+constexpr int kObsThreads = 256;
+constexpr int kObsBlocks = 152 * 4;   // at most; 10-100 points per thread on large grids
+
+// Rows r = j + ny k of the grid are spread over the blocks; 2^tx_log2
+// threads of a row-group take consecutive x indices (coalesced), and each
+// thread keeps its x-dependent table values across the rows it visits.
 template <typename T>
-__global__ void __launch_bounds__(256) observables_kernel(ObsArgs<T> A) {
+__global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, int tx_log2) {
+  using R = obs_r<T>;
   __shared__ double smem[32 * 7];
-  const long np = (long)A.nx * A.ny * A.nz;
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % A.nx);
-    const long r = q / A.nx;
-    const int j = (int)(r % A.ny);
-    const int k = (int)(r / A.ny);
-    const double2 p = ld2<T>(A.psi, q);
-    const double dens = p.x * p.x + p.y * p.y;
-    double g2 = grad2_axis<T>(A.psi, q, i, A.nx, 1, A.hx);
-    if (A.dim > 1) g2 += grad2_axis<T>(A.psi, q, j, A.ny, A.nx, A.hy);
-    if (A.dim > 2) g2 += grad2_axis<T>(A.psi, q, k, A.nz, (long)A.nx * A.ny, A.hz);
-    const double Vq = A.V ? A.V[q] : (A.vx[i] + A.vy[j] + A.vz[k]);
-    const double w = A.wx[i] * A.wy[j] * A.wz[k];
-    const double wd = w * dens;
-    v[0] += wd;
-    v[1] += 0.5 * w * g2;
-    v[2] += wd * Vq;
-    v[3] += wd * dens;
-    v[4] += wd * A.cx[i] * A.cx[i];
-    v[5] += wd * A.cy[j] * A.cy[j];
-    v[6] += wd * A.cz[k] * A.cz[k];
-    if (A.density) A.density[q] = dens;
+  const int TX = 1 << tx_log2;
+  const int tx = threadIdx.x & (TX - 1), ty = threadIdx.x >> tx_log2, rpb = blockDim.x >> tx_log2;
+  const int nrows = A.ny * A.nz;
+  const long sy = A.nx, sz = (long)A.nx * A.ny;
+  const R fx1 = R(1.0 / (2.0 * A.hx)), fx4 = R(1.0 / (12.0 * A.hx));
+  const R fy1 = R(1.0 / (2.0 * A.hy)), fy4 = R(1.0 / (12.0 * A.hy));
+  const R fz1 = R(1.0 / (2.0 * A.hz)), fz4 = R(1.0 / (12.0 * A.hz));
+  R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  for (int i = tx; i < A.nx; i += TX) {
+    const R vxi = A.vx[i], cxi = A.cx[i], wxi = A.wx[i];
+    for (int r = blockIdx.x * rpb + ty; r < nrows; r += gridDim.x * rpb) {
+      const int j = r % A.ny, k = r / A.ny;
+      const long q = (long)r * A.nx + i;
+      const c2_t<T> p = A.psi[q];
+      const R px = R(p.x), py = R(p.y);
+      const R dens = px * px + py * py;
+      R g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4);
+      if (A.dim > 1) g2 += grad2_axis<T, R>(A.psi, q, j, A.ny, sy, fy1, fy4);
+      if (A.dim > 2) g2 += grad2_axis<T, R>(A.psi, q, k, A.nz, sz, fz1, fz4);
+      const R Vq = A.V ? R(A.V[q]) : (vxi + A.vy[j] + A.vz[k]);
+      const R w = wxi * A.wy[j] * A.wz[k];
+      const R wd = w * dens;
+      acc[0] += wd;
+      acc[1] += R(0.5) * w * g2;
+      acc[2] += wd * Vq;
+      acc[3] += wd * dens;
+      acc[4] += wd * cxi * cxi;
+      const R cy = A.cy[j], cz = A.cz[k];
+      acc[5] += wd * cy * cy;
+      acc[6] += wd * cz * cz;
+      if (A.density) A.density[q] = (double)dens;
+    }
   }
+  double v[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) v[q] = (double)acc[q];  // FP64 from here on
   block_sum<7>(v, smem);
   double tot[7];
   if (grid_sum_last<7>(v, A.partials, A.counter, tot, smem) && threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) A.out[q] = tot[q];
+    for (int q = 0; q < 7; ++q) A.out[q] = tot[q] * A.wscale;
   }
+}
+
+// The one launch configuration of the reduction (every caller uses it, so
+// that equal states give bitwise equal sums).
+template <typename T>
+inline void launch_observables(const ObsArgs<T>& a, cudaStream_t s) {
+  int lg = 5;
+  while ((1 << lg) < a.nx && lg < 8) ++lg;  // 32..256 threads per row
+  const int rpb = kObsThreads >> lg;
+  const long nrows = (long)a.ny * a.nz;
+  const long want = (nrows + rpb - 1) / rpb;
+  const int blocks = (int)(want < kObsBlocks ? want : kObsBlocks);
+  observables_kernel<T><<<blocks, kObsThreads, 0, s>>>(a, lg);
 }
 
 }  // namespace gpe

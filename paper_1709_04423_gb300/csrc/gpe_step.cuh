@@ -21,7 +21,6 @@ namespace gpe {
 
 constexpr int kLegacyThreads = 128;
 constexpr int kXWarps = 4;
-constexpr int kObsThreads = 256;
 constexpr int kGraphSteps = 16;  // even: keeps the renormalisation-slot parity
 
 inline LineGeom geom_of(const gp_handle* h, int axis) {
@@ -200,6 +199,7 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
     a.w_axis = (const T*)h->wt[d];
     a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
     a.w_b = (const T*)(d == 2 ? h->wt[1] : h->wt[2]);
+    a.wscale = h->wscale;
     a.partials = h->partials;
     a.counter = h->counter;
     a.scale_out = h->scale + (1 - par);
@@ -381,15 +381,24 @@ int run_observables_t(gp_handle* h, double* dens_dev) {
   a.hy = h->dx[1];
   a.hz = h->dx[2];
   a.V = h->Vd;
-  a.vx = h->vd[0]; a.vy = h->vd[1]; a.vz = h->vd[2];
-  a.cx = h->cdx[0]; a.cy = h->cdx[1]; a.cz = h->cdx[2];
-  a.wx = h->wd[0]; a.wy = h->wd[1]; a.wz = h->wd[2];
+  if constexpr (std::is_same<T, float>::value) {  // tables in the state precision
+    for (int d = 0; d < 3; ++d) {
+      (d == 0 ? a.vx : d == 1 ? a.vy : a.vz) = (const float*)h->vt[d];
+      (d == 0 ? a.cx : d == 1 ? a.cy : a.cz) = (const float*)h->ct[d];
+      (d == 0 ? a.wx : d == 1 ? a.wy : a.wz) = (const float*)h->wt[d];  // Simpson coefficients
+    }
+    a.wscale = h->wscale;
+  } else {
+    a.vx = h->vd[0]; a.vy = h->vd[1]; a.vz = h->vd[2];
+    a.cx = h->cdx[0]; a.cy = h->cdx[1]; a.cz = h->cdx[2];
+    a.wx = h->wd[0]; a.wy = h->wd[1]; a.wz = h->wd[2];
+    a.wscale = 1.0;
+  }
   a.density = dens_dev;
   a.partials = h->partials;
   a.counter = h->counter;
   a.out = h->obs_out;
-  const int blocks = (int)std::min<long>((h->np + kObsThreads - 1) / kObsThreads, 152L * 16);
-  observables_kernel<T><<<blocks, kObsThreads, 0, h->work>>>(a);
+  launch_observables<T>(a, h->work);
   count_launch();
   GP_CUDA(cudaGetLastError());
   return GP_OK;

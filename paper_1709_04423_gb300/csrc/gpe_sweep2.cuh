@@ -79,8 +79,12 @@ struct Sweep2Args {
   const tf3c* tfyz;
   const double* scale_in;
   // norm (LAST)
-  const T* w_axis;       // Simpson weights along the line, state precision
-  const T* w_a; const T* w_b;  // weights of the two transverse indices, state precision
+  // Simpson coefficients (1, 2, 4: exact in any precision) along the line and
+  // of the two transverse indices; the grid factor prod_d dx_d/3 is applied
+  // to the FP64 total, so no rounded weight biases the norm
+  const T* w_axis;
+  const T* w_a; const T* w_b;
+  double wscale;
   double* partials;
   unsigned int* counter;
   double* scale_out;
@@ -125,7 +129,11 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
 }
 
 // FP32 state: p <- exp(-i th) p or exp(-th) p with th = dt (V + g |p|^2)
-// formed per point (library sincos / exp of the state precision).
+// formed per point (library sincos / exp of the state precision).  (Applying
+// the factor as p + (factor - 1) p with expm1 was measured to move the FP32
+// ground state's mu further from FP64: the FP32 iteration stops at an exact
+// fixed point of the rounded map, whose mu depends on how each sub-step
+// rounds, and that form stops 1.3e-6 away against 8e-9 for the product.)
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
   const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
@@ -361,7 +369,7 @@ __device__ __forceinline__ int line_base32(const LineGeom& g, int L) {
 // (fixed order, last block); the result sets the next renormalisation factor.
 template <typename T, bool LAST>
 __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned int* counter, double* scale_out,
-                                            double* red_smem) {
+                                            double wscale, double* red_smem) {
   if (LAST) {
     __shared__ T tred[32];
 #pragma unroll
@@ -376,7 +384,8 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
       for (int o = 16; o > 0; o >>= 1) b += shfl_xor_t(b, o);
       v[0] = (double)b;  // FP64 from here on
     }
-    if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0) *scale_out = 1.0 / sqrt(tot[0]);
+    if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0)
+      *scale_out = 1.0 / sqrt(tot[0] * wscale);
   }
 }
 
@@ -445,7 +454,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
     }
     if (LAST) nval = tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
 }
 
 template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
@@ -551,7 +560,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     const int gbase = (L0 + c) * G.nx;
     for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
@@ -666,7 +675,7 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     if (lane == 31) line[G.n - 1] = mk<T>(0, 0);
     if (LAST) nval = tacc * (A.w_a[ta] * A.w_b[tb]);
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
@@ -837,7 +846,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
     __syncthreads();  // the stage is refilled by the prefetch of the next iteration
   }
   cp_async_wait<0>();
-  finish_norm<T, LAST>(tval, A.partials, A.counter, A.scale_out, red_smem);
+  finish_norm<T, LAST>(tval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
 }
 
 }  // namespace gpe
