@@ -457,7 +457,14 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
   for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, h->np / h->n[d] / 4 + 1);
   if ((rc = dev_alloc(h, (void**)&h->partials, (size_t)maxblocks * 8 * sizeof(double)))) return bail(rc);
   if ((rc = dev_alloc(h, (void**)&h->counter, 64))) return bail(rc);
-  if ((rc = dev_alloc(h, (void**)&h->scale, 2 * sizeof(double)))) return bail(rc);
+  {
+    // one norm sum per block of any last sweep: 32 lines per block (tiles and
+    // y/z sweeps), 4 (one-warp x lines), 128 (long lines), or a persistent grid
+    long maxparts = 152L * 32;
+    for (int d = 0; d < dim; ++d) maxparts = std::max(maxparts, h->np / h->n[d] / 4 + 1);
+    for (int i = 0; i < 2; ++i)
+      if ((rc = dev_alloc(h, (void**)&h->parts[i], (size_t)maxparts * sizeof(double)))) return bail(rc);
+  }
   if ((rc = dev_alloc(h, (void**)&h->obs_out, 8 * sizeof(double)))) return bail(rc);
   {
     cudaError_t e = cudaStreamSynchronize(h->work);

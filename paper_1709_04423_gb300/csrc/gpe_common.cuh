@@ -108,4 +108,29 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials, 
   return true;
 }
 
+// Pending renormalisation factor of an imaginary-time step's input.  The
+// previous step's last sweep left one norm sum per block in parts[0..nparts);
+// one warp of every block of the reading kernel sums them in the same fixed
+// order (lane-strided FP64 sums, then a butterfly), so all blocks -- and every
+// run -- obtain the same factor 1/sqrt(wscale * total).
+__device__ __forceinline__ double pending_factor_warp(const double* parts, int nparts, double wscale) {
+  double acc = 0.0;
+  for (int b = threadIdx.x & 31; b < nparts; b += 32) acc += __ldcg(&parts[b]);
+  return 1.0 / sqrt(warp_sum(acc) * wscale);
+}
+
+// The same for the whole block: parts == nullptr means no pending factor (1).
+// Every thread of the block must call it (two block barriers).
+__device__ __forceinline__ double pending_scale(const double* parts, int nparts, double wscale, double* smem) {
+  if (!parts) return 1.0;
+  if (threadIdx.x < 32) {
+    const double f = pending_factor_warp(parts, nparts, wscale);
+    if (threadIdx.x == 0) smem[0] = f;
+  }
+  __syncthreads();
+  const double f = smem[0];
+  __syncthreads();  // smem free again
+  return f;
+}
+
 }  // namespace gpe

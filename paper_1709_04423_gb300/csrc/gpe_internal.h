@@ -98,7 +98,11 @@ struct gp_handle {
   // persistent double-buffered sweeps (x needs tile_x); only where two
   // shared-memory stages of 32 lines fit
   bool pipe_x = false, pipe_c = false;
-  double* scale = nullptr;   // [2] renormalisation slots
+  // imaginary time: per-block norm sums of a step's last sweep, two slots
+  // alternating with the step parity, their count and grid factor
+  double* parts[2] = {nullptr, nullptr};
+  int parts_n = 0;
+  double parts_ws = 1.0;
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   double* obs_out = nullptr;  // [8]

@@ -41,27 +41,30 @@ inline const c2_t<T>* coef_ptr(const gp_handle* h, int mode, int axis, int slot)
 }
 
 // ---- segmented x sweep
+// Every launcher returns its number of blocks (a LAST sweep leaves one norm
+// sum per block for the next step's reader).
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-void launch_x(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_x(const Sweep2Args<T>& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)((a.geom.nlines + kXWarps - 1) / kXWarps);
   xsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * kXWarps, 0, s>>>(a);
   count_launch();
+  return blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST>
-void launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
   switch (seg) {
-    case 1: launch_x<T, IMAG, FIRST, LAST, 1>(a, s); break;
-    case 2: launch_x<T, IMAG, FIRST, LAST, 2>(a, s); break;
-    case 4: launch_x<T, IMAG, FIRST, LAST, 4>(a, s); break;
-    case 8: launch_x<T, IMAG, FIRST, LAST, 8>(a, s); break;
-    default: launch_x<T, IMAG, FIRST, LAST, 16>(a, s); break;
+    case 1: return launch_x<T, IMAG, FIRST, LAST, 1>(a, s);
+    case 2: return launch_x<T, IMAG, FIRST, LAST, 2>(a, s);
+    case 4: return launch_x<T, IMAG, FIRST, LAST, 4>(a, s);
+    case 8: return launch_x<T, IMAG, FIRST, LAST, 8>(a, s);
+    default: return launch_x<T, IMAG, FIRST, LAST, 16>(a, s);
   }
 }
 
 // ---- segmented y/z sweep (registers, coefficients in shared memory)
 template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
-void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
@@ -74,23 +77,24 @@ void launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
   }
   colsweep_kernel<T, IMAG, LAST, SEG, KEEP><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
+  return blocks;
 }
 
 // keep = 1: input segment in registers (only for short segments); 0: streamed
 template <typename T, bool IMAG, bool LAST>
-void launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s) {
   const bool k = keep && seg * (int)sizeof(T) <= 64;
   switch (seg) {
-    case 4: k ? launch_c<T, IMAG, LAST, 4, true>(a, s) : launch_c<T, IMAG, LAST, 4, false>(a, s); break;
-    case 8: k ? launch_c<T, IMAG, LAST, 8, true>(a, s) : launch_c<T, IMAG, LAST, 8, false>(a, s); break;
-    case 16: k ? launch_c<T, IMAG, LAST, 16, true>(a, s) : launch_c<T, IMAG, LAST, 16, false>(a, s); break;
-    default: launch_c<T, IMAG, LAST, 32, false>(a, s); break;
+    case 4: return k ? launch_c<T, IMAG, LAST, 4, true>(a, s) : launch_c<T, IMAG, LAST, 4, false>(a, s);
+    case 8: return k ? launch_c<T, IMAG, LAST, 8, true>(a, s) : launch_c<T, IMAG, LAST, 8, false>(a, s);
+    case 16: return k ? launch_c<T, IMAG, LAST, 16, true>(a, s) : launch_c<T, IMAG, LAST, 16, false>(a, s);
+    default: return launch_c<T, IMAG, LAST, 32, false>(a, s);
   }
 }
 
 // ---- shared-memory tile x sweep
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-void launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
@@ -103,15 +107,16 @@ void launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
   }
   tsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
+  return blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST>
-void launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
   switch (seg) {
-    case 4: launch_t<T, IMAG, FIRST, LAST, 4>(a, s); break;
-    case 8: launch_t<T, IMAG, FIRST, LAST, 8>(a, s); break;
-    case 16: launch_t<T, IMAG, FIRST, LAST, 16>(a, s); break;
-    default: launch_t<T, IMAG, FIRST, LAST, 32>(a, s); break;
+    case 4: return launch_t<T, IMAG, FIRST, LAST, 4>(a, s);
+    case 8: return launch_t<T, IMAG, FIRST, LAST, 8>(a, s);
+    case 16: return launch_t<T, IMAG, FIRST, LAST, 16>(a, s);
+    default: return launch_t<T, IMAG, FIRST, LAST, 32>(a, s);
   }
 }
 
@@ -123,7 +128,7 @@ inline size_t psweep_smem(int n, bool axis0) {
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool AXIS0>
-void launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const int ntiles = (int)((a.geom.nlines + 31) / 32);
@@ -142,31 +147,44 @@ void launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
   const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * std::max(1, sms)));
   psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0><<<blocks, 32 * nseg, smem, s>>>(a);
   count_launch();
+  return (unsigned)blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, bool AXIS0>
-void launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
   switch (seg) {
-    case 4: launch_p<T, IMAG, FIRST, LAST, 4, AXIS0>(a, s); break;
-    case 8: launch_p<T, IMAG, FIRST, LAST, 8, AXIS0>(a, s); break;
-    case 16: launch_p<T, IMAG, FIRST, LAST, 16, AXIS0>(a, s); break;
-    default: launch_p<T, IMAG, FIRST, LAST, 32, AXIS0>(a, s); break;
+    case 4: return launch_p<T, IMAG, FIRST, LAST, 4, AXIS0>(a, s);
+    case 8: return launch_p<T, IMAG, FIRST, LAST, 8, AXIS0>(a, s);
+    case 16: return launch_p<T, IMAG, FIRST, LAST, 16, AXIS0>(a, s);
+    default: return launch_p<T, IMAG, FIRST, LAST, 32, AXIS0>(a, s);
   }
 }
 
 // ---- thread-per-line fallback (lines longer than the segmented kernels take)
 template <typename T, bool IMAG, bool FIRST, bool LAST>
-void launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
+unsigned launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)((a.geom.nlines + kLegacyThreads - 1) / kLegacyThreads);
   cn_sweep_kernel<T, IMAG, FIRST, LAST><<<blocks, kLegacyThreads, 0, s>>>(a);
   count_launch();
+  return blocks;
 }
 
+// Slots of the imaginary-time renormalisation: step t > 0 of a call reads the
+// per-block norm sums left by step t-1 in slot (t-1) & 1 and its last sweep
+// writes slot t & 1; step 0 reads nothing (the state is taken as given).
+struct NormSlots {
+  int rd = -1, wr = -1;
+};
+
 template <typename T>
-void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nullptr) {
+void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr) {
   const bool first = d == 0, last = d == h->dim - 1;
   const int mode = imag ? MODE_IMAG : MODE_REAL;
   const int seg = d == 0 ? h->seg_x : h->seg_c;
+  const bool read = imag && first && ns.rd >= 0, write = imag && last;
+  const double* parts_in = read ? h->parts[ns.rd] : nullptr;
+  double* parts_out = write ? h->parts[ns.wr] : nullptr;
+  unsigned blocks = 0;
   if (seg > 0) {
     Sweep2Args<T> a;
     std::memset(&a, 0, sizeof(a));
@@ -195,55 +213,59 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
       a.tfx = (const tf3c*)h->tfx[fm];
       a.tfyz = (const tf3c*)h->tfyz[fm];
     }
-    a.scale_in = imag ? h->scale + par : nullptr;
+    a.parts_in = parts_in;
+    a.nparts_in = h->parts_n;
+    a.parts_wscale = h->parts_ws;
     a.w_axis = (const T*)h->wt[d];
     a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
     a.w_b = (const T*)(d == 2 ? h->wt[1] : h->wt[2]);
-    a.wscale = h->wscale;
-    a.partials = h->partials;
-    a.counter = h->counter;
-    a.scale_out = h->scale + (1 - par);
+    a.parts_out = parts_out;
+    bool done = false;
     if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
       if (d == 0 && h->tile_x && h->pipe_x) {
         if (imag) {
-          if (last) launch_p_seg<T, true, true, true, true>(seg, a, h->work);
-          else launch_p_seg<T, true, true, false, true>(seg, a, h->work);
+          blocks = last ? launch_p_seg<T, true, true, true, true>(seg, a, h->work)
+                        : launch_p_seg<T, true, true, false, true>(seg, a, h->work);
         } else {
-          launch_p_seg<T, false, true, false, true>(seg, a, h->work);
+          blocks = launch_p_seg<T, false, true, false, true>(seg, a, h->work);
         }
-        return;
-      }
-      if (d > 0 && h->pipe_c) {
+        done = true;
+      } else if (d > 0 && h->pipe_c) {
         if (imag) {
-          if (last) launch_p_seg<T, true, false, true, false>(seg, a, h->work);
-          else launch_p_seg<T, true, false, false, false>(seg, a, h->work);
+          blocks = last ? launch_p_seg<T, true, false, true, false>(seg, a, h->work)
+                        : launch_p_seg<T, true, false, false, false>(seg, a, h->work);
         } else {
-          launch_p_seg<T, false, false, false, false>(seg, a, h->work);
+          blocks = launch_p_seg<T, false, false, false, false>(seg, a, h->work);
         }
-        return;
+        done = true;
       }
     }
-    if (d == 0 && h->tile_x) {
+    if (done) {
+    } else if (d == 0 && h->tile_x) {
       if (imag) {
-        if (last) launch_t_seg<T, true, true, true>(seg, a, h->work);
-        else launch_t_seg<T, true, true, false>(seg, a, h->work);
+        blocks = last ? launch_t_seg<T, true, true, true>(seg, a, h->work)
+                      : launch_t_seg<T, true, true, false>(seg, a, h->work);
       } else {
-        launch_t_seg<T, false, true, false>(seg, a, h->work);
+        blocks = launch_t_seg<T, false, true, false>(seg, a, h->work);
       }
     } else if (d == 0) {
       if (imag) {
-        if (last) launch_x_seg<T, true, true, true>(seg, a, h->work);
-        else launch_x_seg<T, true, true, false>(seg, a, h->work);
+        blocks = last ? launch_x_seg<T, true, true, true>(seg, a, h->work)
+                      : launch_x_seg<T, true, true, false>(seg, a, h->work);
       } else {
-        launch_x_seg<T, false, true, false>(seg, a, h->work);
+        blocks = launch_x_seg<T, false, true, false>(seg, a, h->work);
       }
     } else {
       if (imag) {
-        if (last) launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work);
-        else launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work);
+        blocks = last ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work)
+                      : launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work);
       } else {
-        launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
+        blocks = launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
       }
+    }
+    if (write) {
+      h->parts_n = (int)blocks;
+      h->parts_ws = h->wscale;  // Simpson coefficients: the factor prod dx/3 is still to come
     }
     return;
   }
@@ -263,21 +285,25 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
   a.vz = (const T*)h->vt[2];
   a.dt = (T)h->dt;
   a.g = (T)h->g;
-  a.scale_in = imag ? h->scale + par : nullptr;
+  a.parts_in = parts_in;
+  a.nparts_in = h->parts_n;
+  a.parts_wscale = h->parts_ws;
   a.w_axis = h->wd[d];
   a.w_a = d == 0 ? h->wd[1] : h->wd[0];
   a.w_b = d == 2 ? h->wd[1] : h->wd[2];
-  a.partials = h->partials;
-  a.counter = h->counter;
-  a.scale_out = h->scale + (1 - par);
+  a.parts_out = parts_out;
   if (imag) {
-    if (first && last) launch_legacy<T, true, true, true>(a, h->work);
-    else if (first) launch_legacy<T, true, true, false>(a, h->work);
-    else if (last) launch_legacy<T, true, false, true>(a, h->work);
-    else launch_legacy<T, true, false, false>(a, h->work);
+    if (first && last) blocks = launch_legacy<T, true, true, true>(a, h->work);
+    else if (first) blocks = launch_legacy<T, true, true, false>(a, h->work);
+    else if (last) blocks = launch_legacy<T, true, false, true>(a, h->work);
+    else blocks = launch_legacy<T, true, false, false>(a, h->work);
   } else {
-    if (first) launch_legacy<T, false, true, false>(a, h->work);
-    else launch_legacy<T, false, false, false>(a, h->work);
+    if (first) blocks = launch_legacy<T, false, true, false>(a, h->work);
+    else blocks = launch_legacy<T, false, false, false>(a, h->work);
+  }
+  if (write) {
+    h->parts_n = (int)blocks;
+    h->parts_ws = 1.0;  // FP64 Simpson weights: the sums are complete
   }
   }
 }
@@ -285,38 +311,49 @@ void enqueue_sweep(gp_handle* h, bool imag, int par, int d, const void* src = nu
 // One step; with src != nullptr the x sweep reads the step's input from src
 // (segmented kernels only) and every sweep writes h->psi.
 template <typename T>
-void enqueue_step(gp_handle* h, bool imag, int par, cudaEvent_t* ev = nullptr, const void* src = nullptr) {
+void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullptr, const void* src = nullptr) {
   for (int d = 0; d < h->dim; ++d) {
     if (ev) cudaEventRecord(ev[2 * d], h->work);
-    enqueue_sweep<T>(h, imag, par, d, src);
+    enqueue_sweep<T>(h, imag, ns, d, src);
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
 }
 
+inline NormSlots slots_of_step(bool imag, long t) {
+  NormSlots ns;
+  if (imag) {
+    ns.rd = t > 0 ? (int)((t - 1) & 1) : -1;
+    ns.wr = (int)(t & 1);
+  }
+  return ns;
+}
+
+// The renormalisation left pending after the last of nsteps imaginary-time steps.
 template <typename T>
 void enqueue_finish_imag(gp_handle* h, long nsteps) {
   const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-  scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->scale + (nsteps & 1));
+  scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->parts[(nsteps - 1) & 1], h->parts_n,
+                                               h->parts_ws);
   count_launch();
 }
 
+// Step 0 eagerly (it has no pending factor), then blocks of kGraphSteps steps
+// replayed from one captured graph (a block starts at an odd step in
+// imaginary time, so its slot pattern is always the same), then the rest.
 template <typename T>
 int run_steps_t(gp_handle* h, bool imag, long nsteps) {
   if (nsteps == 0) return GP_OK;
   int rc = join_in(h);
   if (rc) return rc;
-  if (imag) {
-    set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
-    count_launch();
-  }
   long t = 0;
-  if (nsteps >= 2 * kGraphSteps) {
+  if (imag) enqueue_step<T>(h, true, slots_of_step(true, t++));
+  if (nsteps - t >= 2 * kGraphSteps) {
     cudaGraphExec_t& ge = h->graph[imag ? 1 : 0];
     if (!ge) {
       cudaGraph_t graph;
       GP_CUDA(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
       const unsigned long long before = g_launches.load();
-      for (int s = 0; s < kGraphSteps; ++s) enqueue_step<T>(h, imag, s & 1);
+      for (int s = 0; s < kGraphSteps; ++s) enqueue_step<T>(h, imag, slots_of_step(imag, t + s));
       g_launches.store(before);  // capturing launches nothing
       GP_CUDA(cudaStreamEndCapture(h->work, &graph));
       cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
@@ -331,7 +368,7 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
       count_launch((unsigned long long)kGraphSteps * h->dim);
     }
   }
-  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, (int)(t & 1));
+  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t));
   if (imag) enqueue_finish_imag<T>(h, nsteps);
   GP_CUDA(cudaGetLastError());
   return join_out(h);
@@ -345,12 +382,8 @@ int time_steps_t(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   std::vector<cudaEvent_t> ev((size_t)nsteps * 2 * h->dim);
   for (auto& e : ev) GP_CUDA(cudaEventCreate(&e));
   int rc = join_in(h);
-  if (imag && !rc) {
-    set_scalar_kernel<<<1, 1, 0, h->work>>>(h->scale, 1.0);
-    count_launch();
-  }
   for (long t = 0; t < nsteps && !rc; ++t)
-    enqueue_step<T>(h, imag, (int)(t & 1), ev.data() + (size_t)t * 2 * h->dim);
+    enqueue_step<T>(h, imag, slots_of_step(imag, t), ev.data() + (size_t)t * 2 * h->dim);
   if (imag && !rc && nsteps > 0) enqueue_finish_imag<T>(h, nsteps);
   cudaError_t e = cudaStreamSynchronize(h->work);
   if (!rc && e != cudaSuccess) rc = fail(GP_ERR_CUDA, std::string("gp_time_sweeps: ") + cudaGetErrorString(e));
@@ -493,7 +526,7 @@ int adjoint_backward_t(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
     cudaMemcpyAsync(traj, (const char*)h->adj_ckpt + (size_t)c * sbytes, sbytes, cudaMemcpyDeviceToDevice, h->work);
     for (int j = 0; j + 1 < len; ++j) {
       h->psi = traj + (size_t)(j + 1) * sbytes;
-      enqueue_step<T>(h, false, 0, nullptr, traj + (size_t)j * sbytes);
+      enqueue_step<T>(h, false, NormSlots{}, nullptr, traj + (size_t)j * sbytes);
     }
     for (int j = len - 1; j >= 0; --j) {
       for (int d = h->dim - 1; d >= 0; --d) enqueue_adj_sweep<T>(h, d);

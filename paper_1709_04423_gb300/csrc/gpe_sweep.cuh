@@ -21,8 +21,8 @@
 // imaginary-time renormalisation factor and the sub-step N,
 //     p <- s p,   p <- exp(-i dt (V + g|p|^2)) p   or   exp(-dt (V + g|p|^2)) p.
 // LAST (imaginary time): the sweep along the last axis accumulates the
-// Simpson-weighted norm of its output in FP64, and the last block to finish
-// stores the next step's factor 1/sqrt(norm).
+// Simpson-weighted norm of its output in FP64, one sum per block, from which
+// the next step's first sweep forms the factor 1/sqrt(norm).
 #pragma once
 #include "gpe_common.cuh"
 
@@ -41,14 +41,15 @@ struct SweepArgs {
   const T* vy;         // [ny]
   const T* vz;         // [nz]
   T dt, g;
-  const double* scale_in;  // pending renormalisation factor (imag FIRST), or nullptr
-  // norm (LAST, imaginary time)
+  // pending renormalisation (imag FIRST): previous step's per-block norm sums
+  const double* parts_in;
+  int nparts_in;
+  double parts_wscale;
+  // norm (LAST, imaginary time): one FP64 sum per block into parts_out
   const double* w_axis;    // [n] Simpson weights along the line
   const double* w_a;       // weights of transverse index a
   const double* w_b;       // weights of transverse index b
-  double* partials;
-  unsigned int* counter;
-  double* scale_out;
+  double* parts_out;
 };
 
 template <typename T, bool IMAG>
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(128) cn_sweep_kernel(SweepArgs<T> A) {
   const LineGeom& G = A.geom;
   const long L = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = L < G.nlines;
+  const double pend = FIRST ? pending_scale(A.parts_in, A.nparts_in, A.parts_wscale, red_smem) : 1.0;
   double nacc = 0.0;
   if (active) {
     const long base = line_base(G, L);
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(128) cn_sweep_kernel(SweepArgs<T> A) {
     T vline = T(0), sc = T(1);
     if (FIRST) {
       if (A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
-      if (A.scale_in) sc = (T)(*A.scale_in);
+      sc = (T)pend;
     }
     auto load = [&](int k) -> c2 {
       c2 p = line[(long)k * s];
@@ -140,26 +142,23 @@ __global__ void __launch_bounds__(128) cn_sweep_kernel(SweepArgs<T> A) {
     if (LAST) nacc *= wl;
   }
   if (LAST) {
-    double v[1] = {nacc}, tot[1];
+    double v[1] = {nacc};
     block_sum<1>(v, red_smem);
-    if (grid_sum_last<1>(v, A.partials, A.counter, tot, red_smem) && threadIdx.x == 0) {
-      *A.scale_out = 1.0 / sqrt(tot[0]);
-    }
+    if (threadIdx.x == 0) A.parts_out[blockIdx.x] = v[0];
   }
 }
 
-// psi *= *scale (the renormalisation left pending after the last imaginary-time step)
+// psi *= the renormalisation left pending after the last imaginary-time step
 template <typename T>
-__global__ void scale_kernel(c2_t<T>* psi, long np, const double* scale) {
-  const T s = (T)(*scale);
+__global__ void scale_kernel(c2_t<T>* psi, long np, const double* parts, int nparts, double wscale) {
+  __shared__ double smem[32];
+  const T s = (T)pending_scale(parts, nparts, wscale, smem);
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (long)gridDim.x * blockDim.x) {
     c2_t<T> p = psi[q];
     p.x *= s; p.y *= s;
     psi[q] = p;
   }
 }
-
-static __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
 
 // exp(-i dt V) and exp(-dt V) per point, evaluated in FP64 and stored in T
 template <typename T>

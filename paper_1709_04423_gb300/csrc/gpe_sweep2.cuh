@@ -77,17 +77,18 @@ struct Sweep2Args {
   const tf3c* tfV;
   const tf3c* tfx;
   const tf3c* tfyz;
-  const double* scale_in;
-  // norm (LAST)
-  // Simpson coefficients (1, 2, 4: exact in any precision) along the line and
-  // of the two transverse indices; the grid factor prod_d dx_d/3 is applied
-  // to the FP64 total, so no rounded weight biases the norm
+  // pending renormalisation (FIRST, imaginary time): the previous step's
+  // per-block norm sums, their number and factor (see pending_scale)
+  const double* parts_in;
+  int nparts_in;
+  double parts_wscale;
+  // norm of the output (LAST): Simpson coefficients (1, 2, 4: exact in any
+  // precision) along the line and of the two transverse indices -- the grid
+  // factor prod_d dx_d/3 is applied by the reader to the FP64 total, so no
+  // rounded weight biases the norm -- and one sum per block into parts_out
   const T* w_axis;
   const T* w_a; const T* w_b;
-  double wscale;
-  double* partials;
-  unsigned int* counter;
-  double* scale_out;
+  double* parts_out;
 };
 
 // Sub-step N at one point: p <- F exp(-i a) p (real time) or F exp(-a) p
@@ -365,11 +366,11 @@ __device__ __forceinline__ int line_base32(const LineGeom& g, int L) {
 
 // Norm of the block's output: the per-thread values (in the state
 // precision) are summed over the block in the state precision -- a tree of at
-// most log2(blockDim) levels -- and the per-block totals over the grid in FP64
-// (fixed order, last block); the result sets the next renormalisation factor.
+// most log2(blockDim) levels -- and stored as the block's FP64 sum; the next
+// step's first sweep (or the final scaling) sums the blocks' values in FP64 in
+// a fixed order (pending_scale).  No atomics, fences or last-block tail here.
 template <typename T, bool LAST>
-__device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned int* counter, double* scale_out,
-                                            double wscale, double* red_smem) {
+__device__ __forceinline__ void finish_norm(T tval, double* parts_out) {
   if (LAST) {
     __shared__ T tred[32];
 #pragma unroll
@@ -377,15 +378,12 @@ __device__ __forceinline__ void finish_norm(T tval, double* partials, unsigned i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) tred[warp] = tval;
     __syncthreads();
-    double v[1] = {0.0}, tot[1];
     if (warp == 0) {
       T b = lane < nw ? tred[lane] : T(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) b += shfl_xor_t(b, o);
-      v[0] = (double)b;  // FP64 from here on
+      if (lane == 0) parts_out[blockIdx.x] = (double)b;  // FP64 from here on
     }
-    if (grid_sum_last<1>(v, partials, counter, tot, red_smem) && threadIdx.x == 0)
-      *scale_out = 1.0 / sqrt(tot[0] * wscale);
   }
 }
 
@@ -454,7 +452,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
     }
     if (LAST) nval = tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
+  finish_norm<T, LAST>(nval, A.parts_out);
 }
 
 template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
@@ -485,50 +483,81 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   const int nseg = (M + SEG - 1) / SEG;
   const int nl = min(32, (int)G.nlines - L0);
   load_coefs<T>(A, sc, n);
-  T scl = T(1);
-  if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
-  // ---- load: warp w takes lines w, w + nwarps, ...; lane takes points lane, lane + 32, ...
+  constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
   const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
-  for (int c = s; c < 32; c += nwarps) {
-    const bool line_ok = c < nl;
-    const int gbase = (L0 + c) * G.nx;
-    constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
-    c2 fline = mk<T>(1, 0);
-    T vline = T(0);
-    if (FIRST && line_ok && !is_df<T>::value) {
+  const c2* in = A.src ? A.src : A.psi;
+  // per-line part of the sub-step N (FIRST)
+  auto line_factors = [&](int c, c2& fline, T& vline) {
+    fline = mk<T>(1, 0);
+    vline = T(0);
+    if (FIRST && c < nl && !is_df<T>::value) {
       const int L = L0 + c;
       if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[L % G.ny], A.fz[L / G.ny]);
       if (!kFactors && !A.V) vline = A.vy[L % G.ny] + A.vz[L / G.ny];
     }
-    const c2* in = A.src ? A.src : A.psi;
-    for (int q0 = 0; q0 < per_line; q0 += 4) {
-      c2 v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = (q0 + i) * 32 + lane;
-        v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
+  };
+  // the factor scl and the sub-step N at interior point k of line c
+  auto apply_N = [&](c2 w, int c, int k, const c2& fline, T vline, T scl) -> c2 {
+    const int gbase = (L0 + c) * G.nx;
+    if constexpr (is_df<T>::value) {
+      if (IMAG) { w.x *= scl; w.y *= scl; }
+      return phase_df<IMAG>(w, A, gbase + k, k, L0 + c);
+    } else {
+      w.x *= scl; w.y *= scl;
+      if (kFactors) {
+        const c2 F = A.fV ? A.fV[gbase + k] : fac_mul<T, IMAG>(A.fx[k], fline);
+        return phase_N<T, IMAG>(w, F, A.dtg);
+      } else {
+        return phase_direct<T, IMAG>(w, A.V ? A.V[gbase + k] : A.vx[k] + vline, A.dt, A.g);
       }
+    }
+  };
+  // A pending renormalisation factor (imaginary time, after the first step)
+  // is summed by warp 0 from the previous step's per-block norms while the
+  // other warps bring the tile in unchanged; the factor and N are then
+  // applied in a second pass over the tile.  Otherwise N is applied on the
+  // way in.  Either way: warp w takes lines w, w + nwarps, ...; lane takes
+  // points lane, lane + 32, ... (coalesced rows; tile pitch 33, no conflicts).
+  const bool pend = FIRST && A.parts_in != nullptr;
+  if (pend && s == 0) {
+    const double f = pending_factor_warp(A.parts_in, A.nparts_in, A.parts_wscale);
+    if (lane == 0) red_smem[0] = f;
+  }
+  const int w0 = (pend && nwarps > 1) ? 1 : 0;  // first loading warp
+  if (s >= w0) {
+    for (int c = s - w0; c < 32; c += nwarps - w0) {
+      const bool line_ok = c < nl;
+      const int gbase = (L0 + c) * G.nx;
+      c2 fline;
+      T vline;
+      if (!pend) line_factors(c, fline, vline);
+      for (int q0 = 0; q0 < per_line; q0 += 4) {
+        c2 v[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = (q0 + i) * 32 + lane;
-        if (k >= n) break;
-        c2 w = v[i];
-        if (FIRST && line_ok && k >= 1 && k <= M) {
-          if constexpr (is_df<T>::value) {
-            if (IMAG) { w.x *= scl; w.y *= scl; }
-            w = phase_df<IMAG>(w, A, gbase + k, k, L0 + c);
-          } else {
-            w.x *= scl; w.y *= scl;
-            if (kFactors) {
-              const c2 F = A.fV ? A.fV[gbase + k] : fac_mul<T, IMAG>(A.fx[k], fline);
-              w = phase_N<T, IMAG>(w, F, A.dtg);
-            } else {
-              w = phase_direct<T, IMAG>(w, A.V ? A.V[gbase + k] : A.vx[k] + vline, A.dt, A.g);
-            }
-          }
+        for (int i = 0; i < 4; ++i) {
+          const int k = (q0 + i) * 32 + lane;
+          v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
         }
-        tile[k * kTilePitch + c] = w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int k = (q0 + i) * 32 + lane;
+          if (k >= n) break;
+          c2 w = v[i];
+          if (FIRST && !pend && line_ok && k >= 1 && k <= M) w = apply_N(w, c, k, fline, vline, T(1));
+          tile[k * kTilePitch + c] = w;
+        }
       }
+    }
+  }
+  if (pend) {
+    __syncthreads();
+    const T scl = (T)red_smem[0];
+    for (int c = s; c < nl; c += nwarps) {
+      c2 fline;
+      T vline;
+      line_factors(c, fline, vline);
+      for (int k = lane; k < n; k += 32)
+        if (k >= 1 && k <= M) tile[k * kTilePitch + c] = apply_N(tile[k * kTilePitch + c], c, k, fline, vline, scl);
     }
   }
   __syncthreads();
@@ -560,7 +589,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     const int gbase = (L0 + c) * G.nx;
     for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
+  finish_norm<T, LAST>(nval, A.parts_out);
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
@@ -582,6 +611,8 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
   const LineGeom& G = A.geom;
   const int lane = threadIdx.x & 31;
   const bool active = L < G.nlines;  // warp-uniform
+  // (every thread of the block takes part in the pending-scale reduction)
+  const double pend = FIRST ? pending_scale(A.parts_in, A.nparts_in, A.parts_wscale, red_smem) : 1.0;
   T nval = T(0);
   if (active) {
     const int M = G.n - 2;
@@ -591,13 +622,11 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     const int ta = L % G.ny, tb = L / G.ny;
     constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
     c2 fline = mk<T>(1, 0);
-    T vline = T(0), scl = T(1);
+    T vline = T(0);
+    const T scl = (T)pend;
     if (FIRST && !is_df<T>::value) {
       if (kFactors && A.fV == nullptr) fline = fac_mul<T, IMAG>(A.fy[ta], A.fz[tb]);
       if (!kFactors && A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
-    }
-    if (FIRST) {
-      if (A.scale_in) scl = (T)(*A.scale_in);
     }
     const c2* in = (A.src ? A.src : A.psi) + base;
     c2 p[SEG], e[SEG];
@@ -675,7 +704,7 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     if (lane == 31) line[G.n - 1] = mk<T>(0, 0);
     if (LAST) nval = tacc * (A.w_a[ta] * A.w_b[tb]);
   }
-  finish_norm<T, LAST>(nval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
+  finish_norm<T, LAST>(nval, A.parts_out);
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
@@ -756,7 +785,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
   const int ntiles = (int)((G.nlines + 31) / 32);
   load_coefs<T>(A, sc, n);
   T scl = T(1);
-  if (FIRST && A.scale_in) scl = (T)(*A.scale_in);
+  if (FIRST) scl = (T)pending_scale(A.parts_in, A.nparts_in, A.parts_wscale, red_smem);
   constexpr bool kFactors = std::is_same<T, double>::value;
   static_assert(!is_df<T>::value, "the pipelined sweeps take FP32 and FP64 states");
   T tval = T(0);
@@ -846,7 +875,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
     __syncthreads();  // the stage is refilled by the prefetch of the next iteration
   }
   cp_async_wait<0>();
-  finish_norm<T, LAST>(tval, A.partials, A.counter, A.scale_out, A.wscale, red_smem);
+  finish_norm<T, LAST>(tval, A.parts_out);
 }
 
 }  // namespace gpe
