@@ -18,8 +18,12 @@ template <> struct is_df<df64> { static constexpr bool value = true; };
 template <typename T> using c2_t = typename C2<T>::type;
 
 template <typename T> __device__ __forceinline__ c2_t<T> mk(T x, T y) { c2_t<T> r; r.x = x; r.y = y; return r; }
+// Complex product with its fused multiply-adds spelled out, so that the
+// rounding does not depend on how the compiler contracts the expression in a
+// given kernel (the batched and the single-grid kernels then agree bit for bit).
 template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  if constexpr (is_df<T>::value) return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  else return mk<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 
 // Geometry of the lines of one sweep.  Line L of axis 0 starts at L*nx

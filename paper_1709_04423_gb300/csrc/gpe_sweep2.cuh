@@ -223,7 +223,7 @@ __device__ __forceinline__ df64x2 phase_df(df64x2 p, const Sweep2Args<df64>& A, 
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> fac_mul(c2_t<T> a, c2_t<T> b) {
   if (IMAG) return mk<T>(a.x * b.x, T(0));
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return cmul<T>(a, b);
 }
 
 // a * b for the coefficient type: complex in real time, real in imaginary time
@@ -254,6 +254,14 @@ __device__ __forceinline__ c2_t<T> shfl_down2(c2_t<T> v, int o) {
   return mk<T>(shfl_down_t(v.x, o), shfl_down_t(v.y, o));
 }
 
+// 4 p - 2 (l + r) = -2 lap, the part of the forward step that does not
+// depend on the recurrence (the scalings by 2 and 4 are exact)
+template <typename T>
+__device__ __forceinline__ T neg2lap(T l, T r, T p) {
+  if constexpr (is_df<T>::value) return df_scale(p, 4.f) - df_scale(l + r, 2.f);
+  else return fma(T(4), p, T(-2) * (l + r));
+}
+
 // Segment-local passes over SEG registers.  k0 = first interior index of the
 // segment; points with k > M are padding (p = 0 there).
 template <typename T, bool IMAG, int SEG>
@@ -266,8 +274,7 @@ __device__ __forceinline__ void local_forward(const c2_t<T> (&p)[SEG], c2_t<T> (
     const c2_t<T> left = j == 0 ? pl : p[j - 1];
     const c2_t<T> right = j == SEG - 1 ? pr : p[j + 1];
     // t = e_{k-1} - 2 lap_k,  lap_k = left - 2 p_k + right
-    const c2_t<T> t = mk<T>(prev.x - T(2) * (left.x + right.x) + T(4) * p[j].x,
-                            prev.y - T(2) * (left.y + right.y) + T(4) * p[j].y);
+    const c2_t<T> t = mk<T>(prev.x + neg2lap(left.x, right.x, p[j].x), prev.y + neg2lap(left.y, right.y, p[j].y));
     c2_t<T> v = mk<T>(0, 0);
     if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
     e[j] = v;
@@ -308,7 +315,7 @@ __device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], con
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
     const c2 pn = getp(k + 1);
-    const c2 t = mk<T>(prev.x - T(2) * (pm.x + pn.x) + T(4) * pc.x, prev.y - T(2) * (pm.y + pn.y) + T(4) * pc.y);
+    const c2 t = mk<T>(prev.x + neg2lap(pm.x, pn.x, pc.x), prev.y + neg2lap(pm.y, pn.y, pc.y));
     c2 v = mk<T>(0, 0);
     if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
     e[j] = v;
