@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gpe_df.cuh"
 
 namespace gpe {
@@ -50,6 +52,16 @@ __device__ __forceinline__ void line_transverse(const LineGeom& g, long L, int& 
   if (g.axis == 0) { a = (int)(L % g.ny); b = (int)(L / g.ny); }
   else { a = (int)(L % g.nx); b = (int)(L / g.nx); }
 }
+
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
+// launched as a programmatic dependent of the previous kernel in its stream
+// may start while that kernel is still running: pdl_wait() blocks until the
+// previous grid has completed and its memory is visible (it returns at once
+// when the kernel was launched normally), so everything before it may only
+// touch data no earlier kernel writes (the coefficient tables); pdl_release()
+// lets the next kernel be scheduled before this one ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -135,6 +147,24 @@ __device__ __forceinline__ double pending_scale(const double* parts, int nparts,
   const double f = smem[0];
   __syncthreads();  // smem free again
   return f;
+}
+
+// Launch with or without the programmatic-dependent-launch attribute (the
+// kernel must call pdl_wait() before it reads what earlier kernels wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 }  // namespace gpe

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdlib>
 #include <complex>
 #include <string>
 #include <vector>
@@ -29,6 +30,15 @@ inline int fail(int code, const std::string& msg) {
   } while (0)
 
 inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Programmatic dependent launch of consecutive kernels: on unless GPE_PDL=0.
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("GPE_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 
 // Segment lengths for which segment-product tables are kept.
 constexpr int kNumSegs = 6;
@@ -103,6 +113,7 @@ struct gp_handle {
   double* parts[2] = {nullptr, nullptr};
   int parts_n = 0;
   double parts_ws = 1.0;
+  bool pdl_now = false;  // launch the sweeps as programmatic dependents (inside gp_step_*)
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   double* obs_out = nullptr;  // [8]

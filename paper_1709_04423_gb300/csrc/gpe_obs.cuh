@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, 
   const R fy1 = R(1.0 / (2.0 * A.hy)), fy4 = R(1.0 / (12.0 * A.hy));
   const R fz1 = R(1.0 / (2.0 * A.hz)), fz4 = R(1.0 / (12.0 * A.hz));
   R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  pdl_wait();  // the state is the previous kernel's output
+  pdl_release();
   for (int i = tx; i < A.nx; i += TX) {
     const R vxi = A.vx[i], cxi = A.cx[i], wxi = A.wx[i];
     for (int r = blockIdx.x * rpb + ty; r < nrows; r += gridDim.x * rpb) {
@@ -125,14 +127,14 @@ __global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, 
 // The one launch configuration of the reduction (every caller uses it, so
 // that equal states give bitwise equal sums).
 template <typename T>
-inline void launch_observables(const ObsArgs<T>& a, cudaStream_t s) {
+inline void launch_observables(const ObsArgs<T>& a, cudaStream_t s, bool pdl = false) {
   int lg = 5;
   while ((1 << lg) < a.nx && lg < 8) ++lg;  // 32..256 threads per row
   const int rpb = kObsThreads >> lg;
   const long nrows = (long)a.ny * a.nz;
   const long want = (nrows + rpb - 1) / rpb;
   const int blocks = (int)(want < kObsBlocks ? want : kObsBlocks);
-  observables_kernel<T><<<blocks, kObsThreads, 0, s>>>(a, lg);
+  launch_k(pdl, observables_kernel<T>, dim3(blocks), dim3(kObsThreads), 0, s, a, lg);
 }
 
 }  // namespace gpe

@@ -44,27 +44,27 @@ inline const c2_t<T>* coef_ptr(const gp_handle* h, int mode, int axis, int slot)
 // Every launcher returns its number of blocks (a LAST sweep leaves one norm
 // sum per block for the next step's reader).
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-unsigned launch_x(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_x(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const unsigned blocks = (unsigned)((a.geom.nlines + kXWarps - 1) / kXWarps);
-  xsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * kXWarps, 0, s>>>(a);
+  launch_k(pdl, xsweep_kernel<T, IMAG, FIRST, LAST, SEG>, dim3(blocks), dim3(32 * kXWarps), 0, s, a);
   count_launch();
   return blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST>
-unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 1: return launch_x<T, IMAG, FIRST, LAST, 1>(a, s);
-    case 2: return launch_x<T, IMAG, FIRST, LAST, 2>(a, s);
-    case 4: return launch_x<T, IMAG, FIRST, LAST, 4>(a, s);
-    case 8: return launch_x<T, IMAG, FIRST, LAST, 8>(a, s);
-    default: return launch_x<T, IMAG, FIRST, LAST, 16>(a, s);
+    case 1: return launch_x<T, IMAG, FIRST, LAST, 1>(a, s, pdl);
+    case 2: return launch_x<T, IMAG, FIRST, LAST, 2>(a, s, pdl);
+    case 4: return launch_x<T, IMAG, FIRST, LAST, 4>(a, s, pdl);
+    case 8: return launch_x<T, IMAG, FIRST, LAST, 8>(a, s, pdl);
+    default: return launch_x<T, IMAG, FIRST, LAST, 16>(a, s, pdl);
   }
 }
 
 // ---- segmented y/z sweep (registers, coefficients in shared memory)
 template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
-unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
@@ -75,26 +75,26 @@ unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s) {
                          64 * 1024);
     attr_set = true;
   }
-  colsweep_kernel<T, IMAG, LAST, SEG, KEEP><<<blocks, 32 * nseg, smem, s>>>(a);
+  launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
 // keep = 1: input segment in registers (only for short segments); 0: streamed
 template <typename T, bool IMAG, bool LAST>
-unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const bool k = keep && seg * (int)sizeof(T) <= 64;
   switch (seg) {
-    case 4: return k ? launch_c<T, IMAG, LAST, 4, true>(a, s) : launch_c<T, IMAG, LAST, 4, false>(a, s);
-    case 8: return k ? launch_c<T, IMAG, LAST, 8, true>(a, s) : launch_c<T, IMAG, LAST, 8, false>(a, s);
-    case 16: return k ? launch_c<T, IMAG, LAST, 16, true>(a, s) : launch_c<T, IMAG, LAST, 16, false>(a, s);
-    default: return launch_c<T, IMAG, LAST, 32, false>(a, s);
+    case 4: return k ? launch_c<T, IMAG, LAST, 4, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 4, false>(a, s, pdl);
+    case 8: return k ? launch_c<T, IMAG, LAST, 8, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 8, false>(a, s, pdl);
+    case 16: return k ? launch_c<T, IMAG, LAST, 16, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 16, false>(a, s, pdl);
+    default: return launch_c<T, IMAG, LAST, 32, false>(a, s, pdl);
   }
 }
 
 // ---- shared-memory tile x sweep
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
-unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
@@ -105,18 +105,18 @@ unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s) {
                          200 * 1024);
     attr_set = true;
   }
-  tsweep_kernel<T, IMAG, FIRST, LAST, SEG><<<blocks, 32 * nseg, smem, s>>>(a);
+  launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST>
-unsigned launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 4: return launch_t<T, IMAG, FIRST, LAST, 4>(a, s);
-    case 8: return launch_t<T, IMAG, FIRST, LAST, 8>(a, s);
-    case 16: return launch_t<T, IMAG, FIRST, LAST, 16>(a, s);
-    default: return launch_t<T, IMAG, FIRST, LAST, 32>(a, s);
+    case 4: return launch_t<T, IMAG, FIRST, LAST, 4>(a, s, pdl);
+    case 8: return launch_t<T, IMAG, FIRST, LAST, 8>(a, s, pdl);
+    case 16: return launch_t<T, IMAG, FIRST, LAST, 16>(a, s, pdl);
+    default: return launch_t<T, IMAG, FIRST, LAST, 32>(a, s, pdl);
   }
 }
 
@@ -128,7 +128,7 @@ inline size_t psweep_smem(int n, bool axis0) {
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool AXIS0>
-unsigned launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_p(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
   const int ntiles = (int)((a.geom.nlines + 31) / 32);
@@ -145,18 +145,18 @@ unsigned launch_p(const Sweep2Args<T>& a, cudaStream_t s) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, 32 * nseg,
                                                 smem);
   const int blocks = std::max(1, std::min(ntiles, std::max(1, per_sm) * std::max(1, sms)));
-  psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0><<<blocks, 32 * nseg, smem, s>>>(a);
+  launch_k(pdl, psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return (unsigned)blocks;
 }
 
 template <typename T, bool IMAG, bool FIRST, bool LAST, bool AXIS0>
-unsigned launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s) {
+unsigned launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 4: return launch_p<T, IMAG, FIRST, LAST, 4, AXIS0>(a, s);
-    case 8: return launch_p<T, IMAG, FIRST, LAST, 8, AXIS0>(a, s);
-    case 16: return launch_p<T, IMAG, FIRST, LAST, 16, AXIS0>(a, s);
-    default: return launch_p<T, IMAG, FIRST, LAST, 32, AXIS0>(a, s);
+    case 4: return launch_p<T, IMAG, FIRST, LAST, 4, AXIS0>(a, s, pdl);
+    case 8: return launch_p<T, IMAG, FIRST, LAST, 8, AXIS0>(a, s, pdl);
+    case 16: return launch_p<T, IMAG, FIRST, LAST, 16, AXIS0>(a, s, pdl);
+    default: return launch_p<T, IMAG, FIRST, LAST, 32, AXIS0>(a, s, pdl);
   }
 }
 
@@ -224,18 +224,18 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
       if (d == 0 && h->tile_x && h->pipe_x) {
         if (imag) {
-          blocks = last ? launch_p_seg<T, true, true, true, true>(seg, a, h->work)
-                        : launch_p_seg<T, true, true, false, true>(seg, a, h->work);
+          blocks = last ? launch_p_seg<T, true, true, true, true>(seg, a, h->work, h->pdl_now)
+                        : launch_p_seg<T, true, true, false, true>(seg, a, h->work, h->pdl_now);
         } else {
-          blocks = launch_p_seg<T, false, true, false, true>(seg, a, h->work);
+          blocks = launch_p_seg<T, false, true, false, true>(seg, a, h->work, h->pdl_now);
         }
         done = true;
       } else if (d > 0 && h->pipe_c) {
         if (imag) {
-          blocks = last ? launch_p_seg<T, true, false, true, false>(seg, a, h->work)
-                        : launch_p_seg<T, true, false, false, false>(seg, a, h->work);
+          blocks = last ? launch_p_seg<T, true, false, true, false>(seg, a, h->work, h->pdl_now)
+                        : launch_p_seg<T, true, false, false, false>(seg, a, h->work, h->pdl_now);
         } else {
-          blocks = launch_p_seg<T, false, false, false, false>(seg, a, h->work);
+          blocks = launch_p_seg<T, false, false, false, false>(seg, a, h->work, h->pdl_now);
         }
         done = true;
       }
@@ -243,24 +243,24 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     if (done) {
     } else if (d == 0 && h->tile_x) {
       if (imag) {
-        blocks = last ? launch_t_seg<T, true, true, true>(seg, a, h->work)
-                      : launch_t_seg<T, true, true, false>(seg, a, h->work);
+        blocks = last ? launch_t_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
+                      : launch_t_seg<T, true, true, false>(seg, a, h->work, h->pdl_now);
       } else {
-        blocks = launch_t_seg<T, false, true, false>(seg, a, h->work);
+        blocks = launch_t_seg<T, false, true, false>(seg, a, h->work, h->pdl_now);
       }
     } else if (d == 0) {
       if (imag) {
-        blocks = last ? launch_x_seg<T, true, true, true>(seg, a, h->work)
-                      : launch_x_seg<T, true, true, false>(seg, a, h->work);
+        blocks = last ? launch_x_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
+                      : launch_x_seg<T, true, true, false>(seg, a, h->work, h->pdl_now);
       } else {
-        blocks = launch_x_seg<T, false, true, false>(seg, a, h->work);
+        blocks = launch_x_seg<T, false, true, false>(seg, a, h->work, h->pdl_now);
       }
     } else {
       if (imag) {
-        blocks = last ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work)
-                      : launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work);
+        blocks = last ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work, h->pdl_now)
+                      : launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work, h->pdl_now);
       } else {
-        blocks = launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
+        blocks = launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work, h->pdl_now);
       }
     }
     if (write) {
@@ -332,8 +332,8 @@ inline NormSlots slots_of_step(bool imag, long t) {
 template <typename T>
 void enqueue_finish_imag(gp_handle* h, long nsteps) {
   const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-  scale_kernel<T><<<blocks, 256, 0, h->work>>>((c2_t<T>*)h->psi, h->np, h->parts[(nsteps - 1) & 1], h->parts_n,
-                                               h->parts_ws);
+  launch_k(h->pdl_now, scale_kernel<T>, dim3(blocks), dim3(256), 0, h->work, (c2_t<T>*)h->psi, h->np,
+           (const double*)h->parts[(nsteps - 1) & 1], h->parts_n, h->parts_ws);
   count_launch();
 }
 
@@ -345,6 +345,14 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
   if (nsteps == 0) return GP_OK;
   int rc = join_in(h);
   if (rc) return rc;
+  // consecutive sweeps overlap their launch and prologue (FP32 and
+  // double-float; the FP64 form, bound by its FP64 pipe, was measured 10 %
+  // slower with it)
+  struct PdlScope {
+    gp_handle* h;
+    explicit PdlScope(gp_handle* hh) : h(hh) { h->pdl_now = pdl_enabled() && h->prec != GP_F64; }
+    ~PdlScope() { h->pdl_now = false; }
+  } pdl_scope(h);
   long t = 0;
   if (imag) enqueue_step<T>(h, true, slots_of_step(true, t++));
   if (nsteps - t >= 2 * kGraphSteps) {
@@ -431,7 +439,7 @@ int run_observables_t(gp_handle* h, double* dens_dev) {
   a.partials = h->partials;
   a.counter = h->counter;
   a.out = h->obs_out;
-  launch_observables<T>(a, h->work);
+  launch_observables<T>(a, h->work, pdl_enabled() && h->prec != GP_F64);
   count_launch();
   GP_CUDA(cudaGetLastError());
   return GP_OK;
@@ -452,11 +460,11 @@ void enqueue_adj_sweep(gp_handle* h, int d) {
   a.gf = coef_ptr<T>(h, MODE_REAL_ADJ, d, 1 + 2 * si);
   a.gb = coef_ptr<T>(h, MODE_REAL_ADJ, d, 2 + 2 * si);
   a.ptab = (const c2_t<T>*)h->ctab[MODE_REAL_ADJ][d] + (size_t)si * 512;
-  if (d == 0 && h->tile_x && h->pipe_x) launch_p_seg<T, false, false, false, true>(seg, a, h->work);
-  else if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work);
-  else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work);
-  else if (h->pipe_c) launch_p_seg<T, false, false, false, false>(seg, a, h->work);
-  else launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work);
+  if (d == 0 && h->tile_x && h->pipe_x) launch_p_seg<T, false, false, false, true>(seg, a, h->work, h->pdl_now);
+  else if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work, h->pdl_now);
+  else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work, h->pdl_now);
+  else if (h->pipe_c) launch_p_seg<T, false, false, false, false>(seg, a, h->work, h->pdl_now);
+  else launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work, h->pdl_now);
 }
 
 template <typename T>

@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(128) cn_sweep_kernel(SweepArgs<T> A) {
 template <typename T>
 __global__ void scale_kernel(c2_t<T>* psi, long np, const double* parts, int nparts, double wscale) {
   __shared__ double smem[32];
+  pdl_wait();
+  pdl_release();
   const T s = (T)pending_scale(parts, nparts, wscale, smem);
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (long)gridDim.x * blockDim.x) {
     c2_t<T> p = psi[q];

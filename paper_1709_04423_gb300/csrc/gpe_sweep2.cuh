@@ -414,6 +414,8 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   const int st = (int)G.stride;
   const int k0 = 1 + s * SEG;
   load_coefs<T>(A, sc, n);
+  pdl_wait();  // the state is the previous kernel's output
+  pdl_release();
   c2* line = A.psi + (active ? line_base32(G, L) : 0);
   // KEEP: the input segment stays in registers; otherwise it is streamed in
   // the forward pass and read again (from L2) for u = p - z, which halves the
@@ -490,6 +492,8 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   const int nseg = (M + SEG - 1) / SEG;
   const int nl = min(32, (int)G.nlines - L0);
   load_coefs<T>(A, sc, n);
+  pdl_wait();  // the state and the norm sums are the previous kernels' output
+  pdl_release();
   constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
   const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
   const c2* in = A.src ? A.src : A.psi;
@@ -618,6 +622,8 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
   const LineGeom& G = A.geom;
   const int lane = threadIdx.x & 31;
   const bool active = L < G.nlines;  // warp-uniform
+  pdl_wait();
+  pdl_release();
   // (every thread of the block takes part in the pending-scale reduction)
   const double pend = FIRST ? pending_scale(A.parts_in, A.nparts_in, A.parts_wscale, red_smem) : 1.0;
   T nval = T(0);
@@ -791,6 +797,8 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
   c2* stage[2] = {sc + 3 * n + 512, sc + 3 * n + 512 + stage_elems};
   const int ntiles = (int)((G.nlines + 31) / 32);
   load_coefs<T>(A, sc, n);
+  pdl_wait();
+  pdl_release();
   T scl = T(1);
   if (FIRST) scl = (T)pending_scale(A.parts_in, A.nparts_in, A.parts_wscale, red_smem);
   constexpr bool kFactors = std::is_same<T, double>::value;
