@@ -94,10 +94,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+SWEEP_SOURCES = ("gpe_common.cuh", "gpe_df.cuh", "gpe_sweep2.cuh", "gpe_step.cuh")
+
+
 def src_hash():
+    """Hash of the sources that define and launch the sweep kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1709_04423_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in SWEEP_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -371,7 +375,7 @@ def run_ours(args):
         qn, qdx = [256] * 3, [0.08] * 3
         qnp = 256 ** 3
         qphi = torch.tensor(inputs.gaussian_state(3, qn, qdx, [1.0] * 3, seed=1711, noise=1e-3), device="cuda")
-        for prec in ("f64", "f32", "df64"):
+        for prec in forms_sel:
             with torch.cuda.stream(stream):
                 q = gpe.Propagator(3, qn, qdx, 1e-3, [1.0] * 3, 20.0, precision=prec, stream=stream)
                 q.set_state(qphi)
@@ -385,12 +389,14 @@ def run_ours(args):
                 for _ in range(args.warmup):
                     q.step_real(args.inner)
                 barrier()
+                torch.cuda.nvtx.range_push(f"timed_quench_{prec}")
                 for s_ in range(args.steps):
                     ev[s_][0].record(stream)
                     q.step_real(args.inner)
                     q.observables()
                     ev[s_][1].record(stream)
                 barrier()
+                torch.cuda.nvtx.range_pop()
                 qt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
                 kms = q.time_sweeps(False, 16)
                 ob1 = q.observables()
@@ -550,8 +556,10 @@ def run_ours(args):
                                        f"ground state at g=20 ({args.quench_imag_steps} steps) then g=40; L2 not flushed "
                                        "(state larger than L2)",
                            "f64": qres.get("f64"), "f32": qres.get("f32"), "df64": qres.get("df64"),
-                           "speedup_f32_vs_f64": qres["f32"]["value"] / qres["f64"]["value"],
-                           "speedup_df64_vs_f64": qres["df64"]["value"] / qres["f64"]["value"]} if qres else None),
+                           "speedup_f32_vs_f64": (qres["f32"]["value"] / qres["f64"]["value"]
+                                                  if "f64" in qres else None),
+                           "speedup_df64_vs_f64": (qres["df64"]["value"] / qres["f64"]["value"]
+                                                   if "df64" in qres and "f64" in qres else None)} if qres else None),
             "adjoint": ({"workload": "gradient of |<phi_target|phi(T)>|^2 w.r.t. V (per grid value) and g: 128^3, "
                                      "dx=0.1, dt=5e-4, 1000 real-time steps, g=30, isotropic trap + 8 Gaussian bumps "
                                      "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "
