@@ -364,7 +364,15 @@ def run_ours(args):
         bb.close()
         bres[prec] = {"value": world * args.steps * args.inner * bpts / bt, "ms_per_step": 1e3 * bt / args.steps,
                       "gpu_launches": blaunch}
-    bmu_err = max(abs(a - b_) for a, b_ in zip(bmu["f32"], bmu["f64"])) if bmu else None
+    bmu_err = bmu_rel = bmu_worst = None
+    if bmu:
+        diffs = [(abs(a - b_), abs(a - b_) / abs(b_), b_, i) for i, (a, b_) in enumerate(zip(bmu["f32"], bmu["f64"]))]
+        bmu_err = max(d[0] for d in diffs)
+        bmu_rel = max(d[1] for d in diffs)
+        w_ = max(diffs)
+        # an FP32 state's own rounding (~6e-8 relative) bounds |dmu| at ~6e-8 mu
+        bmu_worst = {"run": w_[3], "mu_f64": w_[2], "abs_diff": w_[0], "rel_diff": w_[1],
+                     "mu_range_f64": [min(bmu["f64"]), max(bmu["f64"])]}
 
     # ---- 3d real-time quench at 256^3 (dx = 0.08, dt = 2e-4, isotropic trap):
     # imaginary-time ground state at g = 20, then real time at g = 40.  The
@@ -573,7 +581,9 @@ def run_ours(args):
                         "value_f32": bres["f32"]["value"], "value_f64": bres["f64"]["value"],
                         "speedup_f32_vs_f64": bres["f32"]["value"] / bres["f64"]["value"],
                         "ms_per_step_f32": bres["f32"]["ms_per_step"], "gpu_launches_f32": bres["f32"]["gpu_launches"],
-                        "max_abs_mu_diff_f32_vs_f64_after_400_steps": bmu_err} if bres else None),
+                        "max_abs_mu_diff_f32_vs_f64_after_400_steps": bmu_err,
+                        "max_rel_mu_diff_f32_vs_f64_after_400_steps": bmu_rel,
+                        "largest_abs_mu_diff_run": bmu_worst} if bres else None),
         },
     }
     print(json.dumps(line), flush=True)
