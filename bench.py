@@ -352,6 +352,7 @@ def run_ours(args):
                 bb.observables()
             barrier()
             l0 = gpe.gp_kernel_launches()
+            torch.cuda.nvtx.range_push(f"timed_batched_{prec}")
             for s in range(args.steps):
                 flush.fill_(float(s))
                 ev[s][0].record(stream)
@@ -359,6 +360,7 @@ def run_ours(args):
                 bb.observables()
                 ev[s][1].record(stream)
             barrier()
+            torch.cuda.nvtx.range_pop()
             blaunch = gpe.gp_kernel_launches() - l0
             bt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
         bb.close()
@@ -450,7 +452,9 @@ def run_ours(args):
                     dJdV = torch.empty(tuple(an), dtype=torch.float64, device="cuda")
                     e_b = torch.cuda.Event(enable_timing=True)
                     e_b.record(stream)
+                    torch.cuda.nvtx.range_push(f"adjoint_backward_{prec}")
                     dJdg = gpe.gp_adjoint_backward(q.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1)
+                    torch.cuda.nvtx.range_pop()
                     e2.record(stream)
                     barrier()
                     if rep:
