@@ -172,6 +172,14 @@ struct gp_batch {
   void* ztab = nullptr;               // the absent z axis: v = c = 0 (slot 0), w = 1 (slot 1)
   double* partials = nullptr;
   unsigned int* counter = nullptr;
+  // one reduction launch for every run: per-run arguments, (run, block,
+  // blocks, tx_log2) items, each run's first item, weight factors, per-item sums
+  void* obs_runs_d = nullptr;
+  void* obs_items_d = nullptr;
+  int* obs_first_d = nullptr;
+  double* obs_ws_d = nullptr;
+  double* obs_parts = nullptr;
+  int nobs_items = 0;
   double* obs_out = nullptr;
   double* obs_host = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -447,10 +455,15 @@ int batch_steps(gp_batch* b, long nsteps) {
   return b_join_out(b);
 }
 
+// Arguments and items of the one-launch reduction over all runs (built once).
 template <typename T>
-int batch_observables(gp_batch* b) {
+int build_obs(gp_batch* b) {
+  std::vector<ObsArgs<T>> runs(b->nruns);
+  std::vector<int4> items;
+  std::vector<int> first(b->nruns + 1, 0);
+  std::vector<double> ws(b->nruns);
   for (int r = 0; r < b->nruns; ++r) {
-    ObsArgs<T> a;
+    ObsArgs<T>& a = runs[r];
     std::memset(&a, 0, sizeof(a));
     a.psi = (const c2_t<T>*)b->psi + b->off[r];
     a.dim = 2;
@@ -468,12 +481,39 @@ int batch_observables(gp_batch* b) {
     a.cz = (const R*)b->ztab;
     a.wz = (const R*)b->ztab + 1;
     a.wscale = b->dx[2 * r] * b->dx[2 * r + 1] / 9.0;  // the tables hold the Simpson coefficients
-    a.partials = b->partials;
-    a.counter = b->counter;
-    a.out = b->obs_out + 8L * r;
-    launch_observables<T>(a, b->work);
-    count_launch();
+    ws[r] = a.wscale;
+    // rows of 32..256 threads; up to 32 blocks per run (10-100 points per thread on the largest grids)
+    const int lg = obs_tx_log2(a.nx), rpb = kObsThreads >> lg;
+    const int nblk = std::max(1, std::min(32, (a.ny + rpb - 1) / rpb));
+    first[r] = (int)items.size();
+    for (int k = 0; k < nblk; ++k) items.push_back(make_int4(r, k, nblk, lg));
   }
+  first[b->nruns] = (int)items.size();
+  b->nobs_items = (int)items.size();
+  int rc;
+  if ((rc = b_alloc(b, &b->obs_runs_d, runs.size() * sizeof(ObsArgs<T>))) ||
+      (rc = b_upload<ObsArgs<T>>(b, b->obs_runs_d, runs)))
+    return rc;
+  if ((rc = b_alloc(b, &b->obs_items_d, items.size() * sizeof(int4))) || (rc = b_upload<int4>(b, b->obs_items_d, items)))
+    return rc;
+  void* p = nullptr;
+  if ((rc = b_alloc(b, &p, first.size() * sizeof(int))) || (rc = b_upload<int>(b, p, first))) return rc;
+  b->obs_first_d = (int*)p;
+  if ((rc = b_alloc(b, &p, ws.size() * sizeof(double))) || (rc = b_upload<double>(b, p, ws))) return rc;
+  b->obs_ws_d = (double*)p;
+  if ((rc = b_alloc(b, &p, 8 * items.size() * sizeof(double)))) return rc;
+  b->obs_parts = (double*)p;
+  return GP_OK;
+}
+
+// Observables of every run: one launch over all runs' blocks, one to finish.
+template <typename T>
+int batch_observables(gp_batch* b) {
+  batch_obs_kernel<T><<<b->nobs_items, kObsThreads, 0, b->work>>>((const ObsArgs<T>*)b->obs_runs_d,
+                                                                    (const int4*)b->obs_items_d, b->obs_parts);
+  count_launch();
+  obs_finish_kernel<<<b->nruns, kObsThreads, 0, b->work>>>(b->obs_parts, b->obs_first_d, b->obs_ws_d, b->obs_out);
+  count_launch();
   GP_CUDA(cudaGetLastError());
   return GP_OK;
 }
@@ -588,6 +628,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   if ((rc = b_alloc(b, (void**)&b->partials, 152L * 16 * 8 * sizeof(double)))) return bail(rc);
   if ((rc = b_alloc(b, (void**)&b->counter, 64))) return bail(rc);
   if ((rc = b_alloc(b, (void**)&b->obs_out, (8L * nruns + 8) * sizeof(double)))) return bail(rc);
+  if ((rc = prec == GP_F64 ? build_obs<double>(b) : build_obs<float>(b))) return bail(rc);
   *out = b;
   return GP_OK;
 }

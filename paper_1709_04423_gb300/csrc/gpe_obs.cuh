@@ -71,13 +71,14 @@ __device__ __forceinline__ R grad2_axis(const c2_t<T>* psi, long q, int i, int n
 constexpr int kObsThreads = 256;
 constexpr int kObsBlocks = 152 * 4;   // at most; 10-100 points per thread on large grids
 
-// Rows r = j + ny k of the grid are spread over the blocks; 2^tx_log2
-// threads of a row-group take consecutive x indices (coalesced), and each
-// thread keeps its x-dependent table values across the rows it visits.
+// Per-thread sums of the seven terms over the thread's points.  Rows
+// r = j + ny k of the grid are spread over nblk blocks (this block is blk);
+// 2^tx_log2 threads of a row-group take consecutive x indices (coalesced),
+// and each thread keeps its x-dependent table values across the rows it visits.
 template <typename T>
-__global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, int tx_log2) {
+__device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2, int blk, int nblk,
+                                               obs_r<T> (&acc)[7]) {
   using R = obs_r<T>;
-  __shared__ double smem[32 * 7];
   const int TX = 1 << tx_log2;
   const int tx = threadIdx.x & (TX - 1), ty = threadIdx.x >> tx_log2, rpb = blockDim.x >> tx_log2;
   const int nrows = A.ny * A.nz;
@@ -85,12 +86,9 @@ __global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, 
   const R fx1 = R(1.0 / (2.0 * A.hx)), fx4 = R(1.0 / (12.0 * A.hx));
   const R fy1 = R(1.0 / (2.0 * A.hy)), fy4 = R(1.0 / (12.0 * A.hy));
   const R fz1 = R(1.0 / (2.0 * A.hz)), fz4 = R(1.0 / (12.0 * A.hz));
-  R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-  pdl_wait();  // the state is the previous kernel's output
-  pdl_release();
   for (int i = tx; i < A.nx; i += TX) {
     const R vxi = A.vx[i], cxi = A.cx[i], wxi = A.wx[i];
-    for (int r = blockIdx.x * rpb + ty; r < nrows; r += gridDim.x * rpb) {
+    for (int r = blk * rpb + ty; r < nrows; r += nblk * rpb) {
       const int j = r % A.ny, k = r / A.ny;
       const long q = (long)r * A.nx + i;
       const c2_t<T> p = A.psi[q];
@@ -113,6 +111,16 @@ __global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, 
       if (A.density) A.density[q] = (double)dens;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, int tx_log2) {
+  using R = obs_r<T>;
+  __shared__ double smem[32 * 7];
+  R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  pdl_wait();  // the state is the previous kernel's output
+  pdl_release();
+  obs_accumulate<T>(A, tx_log2, blockIdx.x, gridDim.x, acc);
   double v[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) v[q] = (double)acc[q];  // FP64 from here on
@@ -124,12 +132,60 @@ __global__ void __launch_bounds__(kObsThreads) observables_kernel(ObsArgs<T> A, 
   }
 }
 
+// Threads per row of the reduction: 32..256, enough for a row of nx points.
+inline int obs_tx_log2(int nx) {
+  int lg = 5;
+  while ((1 << lg) < nx && lg < 8) ++lg;
+  return lg;
+}
+
+// Many independent grids in one launch: block b takes item items[b] =
+// (grid, block index within the grid, blocks of that grid) and stores its
+// FP64 sums in parts[8 b + q]; obs_finish_kernel then sums each grid's blocks
+// in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kObsThreads) batch_obs_kernel(const ObsArgs<T>* __restrict__ runs,
+                                                               const int4* __restrict__ items,
+                                                               double* __restrict__ parts) {
+  using R = obs_r<T>;
+  __shared__ double smem[32 * 7];
+  const int4 it = items[blockIdx.x];  // (run, block, nblocks, tx_log2)
+  const ObsArgs<T> A = runs[it.x];
+  R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  obs_accumulate<T>(A, it.w, it.y, it.z, acc);
+  double v[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) v[q] = (double)acc[q];
+  block_sum<7>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) parts[8L * blockIdx.x + q] = v[q];
+  }
+}
+
+// One block per grid: the sums of items first[g] .. first[g+1]-1, times the
+// grid's weight factor, into out[8 g + q].
+static __global__ void __launch_bounds__(kObsThreads) obs_finish_kernel(const double* __restrict__ parts,
+                                                                const int* __restrict__ first,
+                                                                const double* __restrict__ wscale,
+                                                                double* __restrict__ out) {
+  __shared__ double smem[32 * 7];
+  const int g = blockIdx.x;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = first[g] + threadIdx.x; b < first[g + 1]; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) v[q] += parts[8L * b + q];
+  block_sum<7>(v, smem);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) out[8L * g + q] = v[q] * wscale[g];
+}
+
 // The one launch configuration of the reduction (every caller uses it, so
 // that equal states give bitwise equal sums).
 template <typename T>
 inline void launch_observables(const ObsArgs<T>& a, cudaStream_t s, bool pdl = false) {
-  int lg = 5;
-  while ((1 << lg) < a.nx && lg < 8) ++lg;  // 32..256 threads per row
+  const int lg = obs_tx_log2(a.nx);  // 32..256 threads per row
   const int rpb = kObsThreads >> lg;
   const long nrows = (long)a.ny * a.nz;
   const long want = (nrows + rpb - 1) / rpb;
