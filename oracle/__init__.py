@@ -75,6 +75,7 @@ def _load():
         lib.gpo_norm.argtypes = [_P, _D]
         lib.gpo_norm.restype = ctypes.c_double
         lib.gpo_observables.argtypes = [_P, _D, _D, _D]
+        lib.gpo_reduced_density.argtypes = [_P, _D, ctypes.c_int, _D]
         lib.gpo_adjoint_real.argtypes = [_P, ctypes.c_long, _D, _D, _D, _D, _D]
         lib.gpo_adjoint_real.restype = ctypes.c_double
         lib.gpo_adjoint_phase.argtypes = [_P, _D, _D, _D, _D]
@@ -206,6 +207,19 @@ def observables(grid, phi, density=False):
     if density:
         res["density"] = den
     return res
+
+
+def reduced_density(grid, phi, keep):
+    """Reduced density on the axes in ``keep`` (a tuple of axis numbers, 0 = x):
+    Simpson sum of |phi|^2 over the other axes (reading R12).  Returns an array
+    of shape (n_z, n_y, n_x) restricted to the kept axes."""
+    a = _state(grid, phi)
+    p = grid._struct()
+    mask = sum(1 << d for d in keep)
+    shape = tuple(grid.n[d] for d in reversed(range(grid.dim)) if d in keep)
+    out = np.empty(shape, dtype=np.float64)
+    _load().gpo_reduced_density(ctypes.byref(p), _ptr(a), int(mask), _ptr(out))
+    return out
 
 
 def adjoint_real(grid, phi0, target, nsteps):

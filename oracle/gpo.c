@@ -201,6 +201,32 @@ double gpo_norm(const gpo_problem* p, const double complex* phi) {
   return s;
 }
 
+/* R12: the Simpson weights of every dropped axis times |phi|^2, summed;
+ * kept axes index the output (their own points are not weighted). */
+void gpo_reduced_density(const gpo_problem* p, const double complex* phi, int keep_mask, double* out) {
+  int n[3], keep[3];
+  double* w[3];
+  long stride_out[3], nout = 1;
+  for (int d = 0; d < 3; ++d) {
+    n[d] = axis_n(p, d);
+    keep[d] = d < p->dim && ((keep_mask >> d) & 1);
+    w[d] = malloc(sizeof(double) * n[d]);
+    if (d < p->dim && !keep[d]) gpo_simpson_weights(n[d], p->dx[d], w[d]);
+    else for (int i = 0; i < n[d]; ++i) w[d][i] = 1.0;
+    stride_out[d] = keep[d] ? nout : 0;
+    if (keep[d]) nout *= n[d];
+  }
+  for (long o = 0; o < nout; ++o) out[o] = 0.0;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        const double complex v = phi[i + (long)n[0] * (j + (long)n[1] * k)];
+        const long o = i * stride_out[0] + j * stride_out[1] + k * stride_out[2];
+        out[o] += w[0][i] * w[1][j] * w[2][k] * (creal(v) * creal(v) + cimag(v) * cimag(v));
+      }
+  for (int d = 0; d < 3; ++d) free(w[d]);
+}
+
 /* R3 + R6 */
 void gpo_step(const gpo_problem* p, int imag, double complex* phi) {
   gpo_phase(p, imag, phi);

@@ -43,6 +43,11 @@ void gpo_step(const gpo_problem* p, int imag, double complex* phi);
 void gpo_run(const gpo_problem* p, int imag, long nsteps, double complex* phi);
 
 double gpo_norm(const gpo_problem* p, const double complex* phi);
+/* R12: reduced (integrated) density on the axes in keep_mask (bit d = axis d
+ * kept): out[kept coordinates, x fastest] = sum over the other axes of the
+ * Simpson weights times |phi|^2 (the paper's programs write reduced 1d and 2d
+ * densities; "Summary of revisions"). */
+void gpo_reduced_density(const gpo_problem* p, const double complex* phi, int keep_mask, double* out);
 void gpo_observables(const gpo_problem* p, const double complex* phi, double out[7], double* density);
 
 double gpo_adjoint_real(const gpo_problem* p, long nsteps, const double complex* phi0,

@@ -441,3 +441,70 @@ def test_adjoint_gradient_matches_finite_differences():
         Jp = O.adjoint_real(gr.with_(V=V + h * Gk), phi0, target, steps)[0]
         Jm = O.adjoint_real(gr.with_(V=V - h * Gk), phi0, target, steps)[0]
         assert float(np.sum(dJdV * Gk)) == pytest.approx((Jp - Jm) / (2 * h), rel=1e-6, abs=1e-12)
+
+
+# ---------------------------------------------------------------- reduced densities (R12)
+
+def _keeps(dim):
+    import itertools
+    return [k for r in range(1, dim + 1) for k in itertools.combinations(range(dim), r)]
+
+
+def test_reduced_density_of_trap_ground_state_is_gaussian():
+    """The g = 0 trap ground state prod_d (nu_d/pi)^(1/4) exp(-nu_d x^2/2)
+    integrates over the dropped axes to prod_kept (nu/pi)^(1/2) exp(-nu x^2)
+    (each dropped factor's Simpson integral is 1 to ~1e-12 at dx = 0.1)."""
+    n, dx, nkl = [129, 121, 113], [0.1, 0.1, 0.1], [1.0, 1.4, 1.8]
+    gr = O.Grid(3, n, dx, 1e-3, nkl, 0.0)
+    xs = [O.coords(n[d], dx[d]) for d in range(3)]
+    f = [(nkl[d] / np.pi) ** 0.25 * np.exp(-nkl[d] * xs[d] ** 2 / 2) for d in range(3)]
+    phi = f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+    for keep in _keeps(3):
+        got = O.reduced_density(gr, phi, keep)
+        want = np.ones(())
+        for d in reversed(range(3)):
+            if d in keep:
+                want = np.multiply.outer(want, f[d] ** 2)
+        assert np.max(np.abs(got - want)) <= 1e-9 * np.max(want), keep
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_reduced_density_factorises_on_product_states(dim):
+    """For phi = prod_d f_d(x_d) with random complex factors the reduced
+    density is prod_kept |f_d|^2 times prod_dropped (Simpson norm of f_d):
+    pins which axis is summed, the weights used and the output layout."""
+    n, dx = [9, 8, 7][:dim], [0.3, 0.25, 0.2][:dim]
+    gr = O.Grid(dim, n, dx, 1e-3, [1.0] * dim, 0.0)
+    f = [rand_complex((n[d],), 300 + d) for d in range(dim)]
+    phi = np.ones(())
+    for d in reversed(range(dim)):
+        phi = np.multiply.outer(phi, f[d])
+    norms = [float(np.dot(O.simpson_weights(n[d], dx[d]), np.abs(f[d]) ** 2)) for d in range(dim)]
+    for keep in _keeps(dim):
+        want = np.ones(())
+        scale = 1.0
+        for d in reversed(range(dim)):
+            if d in keep:
+                want = np.multiply.outer(want, np.abs(f[d]) ** 2)
+            else:
+                scale *= norms[d]
+        got = O.reduced_density(gr, phi, keep)
+        assert got.shape == want.shape
+        assert np.allclose(got, want * scale, rtol=1e-13, atol=0), keep
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_reduced_density_integrates_to_the_norm(dim):
+    """Integrating a reduced density over its kept axes gives the full Simpson
+    norm (tensor-product weights), for every choice of kept axes."""
+    n, dx = [11, 10, 9][:dim], [0.3, 0.25, 0.2][:dim]
+    gr = O.Grid(dim, n, dx, 1e-3, [1.0] * dim, 0.0)
+    phi = rand_complex(gr.shape, 310 + dim)
+    N = O.norm(gr, phi)
+    for keep in _keeps(dim):
+        r = O.reduced_density(gr, phi, keep)
+        kept = sorted(keep, reverse=True)        # array axes: outermost kept axis first
+        while np.ndim(r) > 0:                    # contract the last array axis (smallest kept d)
+            d = kept[np.ndim(r) - 1]
+            r = r @ O.simpson_weights(n[d], dx[d])
+        assert float(r) == pytest.approx(N, rel=1e-13), keep
