@@ -314,9 +314,24 @@ def run_ours(args):
             kms = p.time_sweeps(True, 64)
             ob = p.observables()
             shp = p.shapes()
+            # reduced densities of the final state (1d along x, 2d in x-y), device outputs
+            red = {}
+            for keep in ((0,), (0, 1)):
+                for _ in range(3):
+                    p.reduced_density(keep)
+                r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                r0.record(stream)
+                for _ in range(20):
+                    p.reduced_density(keep)
+                r1.record(stream)
+                r1.synchronize()
+                us = r0.elapsed_time(r1) / 20 * 1e3
+                red["keep_" + "".join("xyz"[d] for d in keep)] = {
+                    "us": us, "state_read_gbs": np_ * (8 if prec == "f32" else 16) / (us * 1e-6) / 1e9}
         p.close()
         results[prec] = {"total_s": total_s, "value": value, "ms": ms, "launches": launches,
-                         "clocks": clk.summary(), "kernel_ms": kms, "obs": ob, "shapes": shp}
+                         "clocks": clk.summary(), "kernel_ms": kms, "obs": ob, "shapes": shp,
+                         "reduced_density": red}
     # ---- batched form: 64 independent 2d real-time runs (sizes from
     # {128..512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1, kappa ~ U[1, 2]),
     # each from its g = 0 trap ground state (an interaction quench)
@@ -555,6 +570,7 @@ def run_ours(args):
                      "roofline": forms["f64"]["roofline"], "gpu_launches": results["f64"]["launches"],
                      "clocks": results["f64"]["clocks"]} if "f64" in forms else None),
             "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": ratio("f32", "f64"),
+                    "reduced_density": results["f32"]["reduced_density"],
                     "mu_err_vs_f64_full_job": mu_err, "mu_err_vs_f64_converged_20000_steps": conv_err("f32"),
                     "mu_f32": mu["f32"]["mu"] if "f32" in mu else None,
                     "mu_f64": mu["f64"]["mu"] if "f64" in mu else None},

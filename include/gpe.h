@@ -132,6 +132,18 @@ int gp_step_real(gp_handle* h, long nsteps);
  * if the state holds NaN or Inf. */
 int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device);
 
+/* Reduced (integrated) density: |phi|^2 summed with the composite-Simpson
+ * weights over the axes NOT in keep_mask, on the grid of the kept axes (the
+ * paper's programs write reduced 1d and 2d densities; "Summary of
+ * revisions").  keep_mask: bit d set keeps axis d (0 = x); at least one bit,
+ * only bits d < dim (all bits: the density itself).  out: the product of the
+ * kept axes' lengths, in doubles, kept coordinates x fastest; on the device if
+ * out_on_device != 0 (asynchronous, stream order), else on the host (the call
+ * synchronises).  Sums in FP64, deterministic.  The handle keeps a scratch
+ * buffer of about 1 MB (allocated on the first call or when a larger one is
+ * needed). */
+int gp_reduced_density(gp_handle* h, int keep_mask, double* out, int out_on_device);
+
 /* Instrumentation: runs nsteps steps (imaginary time if imag != 0) launched
  * one by one, with CUDA events on the library's stream around every sweep
  * kernel, and stores the mean duration in milliseconds of the sweep along

@@ -113,7 +113,9 @@ struct gp_handle {
   double* parts[2] = {nullptr, nullptr};
   int parts_n = 0;
   double parts_ws = 1.0;
-  bool pdl_now = false;  // launch the sweeps as programmatic dependents (inside gp_step_*)
+  bool pdl_now = false;
+  double* red_parts = nullptr;  // reduced-density chunk sums (+ host-bound output)
+  size_t red_cap = 0;  // launch the sweeps as programmatic dependents (inside gp_step_*)
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   double* obs_out = nullptr;  // [8]

@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
-    "gp_autotune", "gp_set_shapes", "gp_get_shapes",
+    "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density",
 )
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.gp_autotune.argtypes = [_vp, I, I, ctypes.POINTER(D)]
     lib.gp_set_shapes.argtypes = [_vp, I, I, I, I]
     lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.gp_reduced_density.argtypes = [_vp, I, _vp, I]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
     lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
@@ -163,6 +164,10 @@ def gp_observables(h, density_ptr=None, density_on_device=0):
     out = GpObs()
     _check(load().gp_observables(h, ctypes.byref(out), density_ptr, int(density_on_device)))
     return out
+
+
+def gp_reduced_density(h, keep_mask, out_ptr, out_on_device):
+    return _check(load().gp_reduced_density(h, int(keep_mask), out_ptr, int(out_on_device)))
 
 
 def gp_time_sweeps(h, imag, nsteps):
@@ -409,6 +414,20 @@ class Propagator:
         if density:
             d["density"] = den
         return d
+
+    def reduced_density(self, keep, device=True):
+        """Reduced (integrated) density on the axes in ``keep`` (tuple of axis
+        numbers, 0 = x): |phi|^2 Simpson-summed over the other axes.  Shape:
+        the kept axes' lengths, outermost first (x last)."""
+        mask = sum(1 << int(d) for d in keep)
+        shape = tuple(self.n[d] for d in reversed(range(self.dim)) if d in keep)
+        if device:
+            out = self.torch.empty(shape, dtype=self.torch.float64, device="cuda")
+            gp_reduced_density(self.h, mask, out.data_ptr(), 1)
+            return out
+        out = np.empty(shape, dtype=np.float64)
+        gp_reduced_density(self.h, mask, out.ctypes.data, 0)
+        return out
 
 
 class Batch:
