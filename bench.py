@@ -415,13 +415,16 @@ def run_ours(args):
                     q.step_real(args.inner)
                 barrier()
                 torch.cuda.nvtx.range_push(f"timed_quench_{prec}")
+                recs = []
                 for s_ in range(args.steps):
                     ev[s_][0].record(stream)
-                    q.step_real(args.inner)
-                    q.observables()
+                    # inner steps + the observables at their end, recorded on the device
+                    recs.append(q.step_series(False, args.inner, args.inner, device=True))
                     ev[s_][1].record(stream)
                 barrier()
                 torch.cuda.nvtx.range_pop()
+                rms_t = [[args.warmup * args.inner + (i + 1) * args.inner, float(r_[0, 6])]
+                         for i, r_ in enumerate(recs)]
                 qt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
                 kms = q.time_sweeps(False, 16)
                 ob1 = q.observables()
@@ -433,7 +436,8 @@ def run_ours(args):
                           "kernel_ms": kms, "dominant_sweep_axis": axis, "achieved_gbs": ach,
                           "frac_of_measured_hbm": ach / float(measured_peaks()[0]["hbm_gbs"]),
                           "energy_drift_rel": abs(ob1["energy"] / ob0["energy"] - 1),
-                          "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1)}
+                          "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1),
+                          "rms_r_t": rms_t}
 
     # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V
     # and g at 128^3 (dx = 0.1, dt = 5e-4, 1000 steps, g = 30, isotropic trap +

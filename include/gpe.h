@@ -132,6 +132,20 @@ int gp_step_real(gp_handle* h, long nsteps);
  * if the state holds NaN or Inf. */
 int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_device);
 
+/* Runs nsteps imaginary-time (imag != 0) or real-time steps and records the
+ * observables every `every` steps, for the series the paper's real-time
+ * programs report (rms sizes during the dynamics; "Summary of revisions"):
+ * after steps every, 2 every, ..., floor(nsteps/every) every, a record of 7
+ * doubles -- norm, energy, mu, rms_x, rms_y, rms_z, rms_r, as gp_observables
+ * -- goes to out[7 r + q] (floor(nsteps/every) records; nothing else is
+ * written).  With out_on_device != 0 the call is asynchronous (no host
+ * synchronisation between records; the energy and mu use the g current at the
+ * call); else the records are copied to the host at the end (synchronises).
+ * Imaginary time: each record is of the renormalised state.  Leftover steps
+ * (nsteps mod every) run after the last record.  The handle keeps a scratch
+ * buffer of 8 doubles per record (grown on demand). */
+int gp_step_series(gp_handle* h, int imag, long nsteps, int every, double* out, int out_on_device);
+
 /* Reduced (integrated) density: |phi|^2 summed with the composite-Simpson
  * weights over the axes NOT in keep_mask, on the grid of the kept axes (the
  * paper's programs write reduced 1d and 2d densities; "Summary of

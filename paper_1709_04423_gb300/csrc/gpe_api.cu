@@ -260,10 +260,31 @@ int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms) {
   if (h->prec == GP_DF64) return time_steps_df(h, imag, nsteps, ms);
   return h->prec == GP_F64 ? time_steps_f64(h, imag, nsteps, ms) : time_steps_f32(h, imag, nsteps, ms);
 }
-int run_observables_any(gp_handle* h, double* dens_dev) {
-  if (h->prec == GP_DF64) return run_observables_df(h, dens_dev);
-  return h->prec == GP_F64 ? run_observables_f64(h, dens_dev) : run_observables_f32(h, dens_dev);
+int run_observables_any(gp_handle* h, double* dens_dev, double* sums_out) {
+  if (h->prec == GP_DF64) return run_observables_df(h, dens_dev, sums_out);
+  return h->prec == GP_F64 ? run_observables_f64(h, dens_dev, sums_out) : run_observables_f32(h, dens_dev, sums_out);
 }
+
+namespace {
+// Seven Simpson sums per record -> norm, energy, mu, rms_x, rms_y, rms_z, rms_r
+// (the same formulas as gp_observables).
+__global__ void series_finish_kernel(const double* __restrict__ S, long nrec, double g, double* __restrict__ out) {
+  for (long r = (long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += (long)gridDim.x * blockDim.x) {
+    const double* s = S + 8 * r;
+    const double N = s[0];
+    double* o = out + 7 * r;
+    o[0] = N;
+    o[1] = (s[1] + s[2]) / N + 0.5 * g * s[3] / (N * N);
+    o[2] = (s[1] + s[2]) / N + g * s[3] / (N * N);
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      o[3 + d] = sqrt(s[4 + d] / N);
+      r2 += s[4 + d] / N;
+    }
+    o[6] = sqrt(r2);
+  }
+}
+}  // namespace
 
 namespace {
 // Host triple-float images of complex factors (exact splits of the doubles).
@@ -826,6 +847,46 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     best_ms[1] = cs.empty() ? 0.0 : bc;
   }
   if ((rc = gp_set_shapes(h, best_t, best_x, best_c, best_flags))) return rc;
+  return join_out(h);
+}
+
+int gp_step_series(gp_handle* h, int imag, long nsteps, int every, double* out, int out_on_device) {
+  if (!h || !out) return fail(GP_ERR_INVALID, "gp_step_series: NULL argument");
+  if (nsteps < 0 || every < 1) return fail(GP_ERR_INVALID, "gp_step_series: need nsteps >= 0 and every >= 1");
+  const long nrec = nsteps / every;
+  int rc = join_in(h);
+  if (rc) return rc;
+  const size_t need = 8 * (size_t)nrec + (out_on_device ? 0 : 7 * (size_t)nrec);
+  if (need > h->series_cap) {
+    if (h->series_buf) {
+      cudaStreamSynchronize(h->work);
+      cudaFree(h->series_buf);
+      for (auto& p : h->allocs)
+        if (p == h->series_buf) p = nullptr;
+      h->series_buf = nullptr;
+      h->series_cap = 0;
+    }
+    void* p = nullptr;
+    if ((rc = dev_alloc(h, &p, need * sizeof(double)))) return rc;
+    h->series_buf = (double*)p;
+    h->series_cap = need;
+  }
+  for (long r = 0; r < nrec; ++r) {
+    if ((rc = run_steps_any(h, imag != 0, every))) return rc;
+    if ((rc = run_observables_any(h, nullptr, h->series_buf + 8 * r))) return rc;
+  }
+  if ((rc = run_steps_any(h, imag != 0, nsteps - nrec * every))) return rc;
+  if (nrec > 0) {
+    double* dst = out_on_device ? out : h->series_buf + 8 * nrec;
+    const int blocks = (int)std::min<long>((nrec + 127) / 128, 152L * 4);
+    series_finish_kernel<<<blocks, 128, 0, h->work>>>(h->series_buf, nrec, h->g, dst);
+    count_launch();
+    GP_CUDA(cudaGetLastError());
+    if (!out_on_device) {
+      GP_CUDA(cudaMemcpyAsync(out, dst, 7 * (size_t)nrec * sizeof(double), cudaMemcpyDeviceToHost, h->work));
+      GP_CUDA(cudaStreamSynchronize(h->work));
+    }
+  }
   return join_out(h);
 }
 

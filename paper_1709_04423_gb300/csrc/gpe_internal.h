@@ -115,7 +115,9 @@ struct gp_handle {
   double parts_ws = 1.0;
   bool pdl_now = false;
   double* red_parts = nullptr;  // reduced-density chunk sums (+ host-bound output)
-  size_t red_cap = 0;  // launch the sweeps as programmatic dependents (inside gp_step_*)
+  size_t red_cap = 0;
+  double* series_buf = nullptr;  // gp_step_series: raw sums (8 per record) + host-bound records
+  size_t series_cap = 0;  // launch the sweeps as programmatic dependents (inside gp_step_*)
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   double* obs_out = nullptr;  // [8]
@@ -163,10 +165,11 @@ int upload_factors(gp_handle* h);
 // per-precision entry points (gpe_step_f32.cu / gpe_step_f64.cu)
 int run_steps_any(gp_handle* h, bool imag, long nsteps);  // dispatch on h->prec
 int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms_out);
-int run_observables_any(gp_handle* h, double* dens_dev);
+// sums_out: where the seven FP64 sums go (default: the handle's slot)
+int run_observables_any(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
 int run_steps_df(gp_handle* h, bool imag, long nsteps);
 int time_steps_df(gp_handle* h, bool imag, long nsteps, double* ms_out);
-int run_observables_df(gp_handle* h, double* dens_dev);
+int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
 // double-float state <-> complex128 (device buffers, on the library stream)
 void df_from_c128(gp_handle* h, const void* src);
 void df_to_c128(gp_handle* h, void* dst);
@@ -175,8 +178,8 @@ int run_steps_f32(gp_handle* h, bool imag, long nsteps);
 int run_steps_f64(gp_handle* h, bool imag, long nsteps);
 int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out);
 int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out);
-int run_observables_f32(gp_handle* h, double* dens_dev);
-int run_observables_f64(gp_handle* h, double* dens_dev);
+int run_observables_f32(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
+int run_observables_f64(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
 void to_float(gp_handle* h, float* dst, const double* src, long n);
 void potential_factors(gp_handle* h);  // fV from the FP64 potential (state precision)
 int adjoint_forward_f32(gp_handle* h, long nsteps, int K);

@@ -410,7 +410,7 @@ int time_steps_t(gp_handle* h, bool imag, long nsteps, double* ms_out) {
 }
 
 template <typename T>
-int run_observables_t(gp_handle* h, double* dens_dev) {
+int run_observables_t(gp_handle* h, double* dens_dev, double* sums_out = nullptr) {
   ObsArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.psi = (const c2_t<T>*)h->psi;
@@ -438,7 +438,7 @@ int run_observables_t(gp_handle* h, double* dens_dev) {
   a.density = dens_dev;
   a.partials = h->partials;
   a.counter = h->counter;
-  a.out = h->obs_out;
+  a.out = sums_out ? sums_out : h->obs_out;
   launch_observables<T>(a, h->work, pdl_enabled() && h->prec != GP_F64);
   count_launch();
   GP_CUDA(cudaGetLastError());

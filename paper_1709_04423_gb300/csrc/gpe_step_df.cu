@@ -56,11 +56,11 @@ int time_steps_df(gp_handle* h, bool imag, long nsteps, double* ms_out) {
 }
 
 // The observables take the state rounded to complex128 (the sums are FP64).
-int run_observables_df(gp_handle* h, double* dens_dev) {
+int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out) {
   df_to_c128(h, h->df_stage);
   void* psi = h->psi;
   h->psi = h->df_stage;
-  const int rc = run_observables_t<double>(h, dens_dev);
+  const int rc = run_observables_t<double>(h, dens_dev, sums_out);
   h->psi = psi;
   return rc;
 }

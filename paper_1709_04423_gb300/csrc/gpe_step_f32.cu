@@ -9,7 +9,9 @@ int time_steps_f32(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   return time_steps_t<float>(h, imag, nsteps, ms_out);
 }
 
-int run_observables_f32(gp_handle* h, double* dens_dev) { return run_observables_t<float>(h, dens_dev); }
+int run_observables_f32(gp_handle* h, double* dens_dev, double* sums_out) {
+  return run_observables_t<float>(h, dens_dev, sums_out);
+}
 
 int adjoint_forward_f32(gp_handle* h, long nsteps, int K) { return adjoint_forward_t<float>(h, nsteps, K); }
 

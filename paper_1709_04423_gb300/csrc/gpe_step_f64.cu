@@ -9,7 +9,9 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   return time_steps_t<double>(h, imag, nsteps, ms_out);
 }
 
-int run_observables_f64(gp_handle* h, double* dens_dev) { return run_observables_t<double>(h, dens_dev); }
+int run_observables_f64(gp_handle* h, double* dens_dev, double* sums_out) {
+  return run_observables_t<double>(h, dens_dev, sums_out);
+}
 
 int adjoint_forward_f64(gp_handle* h, long nsteps, int K) { return adjoint_forward_t<double>(h, nsteps, K); }
 

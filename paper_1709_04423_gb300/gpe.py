@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "gp_destroy", "gp_last_error", "gp_kernel_launches", "gp_time_sweeps", "gp_observables_noalloc",
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
-    "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density",
+    "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
 )
 
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.gp_set_shapes.argtypes = [_vp, I, I, I, I]
     lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gp_reduced_density.argtypes = [_vp, I, _vp, I]
+    lib.gp_step_series.argtypes = [_vp, I, L, I, _vp, I]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
     lib.gp_batch_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
@@ -168,6 +169,10 @@ def gp_observables(h, density_ptr=None, density_on_device=0):
 
 def gp_reduced_density(h, keep_mask, out_ptr, out_on_device):
     return _check(load().gp_reduced_density(h, int(keep_mask), out_ptr, int(out_on_device)))
+
+
+def gp_step_series(h, imag, nsteps, every, out_ptr, out_on_device):
+    return _check(load().gp_step_series(h, int(imag), int(nsteps), int(every), out_ptr, int(out_on_device)))
 
 
 def gp_time_sweeps(h, imag, nsteps):
@@ -414,6 +419,19 @@ class Propagator:
         if density:
             d["density"] = den
         return d
+
+    def step_series(self, imag, nsteps, every, device=True):
+        """Runs nsteps steps and returns the observables recorded every
+        ``every`` steps: an array (nsteps // every, 7) with columns norm,
+        energy, mu, rms_x, rms_y, rms_z, rms_r (device tensor or numpy)."""
+        nrec = int(nsteps) // int(every)
+        if device:
+            out = self.torch.empty((max(nrec, 1), 7), dtype=self.torch.float64, device="cuda")
+            gp_step_series(self.h, imag, nsteps, every, out.data_ptr(), 1)
+            return out[:nrec]
+        out = np.empty((max(nrec, 1), 7), dtype=np.float64)
+        gp_step_series(self.h, imag, nsteps, every, out.ctypes.data, 0)
+        return out[:nrec]
 
     def reduced_density(self, keep, device=True):
         """Reduced (integrated) density on the axes in ``keep`` (tuple of axis
