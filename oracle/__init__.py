@@ -51,6 +51,7 @@ class Problem(ctypes.Structure):
         ("nkl", ctypes.c_double * 3),
         ("g", ctypes.c_double),
         ("V", ctypes.POINTER(ctypes.c_double)),
+        ("geom", ctypes.c_int),
     ]
 
 
@@ -95,7 +96,10 @@ class Grid:
     lambda^2 z^2)/2`` or an FP64 array of the grid's shape (z, y, x order).
     """
 
-    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, V=None):
+    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, V=None, geom=0):
+        self.geom = int(geom)         # 0 Cartesian, 1 spherically symmetric 3d trap (dim 1, u = sqrt(4 pi) r phi)
+        if self.geom == 1 and int(dim) != 1:
+            raise ValueError("the spherical trap is a 1d radial problem")
         self.dim = int(dim)
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
@@ -126,10 +130,11 @@ class Grid:
         p.dt = self.dt
         p.g = self.g
         p.V = _ptr(self.V) if self.V is not None else ctypes.cast(None, _D)
+        p.geom = self.geom
         return p
 
     def with_(self, **kw):
-        args = dict(dim=self.dim, n=self.n, dx=self.dx, dt=self.dt, nkl=self.nkl, g=self.g, V=self.V)
+        args = dict(dim=self.dim, n=self.n, dx=self.dx, dt=self.dt, nkl=self.nkl, g=self.g, V=self.V, geom=self.geom)
         args.update(kw)
         return Grid(**args)
 
@@ -225,6 +230,8 @@ def reduced_density(grid, phi, keep):
 def adjoint_real(grid, phi0, target, nsteps):
     """Real-time run of ``nsteps`` from phi0 and the gradient of
     J = |sum conj(target) phi(T) dV|^2.  Returns (J, phiT, dJdV, dJdg)."""
+    if grid.geom != 0:
+        raise ValueError("the oracle adjoint is written for Cartesian grids")
     a0 = _state(grid, phi0)
     tg = _state(grid, target)
     phiT = np.empty(grid.shape, dtype=np.complex128)
@@ -239,6 +246,8 @@ def adjoint_real(grid, phi0, target, nsteps):
 def adjoint_phase(grid, phi_in, lam):
     """Adjoint of the real-time N sub-step at state phi_in applied to lam.
     Returns (lam_in, dJdV contribution, dJdg contribution)."""
+    if grid.geom != 0:
+        raise ValueError("the oracle adjoint is written for Cartesian grids")
     a = _state(grid, phi_in)
     lm = _state(grid, lam)
     dJdV = np.zeros(grid.shape, dtype=np.float64)

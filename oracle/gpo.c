@@ -34,6 +34,18 @@
  *                rms_d = sqrt(int x_d^2 |psi|^2), rms_r = sqrt(sum_d rms_d^2);
  *                derivative: 4th-order central difference for 2 <= i <= n-3,
  *                2nd-order central at i = 1, n-2, zero at the end points.
+ *  R13 spherical  a spherically symmetric 3d trap (the paper's programs cover
+ *                "spherically symmetric" traps; "Nature of problem") is solved
+ *                for u(r) = sqrt(4 pi) r phi(r) on r_i = i dr, i = 0..n-1:
+ *                  i du/dt = [-1/2 d^2/dr^2 + V(r) + g |u|^2/(4 pi r^2)] u,
+ *                with u held at zero at r = 0 and r = (n-1) dr, so that R4-R8
+ *                apply to u unchanged except for the weight 1/(4 pi r^2) on
+ *                the nonlinear term (in N and in the |psi|^4 integral);
+ *                int |u|^2 dr = int |phi|^2 d^3r, int |u'|^2 dr = int |grad
+ *                phi|^2 d^3r, and rms_x is the 3d rms radius sqrt(<r^2>).
+ *                u'(0) is not zero (u ~ sqrt(4 pi) phi(0) r): the derivative
+ *                at r = 0 comes from the odd extension u(-r) = -u(r), second
+ *                order like the one at i = 1: u'(0) = u_1/dr.
  *
  * The tridiagonal solve is written as a back-to-front elimination followed by
  * a front-to-back substitution, with a plain division at every point.
@@ -66,6 +78,26 @@ void gpo_coords(int n, double dx, double* x) {
   for (int i = 0; i < n; ++i) x[i] = -0.5 * n * dx + i * dx;
 }
 
+/* R13 */
+void gpo_radial_coords(int n, double dr, double* r) {
+  for (int i = 0; i < n; ++i) r[i] = i * dr;
+}
+
+double gpo_radial_gweight(double r) {
+  const double pi = 3.14159265358979323846;
+  return r > 0.0 ? 1.0 / (4.0 * pi * r * r) : 0.0;
+}
+
+static void axis_coords(const gpo_problem* p, int d, double* x) {
+  if (p->geom == 1) gpo_radial_coords(p->n[d], p->dx[d], x);
+  else gpo_coords(p->n[d], p->dx[d], x);
+}
+
+/* weight of the nonlinear term at point q (1, or R13's 1/(4 pi r^2)) */
+static double gweight(const gpo_problem* p, long q) {
+  return p->geom == 1 ? gpo_radial_gweight(q * p->dx[0]) : 1.0;
+}
+
 /* R2 */
 void gpo_potential(const gpo_problem* p, double* V) {
   int nx = axis_n(p, 0), ny = axis_n(p, 1), nz = axis_n(p, 2);
@@ -76,9 +108,9 @@ void gpo_potential(const gpo_problem* p, double* V) {
   double* x = malloc(sizeof(double) * nx);
   double* y = malloc(sizeof(double) * ny);
   double* z = malloc(sizeof(double) * nz);
-  gpo_coords(nx, p->dx[0], x);
-  if (p->dim > 1) gpo_coords(ny, p->dx[1], y); else y[0] = 0.0;
-  if (p->dim > 2) gpo_coords(nz, p->dx[2], z); else z[0] = 0.0;
+  axis_coords(p, 0, x);
+  if (p->dim > 1) axis_coords(p, 1, y); else y[0] = 0.0;
+  if (p->dim > 2) axis_coords(p, 2, z); else z[0] = 0.0;
   double nu = p->nkl[0], ka = p->dim > 1 ? p->nkl[1] : 0.0, la = p->dim > 2 ? p->nkl[2] : 0.0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -110,7 +142,7 @@ void gpo_phase(const gpo_problem* p, int imag, double complex* phi) {
 #pragma omp parallel for schedule(static)
   for (long q = 0; q < np; ++q) {
     double dens = creal(phi[q]) * creal(phi[q]) + cimag(phi[q]) * cimag(phi[q]);
-    double theta = p->dt * (V[q] + p->g * dens);
+    double theta = p->dt * (V[q] + p->g * gweight(p, q) * dens);
     if (imag) phi[q] = exp(-theta) * phi[q];
     else phi[q] = cexp(-I * theta) * phi[q];
   }
@@ -263,7 +295,7 @@ void gpo_observables(const gpo_problem* p, const double complex* phi, double out
     c[d] = malloc(sizeof(double) * nn[d]);
     if (d < p->dim) {
       gpo_simpson_weights(nn[d], p->dx[d], w[d]);
-      gpo_coords(nn[d], p->dx[d], c[d]);
+      axis_coords(p, d, c[d]);
     } else {
       w[d][0] = 1.0;
       c[d][0] = 0.0;
@@ -281,12 +313,13 @@ void gpo_observables(const gpo_problem* p, const double complex* phi, double out
         double grad2 = 0.0;
         for (int d = 0; d < p->dim; ++d) {
           double complex dd = deriv(phi + q - idx[d] * stride[d], nn[d], idx[d], stride[d], p->dx[d]);
+          if (p->geom == 1 && idx[d] == 0) dd = phi[q + 1] / p->dx[0];   /* R13 */
           grad2 += creal(dd) * creal(dd) + cimag(dd) * cimag(dd);
         }
         nrm += wt * dens;
         kin += wt * 0.5 * grad2;
         pot += wt * V[q] * dens;
-        quart += wt * dens * dens;
+        quart += wt * dens * dens * gweight(p, q);
         for (int d = 0; d < p->dim; ++d) x2[d] += wt * c[d][idx[d]] * c[d][idx[d]] * dens;
         if (density) density[q] = dens;
       }

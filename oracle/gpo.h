@@ -30,10 +30,15 @@ typedef struct {
   double nkl[3];      /* trap frequencies nu, kappa, lambda */
   double g;           /* nonlinearity */
   const double* V;    /* NULL: harmonic trap; else full potential on the grid */
+  int geom;           /* 0: Cartesian; 1: spherically symmetric 3d trap (dim 1, R13) */
 } gpo_problem;
 
 long gpo_npoints(const gpo_problem* p);
 void gpo_coords(int n, double dx, double* x);
+/* R13 radial grid r_i = i dr, and the weight 1/(4 pi r^2) of the nonlinear
+ * term (0 at r = 0, where u is held at zero) */
+void gpo_radial_coords(int n, double dr, double* r);
+double gpo_radial_gweight(double r);
 void gpo_potential(const gpo_problem* p, double* V);
 void gpo_simpson_weights(int n, double dx, double* w);
 

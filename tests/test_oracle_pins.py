@@ -508,3 +508,54 @@ def test_reduced_density_integrates_to_the_norm(dim):
             d = kept[np.ndim(r) - 1]
             r = r @ O.simpson_weights(n[d], dx[d])
         assert float(r) == pytest.approx(N, rel=1e-13), keep
+
+
+# ---------------------------------------------------------------- spherical trap (R13)
+
+def _sph_ground(n, dr, dt, nu, g, t_end):
+    gr = O.Grid(1, [n], [dr], dt, [nu], g, geom=1)
+    r = np.arange(n) * dr
+    u0 = (np.sqrt(4 * np.pi) * r * np.exp(-0.6 * r ** 2)).astype(complex)   # not the ground state
+    return gr, O.run(gr, u0, True, int(round(t_end / dt)))
+
+
+def test_spherical_harmonic_ground_state():
+    """g = 0, isotropic 3d trap: mu = E = 3 nu/2 and the rms radius is
+    sqrt(3/(2 nu)); the kinetic integral of the exact state converges at
+    second order or better in dr (the derivative at r = 0 from the odd
+    extension of u)."""
+    nu = 1.3
+    gr, u = _sph_ground(321, 0.025, 1e-3, nu, 0.0, 12.0)
+    ob = O.observables(gr, u)
+    assert ob["mu"] == pytest.approx(1.5 * nu, abs=1e-4)
+    assert ob["energy"] == pytest.approx(ob["mu"], abs=1e-14)
+    assert ob["rms_x"] == pytest.approx(np.sqrt(1.5 / nu), abs=1e-3)
+    errs = []
+    for n, dr in ((321, 0.025), (641, 0.0125)):
+        g2 = O.Grid(1, [n], [dr], 1e-3, [1.0], 0.0, geom=1)
+        r = np.arange(n) * dr
+        ue = (np.sqrt(4 * np.pi) * r * np.pi ** -0.75 * np.exp(-r ** 2 / 2)).astype(complex)
+        ob = O.observables(g2, ue)
+        assert ob["norm"] == pytest.approx(1.0, abs=1e-12)
+        assert ob["rms_x"] == pytest.approx(np.sqrt(1.5), abs=1e-12)
+        errs.append(abs(ob["energy"] - 1.5))
+    assert errs[1] <= errs[0] / 4
+
+
+def test_spherical_thomas_fermi_limit():
+    """Large g: mu -> (1/2)(15 g nu^3/(4 pi))^(2/5), the error shrinking as g
+    grows (pins the 1/(4 pi r^2) weight of the nonlinear term)."""
+    rel = []
+    for g in (200.0, 800.0, 3200.0):
+        gr, u = _sph_ground(401, 0.03, 5e-4, 1.0, g, 8.0)
+        mu_tf = 0.5 * (15 * g / (4 * np.pi)) ** 0.4
+        rel.append(O.observables(gr, u)["mu"] / mu_tf - 1)
+    assert all(r > 0 for r in rel) and rel[0] > rel[1] > rel[2] and rel[2] < 0.01
+
+
+def test_spherical_real_time_conserves_norm():
+    gr, u = _sph_ground(201, 0.04, 1e-3, 1.0, 50.0, 2.0)
+    gr2 = gr.with_(g=100.0)
+    n0 = O.norm(gr2, u)
+    u1 = O.run(gr2, u, False, 2000)
+    assert O.norm(gr2, u1) == pytest.approx(n0, rel=1e-12)
