@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
+    ap.add_argument("--no-spherical", action="store_true", help="skip the spherical-trap form")
     ap.add_argument("--forms", default="f64,f32,df64",
                     help="precision forms of the headline workload to time (the line needs f32; f64 for ratios)")
-    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint"],
+    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical"],
                     help="time one form only (for profiling); the other forms are reported as null")
     args = ap.parse_args()
     if "f32" not in args.forms.split(","):
@@ -439,6 +440,39 @@ def run_ours(args):
                           "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1),
                           "rms_r_t": rms_t}
 
+    # ---- spherically symmetric trap (radial problem for u = sqrt(4 pi) r phi):
+    # n = 513 points on [0, 10.24], dt = 1e-4, nu = 1, g = 100, imaginary time
+    # (a 1d line: launch-latency bound, one sweep kernel per step)
+    sres = {}
+    if not args.no_spherical:
+        sn, sdr = 513, 0.02
+        sr = np.arange(sn) * sdr
+        su = torch.tensor((np.sqrt(4 * np.pi) * sr * np.exp(-0.6 * sr ** 2)).astype(np.complex128), device="cuda")
+        smu = {}
+        for prec in forms_sel:
+            with torch.cuda.stream(stream):
+                q = gpe.Propagator(1, [sn], [sdr], 1e-4, [1.0], 100.0, precision=prec, stream=stream, spherical=True)
+                q.set_state(su)
+                q.step_imag(20000)
+                smu[prec] = q.observables()
+                q.set_state(su)
+                for _ in range(args.warmup):
+                    q.step_imag(2000)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    q.step_imag(2000)
+                e1.record(stream)
+                barrier()
+                st = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+                q.close()
+            sres[prec] = {"value": world * args.steps * 2000 * sn / st, "us_per_step": 1e6 * st / (args.steps * 2000),
+                          "mu_after_20000_steps": smu[prec]["mu"], "rms_radius": smu[prec]["rms_x"]}
+        if "f64" in smu:
+            for prec in sres:
+                sres[prec]["mu_diff_vs_f64"] = abs(smu[prec]["mu"] - smu["f64"]["mu"])
+
     # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V
     # and g at 128^3 (dx = 0.1, dt = 5e-4, 1000 steps, g = 30, isotropic trap +
     # 8 Gaussian bumps, checkpoints every 50 steps); FP32 forward, FP64
@@ -489,7 +523,7 @@ def run_ours(args):
         # profiling run of a single form: report it and stop
         if rank == 0:
             print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
-                              "batched": bres or None}), flush=True)
+                              "batched": bres or None, "spherical": sres or None}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -597,6 +631,9 @@ def run_ours(args):
                                      "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "
                                      "point-steps/s; FP32 forward, FP64 gradient accumulation",
                          "f32": ares.get("f32")} if ares else None),
+            "spherical": ({"workload": "spherically symmetric 3d trap as the radial problem for u = sqrt(4 pi) r phi: "
+                                       "513 points on [0, 10.24], dt=1e-4, nu=1, g=100, imaginary time; one 1d line, "
+                                       "launch-latency bound", **sres} if sres else None),
             "batched": ({"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
                                     "(SplitMix64 seed 1712), dx=0.1, dt=5e-4, g~U[0,50], nu=1, kappa~U[1,2], "
                                     "g=0 trap ground state quenched; one launch per sweep and segment class, "
@@ -621,6 +658,7 @@ def main():
         args.no_quench = args.only != "quench256"
         args.no_adjoint = args.only != "adjoint"
         args.no_batched = args.only != "batched"
+        args.no_spherical = args.only != "spherical"
         args.no_headline = args.only != "headline"
         if args.only != "headline":
             args.no_cpu_baseline = True

@@ -100,6 +100,19 @@ typedef struct {
 int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double dt,
             const double nkl[3], double g, gp_precision prec, void* stream);
 
+/* Creates a propagator for a spherically symmetric 3d trap, V = nu^2 r^2/2
+ * ("spherically symmetric" traps are among the paper's programs; "Nature of
+ * problem").  The state is u(r) = sqrt(4 pi) r phi(r) on r_i = i dr,
+ * i = 0..n-1, held at zero at r = 0 and r = (n-1) dr; it obeys the 1d
+ * equation  i du/dt = [-1/2 d^2/dr^2 + V(r) + g |u|^2/(4 pi r^2)] u,  so the
+ * same sweeps run with the nonlinear term weighted by 1/(4 pi r^2).
+ * int |u|^2 dr is the 3d norm; gp_observables returns the 3d energy and mu
+ * and, in rms[0], the rms radius sqrt(<r^2>) (rms[1] = rms[2] = 0).  A user
+ * potential (gp_set_potential) is given on the r grid.  Arguments as gp_init
+ * (n >= 3, dr > 0); no adjoint for this geometry. */
+int gp_init_spherical(gp_handle** out, int n, double dr, double dt, double nu, double g, gp_precision prec,
+                      void* stream);
+
 /* Copies a state in (interleaved re, im, in the handle's precision -- double
  * for GP_DF64 -- npoints values).  on_device != 0: psi is a device pointer
  * read in stream order. */

@@ -309,7 +309,7 @@ int upload_factors(gp_handle* h) {
     std::vector<cd> fr(nd, cd(1, 0)), fi(nd, cd(1, 0));
     if (d < h->dim)
       for (int i = 0; i < nd; ++i) {
-        const double x = -0.5 * nd * h->dx[d] + i * h->dx[d];
+        const double x = h->geom == 1 ? i * h->dx[d] : -0.5 * nd * h->dx[d] + i * h->dx[d];
         const double v = 0.5 * h->nkl[d] * h->nkl[d] * x * x;
         fr[i] = cd(std::cos(h->dt * v), -std::sin(h->dt * v));
         fi[i] = cd(std::exp(-h->dt * v), 0.0);
@@ -367,8 +367,9 @@ int gp_destroy(gp_handle* h) {
   return GP_OK;
 }
 
-int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double dt,
-            const double nkl[3], double g, gp_precision prec, void* stream) {
+namespace {
+int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double dx[3], double dt,
+                const double nkl[3], double g, gp_precision prec, void* stream) {
   g_err.clear();
   if (!out || !n || !dx || !nkl) return fail(GP_ERR_INVALID, "gp_init: NULL argument");
   *out = nullptr;
@@ -387,6 +388,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
 
   gp_handle* h = new gp_handle();
   h->dim = dim;
+  h->geom = geom;
   for (int d = 0; d < 3; ++d) {
     h->n[d] = d < dim ? n[d] : 1;
     h->dx[d] = d < dim ? dx[d] : 1.0;
@@ -415,7 +417,7 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     std::vector<double> x(nd, 0.0), v(nd, 0.0), w(nd, 1.0), wc(nd, 1.0);
     if (d < dim) {
       for (int i = 0; i < nd; ++i) {
-        x[i] = -0.5 * nd * dx[d] + i * dx[d];
+        x[i] = geom == 1 ? i * dx[d] : -0.5 * nd * dx[d] + i * dx[d];  // radial grid from r = 0
         v[i] = 0.5 * nkl[d] * nkl[d] * x[i] * x[i];
       }
       // composite Simpson on the first m points (m = n odd, n-1 even)
@@ -468,6 +470,17 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
     }
     if ((rc = dev_alloc(h, &h->df_stage, (size_t)np * sizeof(double2)))) return bail(rc);
   }
+  if (geom == 1) {
+    // weight of the nonlinear term of the radial problem, 1/(4 pi r^2) (0 at r = 0, where u is held at zero)
+    std::vector<double> gw(n[0], 0.0);
+    for (int i = 1; i < n[0]; ++i) gw[i] = 1.0 / (4.0 * M_PI * (i * dx[0]) * (i * dx[0]));
+    if ((rc = dev_alloc(h, &h->gw_t, n[0] * tsz))) return bail(rc);
+    if ((rc = dev_alloc(h, &h->gw_o, n[0] * sizeof(double)))) return bail(rc);
+    if (prec == GP_DF64) rc = upload_real<df64>(h, h->gw_t, gw);
+    else rc = prec == GP_F64 ? upload_real<double>(h, h->gw_t, gw) : upload_real<float>(h, h->gw_t, gw);
+    if (!rc) rc = prec == GP_F32 ? upload_real<float>(h, h->gw_o, gw) : upload_real<double>(h, h->gw_o, gw);
+    if (rc) return bail(rc);
+  }
   if ((rc = upload_coefs(h))) return bail(rc);
   if ((rc = upload_factors(h))) return bail(rc);
   choose_shapes(h);
@@ -493,6 +506,19 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
   }
   *out = h;
   return GP_OK;
+}
+}  // namespace
+
+int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double dt,
+            const double nkl[3], double g, gp_precision prec, void* stream) {
+  return init_handle(out, 0, dim, n, dx, dt, nkl, g, prec, stream);
+}
+
+int gp_init_spherical(gp_handle** out, int n, double dr, double dt, double nu, double g, gp_precision prec,
+                      void* stream) {
+  const int n3[3] = {n, 1, 1};
+  const double dx3[3] = {dr, 1.0, 1.0}, nkl3[3] = {nu, 0.0, 0.0};
+  return init_handle(out, 1, 1, n3, dx3, dt, nkl3, g, prec, stream);
 }
 
 int gp_set_state(gp_handle* h, const void* psi, int on_device) {
@@ -644,6 +670,7 @@ int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every) {
     return fail(GP_ERR_INVALID, "gp_adjoint_forward: lines longer than 514 points are not supported");
   if (h->prec == GP_DF64)
     return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint takes GP_F64 or GP_F32 states");
+  if (h->geom != 0) return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint is for Cartesian grids");
   const int K = (int)std::min<long>(ckpt_every, nsteps);
   const long nck = (nsteps + K - 1) / K;
   int rc;

@@ -116,6 +116,11 @@ struct gp_handle {
   bool pdl_now = false;
   double* red_parts = nullptr;  // reduced-density chunk sums (+ host-bound output)
   size_t red_cap = 0;
+  // 0: Cartesian; 1: spherically symmetric 3d trap solved for u = sqrt(4 pi) r phi
+  // on r_i = i dr (1d), whose nonlinear term carries gw[i] = 1/(4 pi r_i^2)
+  int geom = 0;
+  void* gw_t = nullptr;      // gw in the state precision (sweeps' sub-step N)
+  void* gw_o = nullptr;      // gw in the observables' arithmetic type
   double* series_buf = nullptr;  // gp_step_series: raw sums (8 per record) + host-bound records
   size_t series_cap = 0;  // launch the sweeps as programmatic dependents (inside gp_step_*)
   double* partials = nullptr;

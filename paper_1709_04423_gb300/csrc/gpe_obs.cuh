@@ -44,6 +44,11 @@ struct ObsArgs {
   const obs_r<T>* cx; const obs_r<T>* cy; const obs_r<T>* cz;
   const obs_r<T>* wx; const obs_r<T>* wy; const obs_r<T>* wz;
   double wscale;            // factor of the FP64 totals (1, or prod dx/3 with coefficient weights)
+  // radial problem of the spherical trap: weight of the |psi|^4 term per x
+  // index (1/(4 pi r^2)), and the derivative at i = 0 from the odd extension
+  // of u (u'(0) = u_1/dx); nullptr / 0 for Cartesian grids
+  const obs_r<T>* gx;
+  int odd0;
   double* density;          // optional |phi|^2 output
   double* partials;
   unsigned int* counter;
@@ -94,7 +99,14 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
       const c2_t<T> p = A.psi[q];
       const R px = R(p.x), py = R(p.y);
       const R dens = px * px + py * py;
-      R g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4);
+      R g2;
+      if (A.odd0 && i == 0) {
+        const c2_t<T> p1 = A.psi[q + 1];
+        const R ux = R(p1.x) * (R(2) * fx1), uy = R(p1.y) * (R(2) * fx1);
+        g2 = ux * ux + uy * uy;
+      } else {
+        g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4);
+      }
       if (A.dim > 1) g2 += grad2_axis<T, R>(A.psi, q, j, A.ny, sy, fy1, fy4);
       if (A.dim > 2) g2 += grad2_axis<T, R>(A.psi, q, k, A.nz, sz, fz1, fz4);
       const R Vq = A.V ? R(A.V[q]) : (vxi + A.vy[j] + A.vz[k]);
@@ -103,7 +115,7 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
       acc[0] += wd;
       acc[1] += R(0.5) * w * g2;
       acc[2] += wd * Vq;
-      acc[3] += wd * dens;
+      acc[3] += A.gx ? wd * dens * A.gx[i] : wd * dens;
       acc[4] += wd * cxi * cxi;
       const R cy = A.cy[j], cz = A.cz[k];
       acc[5] += wd * cy * cy;

@@ -208,6 +208,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.vz = (const T*)h->vt[2];
     a.dt = (T)h->dt;
     a.g = (T)h->g;
+    a.gw = (const T*)h->gw_t;
     if constexpr (is_df<T>::value) {
       a.tfV = h->Vd ? (const tf3c*)h->tfV[fm] : nullptr;
       a.tfx = (const tf3c*)h->tfx[fm];
@@ -285,6 +286,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   a.vz = (const T*)h->vt[2];
   a.dt = (T)h->dt;
   a.g = (T)h->g;
+  a.gw = (const T*)h->gw_t;
   a.parts_in = parts_in;
   a.nparts_in = h->parts_n;
   a.parts_wscale = h->parts_ws;
@@ -434,6 +436,10 @@ int run_observables_t(gp_handle* h, double* dens_dev, double* sums_out = nullptr
     a.cx = h->cdx[0]; a.cy = h->cdx[1]; a.cz = h->cdx[2];
     a.wx = h->wd[0]; a.wy = h->wd[1]; a.wz = h->wd[2];
     a.wscale = 1.0;
+  }
+  if (h->geom == 1) {
+    a.gx = (const obs_r<T>*)h->gw_o;
+    a.odd0 = 1;
   }
   a.density = dens_dev;
   a.partials = h->partials;

@@ -41,6 +41,7 @@ struct SweepArgs {
   const T* vy;         // [ny]
   const T* vz;         // [nz]
   T dt, g;
+  const T* gw;             // nonlinear weight per point along the line (radial problem), or nullptr
   // pending renormalisation (imag FIRST): previous step's per-block norm sums
   const double* parts_in;
   int nparts_in;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(128) cn_sweep_kernel(SweepArgs<T> A) {
       if (FIRST) {
         p.x *= sc; p.y *= sc;
         T V = A.V ? A.V[base + (long)k * s] : (A.vx[k] + vline);
-        p = apply_N<T, IMAG>(p, V, A.dt, A.g);
+        p = apply_N<T, IMAG>(p, V, A.dt, A.gw ? A.g * A.gw[k] : A.g);
       }
       return p;
     };

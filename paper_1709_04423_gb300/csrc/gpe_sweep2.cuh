@@ -72,6 +72,9 @@ struct Sweep2Args {
   const T* V;
   const T* vx; const T* vy; const T* vz;
   T dt, g;
+  // weight of the nonlinear term per x index (the spherical trap's radial
+  // problem: 1/(4 pi r^2)); nullptr = 1.  Used by the 1d sweep only.
+  const T* gw;
   // double-float state: the same factors as exact triple-floats, per point
   // (tfV) or per x index (tfx) and per x line (tfyz = fy[j] fz[k], formed in FP64)
   const tf3c* tfV;
@@ -154,8 +157,9 @@ __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
 // and are summed in float, the leading ones in double-float.  Larger |a|
 // goes through FP64.
 template <bool IMAG>
-__device__ __forceinline__ df64x2 phase_df(df64x2 p, const Sweep2Args<df64>& A, long gidx, int k, int L) {
-  const df64 a = A.dtg * (p.x * p.x + p.y * p.y);
+__device__ __forceinline__ df64x2 phase_df(df64x2 p, const Sweep2Args<df64>& A, long gidx, int k, int L,
+                                           df64 dtg) {
+  const df64 a = dtg * (p.x * p.x + p.y * p.y);
   if (IMAG) {
     df64 e;
     if (fabsf(a.hi) < 0.125f) {
@@ -512,7 +516,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     const int gbase = (L0 + c) * G.nx;
     if constexpr (is_df<T>::value) {
       if (IMAG) { w.x *= scl; w.y *= scl; }
-      return phase_df<IMAG>(w, A, gbase + k, k, L0 + c);
+      return phase_df<IMAG>(w, A, gbase + k, k, L0 + c, A.dtg);
     } else {
       w.x *= scl; w.y *= scl;
       if (kFactors) {
@@ -651,14 +655,14 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
         v = in[k];
         if constexpr (FIRST && is_df<T>::value) {
           if (IMAG) { v.x *= scl; v.y *= scl; }
-          v = phase_df<IMAG>(v, A, base + k, k, L);
+          v = phase_df<IMAG>(v, A, base + k, k, L, A.gw ? A.dtg * A.gw[k] : A.dtg);
         } else if constexpr (FIRST) {
           v.x *= scl; v.y *= scl;
           if (kFactors) {
             const c2 F = A.fV ? A.fV[base + k] : fac_mul<T, IMAG>(A.fx[k], fline);
-            v = phase_N<T, IMAG>(v, F, A.dtg);
+            v = phase_N<T, IMAG>(v, F, A.gw ? A.dtg * A.gw[k] : A.dtg);
           } else {
-            v = phase_direct<T, IMAG>(v, A.V ? A.V[base + k] : A.vx[k] + vline, A.dt, A.g);
+            v = phase_direct<T, IMAG>(v, A.V ? A.V[base + k] : A.vx[k] + vline, A.dt, A.gw ? A.g * A.gw[k] : A.g);
           }
         }
       }

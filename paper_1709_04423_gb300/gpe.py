@@ -40,6 +40,7 @@ ABI_SYMBOLS = (
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
+    "gp_init_spherical",
 )
 
 
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
     lib.gp_set_shapes.argtypes = [_vp, I, I, I, I]
     lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gp_reduced_density.argtypes = [_vp, I, _vp, I]
+    lib.gp_init_spherical.argtypes = [ctypes.POINTER(_vp), I, D, D, D, D, I, _vp]
     lib.gp_step_series.argtypes = [_vp, I, L, I, _vp, I]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
@@ -130,6 +132,13 @@ def gp_init(dim, n, dx, dt, nkl, g, prec=GP_F64, stream=None):
     nkl3 = (ctypes.c_double * 3)(*(list(nkl) + [1.0] * (3 - len(nkl)))[:3])
     _check(load().gp_init(ctypes.byref(h), int(dim), n3, dx3, float(dt), nkl3, float(g), int(prec),
                           stream))
+    return h
+
+
+def gp_init_spherical(n, dr, dt, nu, g, prec=GP_F64, stream=None):
+    h = _vp()
+    _check(load().gp_init_spherical(ctypes.byref(h), int(n), float(dr), float(dt), float(nu), float(g), int(prec),
+                                    stream))
     return h
 
 
@@ -298,7 +307,11 @@ class Propagator:
     tensors of shape (nz, ny, nx) truncated to ``dim`` (x fastest).
     """
 
-    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, precision="f64", stream=None):
+    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, precision="f64", stream=None,
+                 spherical=False):
+        """``spherical=True``: a spherically symmetric 3d trap (dim 1, n radial
+        points, dx = (dr,), nkl = (nu,)); the state is u = sqrt(4 pi) r phi on
+        r_i = i dr (see gp_init_spherical)."""
         import torch
         self.torch = torch
         self.dim = int(dim)
@@ -312,7 +325,12 @@ class Propagator:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self.h = gp_init(dim, n, dx, dt, nkl, g, PRECISIONS[precision], stream.cuda_stream)
+        if spherical:
+            if self.dim != 1:
+                raise ValueError("the spherical trap is a 1d radial problem")
+            self.h = gp_init_spherical(n[0], dx[0], dt, nkl[0], g, PRECISIONS[precision], stream.cuda_stream)
+        else:
+            self.h = gp_init(dim, n, dx, dt, nkl, g, PRECISIONS[precision], stream.cuda_stream)
 
     def close(self):
         if self.h is not None:
