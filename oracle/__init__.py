@@ -52,6 +52,7 @@ class Problem(ctypes.Structure):
         ("g", ctypes.c_double),
         ("V", ctypes.POINTER(ctypes.c_double)),
         ("geom", ctypes.c_int),
+        ("split", ctypes.c_int),
     ]
 
 
@@ -96,7 +97,8 @@ class Grid:
     lambda^2 z^2)/2`` or an FP64 array of the grid's shape (z, y, x order).
     """
 
-    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, V=None, geom=0):
+    def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, V=None, geom=0, split=0):
+        self.split = int(split)       # 0 Lie (N, L_x, L_y, L_z), 1 Strang (N/2, L, N/2)
         self.geom = int(geom)         # 0 Cartesian, 1 spherically symmetric 3d trap (dim 1, u = sqrt(4 pi) r phi)
         if self.geom == 1 and int(dim) != 1:
             raise ValueError("the spherical trap is a 1d radial problem")
@@ -131,10 +133,12 @@ class Grid:
         p.g = self.g
         p.V = _ptr(self.V) if self.V is not None else ctypes.cast(None, _D)
         p.geom = self.geom
+        p.split = self.split
         return p
 
     def with_(self, **kw):
-        args = dict(dim=self.dim, n=self.n, dx=self.dx, dt=self.dt, nkl=self.nkl, g=self.g, V=self.V, geom=self.geom)
+        args = dict(dim=self.dim, n=self.n, dx=self.dx, dt=self.dt, nkl=self.nkl, g=self.g, V=self.V, geom=self.geom,
+                    split=self.split)
         args.update(kw)
         return Grid(**args)
 

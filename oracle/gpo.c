@@ -46,6 +46,10 @@
  *                u'(0) is not zero (u ~ sqrt(4 pi) phi(0) r): the derivative
  *                at r = 0 comes from the odd extension u(-r) = -u(r), second
  *                order like the one at i = 1: u'(0) = u_1/dr.
+ *  R14 Strang    an optional symmetric splitting (not what the paper's
+ *                programs do; second order in dt): N with dt/2, the sweeps
+ *                L_x, L_y, L_z with dt, N with dt/2 (|phi| of its own input),
+ *                then (imaginary time) the renormalisation of R6.
  *
  * The tridiagonal solve is written as a back-to-front elimination followed by
  * a front-to-back substitution, with a plain division at every point.
@@ -135,14 +139,18 @@ void gpo_simpson_weights(int n, double dx, double* w) {
 }
 
 /* R4 */
-void gpo_phase(const gpo_problem* p, int imag, double complex* phi) {
+static void phase_dt(const gpo_problem* p, int imag, double dt, double complex* phi);
+
+void gpo_phase(const gpo_problem* p, int imag, double complex* phi) { phase_dt(p, imag, p->dt, phi); }
+
+static void phase_dt(const gpo_problem* p, int imag, double dt, double complex* phi) {
   long np = gpo_npoints(p);
   double* V = malloc(sizeof(double) * np);
   gpo_potential(p, V);
 #pragma omp parallel for schedule(static)
   for (long q = 0; q < np; ++q) {
     double dens = creal(phi[q]) * creal(phi[q]) + cimag(phi[q]) * cimag(phi[q]);
-    double theta = p->dt * (V[q] + p->g * gweight(p, q) * dens);
+    double theta = dt * (V[q] + p->g * gweight(p, q) * dens);
     if (imag) phi[q] = exp(-theta) * phi[q];
     else phi[q] = cexp(-I * theta) * phi[q];
   }
@@ -261,8 +269,14 @@ void gpo_reduced_density(const gpo_problem* p, const double complex* phi, int ke
 
 /* R3 + R6 */
 void gpo_step(const gpo_problem* p, int imag, double complex* phi) {
-  gpo_phase(p, imag, phi);
-  for (int d = 0; d < p->dim; ++d) gpo_sweep(p, imag, d, 1.0, phi);
+  if (p->split == 1) {  /* R14 */
+    phase_dt(p, imag, 0.5 * p->dt, phi);
+    for (int d = 0; d < p->dim; ++d) gpo_sweep(p, imag, d, 1.0, phi);
+    phase_dt(p, imag, 0.5 * p->dt, phi);
+  } else {
+    gpo_phase(p, imag, phi);
+    for (int d = 0; d < p->dim; ++d) gpo_sweep(p, imag, d, 1.0, phi);
+  }
   if (imag) {
     double s = 1.0 / sqrt(gpo_norm(p, phi));
     long np = gpo_npoints(p);

@@ -31,6 +31,7 @@ typedef struct {
   double g;           /* nonlinearity */
   const double* V;    /* NULL: harmonic trap; else full potential on the grid */
   int geom;           /* 0: Cartesian; 1: spherically symmetric 3d trap (dim 1, R13) */
+  int split;          /* 0: Lie N, L_x, L_y, L_z (R3); 1: Strang N/2, L_x, L_y, L_z, N/2 (R14) */
 } gpo_problem;
 
 long gpo_npoints(const gpo_problem* p);

@@ -559,3 +559,56 @@ def test_spherical_real_time_conserves_norm():
     n0 = O.norm(gr2, u)
     u1 = O.run(gr2, u, False, 2000)
     assert O.norm(gr2, u1) == pytest.approx(n0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- Strang splitting (R14)
+
+def _quenched_ground(n, dx):
+    phi0 = I.gaussian_state(1, [n], [dx], [1.3], seed=3, noise=1e-2)
+    return O.run(O.Grid(1, [n], [dx], 1e-3, [1.0], 5.0), phi0, True, 10000)
+
+
+def test_strang_real_time_is_second_order():
+    """Real time after a quench (|phi| is invariant under N, so the half steps
+    are exact): successive differences of phi(T = 1) shrink 4x per halving of
+    dt for Strang (order 2) and 2x for Lie (order 1)."""
+    n, dx = 201, 0.08
+    gs = _quenched_ground(n, dx)
+    for split, order in ((1, 2.0), (0, 1.0)):
+        st = [O.run(O.Grid(1, [n], [dx], dt, [1.0], 10.0, split=split), gs, False, int(round(1.0 / dt)))
+              for dt in (0.02, 0.01, 0.005, 0.0025)]
+        d = [np.linalg.norm(st[i] - st[i + 1]) for i in range(3)]
+        for i in range(2):
+            assert np.log2(d[i] / d[i + 1]) == pytest.approx(order, abs=0.05), (split, i)
+
+
+def test_strang_real_time_is_reversible():
+    """The symmetric step undoes itself: S(-dt)^m S(dt)^m phi = phi (to
+    rounding), which the Lie step does not (error ~5e-3 here)."""
+    n, dx = 201, 0.08
+    gs = _quenched_ground(n, dx)
+    for split, tol in ((1, 1e-12), (0, None)):
+        gr = O.Grid(1, [n], [dx], 0.01, [1.0], 10.0, split=split)
+        back = O.run(gr.with_(dt=-0.01), O.run(gr, gs, False, 50), False, 50)
+        err = np.linalg.norm(back - gs) / np.linalg.norm(gs)
+        if tol:
+            assert err <= tol
+        else:
+            assert err > 1e-4
+
+
+def test_strang_step_is_half_phases_around_the_sweeps():
+    """One Strang step = N(dt/2), the Lie sweeps, N(dt/2), then (imaginary
+    time) renormalisation, composed from the oracle's own sub-steps."""
+    dim, n, dx = 2, [12, 10], [0.3, 0.35]
+    phi = rand_complex((10, 12), 77) * 0.5
+    for imag in (True, False):
+        gr = O.Grid(dim, n, dx, 4e-3, [1.0, 1.2], 7.0, split=1)
+        half = gr.with_(dt=2e-3, split=0)
+        want = O.phase(half, phi, imag)
+        for d in range(dim):
+            want = O.sweep(gr.with_(split=0), want, imag, d)
+        want = O.phase(half, want, imag)
+        if imag:
+            want = want / np.sqrt(O.norm(gr, want))
+        assert np.allclose(O.step(gr, phi, imag), want, rtol=0, atol=1e-14)
