@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     ap.add_argument("--no-spherical", action="store_true", help="skip the spherical-trap form")
+    ap.add_argument("--no-strang", action="store_true", help="skip the Strang-splitting form")
     ap.add_argument("--forms", default="f64,f32,df64",
                     help="precision forms of the headline workload to time (the line needs f32; f64 for ratios)")
-    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical"],
+    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical", "strang"],
                     help="time one form only (for profiling); the other forms are reported as null")
     args = ap.parse_args()
     if "f32" not in args.forms.split(","):
@@ -473,6 +474,61 @@ def run_ours(args):
             for prec in sres:
                 sres[prec]["mu_diff_vs_f64"] = abs(smu[prec]["mu"] - smu["f64"]["mu"])
 
+    # ---- Strang splitting (N(dt/2), the sweeps, N(dt/2)) on the headline
+    # workload, timed like the Lie step; and its accuracy: real-time runs of a
+    # 64^3 grid (dx = 0.2, trap (1, 1.4, 1.8), g = 50) to t = 0.1 with dt =
+    # 2e-3, 1e-3, 5e-4 against a Strang run with dt = 6.25e-5, FP64, for both
+    # splittings (relative L2 error of phi(t), observed order)
+    stres = {}
+    if not args.no_strang:
+        for prec in forms_sel:
+            p = make(prec)
+            p.set_splitting("strang")
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    p.step_imag(args.inner)
+                    p.observables()
+                barrier()
+                l0 = gpe.gp_kernel_launches()
+                torch.cuda.nvtx.range_push(f"timed_strang_{prec}")
+                for s in range(args.steps):
+                    flush.fill_(float(s))
+                    ev[s][0].record(stream)
+                    p.step_imag(args.inner)
+                    p.observables()
+                    ev[s][1].record(stream)
+                barrier()
+                torch.cuda.nvtx.range_pop()
+                launches = gpe.gp_kernel_launches() - l0
+            ms = [a.elapsed_time(b) for a, b in ev]
+            value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
+            p.close()
+            stres[prec] = {"value": value, "ms_per_step": 1e3 * total_s / args.steps, "gpu_launches": launches,
+                           "time_vs_lie": (results[prec]["value"] / value) if prec in results else None}
+        sn_, sdx, snkl, sT = [64] * 3, [0.2] * 3, [1.0, 1.4, 1.8], 0.1
+        sphi = torch.tensor(inputs.gaussian_state(3, sn_, sdx, snkl, seed=1715, noise=0.0), device="cuda")
+
+        def run_rt(dt, split):
+            with torch.cuda.stream(stream):
+                q = gpe.Propagator(3, sn_, sdx, dt, snkl, 50.0, precision="f64", stream=stream)
+                q.set_splitting(split)
+                q.set_state(sphi)
+                q.step_real(int(round(sT / dt)))
+                out = q.get_state(device=True).clone()
+                q.close()
+            stream.synchronize()
+            return out
+        sdts = [2e-3, 1e-3, 5e-4]
+        fine = run_rt(sdts[-1] / 8, "strang")
+        acc = {}
+        for split in ("lie", "strang"):
+            errs = [float(torch.linalg.norm(run_rt(dt, split) - fine) / torch.linalg.norm(fine)) for dt in sdts]
+            acc[split] = {"rel_l2_err": errs,
+                          "observed_order": [float(np.log2(errs[i] / errs[i + 1])) for i in range(len(sdts) - 1)]}
+        stres["accuracy"] = {"dt": sdts, **acc}
+
     # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V
     # and g at 128^3 (dx = 0.1, dt = 5e-4, 1000 steps, g = 30, isotropic trap +
     # 8 Gaussian bumps, checkpoints every 50 steps); FP32 forward, FP64
@@ -523,7 +579,8 @@ def run_ours(args):
         # profiling run of a single form: report it and stop
         if rank == 0:
             print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
-                              "batched": bres or None, "spherical": sres or None}), flush=True)
+                              "batched": bres or None, "spherical": sres or None,
+                              "strang": stres or None}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -634,6 +691,10 @@ def run_ours(args):
             "spherical": ({"workload": "spherically symmetric 3d trap as the radial problem for u = sqrt(4 pi) r phi: "
                                        "513 points on [0, 10.24], dt=1e-4, nu=1, g=100, imaginary time; one 1d line, "
                                        "launch-latency bound", **sres} if sres else None),
+            "strang": ({"workload": "the headline workload with the Strang splitting N(dt/2), sweeps, N(dt/2) "
+                                    "(imaginary time, renormalised after the closing half); accuracy: 64^3 real time "
+                                    "to t=0.1 against a dt=6.25e-5 Strang run, FP64",
+                        **stres} if stres else None),
             "batched": ({"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
                                     "(SplitMix64 seed 1712), dx=0.1, dt=5e-4, g~U[0,50], nu=1, kappa~U[1,2], "
                                     "g=0 trap ground state quenched; one launch per sweep and segment class, "
@@ -659,6 +720,7 @@ def main():
         args.no_adjoint = args.only != "adjoint"
         args.no_batched = args.only != "batched"
         args.no_spherical = args.only != "spherical"
+        args.no_strang = args.only != "strang"
         args.no_headline = args.only != "headline"
         if args.only != "headline":
             args.no_cpu_baseline = True

@@ -132,6 +132,19 @@ int gp_set_g(gp_handle* h, double g);
 /* Changes the time step and recomputes the elimination coefficients. */
 int gp_set_dt(gp_handle* h, double dt);
 
+/* Chooses the splitting of one step ("Solution method": the step is split
+ * into the sub-step N -- potential and nonlinear term -- and one
+ * Crank-Nicolson sweep per axis).  strang = 0 (the default, as in the
+ * paper's programs): N with dt, then the sweeps (first order in dt).
+ * strang = 1: N with dt/2, the sweeps with dt, N with dt/2 on the sweeps'
+ * output (second order in dt); imaginary time renormalises after the second
+ * half, as after N and the sweeps in the Lie form.  Costs one extra pass over
+ * the state per step.  Takes effect for the next step; the adjoint
+ * (gp_adjoint_forward/backward) and the batched runs (gp_batch_*) take the
+ * Lie splitting only.  Errors: GP_ERR_INVALID for a NULL handle or a value
+ * other than 0 or 1; GP_ERR_CUDA if the dt/2 tables cannot be allocated. */
+int gp_set_splitting(gp_handle* h, int strang);
+
 /* Runs nsteps >= 0 imaginary-time steps, renormalising after each one.
  * Asynchronous: enqueued on the handle's stream. */
 int gp_step_imag(gp_handle* h, long nsteps);

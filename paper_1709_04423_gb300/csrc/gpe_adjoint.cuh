@@ -49,15 +49,18 @@ __global__ void __launch_bounds__(256) adjoint_phase_kernel(AdjPhaseArgs<T> A) {
     }
     const T dens = p.x * p.x + p.y * p.y;
     const T th = A.dt * (Vq + A.g * dens);
-    T sn, cs;
-    sincos(th, &sn, &cs);
-    const c2_t<T> u = mk<T>(cs * p.x + sn * p.y, cs * p.y - sn * p.x);  // exp(-i th) p
+    // rotations in the forward's form (rot_neg): cos th = 1 + cm1, cm1 = -2 sin^2(th/2)
+    T sh, ch;
+    sincos(T(0.5) * th, &sh, &ch);
+    const T sn = T(2) * (sh * ch), cm1 = T(-2) * (sh * sh);
+    const c2_t<T> u = rot_neg<T>(p, th);                                // exp(-i th) p
     const T s = l.x * u.y - l.y * u.x;                                  // Im(conj(lam) u)
     const T ds = A.dt * s;
     A.dJdV[q] += (double)ds;
     gacc += ds * dens;
     const T c2g = T(2) * A.g * ds;
-    l = mk<T>(cs * l.x - sn * l.y + c2g * p.x, cs * l.y + sn * l.x + c2g * p.y);  // exp(i th) lam + 2 g dt s p
+    // exp(i th) lam + 2 g dt s p
+    l = mk<T>((l.x + fma(cm1, l.x, -(sn * l.y))) + c2g * p.x, (l.y + fma(cm1, l.y, sn * l.x)) + c2g * p.y);
     A.lam[q] = l;
   }
   double v[1] = {(double)gacc}, tot[1];  // FP64 from the per-thread sums on

@@ -300,9 +300,12 @@ int upload_tf(gp_handle* h, void* dst, const std::vector<cd>& v) {
 }
 }  // namespace
 
-// Per-axis potential factors of the sub-step N for the current dt (absent
-// axes: a single factor 1); and, with a user potential, the per-point ones.
-int upload_factors(gp_handle* h) {
+// Per-axis potential factors of the sub-step N for the time step dt_eff
+// (absent axes: a single factor 1) into fac[mode][axis] (and, for the
+// double-float state, their triple-float images per x index and per x line);
+// with a user potential, the per-point ones.
+static int upload_factor_set(gp_handle* h, double dt_eff, void* (&fac)[2][3], void* (&tfx)[2], void* (&tfyz)[2],
+                             void* (&fV)[2], void* (&tfV)[2]) {
   std::vector<cd> per_axis[2][3];
   for (int d = 0; d < 3; ++d) {
     const int nd = axis_len(h, d);
@@ -311,13 +314,13 @@ int upload_factors(gp_handle* h) {
       for (int i = 0; i < nd; ++i) {
         const double x = h->geom == 1 ? i * h->dx[d] : -0.5 * nd * h->dx[d] + i * h->dx[d];
         const double v = 0.5 * h->nkl[d] * h->nkl[d] * x * x;
-        fr[i] = cd(std::cos(h->dt * v), -std::sin(h->dt * v));
-        fi[i] = cd(std::exp(-h->dt * v), 0.0);
+        fr[i] = cd(std::cos(dt_eff * v), -std::sin(dt_eff * v));
+        fi[i] = cd(std::exp(-dt_eff * v), 0.0);
       }
     const bool f64 = h->prec != GP_F32;  // the double-float form keeps FP64 factors too
-    int rc = f64 ? upload_c2<double>(h, h->fac[0][d], fr) : upload_c2<float>(h, h->fac[0][d], fr);
+    int rc = f64 ? upload_c2<double>(h, fac[0][d], fr) : upload_c2<float>(h, fac[0][d], fr);
     if (rc) return rc;
-    rc = f64 ? upload_c2<double>(h, h->fac[1][d], fi) : upload_c2<float>(h, h->fac[1][d], fi);
+    rc = f64 ? upload_c2<double>(h, fac[1][d], fi) : upload_c2<float>(h, fac[1][d], fi);
     if (rc) return rc;
     per_axis[0][d] = fr;
     per_axis[1][d] = fi;
@@ -328,16 +331,43 @@ int upload_factors(gp_handle* h) {
       std::vector<cd> yz((size_t)ny * nz);
       for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j) yz[(size_t)k * ny + j] = per_axis[m][1][j] * per_axis[m][2][k];
-      int rc = upload_tf(h, h->tfx[m], per_axis[m][0]);
+      int rc = upload_tf(h, tfx[m], per_axis[m][0]);
       if (rc) return rc;
-      if ((rc = upload_tf(h, h->tfyz[m], yz))) return rc;
+      if ((rc = upload_tf(h, tfyz[m], yz))) return rc;
     }
   }
   if (h->Vd) {
-    potential_factors(h);
+    potential_factors(h, dt_eff, fV, tfV);
     GP_CUDA(cudaGetLastError());
   }
   return GP_OK;
+}
+
+// The buffers of the dt/2 factors of the Strang splitting (those not yet there).
+static int ensure_half_tables(gp_handle* h) {
+  int rc = GP_OK;
+  for (int m = 0; m < 2; ++m) {
+    for (int d = 0; d < 3; ++d)
+      if (!h->fac_h[m][d] && (rc = dev_alloc(h, &h->fac_h[m][d], (size_t)axis_len(h, d) * h->esize))) return rc;
+    if (h->prec == GP_DF64) {
+      const long nyz = (long)axis_len(h, 1) * axis_len(h, 2);
+      if (!h->tfx_h[m] && (rc = dev_alloc(h, &h->tfx_h[m], (size_t)h->n[0] * sizeof(tf3c)))) return rc;
+      if (!h->tfyz_h[m] && (rc = dev_alloc(h, &h->tfyz_h[m], (size_t)nyz * sizeof(tf3c)))) return rc;
+    }
+    if (h->Vbuf) {
+      if (!h->fV_h[m] && (rc = dev_alloc(h, &h->fV_h[m], (size_t)h->np * h->esize))) return rc;
+      if (h->prec == GP_DF64 && !h->tfV_h[m] && (rc = dev_alloc(h, &h->tfV_h[m], (size_t)h->np * sizeof(tf3c))))
+        return rc;
+    }
+  }
+  return rc;
+}
+
+// The factors for dt and, with the Strang splitting, for dt/2.
+int upload_factors(gp_handle* h) {
+  int rc = upload_factor_set(h, h->dt, h->fac, h->tfx, h->tfyz, h->fV, h->tfV);
+  if (!rc && h->strang) rc = upload_factor_set(h, 0.5 * h->dt, h->fac_h, h->tfx_h, h->tfyz_h, h->fV_h, h->tfV_h);
+  return rc;
 }
 
 }  // namespace gpe
@@ -597,9 +627,27 @@ int gp_set_potential(gp_handle* h, const double* V, int on_device) {
     to_float(h, h->Vbuf32, h->Vbuf, h->np);
     h->Vt = h->Vbuf32;
   }
-  potential_factors(h);
+  potential_factors(h, h->dt, h->fV, h->tfV);
+  if (h->strang) {
+    if ((rc = ensure_half_tables(h))) return rc;
+    potential_factors(h, 0.5 * h->dt, h->fV_h, h->tfV_h);
+  }
   GP_CUDA(cudaGetLastError());
   if (!on_device) GP_CUDA(cudaStreamSynchronize(h->work));
+  return join_out(h);
+}
+
+int gp_set_splitting(gp_handle* h, int strang) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_set_splitting: NULL handle");
+  if (strang != 0 && strang != 1) return fail(GP_ERR_INVALID, "gp_set_splitting: splitting must be 0 (Lie) or 1 (Strang)");
+  if ((strang != 0) == h->strang) return GP_OK;
+  int rc = join_in(h);
+  if (rc) return rc;
+  drop_graphs(h);
+  if (strang && (rc = ensure_half_tables(h))) return rc;
+  h->strang = strang != 0;
+  if (h->strang && (rc = upload_factor_set(h, 0.5 * h->dt, h->fac_h, h->tfx_h, h->tfyz_h, h->fV_h, h->tfV_h)))
+    return rc;
   return join_out(h);
 }
 
@@ -671,6 +719,7 @@ int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every) {
   if (h->prec == GP_DF64)
     return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint takes GP_F64 or GP_F32 states");
   if (h->geom != 0) return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint is for Cartesian grids");
+  if (h->strang) return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint is for the Lie splitting");
   const int K = (int)std::min<long>(ckpt_every, nsteps);
   const long nck = (nsteps + K - 1) / K;
   int rc;
@@ -699,6 +748,7 @@ int gp_adjoint_backward(gp_handle* h, const void* lambda_T, int lambda_on_device
                         double* dJdg, void* lambda_0) {
   if (!h || !lambda_T) return fail(GP_ERR_INVALID, "gp_adjoint_backward: NULL argument");
   if (h->adj_nsteps < 1) return fail(GP_ERR_STATE, "gp_adjoint_backward: no gp_adjoint_forward recorded");
+  if (h->strang) return fail(GP_ERR_STATE, "gp_adjoint_backward: the splitting was changed to Strang after the forward run");
   if (h->dt != h->adj_dt || h->pot_version != h->adj_pot_version)
     return fail(GP_ERR_STATE, "gp_adjoint_backward: dt or the potential changed since gp_adjoint_forward");
   int rc = join_in(h);

@@ -28,6 +28,20 @@ template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T>
   else return mk<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 
+// exp(-i th) p (FP32 and FP64 states), as p + ((c - 1) p + s (p.y, -p.x))
+// with c - 1 = -2 sin^2(th/2) and s = 2 sin(th/2) cos(th/2).  The rounded
+// pair (1 + (c - 1), s) has modulus 1 + O(th^2 eps); a rounded cos(th) next
+// to 1 would instead carry an error of up to half an ulp of 1 in the
+// modulus, the same at a point step after step (th changes slowly), so that
+// |phi| would drift linearly with the number of steps.  What remains is the
+// rounding of the final sums, which is unbiased.
+template <typename T> __device__ __forceinline__ c2_t<T> rot_neg(c2_t<T> p, T th) {
+  T sh, ch;
+  sincos(T(0.5) * th, &sh, &ch);
+  const T s = T(2) * (sh * ch), cm1 = T(-2) * (sh * sh);
+  return mk<T>(p.x + fma(cm1, p.x, s * p.y), p.y + fma(cm1, p.y, -(s * p.x)));
+}
+
 // Geometry of the lines of one sweep.  Line L of axis 0 starts at L*nx
 // (L = j + ny*k); of axis 1 at (L % nx) + (L / nx)*nx*ny (L = i + nx*k); of
 // axis 2 at L (L = i + nx*j).  Consecutive L of axes 1 and 2 are

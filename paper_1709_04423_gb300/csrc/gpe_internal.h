@@ -119,6 +119,13 @@ struct gp_handle {
   // 0: Cartesian; 1: spherically symmetric 3d trap solved for u = sqrt(4 pi) r phi
   // on r_i = i dr (1d), whose nonlinear term carries gw[i] = 1/(4 pi r_i^2)
   int geom = 0;
+  // Strang splitting (N/2, sweeps, N/2): the factors for dt/2
+  bool strang = false;
+  void* fac_h[2][3] = {{nullptr}};
+  void* fV_h[2] = {nullptr, nullptr};
+  void* tfx_h[2] = {nullptr, nullptr};
+  void* tfyz_h[2] = {nullptr, nullptr};
+  void* tfV_h[2] = {nullptr, nullptr};
   void* gw_t = nullptr;      // gw in the state precision (sweeps' sub-step N)
   void* gw_o = nullptr;      // gw in the observables' arithmetic type
   double* series_buf = nullptr;  // gp_step_series: raw sums (8 per record) + host-bound records
@@ -186,7 +193,8 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out);
 int run_observables_f32(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
 int run_observables_f64(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
 void to_float(gp_handle* h, float* dst, const double* src, long n);
-void potential_factors(gp_handle* h);  // fV from the FP64 potential (state precision)
+// per-point factors of the FP64 potential for the step dt_eff (state precision; double-float: + triple-float)
+void potential_factors(gp_handle* h, double dt_eff, void* const (&fV)[2], void* const (&tfV)[2]);
 int adjoint_forward_f32(gp_handle* h, long nsteps, int K);
 int adjoint_forward_f64(gp_handle* h, long nsteps, int K);
 int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev);

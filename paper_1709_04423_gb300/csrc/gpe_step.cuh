@@ -176,12 +176,41 @@ struct NormSlots {
   int rd = -1, wr = -1;
 };
 
+// The sub-step N fields of the sweep arguments: step dt, or dt/2 for the
+// halves of the Strang splitting.
+template <typename T, typename A>
+void set_phase_args(const gp_handle* h, bool imag, bool half, A& a) {
+  const int fm = imag ? 1 : 0;
+  const double dt = half ? 0.5 * h->dt : h->dt;
+  void* const* fac = half ? h->fac_h[fm] : h->fac[fm];
+  if constexpr (std::is_same<A, Sweep2Args<T>>::value) {
+    a.fV = h->Vd ? (const c2_t<T>*)(half ? h->fV_h : h->fV)[fm] : nullptr;
+    a.fx = (const c2_t<T>*)fac[0];
+    a.fy = (const c2_t<T>*)fac[1];
+    a.fz = (const c2_t<T>*)fac[2];
+    a.dtg = (T)(dt * h->g);
+    if constexpr (is_df<T>::value) {
+      a.tfV = h->Vd ? (const tf3c*)(half ? h->tfV_h : h->tfV)[fm] : nullptr;
+      a.tfx = (const tf3c*)(half ? h->tfx_h : h->tfx)[fm];
+      a.tfyz = (const tf3c*)(half ? h->tfyz_h : h->tfyz)[fm];
+    }
+  }
+  a.V = (const T*)h->Vt;
+  a.vx = (const T*)h->vt[0];
+  a.vy = (const T*)h->vt[1];
+  a.vz = (const T*)h->vt[2];
+  a.dt = (T)dt;
+  a.g = (T)h->g;
+  a.gw = (const T*)h->gw_t;
+}
+
 template <typename T>
 void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr) {
   const bool first = d == 0, last = d == h->dim - 1;
   const int mode = imag ? MODE_IMAG : MODE_REAL;
   const int seg = d == 0 ? h->seg_x : h->seg_c;
-  const bool read = imag && first && ns.rd >= 0, write = imag && last;
+  // with the Strang splitting the norm is taken after the closing N(dt/2)
+  const bool read = imag && first && ns.rd >= 0, write = imag && last && !h->strang;
   const double* parts_in = read ? h->parts[ns.rd] : nullptr;
   double* parts_out = write ? h->parts[ns.wr] : nullptr;
   unsigned blocks = 0;
@@ -196,24 +225,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
-    const int fm = imag ? 1 : 0;
-    a.fV = h->Vd ? (const c2_t<T>*)h->fV[fm] : nullptr;
-    a.fx = (const c2_t<T>*)h->fac[fm][0];
-    a.fy = (const c2_t<T>*)h->fac[fm][1];
-    a.fz = (const c2_t<T>*)h->fac[fm][2];
-    a.dtg = (T)(h->dt * h->g);
-    a.V = (const T*)h->Vt;
-    a.vx = (const T*)h->vt[0];
-    a.vy = (const T*)h->vt[1];
-    a.vz = (const T*)h->vt[2];
-    a.dt = (T)h->dt;
-    a.g = (T)h->g;
-    a.gw = (const T*)h->gw_t;
-    if constexpr (is_df<T>::value) {
-      a.tfV = h->Vd ? (const tf3c*)h->tfV[fm] : nullptr;
-      a.tfx = (const tf3c*)h->tfx[fm];
-      a.tfyz = (const tf3c*)h->tfyz[fm];
-    }
+    set_phase_args<T>(h, imag, h->strang, a);
     a.parts_in = parts_in;
     a.nparts_in = h->parts_n;
     a.parts_wscale = h->parts_ws;
@@ -225,7 +237,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
       if (d == 0 && h->tile_x && h->pipe_x) {
         if (imag) {
-          blocks = last ? launch_p_seg<T, true, true, true, true>(seg, a, h->work, h->pdl_now)
+          blocks = write ? launch_p_seg<T, true, true, true, true>(seg, a, h->work, h->pdl_now)
                         : launch_p_seg<T, true, true, false, true>(seg, a, h->work, h->pdl_now);
         } else {
           blocks = launch_p_seg<T, false, true, false, true>(seg, a, h->work, h->pdl_now);
@@ -233,7 +245,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
         done = true;
       } else if (d > 0 && h->pipe_c) {
         if (imag) {
-          blocks = last ? launch_p_seg<T, true, false, true, false>(seg, a, h->work, h->pdl_now)
+          blocks = write ? launch_p_seg<T, true, false, true, false>(seg, a, h->work, h->pdl_now)
                         : launch_p_seg<T, true, false, false, false>(seg, a, h->work, h->pdl_now);
         } else {
           blocks = launch_p_seg<T, false, false, false, false>(seg, a, h->work, h->pdl_now);
@@ -244,21 +256,21 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     if (done) {
     } else if (d == 0 && h->tile_x) {
       if (imag) {
-        blocks = last ? launch_t_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
+        blocks = write ? launch_t_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
                       : launch_t_seg<T, true, true, false>(seg, a, h->work, h->pdl_now);
       } else {
         blocks = launch_t_seg<T, false, true, false>(seg, a, h->work, h->pdl_now);
       }
     } else if (d == 0) {
       if (imag) {
-        blocks = last ? launch_x_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
+        blocks = write ? launch_x_seg<T, true, true, true>(seg, a, h->work, h->pdl_now)
                       : launch_x_seg<T, true, true, false>(seg, a, h->work, h->pdl_now);
       } else {
         blocks = launch_x_seg<T, false, true, false>(seg, a, h->work, h->pdl_now);
       }
     } else {
       if (imag) {
-        blocks = last ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work, h->pdl_now)
+        blocks = write ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work, h->pdl_now)
                       : launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work, h->pdl_now);
       } else {
         blocks = launch_c_seg<T, false, false>(seg, h->keep_c, a, h->work, h->pdl_now);
@@ -280,13 +292,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   a.m = (const c2_t<T>*)h->cm[imag][d];
   a.cp = (const c2_t<T>*)h->ccp[imag][d];
   a.beta = (T)(h->dt / (4.0 * h->dx[d] * h->dx[d]));
-  a.V = (const T*)h->Vt;
-  a.vx = (const T*)h->vt[0];
-  a.vy = (const T*)h->vt[1];
-  a.vz = (const T*)h->vt[2];
-  a.dt = (T)h->dt;
-  a.g = (T)h->g;
-  a.gw = (const T*)h->gw_t;
+  set_phase_args<T>(h, imag, h->strang, a);
   a.parts_in = parts_in;
   a.nparts_in = h->parts_n;
   a.parts_wscale = h->parts_ws;
@@ -295,9 +301,9 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   a.w_b = d == 2 ? h->wd[1] : h->wd[2];
   a.parts_out = parts_out;
   if (imag) {
-    if (first && last) blocks = launch_legacy<T, true, true, true>(a, h->work);
+    if (first && write) blocks = launch_legacy<T, true, true, true>(a, h->work);
     else if (first) blocks = launch_legacy<T, true, true, false>(a, h->work);
-    else if (last) blocks = launch_legacy<T, true, false, true>(a, h->work);
+    else if (write) blocks = launch_legacy<T, true, false, true>(a, h->work);
     else blocks = launch_legacy<T, true, false, false>(a, h->work);
   } else {
     if (first) blocks = launch_legacy<T, false, true, false>(a, h->work);
@@ -310,6 +316,31 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   }
 }
 
+// The closing N(dt/2) of a Strang step (and, imaginary time, the norm sums of
+// its result into slot ns.wr).
+template <typename T>
+void enqueue_strang_close(gp_handle* h, bool imag, NormSlots ns) {
+  Sweep2Args<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.psi = (c2_t<T>*)h->psi;
+  a.geom = geom_of(h, 0);
+  set_phase_args<T>(h, imag, true, a);
+  a.w_axis = (const T*)h->wt[0];
+  a.w_a = (const T*)h->wt[1];
+  a.w_b = (const T*)h->wt[2];
+  const long chunks = (long)((a.geom.nx + 31) / 32) * a.geom.nlines;
+  const unsigned blocks = (unsigned)std::min<long>((chunks + 7) / 8, 152L * 8);
+  if (imag) {
+    a.parts_out = h->parts[ns.wr];
+    launch_k(h->pdl_now, strang_phase_kernel<T, true, true>, dim3(blocks), dim3(256), 0, h->work, a);
+    h->parts_n = (int)blocks;
+    h->parts_ws = h->wscale;
+  } else {
+    launch_k(h->pdl_now, strang_phase_kernel<T, false, false>, dim3(blocks), dim3(256), 0, h->work, a);
+  }
+  count_launch();
+}
+
 // One step; with src != nullptr the x sweep reads the step's input from src
 // (segmented kernels only) and every sweep writes h->psi.
 template <typename T>
@@ -319,6 +350,7 @@ void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullp
     enqueue_sweep<T>(h, imag, ns, d, src);
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
+  if (h->strang) enqueue_strang_close<T>(h, imag, ns);
 }
 
 inline NormSlots slots_of_step(bool imag, long t) {
@@ -375,7 +407,7 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
     }
     for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
       GP_CUDA(cudaGraphLaunch(ge, h->work));
-      count_launch((unsigned long long)kGraphSteps * h->dim);
+      count_launch((unsigned long long)kGraphSteps * (h->dim + (h->strang ? 1 : 0)));
     }
   }
   for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t));

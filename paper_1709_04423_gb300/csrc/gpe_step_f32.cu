@@ -22,17 +22,17 @@ int adjoint_backward_f32(gp_handle* h, double* dJdV_dev, void* lam0_dev) {
 }  // namespace gpe
 
 namespace gpe {
-void potential_factors(gp_handle* h) {
+void potential_factors(gp_handle* h, double dt_eff, void* const (&fV)[2], void* const (&tfV)[2]) {
   const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
   if (h->prec != GP_F32)
-    potential_factor_kernel<double><<<blocks, 256, 0, h->work>>>((double2*)h->fV[0], (double2*)h->fV[1], h->Vbuf,
-                                                                h->dt, h->np);
+    potential_factor_kernel<double><<<blocks, 256, 0, h->work>>>((double2*)fV[0], (double2*)fV[1], h->Vbuf,
+                                                                dt_eff, h->np);
   else
-    potential_factor_kernel<float><<<blocks, 256, 0, h->work>>>((float2*)h->fV[0], (float2*)h->fV[1], h->Vbuf,
-                                                               h->dt, h->np);
+    potential_factor_kernel<float><<<blocks, 256, 0, h->work>>>((float2*)fV[0], (float2*)fV[1], h->Vbuf,
+                                                               dt_eff, h->np);
   count_launch();
   if (h->prec == GP_DF64)  // exact triple-float images for the double-float sweeps
-    for (int m = 0; m < 2; ++m) tf_from_c128(h, h->tfV[m], h->fV[m], h->np);
+    for (int m = 0; m < 2; ++m) tf_from_c128(h, tfV[m], fV[m], h->np);
 }
 
 void to_float(gp_handle* h, float* dst, const double* src, long n) {

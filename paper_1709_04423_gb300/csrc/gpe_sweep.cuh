@@ -61,10 +61,7 @@ __device__ __forceinline__ c2_t<T> apply_N(c2_t<T> p, T V, T dt, T g) {
     T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
   } else {
-    T s, c;
-    sincos(th, &s, &c);
-    // exp(-i th) p
-    return mk<T>(c * p.x + s * p.y, c * p.y - s * p.x);
+    return rot_neg<T>(p, th);
   }
 }
 

@@ -133,11 +133,13 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
 }
 
 // FP32 state: p <- exp(-i th) p or exp(-th) p with th = dt (V + g |p|^2)
-// formed per point (library sincos / exp of the state precision).  (Applying
-// the factor as p + (factor - 1) p with expm1 was measured to move the FP32
-// ground state's mu further from FP64: the FP32 iteration stops at an exact
-// fixed point of the rounded map, whose mu depends on how each sub-step
-// rounds, and that form stops 1.3e-6 away against 8e-9 for the product.)
+// formed per point (library sincos / exp of the state precision).  Real time
+// rotates with rot_neg, whose rounded rotation keeps |p| unbiased.
+// (Imaginary time keeps the product form: applying the factor as
+// p + (factor - 1) p with expm1 was measured to move the FP32 ground state's
+// mu further from FP64 -- the FP32 iteration stops at an exact fixed point of
+// the rounded map, whose mu depends on how each sub-step rounds, and that
+// form stops 1.3e-6 away against 8e-9 for the product.)
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
   const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
@@ -145,9 +147,7 @@ __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
     const T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
   }
-  T s, c;
-  sincos(th, &s, &c);
-  return mk<T>(c * p.x + s * p.y, c * p.y - s * p.x);
+  return rot_neg<T>(p, th);
 }
 
 // Double-float state: p <- exp(-i a) p (real time) or exp(-a) p (imaginary
@@ -895,6 +895,46 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
   }
   cp_async_wait<0>();
   finish_norm<T, LAST>(tval, A.parts_out);
+}
+
+// ------------------------------------------------------- closing N of Strang
+// The symmetric splitting's second half sub-step N(dt/2), on the output of
+// the last sweep, with the Simpson-weighted norm of its result (imaginary
+// time, LAST) left per block as the sweeps' LAST does.  A's sub-step fields
+// hold the dt/2 factors and dtg = dt g/2 (FP32: dt/2); w_axis, w_a, w_b are
+// the Simpson coefficients of x, y and z.  One warp takes 32 consecutive points
+// of one x line at a time (coalesced), grid-stride over all such chunks.
+template <typename T, bool IMAG, bool LAST>
+__global__ void __launch_bounds__(256) strang_phase_kernel(Sweep2Args<T> A) {
+  using c2 = c2_t<T>;
+  const LineGeom& G = A.geom;
+  pdl_wait();
+  pdl_release();
+  const int lane = threadIdx.x & 31;
+  const long cpl = (G.nx + 31) >> 5;  // chunks per x line
+  const long nchunks = cpl * G.nlines;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  constexpr bool kFactors = std::is_same<T, double>::value;
+  T tacc = T(0);
+  for (long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < nchunks; u += nwarps) {
+    const long L = u / cpl;
+    const int i = (int)(u - L * cpl) * 32 + lane;
+    if (i >= G.nx) continue;
+    const int j = (int)(L % G.ny), k = (int)(L / G.ny);
+    const long q = L * G.nx + i;
+    c2 v = A.psi[q];
+    if constexpr (is_df<T>::value) {
+      v = phase_df<IMAG>(v, A, q, i, (int)L, A.gw ? A.dtg * A.gw[i] : A.dtg);
+    } else if constexpr (kFactors) {
+      const c2 F = A.fV ? A.fV[q] : fac_mul<T, IMAG>(A.fx[i], fac_mul<T, IMAG>(A.fy[j], A.fz[k]));
+      v = phase_N<T, IMAG>(v, F, A.gw ? A.dtg * A.gw[i] : A.dtg);
+    } else {
+      v = phase_direct<T, IMAG>(v, A.V ? A.V[q] : A.vx[i] + (A.vy[j] + A.vz[k]), A.dt, A.gw ? A.g * A.gw[i] : A.g);
+    }
+    A.psi[q] = v;
+    if (LAST) tacc += (A.w_axis[i] * (A.w_a[j] * A.w_b[k])) * (v.x * v.x + v.y * v.y);
+  }
+  finish_norm<T, LAST>(tacc, A.parts_out);
 }
 
 }  // namespace gpe

@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
-    "gp_init_spherical",
+    "gp_init_spherical", "gp_set_splitting",
 )
 
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
     lib.gp_set_potential.argtypes = [_vp, _vp, I]
     lib.gp_set_g.argtypes = [_vp, D]
     lib.gp_set_dt.argtypes = [_vp, D]
+    lib.gp_set_splitting.argtypes = [_vp, I]
     lib.gp_step_imag.argtypes = [_vp, L]
     lib.gp_step_real.argtypes = [_vp, L]
     lib.gp_observables.argtypes = [_vp, ctypes.POINTER(GpObs), _vp, I]
@@ -160,6 +161,10 @@ def gp_set_g(h, g):
 
 def gp_set_dt(h, dt):
     return _check(load().gp_set_dt(h, float(dt)))
+
+
+def gp_set_splitting(h, strang):
+    return _check(load().gp_set_splitting(h, int(strang)))
 
 
 def gp_step_imag(h, nsteps):
@@ -379,6 +384,13 @@ class Propagator:
 
     def set_dt(self, dt):
         gp_set_dt(self.h, dt)
+
+    def set_splitting(self, splitting):
+        """``"lie"`` (N, then the sweeps; the default) or ``"strang"``
+        (N(dt/2), the sweeps, N(dt/2)); see gp_set_splitting."""
+        if splitting not in ("lie", "strang"):
+            raise ValueError("splitting must be 'lie' or 'strang'")
+        gp_set_splitting(self.h, 1 if splitting == "strang" else 0)
 
     def step_imag(self, nsteps):
         gp_step_imag(self.h, nsteps)
