@@ -204,8 +204,19 @@ void set_phase_args(const gp_handle* h, bool imag, bool half, A& a) {
   a.gw = (const T*)h->gw_t;
 }
 
+// How a step's sub-step N is split under the Strang splitting.  Imaginary-time
+// steps run N(dt/2), the sweeps, N(dt/2).  In a run of real-time steps the
+// closing half of one step and the opening half of the next make one N(dt)
+// (in real time N keeps |phi|, so the two halves compose exactly, up to
+// rounding), so the run is N(dt/2) and the sweeps, then N(dt) and the sweeps
+// per further step, then N(dt/2): the cost of the Lie steps plus one pass.
+struct StepForm {
+  bool half_open = true;  // the x sweep applies N(dt/2) (else N(dt))
+  bool close = true;      // N(dt/2) after the last sweep
+};
+
 template <typename T>
-void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr) {
+void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr, bool half_open = true) {
   const bool first = d == 0, last = d == h->dim - 1;
   const int mode = imag ? MODE_IMAG : MODE_REAL;
   const int seg = d == 0 ? h->seg_x : h->seg_c;
@@ -225,7 +236,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
-    set_phase_args<T>(h, imag, h->strang, a);
+    set_phase_args<T>(h, imag, h->strang && half_open, a);
     a.parts_in = parts_in;
     a.nparts_in = h->parts_n;
     a.parts_wscale = h->parts_ws;
@@ -292,7 +303,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   a.m = (const c2_t<T>*)h->cm[imag][d];
   a.cp = (const c2_t<T>*)h->ccp[imag][d];
   a.beta = (T)(h->dt / (4.0 * h->dx[d] * h->dx[d]));
-  set_phase_args<T>(h, imag, h->strang, a);
+  set_phase_args<T>(h, imag, h->strang && half_open, a);
   a.parts_in = parts_in;
   a.nparts_in = h->parts_n;
   a.parts_wscale = h->parts_ws;
@@ -329,7 +340,8 @@ void enqueue_strang_close(gp_handle* h, bool imag, NormSlots ns) {
   a.w_a = (const T*)h->wt[1];
   a.w_b = (const T*)h->wt[2];
   const long chunks = (long)((a.geom.nx + 31) / 32) * a.geom.nlines;
-  const unsigned blocks = (unsigned)std::min<long>((chunks + 7) / 8, 152L * 8);
+  const long per_block = 8L * kStrangUnroll;  // 8 warps
+  const unsigned blocks = (unsigned)std::min<long>((chunks + per_block - 1) / per_block, 152L * 8);
   if (imag) {
     a.parts_out = h->parts[ns.wr];
     launch_k(h->pdl_now, strang_phase_kernel<T, true, true>, dim3(blocks), dim3(256), 0, h->work, a);
@@ -344,13 +356,14 @@ void enqueue_strang_close(gp_handle* h, bool imag, NormSlots ns) {
 // One step; with src != nullptr the x sweep reads the step's input from src
 // (segmented kernels only) and every sweep writes h->psi.
 template <typename T>
-void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullptr, const void* src = nullptr) {
+void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullptr, const void* src = nullptr,
+                  StepForm f = StepForm{}) {
   for (int d = 0; d < h->dim; ++d) {
     if (ev) cudaEventRecord(ev[2 * d], h->work);
-    enqueue_sweep<T>(h, imag, ns, d, src);
+    enqueue_sweep<T>(h, imag, ns, d, src, f.half_open);
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
-  if (h->strang) enqueue_strang_close<T>(h, imag, ns);
+  if (h->strang && f.close) enqueue_strang_close<T>(h, imag, ns);
 }
 
 inline NormSlots slots_of_step(bool imag, long t) {
@@ -371,9 +384,10 @@ void enqueue_finish_imag(gp_handle* h, long nsteps) {
   count_launch();
 }
 
-// Step 0 eagerly (it has no pending factor), then blocks of kGraphSteps steps
-// replayed from one captured graph (a block starts at an odd step in
-// imaginary time, so its slot pattern is always the same), then the rest.
+// Step 0 eagerly (imaginary time: it has no pending factor; real-time Strang:
+// it opens with N(dt/2)), then blocks of kGraphSteps steps replayed from one
+// captured graph (a block starts at an odd step in imaginary time, so its
+// slot pattern is always the same), then the rest.
 template <typename T>
 int run_steps_t(gp_handle* h, bool imag, long nsteps) {
   if (nsteps == 0) return GP_OK;
@@ -387,15 +401,19 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
     explicit PdlScope(gp_handle* hh) : h(hh) { h->pdl_now = pdl_enabled() && h->prec != GP_F64; }
     ~PdlScope() { h->pdl_now = false; }
   } pdl_scope(h);
+  // real-time Strang: the halves between steps merged (StepForm)
+  const bool merged = h->strang && !imag;
+  const StepForm first_f{true, !merged}, next_f{!merged, !merged};
   long t = 0;
-  if (imag) enqueue_step<T>(h, true, slots_of_step(true, t++));
+  if (imag || merged) enqueue_step<T>(h, imag, slots_of_step(imag, t++), nullptr, nullptr, first_f);
   if (nsteps - t >= 2 * kGraphSteps) {
     cudaGraphExec_t& ge = h->graph[imag ? 1 : 0];
     if (!ge) {
       cudaGraph_t graph;
       GP_CUDA(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
       const unsigned long long before = g_launches.load();
-      for (int s = 0; s < kGraphSteps; ++s) enqueue_step<T>(h, imag, slots_of_step(imag, t + s));
+      for (int s = 0; s < kGraphSteps; ++s)
+        enqueue_step<T>(h, imag, slots_of_step(imag, t + s), nullptr, nullptr, next_f);
       g_launches.store(before);  // capturing launches nothing
       GP_CUDA(cudaStreamEndCapture(h->work, &graph));
       cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
@@ -407,10 +425,11 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
     }
     for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
       GP_CUDA(cudaGraphLaunch(ge, h->work));
-      count_launch((unsigned long long)kGraphSteps * (h->dim + (h->strang ? 1 : 0)));
+      count_launch((unsigned long long)kGraphSteps * (h->dim + (next_f.close && h->strang ? 1 : 0)));
     }
   }
-  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t));
+  for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t), nullptr, nullptr, next_f);
+  if (merged) enqueue_strang_close<T>(h, false, NormSlots{});
   if (imag) enqueue_finish_imag<T>(h, nsteps);
   GP_CUDA(cudaGetLastError());
   return join_out(h);

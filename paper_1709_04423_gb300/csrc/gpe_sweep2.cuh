@@ -902,8 +902,14 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
 // the last sweep, with the Simpson-weighted norm of its result (imaginary
 // time, LAST) left per block as the sweeps' LAST does.  A's sub-step fields
 // hold the dt/2 factors and dtg = dt g/2 (FP32: dt/2); w_axis, w_a, w_b are
-// the Simpson coefficients of x, y and z.  One warp takes 32 consecutive points
-// of one x line at a time (coalesced), grid-stride over all such chunks.
+// the Simpson coefficients of x, y and z.  A warp takes chunks of 32
+// consecutive points of one x line (coalesced), kStrangUnroll chunks at a
+// time with all their loads issued first (a read and a write per point:
+// enough bytes in flight per SM to stream at HBM rate); grid-stride over all
+// chunks.  The chunk count is below 2^26 (np < 2^31), so the index
+// arithmetic is 32-bit.
+constexpr int kStrangUnroll = 4;
+
 template <typename T, bool IMAG, bool LAST>
 __global__ void __launch_bounds__(256) strang_phase_kernel(Sweep2Args<T> A) {
   using c2 = c2_t<T>;
@@ -911,30 +917,44 @@ __global__ void __launch_bounds__(256) strang_phase_kernel(Sweep2Args<T> A) {
   pdl_wait();
   pdl_release();
   const int lane = threadIdx.x & 31;
-  const long cpl = (G.nx + 31) >> 5;  // chunks per x line
-  const long nchunks = cpl * G.nlines;
-  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const unsigned cpl = (unsigned)(G.nx + 31) >> 5;  // chunks per x line
+  const unsigned nchunks = cpl * (unsigned)G.nlines;
+  const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
   constexpr bool kFactors = std::is_same<T, double>::value;
   T tacc = T(0);
-  for (long u = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < nchunks; u += nwarps) {
-    const long L = u / cpl;
-    const int i = (int)(u - L * cpl) * 32 + lane;
-    if (i >= G.nx) continue;
-    const int j = (int)(L % G.ny), k = (int)(L / G.ny);
-    const long q = L * G.nx + i;
-    c2 v = A.psi[q];
-    if constexpr (is_df<T>::value) {
-      v = phase_df<IMAG>(v, A, q, i, (int)L, A.gw ? A.dtg * A.gw[i] : A.dtg);
-    } else if constexpr (kFactors) {
-      const c2 F = A.fV ? A.fV[q] : fac_mul<T, IMAG>(A.fx[i], fac_mul<T, IMAG>(A.fy[j], A.fz[k]));
-      v = phase_N<T, IMAG>(v, F, A.gw ? A.dtg * A.gw[i] : A.dtg);
-    } else {
-      v = phase_direct<T, IMAG>(v, A.V ? A.V[q] : A.vx[i] + (A.vy[j] + A.vz[k]), A.dt, A.gw ? A.g * A.gw[i] : A.g);
+  for (unsigned u0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kStrangUnroll; u0 < nchunks;
+       u0 += nwarps * kStrangUnroll) {
+    c2 v[kStrangUnroll];
+    long q[kStrangUnroll];
+    int ii[kStrangUnroll], ll[kStrangUnroll];
+    bool ok[kStrangUnroll];
+#pragma unroll
+    for (int r = 0; r < kStrangUnroll; ++r) {
+      const unsigned u = u0 + r, L = u / cpl;
+      ii[r] = (int)(u - L * cpl) * 32 + lane;
+      ll[r] = (int)L;
+      ok[r] = u < nchunks && ii[r] < G.nx;
+      q[r] = (long)L * G.nx + ii[r];
+      if (ok[r]) v[r] = A.psi[q[r]];
     }
-    A.psi[q] = v;
-    if (LAST) tacc += (A.w_axis[i] * (A.w_a[j] * A.w_b[k])) * (v.x * v.x + v.y * v.y);
+#pragma unroll
+    for (int r = 0; r < kStrangUnroll; ++r) {
+      if (!ok[r]) continue;
+      const int i = ii[r], L = ll[r], j = L % G.ny, k = L / G.ny;
+      c2 w = v[r];
+      if constexpr (is_df<T>::value) {
+        w = phase_df<IMAG>(w, A, q[r], i, L, A.gw ? A.dtg * A.gw[i] : A.dtg);
+      } else if constexpr (kFactors) {
+        const c2 F = A.fV ? A.fV[q[r]] : fac_mul<T, IMAG>(A.fx[i], fac_mul<T, IMAG>(A.fy[j], A.fz[k]));
+        w = phase_N<T, IMAG>(w, F, A.gw ? A.dtg * A.gw[i] : A.dtg);
+      } else {
+        w = phase_direct<T, IMAG>(w, A.V ? A.V[q[r]] : A.vx[i] + (A.vy[j] + A.vz[k]), A.dt,
+                                  A.gw ? A.g * A.gw[i] : A.g);
+      }
+      A.psi[q[r]] = w;
+      if (LAST) tacc += (A.w_axis[i] * (A.w_a[j] * A.w_b[k])) * (w.x * w.x + w.y * w.y);
+    }
   }
   finish_norm<T, LAST>(tacc, A.parts_out);
 }
-
 }  // namespace gpe

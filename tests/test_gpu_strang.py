@@ -199,3 +199,30 @@ def test_switching_back_and_rejections(G):
         a.set_splitting("yoshida")
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 2e-6), ("df64", 1e-13)])
+def test_real_time_halves_merged(G, prec, tol):
+    """A run of real-time Strang steps merges the closing half of each step
+    with the opening half of the next (one N(dt) between sweeps, N(dt/2) at
+    both ends): the same result as lone steps, up to rounding, with one launch
+    per sweep and a single closing launch."""
+    dim, n, dx, nkl = 3, [24, 20, 18], [0.35, 0.35, 0.35], [1.0, 1.2, 1.4]
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=12, noise=1e-3)
+    a = G.Propagator(dim, n, dx, 5e-4, nkl, 30.0, precision=prec)
+    b = G.Propagator(dim, n, dx, 5e-4, nkl, 30.0, precision=prec)
+    for p in (a, b):
+        p.set_splitting("strang")
+        p.set_state(phi0)
+    for _ in range(40):
+        a.step_real(1)
+    l0 = G.gp_kernel_launches()
+    b.step_real(40)
+    assert G.gp_kernel_launches() - l0 == 40 * dim + 1
+    sa = a.get_state(device=False).astype(np.complex128)
+    sb = b.get_state(device=False).astype(np.complex128)
+    assert rel_l2(sb, sa) <= tol
+    ref = O.run(O.Grid(dim, n, dx, 5e-4, nkl, 30.0, split=1), phi0, False, 40)
+    assert rel_l2(sb, ref) <= (1e-12 if prec != "f32" else 1e-5)
+    a.close()
+    b.close()
