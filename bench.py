@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     ap.add_argument("--no-spherical", action="store_true", help="skip the spherical-trap form")
     ap.add_argument("--no-strang", action="store_true", help="skip the Strang-splitting form")
+    ap.add_argument("--no-real", action="store_true", help="skip the real-state form")
     ap.add_argument("--forms", default="f64,f32,df64",
                     help="precision forms of the headline workload to time (the line needs f32; f64 for ratios)")
-    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical", "strang"],
+    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical", "strang", "real"],
                     help="time one form only (for profiling); the other forms are reported as null")
     args = ap.parse_args()
     if "f32" not in args.forms.split(","):
@@ -474,6 +475,50 @@ def run_ours(args):
             for prec in sres:
                 sres[prec]["mu_diff_vs_f64"] = abs(smu[prec]["mu"] - smu["f64"]["mu"])
 
+    # ---- real state (imaginary-time maps keep the real input real): the
+    # headline workload and loop with the state held as np real values;
+    # mu after the full job against the complex FP64 form's
+    rres = {}
+    if not args.no_real:
+        for prec in [f for f in forms_sel if f != "df64"]:
+            p = make(prec)
+            p.set_real_state(True)
+            p.autotune(imag=True, cache=False)   # shapes for the real state (untimed)
+            with torch.cuda.stream(stream):
+                p.step_imag(w["job_steps"])
+                rmu = p.observables()["mu"]
+                p.set_state(torch.tensor(phi0, device="cuda"))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    p.step_imag(args.inner)
+                    p.observables()
+                barrier()
+                l0 = gpe.gp_kernel_launches()
+                torch.cuda.nvtx.range_push(f"timed_real_{prec}")
+                with ClockSampler(local) as rclk:
+                    for s in range(args.steps):
+                        flush.fill_(float(s))
+                        ev[s][0].record(stream)
+                        p.step_imag(args.inner)
+                        p.observables()
+                        ev[s][1].record(stream)
+                    barrier()
+                torch.cuda.nvtx.range_pop()
+                launches = gpe.gp_kernel_launches() - l0
+            ms = [a.elapsed_time(b) for a, b in ev]
+            value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
+            kms = p.time_sweeps(True, 64)
+            p.close()
+            esz = 4 if prec == "f32" else 8
+            rres[prec] = {"value": value, "ms_per_step": 1e3 * total_s / args.steps, "gpu_launches": launches,
+                          "clocks": rclk.summary(), "kernel_ms": kms,
+                          "sweep_state_gbs": [2 * esz * np_ / (t * 1e-3) / 1e9 for t in kms],
+                          "mu_after_job": rmu,
+                          "mu_err_vs_complex_f64": abs(rmu - mu["f64"]["mu"]) if "f64" in mu else None,
+                          "speedup_vs_complex": (value / results[prec]["value"]) if prec in results else None}
+
     # ---- Strang splitting (N(dt/2), the sweeps, N(dt/2)) on the headline
     # workload, timed like the Lie step; and its accuracy: real-time runs of a
     # 64^3 grid (dx = 0.2, trap (1, 1.4, 1.8), g = 50) to t = 0.1 with dt =
@@ -586,7 +631,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
                               "batched": bres or None, "spherical": sres or None,
-                              "strang": stres or None}), flush=True)
+                              "strang": stres or None, "real": rres or None}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -697,6 +742,9 @@ def run_ours(args):
             "spherical": ({"workload": "spherically symmetric 3d trap as the radial problem for u = sqrt(4 pi) r phi: "
                                        "513 points on [0, 10.24], dt=1e-4, nu=1, g=100, imaginary time; one 1d line, "
                                        "launch-latency bound", **sres} if sres else None),
+            "real_state": ({"workload": "the headline workload (its input is real) with the state held as np real "
+                                        "values: imaginary-time maps keep it real; same loop, observables per step, "
+                                        "L2 flushed", **rres} if rres else None),
             "strang": ({"workload": "the headline grid (128^3, dt=1e-3, g=50) stepped with the Lie and the Strang "
                                     "splitting N(dt/2), sweeps, N(dt/2), imaginary time (renormalised after the "
                                     "closing half) and real time (halves between steps merged), no observables, L2 "
@@ -729,6 +777,7 @@ def main():
         args.no_batched = args.only != "batched"
         args.no_spherical = args.only != "spherical"
         args.no_strang = args.only != "strang"
+        args.no_real = args.only != "real"
         args.no_headline = args.only != "headline"
         if args.only != "headline":
             args.no_cpu_baseline = True

@@ -145,6 +145,29 @@ int gp_set_dt(gp_handle* h, double dt);
  * other than 0 or 1; GP_ERR_CUDA if the dt/2 tables cannot be allocated. */
 int gp_set_splitting(gp_handle* h, int strang);
 
+/* Holds the state as real numbers (real = 1) or as complex ones (real = 0,
+ * the default).  In imaginary time the Crank-Nicolson coefficients and the
+ * sub-step N are real ("Solution method"), so a state with zero imaginary
+ * parts stays real: a real state takes half the bytes and half the
+ * arithmetic per step and gives the complex path's real parts.  Takes
+ * GP_F64 or GP_F32 handles of 2d or 3d Cartesian grids with an even number
+ * of x points, at most 514 points per axis, the shared-memory x tile (its
+ * 36 nx + 512 complex values within 200 KB: FP64 nx <= 341; real = 1 moves
+ * the x sweep to the tile if another shape was chosen) and the Lie
+ * splitting; gp_set_shapes may not turn the tile off while the state is real.
+ * real = 1 converts the current state; it synchronises the stream and
+ * fails with GP_ERR_STATE (leaving the complex state) if an imaginary part
+ * is nonzero.  While real: gp_set_state still takes complex values, checks
+ * them the same way (and on GP_ERR_STATE leaves real mode with the state it
+ * was given), gp_get_state and the observables see the state with zero
+ * imaginary parts, and gp_step_real, gp_time_sweeps/gp_step_series in real
+ * time, gp_set_splitting(h, 1) and the adjoint return GP_ERR_STATE;
+ * gp_autotune (imaginary time) picks among the shapes a real state takes and
+ * keeps its result apart from the complex state's.  Errors: GP_ERR_INVALID for a NULL handle, a value other
+ * than 0 or 1, or a grid or precision it does not take; GP_ERR_CUDA if the
+ * real buffer (npoints values) cannot be allocated. */
+int gp_set_real_state(gp_handle* h, int real);
+
 /* Runs nsteps >= 0 imaginary-time steps, renormalising after each one.
  * Asynchronous: enqueued on the handle's stream. */
 int gp_step_imag(gp_handle* h, long nsteps);

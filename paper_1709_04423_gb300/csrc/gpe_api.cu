@@ -261,6 +261,7 @@ int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms) {
   return h->prec == GP_F64 ? time_steps_f64(h, imag, nsteps, ms) : time_steps_f32(h, imag, nsteps, ms);
 }
 int run_observables_any(gp_handle* h, double* dens_dev, double* sums_out) {
+  materialize_complex(h);
   if (h->prec == GP_DF64) return run_observables_df(h, dens_dev, sums_out);
   return h->prec == GP_F64 ? run_observables_f64(h, dens_dev, sums_out) : run_observables_f32(h, dens_dev, sums_out);
 }
@@ -566,6 +567,12 @@ int gp_set_state(gp_handle* h, const void* psi, int on_device) {
   } else {
     GP_CUDA(cudaMemcpyAsync(h->psi, psi, (size_t)h->np * h->esize,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->work));
+    if (h->real_mode && (rc = real_from_complex(h))) {
+      h->real_mode = false;  // the complex state just set stays
+      drop_graphs(h);
+      join_out(h);
+      return rc;
+    }
   }
   if (!on_device) GP_CUDA(cudaStreamSynchronize(h->work));
   return join_out(h);
@@ -581,6 +588,7 @@ int gp_get_state(gp_handle* h, void* psi, int on_device) {
     if (!on_device)
       GP_CUDA(cudaMemcpyAsync(psi, h->df_stage, (size_t)h->np * sizeof(double2), cudaMemcpyDeviceToHost, h->work));
   } else {
+    materialize_complex(h);  // a real state: its complex copy
     GP_CUDA(cudaMemcpyAsync(psi, h->psi, (size_t)h->np * h->esize,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->work));
   }
@@ -641,6 +649,7 @@ int gp_set_splitting(gp_handle* h, int strang) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_splitting: NULL handle");
   if (strang != 0 && strang != 1) return fail(GP_ERR_INVALID, "gp_set_splitting: splitting must be 0 (Lie) or 1 (Strang)");
   if ((strang != 0) == h->strang) return GP_OK;
+  if (strang && h->real_mode) return fail(GP_ERR_STATE, "gp_set_splitting: the Strang splitting takes the complex state");
   int rc = join_in(h);
   if (rc) return rc;
   drop_graphs(h);
@@ -681,12 +690,14 @@ int gp_step_imag(gp_handle* h, long nsteps) {
 int gp_step_real(gp_handle* h, long nsteps) {
   if (!h) return fail(GP_ERR_INVALID, "gp_step_real: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_step_real: nsteps < 0");
+  if (h->real_mode) return fail(GP_ERR_STATE, "gp_step_real: real-time steps need the complex state (gp_set_real_state(h, 0))");
   return run_steps_any(h, false, nsteps);
 }
 
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch) {
   if (!h || !ms_per_launch) return fail(GP_ERR_INVALID, "gp_time_sweeps: NULL argument");
   if (nsteps < 0 || nsteps > 4096) return fail(GP_ERR_INVALID, "gp_time_sweeps: nsteps must be in [0, 4096]");
+  if (h->real_mode && !imag) return fail(GP_ERR_STATE, "gp_time_sweeps: a real state takes imaginary-time steps only");
   return time_steps_any(h, imag != 0, nsteps, ms_per_launch);
 }
 
@@ -720,6 +731,7 @@ int gp_adjoint_forward(gp_handle* h, long nsteps, int ckpt_every) {
     return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint takes GP_F64 or GP_F32 states");
   if (h->geom != 0) return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint is for Cartesian grids");
   if (h->strang) return fail(GP_ERR_INVALID, "gp_adjoint_forward: the adjoint is for the Lie splitting");
+  if (h->real_mode) return fail(GP_ERR_STATE, "gp_adjoint_forward: the adjoint takes the complex state");
   const int K = (int)std::min<long>(ckpt_every, nsteps);
   const long nck = (nsteps + K - 1) / K;
   int rc;
@@ -794,9 +806,9 @@ bool shapes_valid(const gp_handle* h, int tile_x, int seg_x, int seg_c) {
 }
 
 struct TuneKey {
-  int dim, n0, n1, n2, prec, imag;
+  int dim, n0, n1, n2, prec, imag, real;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dim, n0, n1, n2, prec, imag) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.imag);
+    return std::tie(dim, n0, n1, n2, prec, imag, real) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.imag, o.real);
   }
 };
 std::map<TuneKey, std::array<int, 4>> g_tuned;  // process-wide results
@@ -807,6 +819,8 @@ std::mutex g_tune_mutex;
 int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
+  if (h->real_mode && (!tile_x || seg_x == 0 || seg_c == 0))
+    return fail(GP_ERR_STATE, "gp_set_shapes: a real state needs the x tile and segmented y/z sweeps");
   const bool px = (flags & GP_SHAPE_PIPE_X) != 0, pc = (flags & GP_SHAPE_PIPE_YZ) != 0;
   if ((px || pc) && h->prec == GP_DF64)
     return fail(GP_ERR_INVALID, "gp_set_shapes: the pipelined sweeps take GP_F64 or GP_F32 states");
@@ -839,7 +853,9 @@ int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* 
 int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   if (!h) return fail(GP_ERR_INVALID, "gp_autotune: NULL handle");
   if (nsteps < 1 || nsteps > 256) return fail(GP_ERR_INVALID, "gp_autotune: nsteps must be in [1, 256]");
-  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], h->prec, imag != 0};
+  if (h->real_mode && !imag) return fail(GP_ERR_STATE, "gp_autotune: a real state takes imaginary-time steps only");
+  const bool real = h->real_mode;  // tile x sweep, no pipelined shapes, the real buffer saved
+  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], h->prec, imag != 0, real ? 1 : 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
@@ -852,10 +868,10 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   for (int sg : {4, 8, 16, 32})
     if (shapes_valid(h, 1, sg, h->seg_c)) {
       xs.push_back({1, sg, 0});
-      if (h->prec != GP_DF64 && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
+      if (h->prec != GP_DF64 && !real && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
     }
   for (int sg : {1, 2, 4, 8, 16})
-    if (shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }
+    if (!real && shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }
   std::vector<std::array<int, 3>> cs;  // (seg, keep input in registers, pipelined)
   int nmax = 0;
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
@@ -864,15 +880,17 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
       if (shapes_valid(h, h->tile_x, h->seg_x, sg)) {
         if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1, 0});
         cs.push_back({sg, 0, 0});
-        if (h->prec != GP_DF64 && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
+        if (h->prec != GP_DF64 && !real && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
       }
   const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
   const bool keep_px = h->pipe_x, keep_pc = h->pipe_c;
   void* saved = nullptr;
-  GP_CUDA(cudaMalloc(&saved, (size_t)h->np * h->esize));
+  void* const state = real ? h->rpsi : h->psi;
+  const size_t sbytes = (size_t)h->np * (real ? h->esize / 2 : h->esize);
+  GP_CUDA(cudaMalloc(&saved, sbytes));
   int rc = join_in(h);
   if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(saved, h->psi, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
+    cudaError_t e = cudaMemcpyAsync(saved, state, sbytes, cudaMemcpyDeviceToDevice, h->work);
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
   auto time_shape = [&](int t, int sx, int px, int sc, int kc, int pc, double* ms3) -> int {
@@ -903,7 +921,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; }
   }
   if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(h->psi, saved, (size_t)h->np * h->esize, cudaMemcpyDeviceToDevice, h->work);
+    cudaError_t e = cudaMemcpyAsync(state, saved, sbytes, cudaMemcpyDeviceToDevice, h->work);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->work);
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -930,6 +948,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
 int gp_step_series(gp_handle* h, int imag, long nsteps, int every, double* out, int out_on_device) {
   if (!h || !out) return fail(GP_ERR_INVALID, "gp_step_series: NULL argument");
   if (nsteps < 0 || every < 1) return fail(GP_ERR_INVALID, "gp_step_series: need nsteps >= 0 and every >= 1");
+  if (h->real_mode && !imag) return fail(GP_ERR_STATE, "gp_step_series: a real state takes imaginary-time steps only");
   const long nrec = nsteps / every;
   int rc = join_in(h);
   if (rc) return rc;

@@ -119,6 +119,11 @@ struct gp_handle {
   // 0: Cartesian; 1: spherically symmetric 3d trap solved for u = sqrt(4 pi) r phi
   // on r_i = i dr (1d), whose nonlinear term carries gw[i] = 1/(4 pi r_i^2)
   int geom = 0;
+  // a real imaginary-time state (gp_set_real_state): np values of the state
+  // precision in rpsi; psi then serves as the complex staging copy
+  bool real_mode = false;
+  void* rpsi = nullptr;
+  int* real_flag = nullptr;  // device flag: a nonzero imaginary part was seen
   // Strang splitting (N/2, sweeps, N/2): the factors for dt/2
   bool strang = false;
   void* fac_h[2][3] = {{nullptr}};
@@ -185,6 +190,11 @@ int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out = nullpt
 // double-float state <-> complex128 (device buffers, on the library stream)
 void df_from_c128(gp_handle* h, const void* src);
 void df_to_c128(gp_handle* h, void* dst);
+// real imaginary-time state: its complex copy into psi (no-op for a complex
+// state); the real state from psi (synchronises; GP_ERR_STATE if an
+// imaginary part is nonzero)
+void materialize_complex(gp_handle* h);
+int real_from_complex(gp_handle* h);
 void tf_from_c128(gp_handle* h, void* dst, const void* src, long n);  // exact triple-float split
 int run_steps_f32(gp_handle* h, bool imag, long nsteps);
 int run_steps_f64(gp_handle* h, bool imag, long nsteps);

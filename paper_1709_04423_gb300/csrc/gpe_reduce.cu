@@ -133,6 +133,7 @@ extern "C" int gp_reduced_density(gp_handle* h, int keep_mask, double* out, int 
     h->red_cap = need;
   }
   double* dout = out_on_device ? out : h->red_parts + (size_t)G.nchunks * G.nout;
+  materialize_complex(h);  // a real state: its complex copy
   const void* psi = h->psi;
   if (h->prec == GP_DF64) {  // rounded to complex128 first
     df_to_c128(h, h->df_stage);

@@ -63,7 +63,7 @@ unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl)
 }
 
 // ---- segmented y/z sweep (registers, coefficients in shared memory)
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false>
 unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
@@ -71,52 +71,57 @@ unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
   static bool attr_set = false;  // static + dynamic shared memory can pass 48 KB
   if (!attr_set) {
-    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          64 * 1024);
     attr_set = true;
   }
-  launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP>, dim3(blocks), dim3(32 * nseg), smem, s, a);
+  launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
 // keep = 1: input segment in registers (only for short segments); 0: streamed
-template <typename T, bool IMAG, bool LAST>
+template <typename T, bool IMAG, bool LAST, bool RP = false>
 unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const bool k = keep && seg * (int)sizeof(T) <= 64;
   switch (seg) {
-    case 4: return k ? launch_c<T, IMAG, LAST, 4, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 4, false>(a, s, pdl);
-    case 8: return k ? launch_c<T, IMAG, LAST, 8, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 8, false>(a, s, pdl);
-    case 16: return k ? launch_c<T, IMAG, LAST, 16, true>(a, s, pdl) : launch_c<T, IMAG, LAST, 16, false>(a, s, pdl);
-    default: return launch_c<T, IMAG, LAST, 32, false>(a, s, pdl);
+    case 4:
+      return k ? launch_c<T, IMAG, LAST, 4, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 4, false, RP>(a, s, pdl);
+    case 8:
+      return k ? launch_c<T, IMAG, LAST, 8, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 8, false, RP>(a, s, pdl);
+    case 16:
+      return k ? launch_c<T, IMAG, LAST, 16, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 16, false, RP>(a, s, pdl);
+    default: return launch_c<T, IMAG, LAST, 32, false, RP>(a, s, pdl);
   }
 }
 
 // ---- shared-memory tile x sweep
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+// (RL: a.geom.nlines real lines, two per tile column)
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
 unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
-  const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
+  const long ncols = RL ? (a.geom.nlines + 1) / 2 : a.geom.nlines;
+  const unsigned blocks = (unsigned)((ncols + 31) / 32);
   const size_t smem = (size_t)a.geom.n * (kTilePitch + 3) * sizeof(c2_t<T>) + 512 * sizeof(c2_t<T>);
   static bool attr_set = false;  // one opt-in per instantiation
   if (!attr_set) {
-    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr_set = true;
   }
-  launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG>, dim3(blocks), dim3(32 * nseg), smem, s, a);
+  launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST>
+template <typename T, bool IMAG, bool FIRST, bool LAST, bool RL = false>
 unsigned launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 4: return launch_t<T, IMAG, FIRST, LAST, 4>(a, s, pdl);
-    case 8: return launch_t<T, IMAG, FIRST, LAST, 8>(a, s, pdl);
-    case 16: return launch_t<T, IMAG, FIRST, LAST, 16>(a, s, pdl);
-    default: return launch_t<T, IMAG, FIRST, LAST, 32>(a, s, pdl);
+    case 4: return launch_t<T, IMAG, FIRST, LAST, 4, RL>(a, s, pdl);
+    case 8: return launch_t<T, IMAG, FIRST, LAST, 8, RL>(a, s, pdl);
+    case 16: return launch_t<T, IMAG, FIRST, LAST, 16, RL>(a, s, pdl);
+    default: return launch_t<T, IMAG, FIRST, LAST, 32, RL>(a, s, pdl);
   }
 }
 
@@ -327,6 +332,54 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   }
 }
 
+// A real imaginary-time state (h->rpsi, np values of T; imaginary-time maps
+// keep a real state real): the x sweep packs two real lines per tile column,
+// the y/z sweeps view the array as complex with nx/2 points per row (x = 2i'
+// as re, 2i' + 1 as im).  Half the bytes and half the arithmetic of the
+// complex state, the same operations on the real parts.
+template <typename T>
+void enqueue_sweep_real(gp_handle* h, NormSlots ns, int d) {
+  if constexpr (!is_df<T>::value) {
+    const bool first = d == 0, last = d == h->dim - 1;
+    const int seg = d == 0 ? h->seg_x : h->seg_c;
+    const bool read = first && ns.rd >= 0, write = last;
+    Sweep2Args<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = (c2_t<T>*)h->rpsi;
+    LineGeom g = geom_of(h, d);
+    if (d > 0) {
+      g.nx /= 2;
+      g.stride = d == 1 ? g.nx : (long)g.nx * g.ny;
+      g.nlines = h->np / 2 / g.n;
+    }
+    a.geom = g;
+    const int si = seg_index(seg);
+    a.alpha = coef_ptr<T>(h, MODE_IMAG, d, 0);
+    a.gf = coef_ptr<T>(h, MODE_IMAG, d, 1 + 2 * si);
+    a.gb = coef_ptr<T>(h, MODE_IMAG, d, 2 + 2 * si);
+    a.ptab = (const c2_t<T>*)h->ctab[MODE_IMAG][d] + (size_t)si * 512;
+    set_phase_args<T>(h, true, false, a);
+    a.parts_in = read ? h->parts[ns.rd] : nullptr;
+    a.nparts_in = h->parts_n;
+    a.parts_wscale = h->parts_ws;
+    a.w_axis = (const T*)h->wt[d];
+    a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
+    a.w_b = (const T*)(d == 2 ? h->wt[1] : h->wt[2]);
+    a.parts_out = write ? h->parts[ns.wr] : nullptr;
+    unsigned blocks;
+    if (d == 0)
+      blocks = launch_t_seg<T, true, true, false, true>(seg, a, h->work, h->pdl_now);
+    else if (write)
+      blocks = launch_c_seg<T, true, true, true>(seg, h->keep_c, a, h->work, h->pdl_now);
+    else
+      blocks = launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work, h->pdl_now);
+    if (write) {
+      h->parts_n = (int)blocks;
+      h->parts_ws = h->wscale;
+    }
+  }
+}
+
 // The closing N(dt/2) of a Strang step (and, imaginary time, the norm sums of
 // its result into slot ns.wr).
 template <typename T>
@@ -360,7 +413,10 @@ void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullp
                   StepForm f = StepForm{}) {
   for (int d = 0; d < h->dim; ++d) {
     if (ev) cudaEventRecord(ev[2 * d], h->work);
-    enqueue_sweep<T>(h, imag, ns, d, src, f.half_open);
+    if (h->real_mode)
+      enqueue_sweep_real<T>(h, ns, d);  // imaginary time only
+    else
+      enqueue_sweep<T>(h, imag, ns, d, src, f.half_open);
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
   if (h->strang && f.close) enqueue_strang_close<T>(h, imag, ns);
@@ -379,7 +435,9 @@ inline NormSlots slots_of_step(bool imag, long t) {
 template <typename T>
 void enqueue_finish_imag(gp_handle* h, long nsteps) {
   const int blocks = (int)std::min<long>((h->np + 255) / 256, 152L * 8);
-  launch_k(h->pdl_now, scale_kernel<T>, dim3(blocks), dim3(256), 0, h->work, (c2_t<T>*)h->psi, h->np,
+  // (a real state: its np values scaled as np/2 complex ones)
+  c2_t<T>* psi = (c2_t<T>*)(h->real_mode ? h->rpsi : h->psi);
+  launch_k(h->pdl_now, scale_kernel<T>, dim3(blocks), dim3(256), 0, h->work, psi, h->real_mode ? h->np / 2 : h->np,
            (const double*)h->parts[(nsteps - 1) & 1], h->parts_n, h->parts_ws);
   count_launch();
 }

@@ -404,7 +404,11 @@ __device__ __forceinline__ void finish_norm(T tval, double* parts_out) {
 // Body shared with the batched kernels: lines L0 .. L0+31 of the grid
 // described by A; nseg = ceil((n-2)/SEG) warps take part, the other warps of
 // the block (if any) only join the barriers.
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP = (SEG * sizeof(T) <= 64)>
+// RP (a real imaginary-time state viewed as complex): the complex point i' of
+// a line holds the real values at x = 2i' (re) and 2i' + 1 (im); with real
+// coefficients one complex sweep is the two real sweeps, and only the norm
+// (LAST) needs the two x weights w_a[2i'], w_a[2i' + 1] apart.
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP = (SEG * sizeof(T) <= 64), bool RP = false>
 __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
                                               c2_t<T> (*cb)[33], double* red_smem) {
   using c2 = c2_t<T>;
@@ -446,7 +450,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   T nval = T(0);
   if (active) {
     const T* w = A.w_axis;
-    T tacc = T(0);
+    T tacc = T(0), tim = T(0);
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
@@ -456,25 +460,35 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
         else pk = __ldcg(&line[k * st]);
         const c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
         line[k * st] = u;
-        if (LAST) tacc += w[k] * (u.x * u.x + u.y * u.y);
+        if constexpr (LAST && RP) {
+          tacc += w[k] * (u.x * u.x);
+          tim += w[k] * (u.y * u.y);
+        } else if (LAST) {
+          tacc += w[k] * (u.x * u.x + u.y * u.y);
+        }
       }
     }
     if (s == 0) {
       line[0] = mk<T>(0, 0);
       line[(n - 1) * st] = mk<T>(0, 0);
     }
-    if (LAST) nval = tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
+    if constexpr (LAST && RP) {
+      const int i2 = 2 * (L % G.nx);
+      nval = (tacc * A.w_a[i2] + tim * A.w_a[i2 + 1]) * A.w_b[L / G.nx];
+    } else if (LAST) {
+      nval = tacc * (A.w_a[L % G.nx] * A.w_b[L / G.nx]);
+    }
   }
   finish_norm<T, LAST>(nval, A.parts_out);
 }
 
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false>
 __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
   extern __shared__ __align__(16) unsigned char csmem_raw[];
   __shared__ c2_t<T> cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
-  colsweep_body<T, IMAG, LAST, SEG, KEEP>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb,
-                                          red_smem);
+  colsweep_body<T, IMAG, LAST, SEG, KEEP, RP>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb,
+                                              red_smem);
 }
 
 // ---------------------------------------------------------------- x sweep (2d/3d)
@@ -485,38 +499,45 @@ constexpr int kTilePitch = 33;
 
 // Body shared with the batched kernels: x lines L0 .. L0+31; sc points to
 // 3n + 512 + 33n complex values of shared memory.
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+// RL (a real imaginary-time state, 2d/3d): tile column c holds the real x
+// lines 2(L0+c) (re) and 2(L0+c) + 1 (im), so a tile covers 64 real lines
+// and G.nlines counts real lines; N is applied to each real line with its own
+// density and potential, and with real coefficients the complex solve of a
+// column is the two real solves.
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
 __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
                                             c2_t<T> (*cb)[33], double* red_smem) {
+  static_assert(!(RL && (LAST || is_df<T>::value || !IMAG)), "packed real lines: imaginary-time x sweeps of 2d/3d");
   using c2 = c2_t<T>;
   const LineGeom& G = A.geom;
   const int n = G.n, M = n - 2;
   c2* tile = sc + 3 * n + 512;
   const int lane = threadIdx.x & 31, s = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nseg = (M + SEG - 1) / SEG;
-  const int nl = min(32, (int)G.nlines - L0);
+  const int ncols = RL ? (int)((G.nlines + 1) / 2) : (int)G.nlines;  // tile columns in the grid
+  const int nl = min(32, ncols - L0);
   load_coefs<T>(A, sc, n);
   pdl_wait();  // the state and the norm sums are the previous kernels' output
   pdl_release();
   constexpr bool kFactors = std::is_same<T, double>::value;  // FP64: precomputed potential factors
   const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
   const c2* in = A.src ? A.src : A.psi;
-  // per-line part of the sub-step N (FIRST)
-  auto line_factors = [&](int c, c2& fline, T& vline) {
+  const T* rin = reinterpret_cast<const T*>(in);  // RL
+  // per-line part of the sub-step N (FIRST) of grid line Lg
+  auto line_factors = [&](int Lg, c2& fline, T& vline) {
     fline = mk<T>(1, 0);
     vline = T(0);
-    if (FIRST && c < nl && !is_df<T>::value) {
-      const int L = L0 + c;
-      if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[L % G.ny], A.fz[L / G.ny]);
-      if (!kFactors && !A.V) vline = A.vy[L % G.ny] + A.vz[L / G.ny];
+    if (FIRST && Lg < G.nlines && !is_df<T>::value) {
+      if (kFactors && !A.fV) fline = fac_mul<T, IMAG>(A.fy[Lg % G.ny], A.fz[Lg / G.ny]);
+      if (!kFactors && !A.V) vline = A.vy[Lg % G.ny] + A.vz[Lg / G.ny];
     }
   };
-  // the factor scl and the sub-step N at interior point k of line c
-  auto apply_N = [&](c2 w, int c, int k, const c2& fline, T vline, T scl) -> c2 {
-    const int gbase = (L0 + c) * G.nx;
+  // the factor scl and the sub-step N at interior point k of grid line Lg
+  auto apply_N = [&](c2 w, int Lg, int k, const c2& fline, T vline, T scl) -> c2 {
+    const int gbase = Lg * G.nx;
     if constexpr (is_df<T>::value) {
       if (IMAG) { w.x *= scl; w.y *= scl; }
-      return phase_df<IMAG>(w, A, gbase + k, k, L0 + c, A.dtg);
+      return phase_df<IMAG>(w, A, gbase + k, k, Lg, A.dtg);
     } else {
       w.x *= scl; w.y *= scl;
       if (kFactors) {
@@ -527,11 +548,15 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
       }
     }
   };
+  // RL: N on one real value (as the complex path does on (x, 0))
+  auto apply_R = [&](T x, int Lg, int k, const c2& fline, T vline, T scl) -> T {
+    return apply_N(mk<T>(x, T(0)), Lg, k, fline, vline, scl).x;
+  };
   // A pending renormalisation factor (imaginary time, after the first step)
   // is summed by warp 0 from the previous step's per-block norms while the
   // other warps bring the tile in unchanged; the factor and N are then
   // applied in a second pass over the tile.  Otherwise N is applied on the
-  // way in.  Either way: warp w takes lines w, w + nwarps, ...; lane takes
+  // way in.  Either way: warp w takes columns w, w + nwarps, ...; lane takes
   // points lane, lane + 32, ... (coalesced rows; tile pitch 33, no conflicts).
   const bool pend = FIRST && A.parts_in != nullptr;
   if (pend && s == 0) {
@@ -542,24 +567,55 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   if (s >= w0) {
     for (int c = s - w0; c < 32; c += nwarps - w0) {
       const bool line_ok = c < nl;
-      const int gbase = (L0 + c) * G.nx;
-      c2 fline;
-      T vline;
-      if (!pend) line_factors(c, fline, vline);
-      for (int q0 = 0; q0 < per_line; q0 += 4) {
-        c2 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int k = (q0 + i) * 32 + lane;
-          v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
+      if constexpr (RL) {
+        const int La = 2 * (L0 + c), Lb = La + 1;
+        const bool oka = line_ok, okb = line_ok && Lb < G.nlines;
+        c2 fa, fb;
+        T va, vb;
+        if (!pend) {
+          line_factors(La, fa, va);
+          line_factors(Lb, fb, vb);
         }
+        for (int q0 = 0; q0 < per_line; q0 += 4) {
+          c2 v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int k = (q0 + i) * 32 + lane;
-          if (k >= n) break;
-          c2 w = v[i];
-          if (FIRST && !pend && line_ok && k >= 1 && k <= M) w = apply_N(w, c, k, fline, vline, T(1));
-          tile[k * kTilePitch + c] = w;
+          for (int i = 0; i < 4; ++i) {
+            const int k = (q0 + i) * 32 + lane;
+            const bool in_k = k >= 1 && k <= M;
+            v[i] = mk<T>((oka && in_k) ? rin[La * G.nx + k] : T(0), (okb && in_k) ? rin[Lb * G.nx + k] : T(0));
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = (q0 + i) * 32 + lane;
+            if (k >= n) break;
+            c2 w = v[i];
+            if (FIRST && !pend && k >= 1 && k <= M) {
+              if (oka) w.x = apply_R(w.x, La, k, fa, va, T(1));
+              if (okb) w.y = apply_R(w.y, Lb, k, fb, vb, T(1));
+            }
+            tile[k * kTilePitch + c] = w;
+          }
+        }
+      } else {
+        const int gbase = (L0 + c) * G.nx;
+        c2 fline;
+        T vline;
+        if (!pend) line_factors(L0 + c, fline, vline);
+        for (int q0 = 0; q0 < per_line; q0 += 4) {
+          c2 v[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = (q0 + i) * 32 + lane;
+            v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = (q0 + i) * 32 + lane;
+            if (k >= n) break;
+            c2 w = v[i];
+            if (FIRST && !pend && line_ok && k >= 1 && k <= M) w = apply_N(w, L0 + c, k, fline, vline, T(1));
+            tile[k * kTilePitch + c] = w;
+          }
         }
       }
     }
@@ -568,11 +624,28 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     __syncthreads();
     const T scl = (T)red_smem[0];
     for (int c = s; c < nl; c += nwarps) {
-      c2 fline;
-      T vline;
-      line_factors(c, fline, vline);
-      for (int k = lane; k < n; k += 32)
-        if (k >= 1 && k <= M) tile[k * kTilePitch + c] = apply_N(tile[k * kTilePitch + c], c, k, fline, vline, scl);
+      if constexpr (RL) {
+        const int La = 2 * (L0 + c), Lb = La + 1;
+        const bool okb = Lb < G.nlines;
+        c2 fa, fb;
+        T va, vb;
+        line_factors(La, fa, va);
+        line_factors(Lb, fb, vb);
+        for (int k = lane; k < n; k += 32)
+          if (k >= 1 && k <= M) {
+            c2 w = tile[k * kTilePitch + c];
+            w.x = apply_R(w.x, La, k, fa, va, scl);
+            if (okb) w.y = apply_R(w.y, Lb, k, fb, vb, scl);
+            tile[k * kTilePitch + c] = w;
+          }
+      } else {
+        c2 fline;
+        T vline;
+        line_factors(L0 + c, fline, vline);
+        for (int k = lane; k < n; k += 32)
+          if (k >= 1 && k <= M)
+            tile[k * kTilePitch + c] = apply_N(tile[k * kTilePitch + c], L0 + c, k, fline, vline, scl);
+      }
     }
   }
   __syncthreads();
@@ -601,18 +674,26 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   __syncthreads();
   // ---- store (tile end points are zero)
   for (int c = s; c < nl; c += nwarps) {
-    const int gbase = (L0 + c) * G.nx;
-    for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
+    if constexpr (RL) {
+      T* rout = reinterpret_cast<T*>(A.psi);
+      const int La = 2 * (L0 + c), Lb = La + 1;
+      for (int k = lane; k < n; k += 32) rout[La * G.nx + k] = tile[k * kTilePitch + c].x;
+      if (Lb < G.nlines)
+        for (int k = lane; k < n; k += 32) rout[Lb * G.nx + k] = tile[k * kTilePitch + c].y;
+    } else {
+      const int gbase = (L0 + c) * G.nx;
+      for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
+    }
   }
   finish_norm<T, LAST>(nval, A.parts_out);
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
 __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
   extern __shared__ __align__(16) unsigned char tsmem_raw[];
   __shared__ c2_t<T> cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
-  tsweep_body<T, IMAG, FIRST, LAST, SEG>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(tsmem_raw), cf, cb,
+  tsweep_body<T, IMAG, FIRST, LAST, SEG, RL>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(tsmem_raw), cf, cb,
                                          red_smem);
 }
 

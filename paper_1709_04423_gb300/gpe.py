@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
-    "gp_init_spherical", "gp_set_splitting",
+    "gp_init_spherical", "gp_set_splitting", "gp_set_real_state",
 )
 
 
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.gp_set_g.argtypes = [_vp, D]
     lib.gp_set_dt.argtypes = [_vp, D]
     lib.gp_set_splitting.argtypes = [_vp, I]
+    lib.gp_set_real_state.argtypes = [_vp, I]
     lib.gp_step_imag.argtypes = [_vp, L]
     lib.gp_step_real.argtypes = [_vp, L]
     lib.gp_observables.argtypes = [_vp, ctypes.POINTER(GpObs), _vp, I]
@@ -165,6 +166,10 @@ def gp_set_dt(h, dt):
 
 def gp_set_splitting(h, strang):
     return _check(load().gp_set_splitting(h, int(strang)))
+
+
+def gp_set_real_state(h, real):
+    return _check(load().gp_set_real_state(h, int(real)))
 
 
 def gp_step_imag(h, nsteps):
@@ -324,6 +329,7 @@ class Propagator:
         self.shape = tuple(reversed(self.n))
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.real_state = False
         self.precision = precision
         self.ctype = torch.complex64 if precision == "f32" else torch.complex128
         self.npdtype = np.complex64 if precision == "f32" else np.complex128
@@ -385,6 +391,12 @@ class Propagator:
     def set_dt(self, dt):
         gp_set_dt(self.h, dt)
 
+    def set_real_state(self, real=True):
+        """Hold the state as real numbers (imaginary time only; see
+        gp_set_real_state).  States in and out stay complex."""
+        gp_set_real_state(self.h, 1 if real else 0)
+        self.real_state = bool(real)
+
     def set_splitting(self, splitting):
         """``"lie"`` (N, then the sweeps; the default) or ``"strang"``
         (N(dt/2), the sweeps, N(dt/2)); see gp_set_splitting."""
@@ -414,7 +426,7 @@ class Propagator:
         path = os.environ.get("GPE_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gpe_gb300",
                                                              "shapes.json"))
         key = "|".join([torch.cuda.get_device_name(), "x".join(map(str, self.n)), self.precision,
-                        "imag" if imag else "real"])
+                        "imag" if imag else "real"] + (["real_state"] if self.real_state else []))
         table = {}
         if cache and os.path.exists(path):
             try:
