@@ -70,6 +70,8 @@ def _load():
         lib.gpo_coords.argtypes = [ctypes.c_int, ctypes.c_double, _D]
         lib.gpo_potential.argtypes = [_P, _D]
         lib.gpo_simpson_weights.argtypes = [ctypes.c_int, ctypes.c_double, _D]
+        lib.gpo_axisym_coords.argtypes = [ctypes.c_int, ctypes.c_double, _D]
+        lib.gpo_axisym_weights.argtypes = [ctypes.c_int, ctypes.c_double, _D]
         lib.gpo_phase.argtypes = [_P, ctypes.c_int, _D]
         lib.gpo_sweep.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
         lib.gpo_step.argtypes = [_P, ctypes.c_int, _D]
@@ -99,9 +101,13 @@ class Grid:
 
     def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, V=None, geom=0, split=0):
         self.split = int(split)       # 0 Lie (N, L_x, L_y, L_z), 1 Strang (N/2, L, N/2)
-        self.geom = int(geom)         # 0 Cartesian, 1 spherically symmetric 3d trap (dim 1, u = sqrt(4 pi) r phi)
+        # 0 Cartesian, 1 spherically symmetric 3d trap (dim 1, u = sqrt(4 pi) r phi), 2 circularly (dim 1)
+        # or axially (dim 2) symmetric trap with axis 0 = rho on rho_i = (i - 1/2) drho
+        self.geom = int(geom)
         if self.geom == 1 and int(dim) != 1:
             raise ValueError("the spherical trap is a 1d radial problem")
+        if self.geom == 2 and int(dim) not in (1, 2):
+            raise ValueError("the circular (dim 1) and axial (dim 2) traps have one or two axes")
         self.dim = int(dim)
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
@@ -164,6 +170,20 @@ def potential(grid):
 def simpson_weights(n, dx):
     out = np.empty(int(n), dtype=np.float64)
     _load().gpo_simpson_weights(int(n), float(dx), _ptr(out))
+    return out
+
+
+def axisym_coords(n, drho):
+    """R15: rho_i = (i - 1/2) drho (i = 0 is the phantom point)."""
+    out = np.empty(int(n), dtype=np.float64)
+    _load().gpo_axisym_coords(int(n), float(drho), _ptr(out))
+    return out
+
+
+def axisym_weights(n, drho):
+    """R15: midpoint weights 2 pi rho_i drho on i = 1..n-2, 0 at the ends."""
+    out = np.empty(int(n), dtype=np.float64)
+    _load().gpo_axisym_weights(int(n), float(drho), _ptr(out))
     return out
 
 

@@ -50,6 +50,22 @@
  *                programs do; second order in dt): N with dt/2, the sweeps
  *                L_x, L_y, L_z with dt, N with dt/2 (|phi| of its own input),
  *                then (imaginary time) the renormalisation of R6.
+ *  R15 axisym    circularly symmetric 2d traps (dim 1: phi(rho)) and axially
+ *                symmetric 3d traps (dim 2: phi(rho, z)), the paper's other
+ *                symmetric programs ("Nature of problem"): axis 0 is rho on
+ *                the staggered grid rho_i = (i - 1/2) drho, i = 0..n-1, where
+ *                i = 0 is a phantom point at the mirror image of rho_1 and
+ *                i = n-1 the outer wall (both held at zero, as in R5); z as
+ *                in R1.  The rho part of the Laplacian, (1/rho)(rho phi')',
+ *                is the conservative difference
+ *                  [(1 + h_i) phi_{i+1} - 2 phi_i + (1 - h_i) phi_{i-1}]/drho^2,
+ *                h_i = drho/(2 rho_i), whose coupling to the phantom vanishes
+ *                (h_1 = 1): the axis needs no boundary condition.  CN along
+ *                rho then has the sub-diagonal -r(1 - h_k) and the super-
+ *                diagonal -r(1 + h_k).  Integrals take the midpoint weight
+ *                2 pi rho_i drho on i = 1..n-2 along rho (Simpson along z);
+ *                the derivative along rho in R8 reads phi_0 as phi_1 (the even
+ *                extension across the axis).  N as R4, no extra weight.
  *
  * The tridiagonal solve is written as a back-to-front elimination followed by
  * a front-to-back substitution, with a plain division at every point.
@@ -92,9 +108,26 @@ double gpo_radial_gweight(double r) {
   return r > 0.0 ? 1.0 / (4.0 * pi * r * r) : 0.0;
 }
 
+/* R15 */
+void gpo_axisym_coords(int n, double drho, double* rho) {
+  for (int i = 0; i < n; ++i) rho[i] = (i - 0.5) * drho;
+}
+
+void gpo_axisym_weights(int n, double drho, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) w[i] = (i >= 1 && i <= n - 2) ? 2.0 * pi * (i - 0.5) * drho * drho : 0.0;
+}
+
 static void axis_coords(const gpo_problem* p, int d, double* x) {
   if (p->geom == 1) gpo_radial_coords(p->n[d], p->dx[d], x);
+  else if (p->geom == 2 && d == 0) gpo_axisym_coords(p->n[d], p->dx[d], x);
   else gpo_coords(p->n[d], p->dx[d], x);
+}
+
+/* integration weights along axis d < dim (R7, or R15's midpoint rho weight) */
+static void axis_weights(const gpo_problem* p, int d, double* w) {
+  if (p->geom == 2 && d == 0) gpo_axisym_weights(p->n[d], p->dx[d], w);
+  else gpo_simpson_weights(p->n[d], p->dx[d], w);
 }
 
 /* weight of the nonlinear term at point q (1, or R13's 1/(4 pi r^2)) */
@@ -160,29 +193,35 @@ static void phase_dt(const gpo_problem* p, int imag, double dt, double complex* 
 /* R5: one tridiagonal CN solve on a single line of n points, in place.
  * `sign` = +1 for the forward step, -1 for the step with dt -> -dt (used by
  * the adjoint, whose sweep is the conjugate-transposed map). */
+/* hl, hr (R15, NULL for 1): the sub- and super-diagonal of row k are
+ * -r hl[k] and -r hr[k] (1 - h_k and 1 + h_k along rho). */
 static void cn_line(int n, double complex r, double complex* line, long stride,
-                    double complex* p, double complex* q, double complex* rhs) {
+                    double complex* p, double complex* q, double complex* rhs,
+                    const double* hl, const double* hr) {
   if (n < 3) {
     for (int i = 0; i < n; ++i) line[i * stride] = 0.0;
     return;
   }
   int M = n - 2;                 /* unknowns are points 1..n-2 */
-  double complex a = -r;         /* sub- and super-diagonal */
   double complex b = 1.0 + 2.0 * r;
   for (int k = 1; k <= M; ++k) {
     double complex left = (k - 1 >= 1) ? line[(k - 1) * stride] : 0.0;
     double complex mid = line[k * stride];
     double complex right = (k + 1 <= M) ? line[(k + 1) * stride] : 0.0;
-    rhs[k] = r * left + (1.0 - 2.0 * r) * mid + r * right;
+    double complex rl = hl ? r * hl[k] : r, rr = hr ? r * hr[k] : r;
+    rhs[k] = rl * left + (1.0 - 2.0 * r) * mid + rr * right;
   }
   /* back-to-front elimination: u[k] = p[k] - q[k] u[k-1] */
+  double complex am = hl ? -r * hl[M] : -r;
   double complex den = b;
-  q[M] = a / den;
+  q[M] = am / den;
   p[M] = rhs[M] / den;
   for (int k = M - 1; k >= 1; --k) {
-    den = b - a * q[k + 1];
-    q[k] = a / den;
-    p[k] = (rhs[k] - a * p[k + 1]) / den;
+    double complex ak = hl ? -r * hl[k] : -r;   /* sub-diagonal of row k */
+    double complex ck = hr ? -r * hr[k] : -r;   /* super-diagonal of row k */
+    den = b - ck * q[k + 1];
+    q[k] = ak / den;
+    p[k] = (rhs[k] - ck * p[k + 1]) / den;
   }
   /* front-to-back substitution, u[0] = 0 */
   double complex prev = 0.0;
@@ -203,6 +242,18 @@ void gpo_sweep(const gpo_problem* p, int imag, int axis, double sign, double com
   long stride = axis == 0 ? 1 : axis == 1 ? nx : (long)nx * ny;
   /* lines: every combination of the other two indices */
   long nlines = gpo_npoints(p) / n;
+  /* R15: the rho axis' off-diagonal factors 1 -/+ h_k, h_k = drho/(2 rho_k) */
+  double* hl = NULL;
+  double* hr = NULL;
+  if (p->geom == 2 && axis == 0) {
+    hl = malloc(sizeof(double) * n);
+    hr = malloc(sizeof(double) * n);
+    for (int k = 0; k < n; ++k) {
+      double hk = k >= 1 ? 1.0 / (2.0 * k - 1.0) : 0.0;   /* drho / (2 (k - 1/2) drho) */
+      hl[k] = 1.0 - hk;
+      hr[k] = 1.0 + hk;
+    }
+  }
 #pragma omp parallel
   {
     double complex* pp = malloc(sizeof(double complex) * (n + 1));
@@ -214,10 +265,12 @@ void gpo_sweep(const gpo_problem* p, int imag, int axis, double sign, double com
       if (axis == 0) base = L * nx;                               /* (j,k) */
       else if (axis == 1) base = (L % nx) + (L / nx) * (long)nx * ny; /* (i,k) */
       else base = L;                                              /* (i,j) */
-      cn_line(n, r, phi + base, stride, pp, qq, rr);
+      cn_line(n, r, phi + base, stride, pp, qq, rr, hl, hr);
     }
     free(pp); free(qq); free(rr);
   }
+  free(hl);
+  free(hr);
   (void)nz;
 }
 
@@ -227,9 +280,9 @@ double gpo_norm(const gpo_problem* p, const double complex* phi) {
   double* wx = malloc(sizeof(double) * nx);
   double* wy = malloc(sizeof(double) * ny);
   double* wz = malloc(sizeof(double) * nz);
-  gpo_simpson_weights(nx, p->dx[0], wx);
-  if (p->dim > 1) gpo_simpson_weights(ny, p->dx[1], wy); else wy[0] = 1.0;
-  if (p->dim > 2) gpo_simpson_weights(nz, p->dx[2], wz); else wz[0] = 1.0;
+  axis_weights(p, 0, wx);
+  if (p->dim > 1) axis_weights(p, 1, wy); else wy[0] = 1.0;
+  if (p->dim > 2) axis_weights(p, 2, wz); else wz[0] = 1.0;
   double s = 0.0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -251,7 +304,7 @@ void gpo_reduced_density(const gpo_problem* p, const double complex* phi, int ke
     n[d] = axis_n(p, d);
     keep[d] = d < p->dim && ((keep_mask >> d) & 1);
     w[d] = malloc(sizeof(double) * n[d]);
-    if (d < p->dim && !keep[d]) gpo_simpson_weights(n[d], p->dx[d], w[d]);
+    if (d < p->dim && !keep[d]) axis_weights(p, d, w[d]);
     else for (int i = 0; i < n[d]; ++i) w[d][i] = 1.0;
     stride_out[d] = keep[d] ? nout : 0;
     if (keep[d]) nout *= n[d];
@@ -308,7 +361,7 @@ void gpo_observables(const gpo_problem* p, const double complex* phi, double out
     w[d] = malloc(sizeof(double) * nn[d]);
     c[d] = malloc(sizeof(double) * nn[d]);
     if (d < p->dim) {
-      gpo_simpson_weights(nn[d], p->dx[d], w[d]);
+      axis_weights(p, d, w[d]);
       axis_coords(p, d, c[d]);
     } else {
       w[d][0] = 1.0;
@@ -328,6 +381,11 @@ void gpo_observables(const gpo_problem* p, const double complex* phi, double out
         for (int d = 0; d < p->dim; ++d) {
           double complex dd = deriv(phi + q - idx[d] * stride[d], nn[d], idx[d], stride[d], p->dx[d]);
           if (p->geom == 1 && idx[d] == 0) dd = phi[q + 1] / p->dx[0];   /* R13 */
+          if (p->geom == 2 && d == 0 && (idx[0] == 1 || (idx[0] == 2 && nn[0] >= 5))) {  /* R15: phi_0 as phi_1 */
+            double complex f0 = phi[q - idx[0] + 1];
+            if (idx[0] == 1) dd = (phi[q + 1] - f0) / (2.0 * p->dx[0]);
+            else dd = (f0 - 8.0 * phi[q - 1] + 8.0 * phi[q + 1] - phi[q + 2]) / (12.0 * p->dx[0]);
+          }
           grad2 += creal(dd) * creal(dd) + cimag(dd) * cimag(dd);
         }
         nrm += wt * dens;

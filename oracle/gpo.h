@@ -30,7 +30,8 @@ typedef struct {
   double nkl[3];      /* trap frequencies nu, kappa, lambda */
   double g;           /* nonlinearity */
   const double* V;    /* NULL: harmonic trap; else full potential on the grid */
-  int geom;           /* 0: Cartesian; 1: spherically symmetric 3d trap (dim 1, R13) */
+  int geom;           /* 0: Cartesian; 1: spherically symmetric 3d trap (dim 1, R13);
+                         2: circularly (dim 1) / axially (dim 2) symmetric trap, axis 0 = rho (R15) */
   int split;          /* 0: Lie N, L_x, L_y, L_z (R3); 1: Strang N/2, L_x, L_y, L_z, N/2 (R14) */
 } gpo_problem;
 
@@ -40,6 +41,8 @@ void gpo_coords(int n, double dx, double* x);
  * term (0 at r = 0, where u is held at zero) */
 void gpo_radial_coords(int n, double dr, double* r);
 double gpo_radial_gweight(double r);
+void gpo_axisym_coords(int n, double drho, double* rho);     /* R15: rho_i = (i - 1/2) drho */
+void gpo_axisym_weights(int n, double drho, double* w);      /* R15: 2 pi rho_i drho on 1..n-2 */
 void gpo_potential(const gpo_problem* p, double* V);
 void gpo_simpson_weights(int n, double dx, double* w);
 

@@ -612,3 +612,140 @@ def test_strang_step_is_half_phases_around_the_sweeps():
         if imag:
             want = want / np.sqrt(O.norm(gr, want))
         assert np.allclose(O.step(gr, phi, imag), want, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- circular and axial traps (R15)
+
+def _gauss_rho(rho, nu):
+    return np.sqrt(nu / np.pi) * np.exp(-nu * rho ** 2 / 2)
+
+
+def test_axisym_grid_and_weights():
+    """rho_i = (i - 1/2) drho with the phantom i = 0 at the mirror image of
+    rho_1; the midpoint weights integrate 2 pi rho over [0, (n - 2) drho]
+    exactly and 2 pi rho^3 to second order."""
+    n, dr = 41, 0.1
+    rho, w = O.axisym_coords(n, dr), O.axisym_weights(n, dr)
+    assert rho[0] == pytest.approx(-rho[1]) and rho[1] == pytest.approx(0.05)
+    assert w[0] == 0.0 and w[-1] == 0.0
+    R = (n - 2) * dr
+    assert np.sum(w) == pytest.approx(np.pi * R ** 2, rel=1e-13)
+    e = [abs(np.sum(O.axisym_weights(m, R / (m - 2)) * O.axisym_coords(m, R / (m - 2)) ** 2) - np.pi * R ** 4 / 2)
+         for m in (22, 42)]
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.01)
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_rho_sweep_is_the_dense_cn_solve(imag):
+    """One CN sweep along rho against a dense solve of (1 + A) u = (1 - A) p
+    with A = r T, T's row k = (-(1 - h_k), 2, -(1 + h_k)), h_k = drho/(2 rho_k),
+    on a small axial grid (every z line), ends held at zero."""
+    nr, nz, dr, dz, dt = 7, 5, 0.3, 0.4, 0.05
+    gr = O.Grid(2, [nr, nz], [dr, dz], dt, [1.0, 1.3], 2.0, geom=2)
+    phi = rand_complex((nz, nr), 91)
+    got = O.sweep(gr, phi, imag, 0)
+    r = dt / (4 * dr * dr) * (1 if imag else 1j)
+    rho = O.axisym_coords(nr, dr)
+    M = nr - 2
+    T = np.zeros((M, M))
+    for a in range(M):
+        k = a + 1
+        h = dr / (2 * rho[k])
+        T[a, a] = 2
+        if a > 0:
+            T[a, a - 1] = -(1 - h)
+        if a < M - 1:
+            T[a, a + 1] = -(1 + h)
+    A = r * T
+    for j in range(nz):
+        p = phi[j, 1:-1]
+        u = np.linalg.solve(np.eye(M) + A, (np.eye(M) - A) @ p)
+        assert np.allclose(got[j, 1:-1], u, rtol=0, atol=1e-13)
+        assert got[j, 0] == 0 and got[j, -1] == 0
+
+
+def test_circular_harmonic_ground_state():
+    """g = 0 circular trap: mu = E = nu, and the exact state
+    sqrt(nu/pi) exp(-nu rho^2/2) has norm 1, energy nu and rms radius
+    1/sqrt(nu) up to errors that shrink 4x per halving of drho (the even
+    extension across the axis in the derivative)."""
+    nu = 1.3
+    n, dr = 161, 0.05
+    gr = O.Grid(1, [n], [dr], 1e-3, [nu], 0.0, geom=2)
+    rho = O.axisym_coords(n, dr)
+    u = O.run(gr, np.exp(-0.5 * rho ** 2).astype(complex), True, 12000)
+    ob = O.observables(gr, u)
+    assert ob["mu"] == pytest.approx(nu, abs=5e-4)
+    assert ob["energy"] == pytest.approx(ob["mu"], abs=1e-14)
+    errs = []
+    for m, h in ((161, 0.05), (321, 0.025)):
+        g2 = O.Grid(1, [m], [h], 1e-3, [nu], 0.0, geom=2)
+        ob = O.observables(g2, _gauss_rho(O.axisym_coords(m, h), nu).astype(complex))
+        errs.append([abs(ob["norm"] - 1), abs(ob["energy"] - nu), abs(ob["rms_x"] - 1 / np.sqrt(nu))])
+    for a, b in zip(*errs):
+        assert a / b == pytest.approx(4.0, rel=0.05)
+
+
+def test_axial_harmonic_ground_state():
+    """g = 0 axial trap: the exact state has energy nu + lambda/2, rms_rho =
+    1/sqrt(nu), rms_z = 1/sqrt(2 lambda) (errors second order or better); the
+    imaginary-time ground state reaches mu = nu + lambda/2."""
+    nu, lam = 1.2, 1.6
+    errs = []
+    for nr, nz, dr, dz in ((81, 64, 0.1, 0.15), (161, 128, 0.05, 0.075)):
+        gr = O.Grid(2, [nr, nz], [dr, dz], 1e-3, [nu, lam], 0.0, geom=2)
+        rho, z = O.axisym_coords(nr, dr), O.coords(nz, dz)
+        ex = (_gauss_rho(rho, nu)[None, :] * (lam / np.pi) ** 0.25 * np.exp(-lam * z[:, None] ** 2 / 2)).astype(complex)
+        ob = O.observables(gr, ex)
+        assert ob["rms_y"] == pytest.approx(1 / np.sqrt(2 * lam), abs=1e-12)
+        errs.append([abs(ob["norm"] - 1), abs(ob["energy"] - (nu + lam / 2)), abs(ob["rms_x"] - 1 / np.sqrt(nu))])
+    for a, b in zip(*errs):   # second order or better (the z part converges faster)
+        assert 3.5 <= a / b <= 5.0
+    gr = O.Grid(2, [81, 64], [0.1, 0.15], 2e-3, [nu, lam], 0.0, geom=2)
+    rho, z = O.axisym_coords(81, 0.1), O.coords(64, 0.15)
+    u = O.run(gr, np.exp(-0.4 * (rho[None, :] ** 2 + z[:, None] ** 2)).astype(complex), True, 5000)
+    assert O.observables(gr, u)["mu"] == pytest.approx(nu + lam / 2, abs=2e-3)
+
+
+def test_circular_thomas_fermi_limit():
+    """Large g: mu -> nu sqrt(g/pi) (2d Thomas-Fermi), the relative error
+    shrinking as g grows (pins the 2 pi rho weight of the norm)."""
+    rel = []
+    for g in (100.0, 400.0, 1600.0):
+        gr = O.Grid(1, [201], [0.05], 5e-4, [1.0], g, geom=2)
+        rho = O.axisym_coords(201, 0.05)
+        u = O.run(gr, np.exp(-0.1 * rho ** 2).astype(complex), True, 16000)
+        rel.append(O.observables(gr, u)["mu"] / np.sqrt(g / np.pi) - 1)
+    assert all(r > 0 for r in rel) and rel[0] > rel[1] > rel[2] and rel[2] < 0.005
+
+
+def test_circular_real_time_conserves_the_rho_weighted_norm():
+    """(1 + h_k) rho_k = (1 - h_{k+1}) rho_{k+1}: the rho operator is symmetric
+    in the rho-weighted inner product, so CN keeps the midpoint norm (to
+    rounding) through a quench; a transposed coefficient pair would not."""
+    gr = O.Grid(1, [201], [0.04], 1e-3, [1.0], 20.0, geom=2)
+    rho = O.axisym_coords(201, 0.04)
+    u = O.run(gr, np.exp(-0.5 * rho ** 2).astype(complex), True, 3000)
+    g2 = gr.with_(g=40.0)
+    u1 = O.run(g2, u, False, 2000)
+    assert O.norm(g2, u1) == pytest.approx(O.norm(g2, u), rel=1e-12)
+    assert abs(O.observables(g2, u1)["rms_x"] - O.observables(g2, u)["rms_x"]) > 0.1   # it does breathe
+
+
+def test_axial_ground_state_approaches_the_3d_cartesian_one():
+    """An axial trap (nu, lambda) is the 3d trap (nu, nu, lambda): at g = 10
+    the axial mu approaches the 3d Cartesian mu as drho shrinks, and the
+    rms radius matches sqrt(rms_x^2 + rms_y^2)."""
+    nu, lam, g = 1.0, 1.5, 10.0
+    gr3 = O.Grid(3, [40] * 3, [0.3] * 3, 2e-3, [nu, nu, lam], g)
+    u3 = O.run(gr3, I.gaussian_state(3, [40] * 3, [0.3] * 3, [nu, nu, lam]), True, 2500)
+    ob3 = O.observables(gr3, u3)
+    diffs = []
+    for nr, nz, dr, dz in ((21, 40, 0.3, 0.3), (41, 80, 0.15, 0.15)):
+        gra = O.Grid(2, [nr, nz], [dr, dz], 2e-3, [nu, lam], g, geom=2)
+        rho, z = O.axisym_coords(nr, dr), O.coords(nz, dz)
+        ua = O.run(gra, np.exp(-0.5 * (nu * rho[None, :] ** 2 + lam * z[:, None] ** 2)).astype(complex), True, 2500)
+        oba = O.observables(gra, ua)
+        diffs.append(abs(oba["mu"] - ob3["mu"]))
+    assert diffs[1] < diffs[0] and diffs[1] < 3e-3 * ob3["mu"]
+    assert oba["rms_x"] == pytest.approx(np.hypot(ob3["rms_x"], ob3["rms_y"]), rel=2e-3)
