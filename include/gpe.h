@@ -113,6 +113,29 @@ int gp_init(gp_handle** out, int dim, const int n[3], const double dx[3], double
 int gp_init_spherical(gp_handle** out, int n, double dr, double dt, double nu, double g, gp_precision prec,
                       void* stream);
 
+/* Circularly symmetric 2d trap, V = nu^2 rho^2/2 (gp_init_circular), and
+ * axially symmetric 3d trap, V = (nu^2 rho^2 + lambda^2 z^2)/2
+ * (gp_init_axial): the paper's other symmetric programs ("Nature of
+ * problem").  The state is phi(rho) (npoints = n) or phi(rho, z) (rho
+ * fastest, npoints = n_rho n_z) with rho_i = (i - 1/2) drho, i = 0..n-1:
+ * point 0 is the mirror image of point 1 across the axis (held at zero and
+ * never coupled: the conservative difference of (1/rho)(rho phi')' puts the
+ * factor 1 - drho/(2 rho_1) = 0 on it) and point n-1 is the outer wall (held
+ * at zero); z as gp_init's grid.  The rho sweeps solve the non-symmetric
+ * Crank-Nicolson system with rows (-(1 - h_k), 2, -(1 + h_k)) r, h_k =
+ * drho/(2 rho_k).  Integrals take the weight 2 pi rho_i drho along rho
+ * (Simpson along z): the norm is the 2d (circular) or 3d (axial) norm, the
+ * energy and mu are those of the 2d / 3d problem, rms[0] is the rms radius
+ * sqrt(<rho^2>) and (axial) rms[1] the rms z.  The derivative along rho in the
+ * observables reads point 0 as point 1.  At most 514 points per axis; the
+ * pipelined x sweep and the adjoint are not offered; the Strang splitting,
+ * user potentials, reduced densities and the recorded series are.  Errors as
+ * gp_init. */
+int gp_init_circular(gp_handle** out, int n, double drho, double dt, double nu, double g, gp_precision prec,
+                     void* stream);
+int gp_init_axial(gp_handle** out, int n_rho, int n_z, double drho, double dz, double dt, double nu, double lambda,
+                  double g, gp_precision prec, void* stream);
+
 /* Copies a state in (interleaved re, im, in the handle's precision -- double
  * for GP_DF64 -- npoints values).  on_device != 0: psi is a device pointer
  * read in stream order. */

@@ -80,9 +80,51 @@ AxisFactors thomas_factors(int n, double beta, bool imag) {
   return f;
 }
 
+// Grid coordinate i of axis d (n points, spacing dx): Cartesian (R1)
+// -n dx/2 + i dx; the spherical trap's r = i dr; the rho axis of a circular
+// or axial trap (i - 1/2) drho (point 0 the mirror image of point 1).
+double axis_coord(int geom, int d, int n, double dx, int i) {
+  if (geom == 1) return i * dx;
+  if (geom == 2 && d == 0) return (i - 0.5) * dx;
+  return -0.5 * n * dx + i * dx;
+}
+
+// The rho axis of a circular or axial trap (geom 2): row k of T is
+// (-(1 - h_k), 2, -(1 + h_k)) with h_k = drho/(2 rho_k) = 1/(2k - 1) on
+// rho_k = (k - 1/2) drho.  Thomas factors of (1 + rT): m_k = 1/(b - a_k
+// c'_{k-1}) with a_k = -r(1 - h_k), c_k = -r(1 + h_k), c'_k = c_k m_k; the
+// increment form's forward recurrence e_k = af_k e_{k-1} + bf_k lapv_k and
+// backward recurrence z_k = e_k + ab_k z_{k+1} have af_k = r(1 - h_k) m_k,
+// bf_k = 2 r m_k, ab_k = r(1 + h_k) m_k; hh_k = (1 - h_k, 1 + h_k).
+static void rho_factors(int n, double beta, bool imag, std::vector<cd>& af, std::vector<cd>& ab, std::vector<cd>& bf,
+                 std::vector<cd>& hh) {
+  af.assign(n, cd(0, 0));
+  ab.assign(n, cd(0, 0));
+  bf.assign(n, cd(0, 0));
+  hh.assign(n, cd(0, 0));
+  const cd r = imag ? cd(beta, 0) : cd(0, beta);
+  const cd b = 1.0 + 2.0 * r;
+  cd cprev(0, 0);
+  for (int k = 1; k <= n - 2; ++k) {
+    const double h = 1.0 / (2.0 * k - 1.0);
+    const cd a = -r * (1.0 - h), c = -r * (1.0 + h);
+    const cd m = 1.0 / (b - a * cprev);
+    af[k] = r * (1.0 - h) * m;
+    ab[k] = r * (1.0 + h) * m;
+    bf[k] = 2.0 * r * m;
+    hh[k] = cd(1.0 - h, 1.0 + h);
+    cprev = c * m;
+  }
+}
+
 // Segment products for segments of `seg` interior points starting at k = 1:
-// gf[k] = prod_{i=start..k} alpha_i, gb[k] = prod_{i=k..end} alpha_i.
+// gf[k] = prod_{i=start..k} af_i, gb[k] = prod_{i=k..end} ab_i.
 void segment_products(const std::vector<cd>& alpha, int n, int seg, std::vector<cd>& gf, std::vector<cd>& gb) {
+  segment_products(alpha, alpha, n, seg, gf, gb);
+}
+
+void segment_products(const std::vector<cd>& af, const std::vector<cd>& ab, int n, int seg, std::vector<cd>& gf,
+                      std::vector<cd>& gb) {
   const int M = n - 2;
   gf.assign(n, cd(0, 0));
   gb.assign(n, cd(0, 0));
@@ -90,27 +132,35 @@ void segment_products(const std::vector<cd>& alpha, int n, int seg, std::vector<
     const int k1 = std::min(M, k0 + seg - 1);
     cd acc(1, 0);
     for (int k = k0; k <= k1; ++k) {
-      acc *= alpha[k];
+      acc *= af[k];
       gf[k] = acc;
     }
     acc = cd(1, 0);
     for (int k = k1; k >= k0; --k) {
-      acc *= alpha[k];
+      acc *= ab[k];
       gb[k] = acc;
     }
   }
 }
 
-// Carry tables of the segment scans for segment length sg: with A_q the
-// product of alpha over segment q, Pf[q][t] = prod_{q<r<=t} A_r (q <= t) and
-// Pb[q][t] = prod_{t<=r<q} A_r (q >= t); 16 x 16 each, Pf then Pb.
+// Carry tables of the segment scans for segment length sg: with A_q (B_q)
+// the product of af (ab) over segment q, Pf[q][t] = prod_{q<r<=t} A_r (q <= t)
+// and Pb[q][t] = prod_{t<=r<q} B_r (q >= t); 16 x 16 each, Pf then Pb.
 void carry_tables(const std::vector<cd>& alpha, int n, int sg, cd* out /* 512 */) {
+  carry_tables(alpha, alpha, n, sg, out);
+}
+
+void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, int sg, cd* out /* 512 */) {
   const int M = n - 2;
-  cd Aseg[16];
+  cd Aseg[16], Bseg[16];
   for (int q = 0; q < 16; ++q) {
-    cd acc(1, 0);
-    for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) acc *= alpha[k];
+    cd acc(1, 0), bcc(1, 0);
+    for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) {
+      acc *= af[k];
+      bcc *= ab[k];
+    }
     Aseg[q] = acc;
+    Bseg[q] = bcc;
   }
   cd* Pf = out;
   cd* Pb = out + 256;
@@ -125,7 +175,7 @@ void carry_tables(const std::vector<cd>& alpha, int n, int sg, cd* out /* 512 */
       }
       acc = cd(1, 0);
       if (q >= t) {
-        for (int r = t; r < q; ++r) acc *= Aseg[r];
+        for (int r = t; r < q; ++r) acc *= Bseg[r];
         Pb[q * 16 + t] = acc;
       }
     }
@@ -161,16 +211,28 @@ int upload_coefs_t(gp_handle* h) {
       const double sign = mode == MODE_REAL_ADJ ? -1.0 : 1.0;
       const double beta = sign * h->dt / (4.0 * h->dx[d] * h->dx[d]);
       const AxisFactors f = thomas_factors(n, beta, mode == MODE_IMAG);
+      // forward / backward coefficients: alpha for both, or the rho axis' own
+      std::vector<cd> af = f.alpha, ab = f.alpha;
+      if (h->geom == 2 && d == 0) {
+        std::vector<cd> bf, hh;
+        rho_factors(n, beta, mode == MODE_IMAG, af, ab, bf, hh);
+        std::vector<cd> cv((size_t)3 * n);
+        std::copy(ab.begin(), ab.end(), cv.begin());
+        std::copy(bf.begin(), bf.end(), cv.begin() + n);
+        std::copy(hh.begin(), hh.end(), cv.begin() + 2 * n);
+        int rc = upload_c2<T>(h, h->cvar[mode], cv);
+        if (rc) return rc;
+      }
       std::vector<cd> all((size_t)(1 + 2 * kNumSegs) * n);
-      std::copy(f.alpha.begin(), f.alpha.end(), all.begin());
+      std::copy(af.begin(), af.end(), all.begin());
       std::vector<cd> gf, gb;
       for (int s = 0; s < kNumSegs; ++s) {
-        segment_products(f.alpha, n, kSegs[s], gf, gb);
+        segment_products(af, ab, n, kSegs[s], gf, gb);
         std::copy(gf.begin(), gf.end(), all.begin() + (size_t)(1 + 2 * s) * n);
         std::copy(gb.begin(), gb.end(), all.begin() + (size_t)(2 + 2 * s) * n);
       }
       std::vector<cd> tabs((size_t)kNumSegs * 512, cd(0, 0));
-      for (int si = 0; si < kNumSegs; ++si) carry_tables(f.alpha, n, kSegs[si], tabs.data() + (size_t)si * 512);
+      for (int si = 0; si < kNumSegs; ++si) carry_tables(af, ab, n, kSegs[si], tabs.data() + (size_t)si * 512);
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
       if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;
@@ -240,7 +302,7 @@ void choose_shapes(gp_handle* h) {
   int nmax = 0;
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
   const bool pipe = env_int("GPE_PIPE", 0) != 0 && h->prec != GP_DF64;
-  h->pipe_x = pipe && h->tile_x && pipe_fits(h, h->n[0], true);
+  h->pipe_x = pipe && h->tile_x && h->geom != 2 && pipe_fits(h, h->n[0], true);  // (no rho-axis pipelined sweep)
   h->pipe_c = pipe && h->dim > 1 && sc > 0 && pipe_fits(h, nmax, false);
 }
 
@@ -313,7 +375,7 @@ static int upload_factor_set(gp_handle* h, double dt_eff, void* (&fac)[2][3], vo
     std::vector<cd> fr(nd, cd(1, 0)), fi(nd, cd(1, 0));
     if (d < h->dim)
       for (int i = 0; i < nd; ++i) {
-        const double x = h->geom == 1 ? i * h->dx[d] : -0.5 * nd * h->dx[d] + i * h->dx[d];
+        const double x = axis_coord(h->geom, d, nd, h->dx[d], i);
         const double v = 0.5 * h->nkl[d] * h->nkl[d] * x * x;
         fr[i] = cd(std::cos(dt_eff * v), -std::sin(dt_eff * v));
         fi[i] = cd(std::exp(-dt_eff * v), 0.0);
@@ -448,18 +510,29 @@ int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double
     std::vector<double> x(nd, 0.0), v(nd, 0.0), w(nd, 1.0), wc(nd, 1.0);
     if (d < dim) {
       for (int i = 0; i < nd; ++i) {
-        x[i] = geom == 1 ? i * dx[d] : -0.5 * nd * dx[d] + i * dx[d];  // radial grid from r = 0
+        x[i] = axis_coord(geom, d, nd, dx[d], i);
         v[i] = 0.5 * nkl[d] * nkl[d] * x[i] * x[i];
       }
-      // composite Simpson on the first m points (m = n odd, n-1 even)
-      const int m = (nd % 2 == 1) ? nd : nd - 1;
-      for (int i = 0; i < nd; ++i) {
-        double c = 0.0;
-        if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
-        wc[i] = c;
-        w[i] = c * dx[d] / 3.0;
+      if (geom == 2 && d == 0) {
+        // rho of a circular / axial trap: midpoint weights 2 pi rho_i drho =
+        // (2i - 1) pi drho^2 on i = 1..n-2 (coefficients 2i - 1, exact in FP32)
+        for (int i = 0; i < nd; ++i) {
+          const double c = (i >= 1 && i <= nd - 2) ? 2.0 * i - 1.0 : 0.0;
+          wc[i] = c;
+          w[i] = c * M_PI * dx[d] * dx[d];
+        }
+        h->wscale *= M_PI * dx[d] * dx[d];
+      } else {
+        // composite Simpson on the first m points (m = n odd, n-1 even)
+        const int m = (nd % 2 == 1) ? nd : nd - 1;
+        for (int i = 0; i < nd; ++i) {
+          double c = 0.0;
+          if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);
+          wc[i] = c;
+          w[i] = c * dx[d] / 3.0;
+        }
+        h->wscale *= dx[d] / 3.0;
       }
-      h->wscale *= dx[d] / 3.0;
     }
     if ((rc = dev_alloc(h, &h->vt[d], nd * tsz))) return bail(rc);
     if ((rc = dev_alloc(h, &h->fac[0][d], nd * h->esize))) return bail(rc);
@@ -501,6 +574,9 @@ int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double
     }
     if ((rc = dev_alloc(h, &h->df_stage, (size_t)np * sizeof(double2)))) return bail(rc);
   }
+  if (geom == 2)
+    for (int mode = 0; mode < NUM_MODES; ++mode)
+      if ((rc = dev_alloc(h, &h->cvar[mode], (size_t)3 * h->n[0] * h->esize))) return bail(rc);
   if (geom == 1) {
     // weight of the nonlinear term of the radial problem, 1/(4 pi r^2) (0 at r = 0, where u is held at zero)
     std::vector<double> gw(n[0], 0.0);
@@ -517,6 +593,8 @@ int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double
   choose_shapes(h);
   if (prec == GP_DF64 && (h->seg_x == 0 || (dim > 1 && h->seg_c == 0)))
     return bail(fail(GP_ERR_INVALID, "gp_init: the double-float form takes at most 514 points per axis"));
+  if (geom == 2 && (h->seg_x == 0 || (dim > 1 && h->seg_c == 0)))
+    return bail(fail(GP_ERR_INVALID, "gp_init: circular and axial traps take at most 514 points per axis"));
   // reduction scratch: enough partial slots for any sweep or observables grid
   long maxblocks = 152L * 16;
   for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, h->np / h->n[d] / 4 + 1);
@@ -550,6 +628,20 @@ int gp_init_spherical(gp_handle** out, int n, double dr, double dt, double nu, d
   const int n3[3] = {n, 1, 1};
   const double dx3[3] = {dr, 1.0, 1.0}, nkl3[3] = {nu, 0.0, 0.0};
   return init_handle(out, 1, 1, n3, dx3, dt, nkl3, g, prec, stream);
+}
+
+int gp_init_circular(gp_handle** out, int n, double drho, double dt, double nu, double g, gp_precision prec,
+                     void* stream) {
+  const int n3[3] = {n, 1, 1};
+  const double dx3[3] = {drho, 1.0, 1.0}, nkl3[3] = {nu, 0.0, 0.0};
+  return init_handle(out, 2, 1, n3, dx3, dt, nkl3, g, prec, stream);
+}
+
+int gp_init_axial(gp_handle** out, int n_rho, int n_z, double drho, double dz, double dt, double nu, double lambda,
+                  double g, gp_precision prec, void* stream) {
+  const int n3[3] = {n_rho, n_z, 1};
+  const double dx3[3] = {drho, dz, 1.0}, nkl3[3] = {nu, lambda, 0.0};
+  return init_handle(out, 2, 2, n3, dx3, dt, nkl3, g, prec, stream);
 }
 
 int gp_set_state(gp_handle* h, const void* psi, int on_device) {
@@ -821,6 +913,8 @@ int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
   if (h->real_mode && (!tile_x || seg_x == 0 || seg_c == 0))
     return fail(GP_ERR_STATE, "gp_set_shapes: a real state needs the x tile and segmented y/z sweeps");
+  if (h->geom == 2 && (seg_x == 0 || (h->dim > 1 && seg_c == 0) || (flags & GP_SHAPE_PIPE_X)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: the rho axis takes the segmented, non-pipelined x sweeps");
   const bool px = (flags & GP_SHAPE_PIPE_X) != 0, pc = (flags & GP_SHAPE_PIPE_YZ) != 0;
   if ((px || pc) && h->prec == GP_DF64)
     return fail(GP_ERR_INVALID, "gp_set_shapes: the pipelined sweeps take GP_F64 or GP_F32 states");
@@ -868,7 +962,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   for (int sg : {4, 8, 16, 32})
     if (shapes_valid(h, 1, sg, h->seg_c)) {
       xs.push_back({1, sg, 0});
-      if (h->prec != GP_DF64 && !real && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
+      if (h->prec != GP_DF64 && !real && h->geom != 2 && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
     }
   for (int sg : {1, 2, 4, 8, 16})
     if (!real && shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }

@@ -271,7 +271,7 @@ int build_tables(gp_batch* b) {
       for (int q = 0; q < 512; ++q) { pt[2 * q] = (T)tabs[q].real(); pt[2 * q + 1] = (T)tabs[q].imag(); }
       const double w = b->nk[2 * r + a];
       for (int i = 0; i < n; ++i) {
-        const double x = -0.5 * n * h + i * h;
+        const double x = axis_coord(0, a, n, h, i);  // the single-grid handle's coordinates, bit for bit
         const double v = 0.5 * w * w * x * x;
         vbuf[2 * (voff[2 * r + a] + i)] = (T)std::cos(b->dt * v);
         vbuf[2 * (voff[2 * r + a] + i) + 1] = (T)(-std::sin(b->dt * v));
@@ -599,7 +599,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
       std::vector<double> x(na), v(na), wt(na);
       const int m = (na % 2 == 1) ? na : na - 1;
       for (int i = 0; i < na; ++i) {
-        x[i] = -0.5 * na * h + i * h;
+        x[i] = axis_coord(0, a, na, h, i);
         v[i] = 0.5 * w * w * x[i] * x[i];
         double c = 0.0;
         if (i < m) c = (i == 0 || i == m - 1) ? 1.0 : (i % 2 == 1 ? 4.0 : 2.0);

@@ -96,6 +96,10 @@ struct gp_handle {
   // per (mode, axis): for each segment length, the carry tables Pf and Pb
   // (16 x 16 complex each) of the segment scans
   void* ctab[gpe::NUM_MODES][3] = {{nullptr}};
+  // circular / axial traps (geom 2): per mode, the rho axis' backward
+  // coefficients, forward right-hand-side factors and stencil factors
+  // (vab, vbf, vh of Sweep2Args; 3 n[0] complex values)
+  void* cvar[gpe::NUM_MODES] = {nullptr};
   // legacy thread-per-line factors (m_k, c'_k) per (imag, axis), used when a
   // line is too long for the segmented kernels
   void* cm[2][3] = {{nullptr}};
@@ -169,6 +173,12 @@ AxisFactors thomas_factors(int n, double beta, bool imag);
 void segment_products(const std::vector<std::complex<double>>& alpha, int n, int seg,
                       std::vector<std::complex<double>>& gf, std::vector<std::complex<double>>& gb);
 void carry_tables(const std::vector<std::complex<double>>& alpha, int n, int sg, std::complex<double>* out);
+// the same with separate forward (af) and backward (ab) coefficients
+double axis_coord(int geom, int d, int n, double dx, int i);  // grid coordinate (Cartesian, r, or rho)
+void segment_products(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
+                      int seg, std::vector<std::complex<double>>& gf, std::vector<std::complex<double>>& gb);
+void carry_tables(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
+                  int sg, std::complex<double>* out);
 int tile_seg(int M);
 
 int dev_alloc(gp_handle* h, void** p, size_t bytes);

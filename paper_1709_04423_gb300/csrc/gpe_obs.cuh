@@ -45,10 +45,13 @@ struct ObsArgs {
   const obs_r<T>* wx; const obs_r<T>* wy; const obs_r<T>* wz;
   double wscale;            // factor of the FP64 totals (1, or prod dx/3 with coefficient weights)
   // radial problem of the spherical trap: weight of the |psi|^4 term per x
-  // index (1/(4 pi r^2)), and the derivative at i = 0 from the odd extension
-  // of u (u'(0) = u_1/dx); nullptr / 0 for Cartesian grids
+  // index (1/(4 pi r^2)); nullptr for the other grids.  x0: how the x
+  // derivative treats the start of the axis -- 0 Cartesian (R8), 1 the
+  // spherical u's odd extension (u'(0) = u_1/dx), 2 the even extension across
+  // the axis of a circular or axial trap (point 0 is the mirror image of
+  // point 1, so the stencils at i = 1, 2 read psi_0 as psi_1)
   const obs_r<T>* gx;
-  int odd0;
+  int x0;
   double* density;          // optional |phi|^2 output
   double* partials;
   unsigned int* counter;
@@ -100,9 +103,21 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
       const R px = R(p.x), py = R(p.y);
       const R dens = px * px + py * py;
       R g2;
-      if (A.odd0 && i == 0) {
+      if (A.x0 == 1 && i == 0) {
         const c2_t<T> p1 = A.psi[q + 1];
         const R ux = R(p1.x) * (R(2) * fx1), uy = R(p1.y) * (R(2) * fx1);
+        g2 = ux * ux + uy * uy;
+      } else if (A.x0 == 2 && (i == 1 || (i == 2 && A.nx >= 5))) {
+        const c2_t<T> m = A.psi[q - i + 1], b = A.psi[q + 1];  // psi_0 read as psi_1
+        R ux, uy;
+        if (i == 1) {
+          ux = (R(b.x) - R(m.x)) * fx1;
+          uy = (R(b.y) - R(m.y)) * fx1;
+        } else {
+          const c2_t<T> e = A.psi[q + 2];
+          ux = (R(m.x) - R(8) * R(m.x) + R(8) * R(b.x) - R(e.x)) * fx4;
+          uy = (R(m.y) - R(8) * R(m.y) + R(8) * R(b.y) - R(e.y)) * fx4;
+        }
         g2 = ux * ux + uy * uy;
       } else {
         g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4);

@@ -43,22 +43,22 @@ inline const c2_t<T>* coef_ptr(const gp_handle* h, int mode, int axis, int slot)
 // ---- segmented x sweep
 // Every launcher returns its number of blocks (a LAST sweep leaves one norm
 // sum per block for the next step's reader).
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool VAR = false>
 unsigned launch_x(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const unsigned blocks = (unsigned)((a.geom.nlines + kXWarps - 1) / kXWarps);
-  launch_k(pdl, xsweep_kernel<T, IMAG, FIRST, LAST, SEG>, dim3(blocks), dim3(32 * kXWarps), 0, s, a);
+  launch_k(pdl, xsweep_kernel<T, IMAG, FIRST, LAST, SEG, VAR>, dim3(blocks), dim3(32 * kXWarps), 0, s, a);
   count_launch();
   return blocks;
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST>
+template <typename T, bool IMAG, bool FIRST, bool LAST, bool VAR = false>
 unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 1: return launch_x<T, IMAG, FIRST, LAST, 1>(a, s, pdl);
-    case 2: return launch_x<T, IMAG, FIRST, LAST, 2>(a, s, pdl);
-    case 4: return launch_x<T, IMAG, FIRST, LAST, 4>(a, s, pdl);
-    case 8: return launch_x<T, IMAG, FIRST, LAST, 8>(a, s, pdl);
-    default: return launch_x<T, IMAG, FIRST, LAST, 16>(a, s, pdl);
+    case 1: return launch_x<T, IMAG, FIRST, LAST, 1, VAR>(a, s, pdl);
+    case 2: return launch_x<T, IMAG, FIRST, LAST, 2, VAR>(a, s, pdl);
+    case 4: return launch_x<T, IMAG, FIRST, LAST, 4, VAR>(a, s, pdl);
+    case 8: return launch_x<T, IMAG, FIRST, LAST, 8, VAR>(a, s, pdl);
+    default: return launch_x<T, IMAG, FIRST, LAST, 16, VAR>(a, s, pdl);
   }
 }
 
@@ -96,8 +96,8 @@ unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s,
 }
 
 // ---- shared-memory tile x sweep
-// (RL: a.geom.nlines real lines, two per tile column)
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
+// (RL: a.geom.nlines real lines, two per tile column; VAR: a rho axis)
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false, bool VAR = false>
 unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
@@ -106,22 +106,22 @@ unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const size_t smem = (size_t)a.geom.n * (kTilePitch + 3) * sizeof(c2_t<T>) + 512 * sizeof(c2_t<T>);
   static bool attr_set = false;  // one opt-in per instantiation
   if (!attr_set) {
-    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL, VAR>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL>, dim3(blocks), dim3(32 * nseg), smem, s, a);
+  launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL, VAR>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST, bool RL = false>
+template <typename T, bool IMAG, bool FIRST, bool LAST, bool RL = false, bool VAR = false>
 unsigned launch_t_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   switch (seg) {
-    case 4: return launch_t<T, IMAG, FIRST, LAST, 4, RL>(a, s, pdl);
-    case 8: return launch_t<T, IMAG, FIRST, LAST, 8, RL>(a, s, pdl);
-    case 16: return launch_t<T, IMAG, FIRST, LAST, 16, RL>(a, s, pdl);
-    default: return launch_t<T, IMAG, FIRST, LAST, 32, RL>(a, s, pdl);
+    case 4: return launch_t<T, IMAG, FIRST, LAST, 4, RL, VAR>(a, s, pdl);
+    case 8: return launch_t<T, IMAG, FIRST, LAST, 8, RL, VAR>(a, s, pdl);
+    case 16: return launch_t<T, IMAG, FIRST, LAST, 16, RL, VAR>(a, s, pdl);
+    default: return launch_t<T, IMAG, FIRST, LAST, 32, RL, VAR>(a, s, pdl);
   }
 }
 
@@ -249,9 +249,30 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.w_a = (const T*)(d == 0 ? h->wt[1] : h->wt[0]);
     a.w_b = (const T*)(d == 2 ? h->wt[1] : h->wt[2]);
     a.parts_out = parts_out;
+    // the rho axis of a circular or axial trap: non-symmetric coefficients
+    const bool var = h->geom == 2 && d == 0;
+    if (var) {
+      const c2_t<T>* cv = (const c2_t<T>*)h->cvar[mode];
+      a.vab = cv;
+      a.vbf = cv + h->n[0];
+      a.vh = cv + 2 * h->n[0];
+    }
     bool done = false;
+    if (var) {
+      if (h->tile_x) {  // axial trap: x is not the last axis
+        blocks = imag ? launch_t_seg<T, true, true, false, false, true>(seg, a, h->work, h->pdl_now)
+                      : launch_t_seg<T, false, true, false, false, true>(seg, a, h->work, h->pdl_now);
+      } else if (imag) {
+        blocks = write ? launch_x_seg<T, true, true, true, true>(seg, a, h->work, h->pdl_now)
+                       : launch_x_seg<T, true, true, false, true>(seg, a, h->work, h->pdl_now);
+      } else {
+        blocks = launch_x_seg<T, false, true, false, true>(seg, a, h->work, h->pdl_now);
+      }
+      done = true;
+    }
     if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
-      if (d == 0 && h->tile_x && h->pipe_x) {
+      if (done) {
+      } else if (d == 0 && h->tile_x && h->pipe_x) {
         if (imag) {
           blocks = write ? launch_p_seg<T, true, true, true, true>(seg, a, h->work, h->pdl_now)
                         : launch_p_seg<T, true, true, false, true>(seg, a, h->work, h->pdl_now);
@@ -548,8 +569,9 @@ int run_observables_t(gp_handle* h, double* dens_dev, double* sums_out = nullptr
   }
   if (h->geom == 1) {
     a.gx = (const obs_r<T>*)h->gw_o;
-    a.odd0 = 1;
+    a.x0 = 1;
   }
+  if (h->geom == 2) a.x0 = 2;
   a.density = dens_dev;
   a.partials = h->partials;
   a.counter = h->counter;

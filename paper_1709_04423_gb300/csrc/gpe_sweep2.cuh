@@ -92,6 +92,16 @@ struct Sweep2Args {
   const T* w_axis;
   const T* w_a; const T* w_b;
   double* parts_out;
+  // rho axis of a circular or axial trap (x sweeps with VAR): the matrix is
+  // not symmetric -- row k of T is (-(1 - h_k), 2, -(1 + h_k)) -- so the
+  // forward recurrence is e_k = alpha_k e_{k-1} + vbf_k lapv_k with alpha_k =
+  // r (1 - h_k) m_k, vbf_k = 2 r m_k and lapv_k = 2 p_k - (1 - h_k) p_{k-1} -
+  // (1 + h_k) p_{k+1} (vh_k = (1 - h_k, 1 + h_k)), and the backward one is
+  // z_k = e_k + vab_k z_{k+1} with vab_k = r (1 + h_k) m_k; gf / gb and the
+  // carry tables are the segment products of alpha / vab.
+  const c2_t<T>* vab;
+  const c2_t<T>* vbf;
+  const c2_t<T>* vh;
 };
 
 // Sub-step N at one point: p <- F exp(-i a) p (real time) or F exp(-a) p
@@ -99,17 +109,31 @@ struct Sweep2Args {
 // potential factor and a = dt g |p|^2.  For |a| < 1/8 the exponential of the
 // nonlinear part is its Taylor series (sin to a^11, cos to a^12, exp to
 // a^13): the first omitted term is below 1.2e-21 relative, far under FP64
-// rounding; larger |a| takes the library sincos/exp.
+// rounding; larger |a| takes the library sincos/exp.  The multiply-adds are
+// spelled out (Horner steps as fma, the products as cmul), so that the
+// rounding does not depend on how the compiler contracts the expression in a
+// given kernel: the batched and single-grid sweeps agree bit for bit.
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
-  const T a = dtg * (p.x * p.x + p.y * p.y);
+  const T a = dtg * fma(p.x, p.x, p.y * p.y);
   if (IMAG) {
     T e;
     if (fabs(a) < T(0.125)) {
       const T m = -a;
-      e = T(1) + m * (T(1) + m * (T(1.0 / 2) + m * (T(1.0 / 6) + m * (T(1.0 / 24) + m * (T(1.0 / 120) +
-          m * (T(1.0 / 720) + m * (T(1.0 / 5040) + m * (T(1.0 / 40320) + m * (T(1.0 / 362880) +
-          m * (T(1.0 / 3628800) + m * (T(1.0 / 39916800) + m * (T(1.0 / 479001600) + m * T(1.0 / 6227020800.0)))))))))))));
+      T t = T(1.0 / 6227020800.0);
+      t = fma(m, t, T(1.0 / 479001600));
+      t = fma(m, t, T(1.0 / 39916800));
+      t = fma(m, t, T(1.0 / 3628800));
+      t = fma(m, t, T(1.0 / 362880));
+      t = fma(m, t, T(1.0 / 40320));
+      t = fma(m, t, T(1.0 / 5040));
+      t = fma(m, t, T(1.0 / 720));
+      t = fma(m, t, T(1.0 / 120));
+      t = fma(m, t, T(1.0 / 24));
+      t = fma(m, t, T(1.0 / 6));
+      t = fma(m, t, T(1.0 / 2));
+      t = fma(m, t, T(1));
+      e = fma(m, t, T(1));
     } else {
       e = exp(-a);
     }
@@ -119,16 +143,25 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
     T sn, cs;
     if (fabs(a) < T(0.125)) {
       const T a2 = a * a;
-      sn = a * (T(1) + a2 * (T(-1.0 / 6) + a2 * (T(1.0 / 120) + a2 * (T(-1.0 / 5040) + a2 * (T(1.0 / 362880) +
-               a2 * T(-1.0 / 39916800))))));
-      cs = T(1) + a2 * (T(-1.0 / 2) + a2 * (T(1.0 / 24) + a2 * (T(-1.0 / 720) + a2 * (T(1.0 / 40320) +
-               a2 * (T(-1.0 / 3628800) + a2 * T(1.0 / 479001600))))));
+      T s = T(-1.0 / 39916800);
+      s = fma(a2, s, T(1.0 / 362880));
+      s = fma(a2, s, T(-1.0 / 5040));
+      s = fma(a2, s, T(1.0 / 120));
+      s = fma(a2, s, T(-1.0 / 6));
+      sn = a * fma(a2, s, T(1));
+      T c = T(1.0 / 479001600);
+      c = fma(a2, c, T(-1.0 / 3628800));
+      c = fma(a2, c, T(1.0 / 40320));
+      c = fma(a2, c, T(-1.0 / 720));
+      c = fma(a2, c, T(1.0 / 24));
+      c = fma(a2, c, T(-1.0 / 2));
+      cs = fma(a2, c, T(1));
     } else {
       sincos(a, &sn, &cs);
     }
     // w = F exp(-i a) = (cs F.x + sn F.y) + i (cs F.y - sn F.x); return w p
-    const c2_t<T> w = mk<T>(cs * F.x + sn * F.y, cs * F.y - sn * F.x);
-    return mk<T>(w.x * p.x - w.y * p.y, w.x * p.y + w.y * p.x);
+    const c2_t<T> w = mk<T>(fma(cs, F.x, sn * F.y), fma(cs, F.y, -(sn * F.x)));
+    return cmul<T>(w, p);
   }
 }
 
@@ -266,21 +299,42 @@ __device__ __forceinline__ T neg2lap(T l, T r, T p) {
   else return fma(T(4), p, T(-2) * (l + r));
 }
 
+// 2 p - hl l - hr r, the stencil of a rho row (VAR)
+template <typename T>
+__device__ __forceinline__ T lapv(T l, T r, T p, T hl, T hr) {
+  if constexpr (is_df<T>::value) return df_scale(p, 2.f) - (hl * l + hr * r);
+  else return fma(T(2), p, -fma(hl, l, hr * r));
+}
+
+// One forward step of the VAR recurrence at interior point k.
+template <typename T, bool IMAG>
+__device__ __forceinline__ c2_t<T> var_forward(c2_t<T> prev, c2_t<T> left, c2_t<T> mid, c2_t<T> right,
+                                               const c2_t<T>* alpha, const c2_t<T>* vbf, const c2_t<T>* vh, int k) {
+  const c2_t<T> h = vh[k];
+  const c2_t<T> lv = mk<T>(lapv(left.x, right.x, mid.x, h.x, h.y), lapv(left.y, right.y, mid.y, h.x, h.y));
+  return cf_fma<T, IMAG>(alpha[k], prev, cf_mul<T, IMAG>(vbf[k], lv));
+}
+
 // Segment-local passes over SEG registers.  k0 = first interior index of the
 // segment; points with k > M are padding (p = 0 there).
-template <typename T, bool IMAG, int SEG>
+template <typename T, bool IMAG, int SEG, bool VAR = false>
 __device__ __forceinline__ void local_forward(const c2_t<T> (&p)[SEG], c2_t<T> (&e)[SEG], c2_t<T> pl, c2_t<T> pr,
-                                              const c2_t<T>* alpha, int k0, int M) {
+                                              const c2_t<T>* alpha, int k0, int M, const c2_t<T>* vbf = nullptr,
+                                              const c2_t<T>* vh = nullptr) {
   c2_t<T> prev = mk<T>(0, 0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
     const c2_t<T> left = j == 0 ? pl : p[j - 1];
     const c2_t<T> right = j == SEG - 1 ? pr : p[j + 1];
-    // t = e_{k-1} - 2 lap_k,  lap_k = left - 2 p_k + right
-    const c2_t<T> t = mk<T>(prev.x + neg2lap(left.x, right.x, p[j].x), prev.y + neg2lap(left.y, right.y, p[j].y));
     c2_t<T> v = mk<T>(0, 0);
-    if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
+    if constexpr (VAR) {
+      if (k <= M) v = var_forward<T, IMAG>(prev, left, p[j], right, alpha, vbf, vh, k);
+    } else {
+      // t = e_{k-1} - 2 lap_k,  lap_k = left - 2 p_k + right
+      const c2_t<T> t = mk<T>(prev.x + neg2lap(left.x, right.x, p[j].x), prev.y + neg2lap(left.y, right.y, p[j].y));
+      if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
+    }
     e[j] = v;
     prev = v;
   }
@@ -311,17 +365,22 @@ __device__ __forceinline__ void load_coefs(const Sweep2Args<T>& A, c2_t<T>* sc, 
 
 // Forward pass over a segment whose points are fetched one at a time by
 // getp(k) (0 outside 1..M), so the input segment need not sit in registers.
-template <typename T, bool IMAG, int SEG, typename GetP>
-__device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], const c2_t<T>* alpha, int k0, int M) {
+template <typename T, bool IMAG, int SEG, bool VAR = false, typename GetP>
+__device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], const c2_t<T>* alpha, int k0, int M,
+                                               const c2_t<T>* vbf = nullptr, const c2_t<T>* vh = nullptr) {
   using c2 = c2_t<T>;
   c2 pm = getp(k0 - 1), pc = getp(k0), prev = mk<T>(0, 0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
     const c2 pn = getp(k + 1);
-    const c2 t = mk<T>(prev.x + neg2lap(pm.x, pn.x, pc.x), prev.y + neg2lap(pm.y, pn.y, pc.y));
     c2 v = mk<T>(0, 0);
-    if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
+    if constexpr (VAR) {
+      if (k <= M) v = var_forward<T, IMAG>(prev, pm, pc, pn, alpha, vbf, vh, k);
+    } else {
+      const c2 t = mk<T>(prev.x + neg2lap(pm.x, pn.x, pc.x), prev.y + neg2lap(pm.y, pn.y, pc.y));
+      if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
+    }
     e[j] = v;
     prev = v;
     pm = pc;
@@ -332,10 +391,12 @@ __device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], con
 // Completes the segment of thread (lane, warp s) of a block whose lines run
 // one per lane and whose segments run one per warp: on entry z holds the
 // segment-local forward values e^ (zero carry-in); on exit the increment z_k.
-// Two block barriers; every thread of the block must call it.
+// Two block barriers; every thread of the block must call it.  vab: the
+// backward coefficients of a rho axis (VAR), else those of sc.
 template <typename T, bool IMAG, int SEG>
 __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc, int n, c2_t<T> (*cf)[33],
-                                            c2_t<T> (*cb)[33], int s, int nseg, int lane) {
+                                            c2_t<T> (*cb)[33], int s, int nseg, int lane,
+                                            const c2_t<T>* vab = nullptr) {
   using c2 = c2_t<T>;
   const int M = n - 2, k0 = 1 + s * SEG;
   const c2* al = sc;
@@ -357,7 +418,7 @@ __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc
     const int k = k0 + j;
     if (k <= M) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
   }
-  local_backward<T, IMAG, SEG>(z, al, k0, M);
+  local_backward<T, IMAG, SEG>(z, vab ? vab : al, k0, M);
   cb[s][lane] = z[0];
   __syncthreads();
   c2 Zin = mk<T>(0, 0);
@@ -504,7 +565,8 @@ constexpr int kTilePitch = 33;
 // and G.nlines counts real lines; N is applied to each real line with its own
 // density and potential, and with real coefficients the complex solve of a
 // column is the two real solves.
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
+// VAR: the rho axis of an axial trap (see Sweep2Args::vab).
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false, bool VAR = false>
 __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
                                             c2_t<T> (*cb)[33], double* red_smem) {
   static_assert(!(RL && (LAST || is_df<T>::value || !IMAG)), "packed real lines: imaginary-time x sweeps of 2d/3d");
@@ -652,9 +714,10 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   // ---- segments: lane = line, warp = segment; the input stays in the tile
   const int k0 = 1 + s * SEG;
   c2 z[SEG];
-  stream_forward<T, IMAG, SEG>([&](int k) { return (k >= 1 && k <= M) ? tile[k * kTilePitch + lane] : mk<T>(0, 0); },
-                               z, sc, k0, M);
-  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
+  stream_forward<T, IMAG, SEG, VAR>(
+      [&](int k) { return (k >= 1 && k <= M) ? tile[k * kTilePitch + lane] : mk<T>(0, 0); }, z, sc, k0, M, A.vbf,
+      A.vh);
+  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane, VAR ? A.vab : nullptr);
   T tacc = T(0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
@@ -688,12 +751,12 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   finish_norm<T, LAST>(nval, A.parts_out);
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false>
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false, bool VAR = false>
 __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
   extern __shared__ __align__(16) unsigned char tsmem_raw[];
   __shared__ c2_t<T> cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
-  tsweep_body<T, IMAG, FIRST, LAST, SEG, RL>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(tsmem_raw), cf, cb,
+  tsweep_body<T, IMAG, FIRST, LAST, SEG, RL, VAR>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(tsmem_raw), cf, cb,
                                          red_smem);
 }
 
@@ -701,7 +764,8 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
 // One warp per line; lane j owns interior points k = 1 + j*SEG .. (j+1)*SEG;
 // carries by a Kogge-Stone affine scan over shuffles.
 // Body shared with the batched kernels: each warp takes line L.
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+// VAR: the rho axis of a circular or axial trap (see Sweep2Args::vab).
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool VAR = false>
 __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, double* red_smem) {
   using c2 = c2_t<T>;
   const LineGeom& G = A.geom;
@@ -753,7 +817,7 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
     c2 pr = shfl_down2<T>(p[0], 1);
     if (lane == 0) pl = mk<T>(0, 0);
     if (lane == 31) pr = mk<T>(0, 0);
-    local_forward<T, IMAG, SEG>(p, e, pl, pr, A.alpha, k0, M);
+    local_forward<T, IMAG, SEG, VAR>(p, e, pl, pr, A.alpha, k0, M, A.vbf, A.vh);
     const int kend = k0 + SEG - 1;
     c2 Pm = (k0 <= M) ? __ldg(&A.gf[min(kend, M)]) : mk<T>(1, 0);
     c2 Bc = e[SEG - 1];
@@ -774,7 +838,7 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       const int k = k0 + j;
       if (k <= M) e[j] = cf_fma<T, IMAG>(__ldg(&A.gf[k]), Ein, e[j]);
     }
-    local_backward<T, IMAG, SEG>(e, A.alpha, k0, M);
+    local_backward<T, IMAG, SEG>(e, VAR ? A.vab : A.alpha, k0, M);
     c2 Qm = (k0 <= M) ? __ldg(&A.gb[k0]) : mk<T>(1, 0);
     c2 Dc = e[0];
 #pragma unroll
@@ -805,10 +869,10 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
   finish_norm<T, LAST>(nval, A.parts_out);
 }
 
-template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG>
+template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool VAR = false>
 __global__ void __launch_bounds__(128) xsweep_kernel(Sweep2Args<T> A) {
   __shared__ double red_smem[32];
-  xsweep_body<T, IMAG, FIRST, LAST, SEG>(A, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), red_smem);
+  xsweep_body<T, IMAG, FIRST, LAST, SEG, VAR>(A, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), red_smem);
 }
 
 }  // namespace gpe

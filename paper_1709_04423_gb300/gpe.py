@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gp_batch_init", "gp_batch_set_state", "gp_batch_get_state", "gp_batch_step_real", "gp_batch_observables",
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
-    "gp_init_spherical", "gp_set_splitting", "gp_set_real_state",
+    "gp_init_spherical", "gp_set_splitting", "gp_set_real_state", "gp_init_circular", "gp_init_axial",
 )
 
 
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.gp_get_shapes.argtypes = [_vp, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.gp_reduced_density.argtypes = [_vp, I, _vp, I]
     lib.gp_init_spherical.argtypes = [ctypes.POINTER(_vp), I, D, D, D, D, I, _vp]
+    lib.gp_init_circular.argtypes = [ctypes.POINTER(_vp), I, D, D, D, D, I, _vp]
+    lib.gp_init_axial.argtypes = [ctypes.POINTER(_vp), I, I, D, D, D, D, D, D, I, _vp]
     lib.gp_step_series.argtypes = [_vp, I, L, I, _vp, I]
     lib.gp_adjoint_forward.argtypes = [_vp, L, I]
     lib.gp_adjoint_backward.argtypes = [_vp, _vp, I, _vp, I, ctypes.POINTER(D), _vp]
@@ -141,6 +143,20 @@ def gp_init_spherical(n, dr, dt, nu, g, prec=GP_F64, stream=None):
     h = _vp()
     _check(load().gp_init_spherical(ctypes.byref(h), int(n), float(dr), float(dt), float(nu), float(g), int(prec),
                                     stream))
+    return h
+
+
+def gp_init_circular(n, drho, dt, nu, g, prec=GP_F64, stream=None):
+    h = _vp()
+    _check(load().gp_init_circular(ctypes.byref(h), int(n), float(drho), float(dt), float(nu), float(g), int(prec),
+                                   stream))
+    return h
+
+
+def gp_init_axial(n_rho, n_z, drho, dz, dt, nu, lam, g, prec=GP_F64, stream=None):
+    h = _vp()
+    _check(load().gp_init_axial(ctypes.byref(h), int(n_rho), int(n_z), float(drho), float(dz), float(dt), float(nu),
+                                float(lam), float(g), int(prec), stream))
     return h
 
 
@@ -318,10 +334,13 @@ class Propagator:
     """
 
     def __init__(self, dim, n, dx, dt, nkl=(1.0, 1.0, 1.0), g=0.0, precision="f64", stream=None,
-                 spherical=False):
+                 spherical=False, axisym=False):
         """``spherical=True``: a spherically symmetric 3d trap (dim 1, n radial
         points, dx = (dr,), nkl = (nu,)); the state is u = sqrt(4 pi) r phi on
-        r_i = i dr (see gp_init_spherical)."""
+        r_i = i dr (see gp_init_spherical).  ``axisym=True``: a circularly
+        symmetric 2d trap (dim 1: n = (n_rho,)) or an axially symmetric 3d
+        trap (dim 2: n = (n_rho, n_z), dx = (drho, dz), nkl = (nu, lambda)) on
+        rho_i = (i - 1/2) drho (see gp_init_circular / gp_init_axial)."""
         import torch
         self.torch = torch
         self.dim = int(dim)
@@ -340,6 +359,14 @@ class Propagator:
             if self.dim != 1:
                 raise ValueError("the spherical trap is a 1d radial problem")
             self.h = gp_init_spherical(n[0], dx[0], dt, nkl[0], g, PRECISIONS[precision], stream.cuda_stream)
+        elif axisym:
+            if self.dim == 1:
+                self.h = gp_init_circular(n[0], dx[0], dt, nkl[0], g, PRECISIONS[precision], stream.cuda_stream)
+            elif self.dim == 2:
+                self.h = gp_init_axial(n[0], n[1], dx[0], dx[1], dt, nkl[0], nkl[1], g, PRECISIONS[precision],
+                                       stream.cuda_stream)
+            else:
+                raise ValueError("the circular (dim 1) and axial (dim 2) traps have one or two axes")
         else:
             self.h = gp_init(dim, n, dx, dt, nkl, g, PRECISIONS[precision], stream.cuda_stream)
 
