@@ -173,7 +173,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_rate(target_s=10.0, max_steps=40):
+def oracle_rate(target_s=12.0, max_steps=2000):
     """Oracle (FP64, C, OpenMP over lines) on the host cores: imaginary-time
     steps of the same workload, as many as fit in about target_s seconds."""
     import numpy as np
@@ -209,7 +209,7 @@ def run_reference(args):
     gr = O.Grid(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"])
     phi = inputs.gaussian_state(w["dim"], w["n"], w["dx"], w["nkl"], seed=w["seed"], noise=1e-3)
     np_ = int(np.prod(w["n"]))
-    per = 2  # imaginary-time steps of the oracle per bench step
+    per = 40  # imaginary-time steps of the oracle per bench step (~0.6 s on 16 Grace cores)
     for _ in range(args.warmup):
         phi = O.run(gr, phi, True, per)
     t0 = time.perf_counter()
@@ -475,6 +475,50 @@ def run_ours(args):
             for prec in sres:
                 sres[prec]["mu_diff_vs_f64"] = abs(smu[prec]["mu"] - smu["f64"]["mu"])
 
+    # ---- circularly symmetric 2d trap (513 rho points, drho = 0.02, g = 100,
+    # dt = 1e-4) and axially symmetric 3d trap (rho x z = 256 x 512, drho = dz
+    # = 0.04, nu = 1, lambda = 2, g = 100, dt = 5e-4), imaginary time, every
+    # form; mu after 20000 / 4000 steps against the FP64 form's
+    ares_sym = {}
+    if not args.no_spherical:
+        cases = {"circular": (1, [513], [0.02], [1.0], 1e-4, 20000, 2000),
+                 "axial": (2, [256, 512], [0.04, 0.04], [1.0, 2.0], 5e-4, 4000, 200)}
+        for name, (cd, cn, cdx, cnkl, cdt, cmu_steps, cblock) in cases.items():
+            rho = np.arange(cn[0]) * cdx[0] - 0.5 * cdx[0]
+            if cd == 1:
+                cphi = np.exp(-0.3 * rho ** 2)
+            else:
+                zz = inputs.axis_coords(cn[1], cdx[1])
+                cphi = np.exp(-0.3 * (rho[None, :] ** 2 + 2.0 * zz[:, None] ** 2))
+            cphi = torch.tensor(cphi.astype(np.complex128), device="cuda")
+            cmu, cres = {}, {}
+            for prec in forms_sel:
+                with torch.cuda.stream(stream):
+                    q = gpe.Propagator(cd, cn, cdx, cdt, cnkl, 100.0, precision=prec, stream=stream, axisym=True)
+                    q.set_state(cphi)
+                    q.step_imag(cmu_steps)
+                    cmu[prec] = q.observables()
+                    q.set_state(cphi)
+                    for _ in range(args.warmup):
+                        q.step_imag(cblock)
+                    barrier()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        q.step_imag(cblock)
+                    e1.record(stream)
+                    barrier()
+                    st = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+                    q.close()
+                npts = int(np.prod(cn))
+                cres[prec] = {"value": world * args.steps * cblock * npts / st,
+                              "us_per_step": 1e6 * st / (args.steps * cblock),
+                              "mu": cmu[prec]["mu"], "rms_rho": cmu[prec]["rms_x"]}
+            if "f64" in cmu:
+                for prec in cres:
+                    cres[prec]["mu_diff_vs_f64"] = abs(cmu[prec]["mu"] - cmu["f64"]["mu"])
+            ares_sym[name] = cres
+
     # ---- real state (imaginary-time maps keep the real input real): the
     # headline workload and loop with the state held as np real values;
     # mu after the full job against the complex FP64 form's
@@ -631,7 +675,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
                               "batched": bres or None, "spherical": sres or None,
-                              "strang": stres or None, "real": rres or None}), flush=True)
+                              "axisym": ares_sym or None, "strang": stres or None, "real": rres or None}),
+                  flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -742,6 +787,10 @@ def run_ours(args):
             "spherical": ({"workload": "spherically symmetric 3d trap as the radial problem for u = sqrt(4 pi) r phi: "
                                        "513 points on [0, 10.24], dt=1e-4, nu=1, g=100, imaginary time; one 1d line, "
                                        "launch-latency bound", **sres} if sres else None),
+            "axisym": ({"workload": "circularly symmetric 2d trap (513 rho points, drho=0.02, nu=1, g=100, "
+                                    "dt=1e-4) and axially symmetric 3d trap (rho x z = 256 x 512, drho=dz=0.04, nu=1, "
+                                    "lambda=2, g=100, dt=5e-4), imaginary time; rho_i = (i - 1/2) drho",
+                        **ares_sym} if ares_sym else None),
             "real_state": ({"workload": "the headline workload (its input is real) with the state held as np real "
                                         "values: imaginary-time maps keep it real; same loop, observables per step, "
                                         "L2 flushed", **rres} if rres else None),

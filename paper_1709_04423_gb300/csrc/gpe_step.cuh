@@ -63,7 +63,7 @@ unsigned launch_x_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl)
 }
 
 // ---- segmented y/z sweep (registers, coefficients in shared memory)
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false, bool CLOSE = false>
 unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int M = a.geom.n - 2;
   const int nseg = (M + SEG - 1) / SEG;
@@ -71,27 +71,30 @@ unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
   static bool attr_set = false;  // static + dynamic shared memory can pass 48 KB
   if (!attr_set) {
-    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         64 * 1024);
+    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr_set = true;
   }
-  launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP>, dim3(blocks), dim3(32 * nseg), smem, s, a);
+  launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
 }
 
 // keep = 1: input segment in registers (only for short segments); 0: streamed
-template <typename T, bool IMAG, bool LAST, bool RP = false>
+template <typename T, bool IMAG, bool LAST, bool RP = false, bool CLOSE = false>
 unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const bool k = keep && seg * (int)sizeof(T) <= 64;
   switch (seg) {
     case 4:
-      return k ? launch_c<T, IMAG, LAST, 4, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 4, false, RP>(a, s, pdl);
+      return k ? launch_c<T, IMAG, LAST, 4, true, RP, CLOSE>(a, s, pdl)
+               : launch_c<T, IMAG, LAST, 4, false, RP, CLOSE>(a, s, pdl);
     case 8:
-      return k ? launch_c<T, IMAG, LAST, 8, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 8, false, RP>(a, s, pdl);
+      return k ? launch_c<T, IMAG, LAST, 8, true, RP, CLOSE>(a, s, pdl)
+               : launch_c<T, IMAG, LAST, 8, false, RP, CLOSE>(a, s, pdl);
     case 16:
-      return k ? launch_c<T, IMAG, LAST, 16, true, RP>(a, s, pdl) : launch_c<T, IMAG, LAST, 16, false, RP>(a, s, pdl);
-    default: return launch_c<T, IMAG, LAST, 32, false, RP>(a, s, pdl);
+      return k ? launch_c<T, IMAG, LAST, 16, true, RP, CLOSE>(a, s, pdl)
+               : launch_c<T, IMAG, LAST, 16, false, RP, CLOSE>(a, s, pdl);
+    default: return launch_c<T, IMAG, LAST, 32, false, RP, CLOSE>(a, s, pdl);
   }
 }
 
@@ -220,13 +223,22 @@ struct StepForm {
   bool close = true;      // N(dt/2) after the last sweep
 };
 
+// Whether an imaginary-time Strang step applies its closing N(dt/2) inside
+// its last sweep (a segmented y/z sweep of a 2d/3d grid) rather than in
+// strang_phase_kernel.
+inline bool strang_close_fused(const gp_handle* h, bool imag) {
+  return imag && h->strang && h->dim > 1 && h->seg_c > 0 && !h->pipe_c;
+}
+
+// Returns whether the sweep applied the step's closing N(dt/2).
 template <typename T>
-void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr, bool half_open = true) {
+bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src = nullptr, bool half_open = true) {
   const bool first = d == 0, last = d == h->dim - 1;
   const int mode = imag ? MODE_IMAG : MODE_REAL;
   const int seg = d == 0 ? h->seg_x : h->seg_c;
+  const bool fuse_close = last && d > 0 && strang_close_fused(h, imag);
   // with the Strang splitting the norm is taken after the closing N(dt/2)
-  const bool read = imag && first && ns.rd >= 0, write = imag && last && !h->strang;
+  const bool read = imag && first && ns.rd >= 0, write = imag && last && (!h->strang || fuse_close);
   const double* parts_in = read ? h->parts[ns.rd] : nullptr;
   double* parts_out = write ? h->parts[ns.wr] : nullptr;
   unsigned blocks = 0;
@@ -241,7 +253,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
-    set_phase_args<T>(h, imag, h->strang && half_open, a);
+    set_phase_args<T>(h, imag, (h->strang && half_open) || fuse_close, a);
     a.parts_in = parts_in;
     a.nparts_in = h->parts_n;
     a.parts_wscale = h->parts_ws;
@@ -306,7 +318,9 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
         blocks = launch_x_seg<T, false, true, false>(seg, a, h->work, h->pdl_now);
       }
     } else {
-      if (imag) {
+      if (fuse_close) {
+        blocks = launch_c_seg<T, true, true, false, true>(seg, h->keep_c, a, h->work, h->pdl_now);
+      } else if (imag) {
         blocks = write ? launch_c_seg<T, true, true>(seg, h->keep_c, a, h->work, h->pdl_now)
                       : launch_c_seg<T, true, false>(seg, h->keep_c, a, h->work, h->pdl_now);
       } else {
@@ -317,10 +331,10 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
       h->parts_n = (int)blocks;
       h->parts_ws = h->wscale;  // Simpson coefficients: the factor prod dx/3 is still to come
     }
-    return;
+    return fuse_close;
   }
   if constexpr (is_df<T>::value) {
-    return;  // the double-float form needs the segmented kernels (checked at gp_init)
+    return false;  // the double-float form needs the segmented kernels (checked at gp_init)
   } else {
   SweepArgs<T> a;
   std::memset(&a, 0, sizeof(a));
@@ -350,6 +364,7 @@ void enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     h->parts_n = (int)blocks;
     h->parts_ws = 1.0;  // FP64 Simpson weights: the sums are complete
   }
+  return false;
   }
 }
 
@@ -432,15 +447,16 @@ void enqueue_strang_close(gp_handle* h, bool imag, NormSlots ns) {
 template <typename T>
 void enqueue_step(gp_handle* h, bool imag, NormSlots ns, cudaEvent_t* ev = nullptr, const void* src = nullptr,
                   StepForm f = StepForm{}) {
+  bool closed = false;
   for (int d = 0; d < h->dim; ++d) {
     if (ev) cudaEventRecord(ev[2 * d], h->work);
     if (h->real_mode)
       enqueue_sweep_real<T>(h, ns, d);  // imaginary time only
     else
-      enqueue_sweep<T>(h, imag, ns, d, src, f.half_open);
+      closed = enqueue_sweep<T>(h, imag, ns, d, src, f.half_open) || closed;
     if (ev) cudaEventRecord(ev[2 * d + 1], h->work);
   }
-  if (h->strang && f.close) enqueue_strang_close<T>(h, imag, ns);
+  if (h->strang && f.close && !closed) enqueue_strang_close<T>(h, imag, ns);
 }
 
 inline NormSlots slots_of_step(bool imag, long t) {
@@ -504,7 +520,8 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
     }
     for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
       GP_CUDA(cudaGraphLaunch(ge, h->work));
-      count_launch((unsigned long long)kGraphSteps * (h->dim + (next_f.close && h->strang ? 1 : 0)));
+      count_launch((unsigned long long)kGraphSteps *
+                   (h->dim + (next_f.close && h->strang && !strang_close_fused(h, imag) ? 1 : 0)));
     }
   }
   for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t), nullptr, nullptr, next_f);

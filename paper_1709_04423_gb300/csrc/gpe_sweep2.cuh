@@ -436,6 +436,21 @@ __device__ __forceinline__ int line_base32(const LineGeom& g, int L) {
   return L;
 }
 
+// The closing half sub-step N(dt/2) of a Strang step at grid point q = (i, j,
+// kz) (A's sub-step fields hold the dt/2 factors; no weight on the nonlinear
+// term: 2d/3d grids).  The arithmetic of strang_phase_kernel.
+template <typename T, bool IMAG>
+__device__ __forceinline__ c2_t<T> half_phase(const Sweep2Args<T>& A, c2_t<T> w, long q, int i, int j, int kz) {
+  if constexpr (is_df<T>::value) {
+    return phase_df<IMAG>(w, A, q, i, j + A.geom.ny * kz, A.dtg);
+  } else if constexpr (std::is_same<T, double>::value) {
+    const c2_t<T> F = A.fV ? A.fV[q] : fac_mul<T, IMAG>(A.fx[i], fac_mul<T, IMAG>(A.fy[j], A.fz[kz]));
+    return phase_N<T, IMAG>(w, F, A.dtg);
+  } else {
+    return phase_direct<T, IMAG>(w, A.V ? A.V[q] : A.vx[i] + (A.vy[j] + A.vz[kz]), A.dt, A.g);
+  }
+}
+
 // Norm of the block's output: the per-thread values (in the state
 // precision) are summed over the block in the state precision -- a tree of at
 // most log2(blockDim) levels -- and stored as the block's FP64 sum; the next
@@ -469,7 +484,12 @@ __device__ __forceinline__ void finish_norm(T tval, double* parts_out) {
 // a line holds the real values at x = 2i' (re) and 2i' + 1 (im); with real
 // coefficients one complex sweep is the two real sweeps, and only the norm
 // (LAST) needs the two x weights w_a[2i'], w_a[2i' + 1] apart.
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP = (SEG * sizeof(T) <= 64), bool RP = false>
+// CLOSE (the last sweep of a Strang step): the closing sub-step N(dt/2) --
+// A's sub-step fields hold the dt/2 factors -- is applied to every output
+// point before it is stored and enters the norm, the same arithmetic as
+// strang_phase_kernel's, so the step needs no extra pass over the state.
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP = (SEG * sizeof(T) <= 64), bool RP = false,
+          bool CLOSE = false>
 __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2_t<T>* sc, c2_t<T> (*cf)[33],
                                               c2_t<T> (*cb)[33], double* red_smem) {
   using c2 = c2_t<T>;
@@ -512,6 +532,9 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   if (active) {
     const T* w = A.w_axis;
     T tacc = T(0), tim = T(0);
+    // CLOSE: the line's x index and its other fixed index (z for y lines, y for z lines)
+    const int ci = L % G.nx, cf2 = L / G.nx;
+    const long qb = line - A.psi;
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
@@ -519,7 +542,11 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
         c2 pk;
         if constexpr (KEEP) pk = p[j];
         else pk = __ldcg(&line[k * st]);
-        const c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
+        c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
+        if constexpr (CLOSE) {
+          const int jy = G.axis == 2 ? cf2 : k, kz = G.axis == 2 ? k : cf2;
+          u = half_phase<T, IMAG>(A, u, qb + (long)k * st, ci, jy, kz);
+        }
         line[k * st] = u;
         if constexpr (LAST && RP) {
           tacc += w[k] * (u.x * u.x);
@@ -543,13 +570,13 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   finish_norm<T, LAST>(nval, A.parts_out);
 }
 
-template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false>
+template <typename T, bool IMAG, bool LAST, int SEG, bool KEEP, bool RP = false, bool CLOSE = false>
 __global__ void __launch_bounds__(512) colsweep_kernel(Sweep2Args<T> A) {
   extern __shared__ __align__(16) unsigned char csmem_raw[];
   __shared__ c2_t<T> cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
-  colsweep_body<T, IMAG, LAST, SEG, KEEP, RP>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf, cb,
-                                              red_smem);
+  colsweep_body<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>(A, blockIdx.x * 32, reinterpret_cast<c2_t<T>*>(csmem_raw), cf,
+                                                     cb, red_smem);
 }
 
 // ---------------------------------------------------------------- x sweep (2d/3d)

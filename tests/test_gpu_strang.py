@@ -226,3 +226,27 @@ def test_real_time_halves_merged(G, prec, tol):
     assert rel_l2(sb, ref) <= (1e-12 if prec != "f32" else 1e-5)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5), ("df64", 1e-12)])
+@pytest.mark.parametrize("env,fused", [({}, True), ({"GPE_KEEP": "0"}, True), ({"GPE_PIPE": "1"}, False)],
+                         ids=["keep", "streamed", "pipelined"])
+def test_imaginary_time_closing_half_fused_into_the_last_sweep(G, monkeypatch, env, fused, prec, tol):
+    """2d/3d imaginary time: the closing N(dt/2) runs inside the last y/z sweep
+    (one launch per sweep) or, for the pipelined y/z sweeps, in its own pass;
+    both against the oracle."""
+    if prec == "df64" and "GPE_PIPE" in env:
+        pytest.skip("no pipelined double-float sweeps")
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    dim, n, dx, nkl = 3, [40, 33, 24], [0.25, 0.3, 0.35], [1.0, 1.4, 1.8]
+    p, gr = make(G, dim, n, dx, 1e-3, nkl, 20.0, prec=prec)
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=13, noise=1e-3)
+    p.set_state(phi0)
+    l0 = G.gp_kernel_launches()
+    p.step_imag(40)
+    launches = G.gp_kernel_launches() - l0
+    assert launches == 40 * (dim + (0 if fused else 1)) + 1
+    ref = O.run(gr, phi0, True, 40)
+    assert rel_l2(p.get_state(device=False).astype(np.complex128), ref) <= tol
+    p.close()
