@@ -215,6 +215,23 @@ def test_full_size_128cube_two_steps(G, imag):
         p.close()
 
 
+def test_full_size_256cube_quench_two_steps(G):
+    """The 256^3 real-time quench grid (dx = 0.08, isotropic trap, g = 40, dt =
+    2e-4) in the shapes the benchmark's autotuner picks for it (the pipelined
+    y/z sweeps among the candidates): two real-time steps of every precision
+    form against the oracle."""
+    n, dx, nkl = [256] * 3, [0.08] * 3, [1.0] * 3
+    phi0 = I.gaussian_state(3, n, dx, nkl, seed=1711, noise=1e-3)
+    ref = O.run(O.Grid(3, n, dx, 2e-4, nkl, 40.0), phi0, False, 2)
+    for prec, tol in (("f64", 1e-13), ("f32", 2e-6), ("df64", 1e-13)):
+        p = G.Propagator(3, n, dx, 2e-4, nkl, 40.0, precision=prec)
+        p.autotune(imag=False, cache=False)
+        p.set_state(phi0)
+        p.step_real(2)
+        assert rel_l2(p.get_state(device=False).astype(np.complex128), ref) <= tol, (prec, p.shapes())
+        p.close()
+
+
 SHAPES = [
     {"GPE_SEG_X": "0", "GPE_SEG_YZ": "0"},                     # thread-per-line kernels
     {"GPE_TILE_X": "0"},                                       # warp-per-line x sweep
