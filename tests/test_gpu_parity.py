@@ -300,3 +300,39 @@ def test_autotune_picks_valid_shapes_and_keeps_parity(G, tmp_path, monkeypatch):
             G.gp_set_shapes(q.h, 1, 3, 8, 1)      # 3 is not a segment length
         p.close()
         q.close()
+
+
+EDGE_GRIDS = [
+    (1, [3], [0.4]), (1, [4], [0.4]), (1, [5], [0.4]),      # one, two, three interior points
+    (2, [3, 3], [0.4, 0.4]), (2, [3, 40], [0.4, 0.2]), (2, [40, 3], [0.2, 0.4]),
+    (3, [3, 4, 5], [0.4, 0.4, 0.4]), (3, [5, 3, 17], [0.4, 0.4, 0.3]),
+    (1, [514], [0.02]),                                     # longest segmented line (16 x 32)
+    (2, [514, 6], [0.02, 0.3]), (2, [6, 514], [0.3, 0.02]),
+    (1, [515], [0.02]),                                     # one point more: thread-per-line kernels
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
+@pytest.mark.parametrize("dim,n,dx", EDGE_GRIDS, ids=lambda v: str(v) if not isinstance(v, list) else "x".join(map(str, v)))
+def test_degenerate_and_boundary_sizes(G, dim, n, dx, prec):
+    """Grids with one interior point per axis up to the longest lines each
+    kernel family takes, imaginary and real time, against the oracle (the
+    double-float form refuses lines over 514 points)."""
+    nkl = [1.0, 1.3, 1.6][:dim]
+    if prec == "df64" and max(n) > 514:
+        with pytest.raises(G.GPError):
+            G.Propagator(dim, n, dx, 1e-3, nkl, 5.0, precision=prec)
+        return
+    phi0 = I.gaussian_state(dim, n, dx, nkl, seed=77, noise=1e-2)
+    tol = 2e-5 if prec == "f32" else 1e-12
+    for imag in (True, False):
+        p, gr = make(G, dim, n, dx, 1e-3, nkl, 5.0, prec=prec)
+        p.set_state(phi0)
+        (p.step_imag if imag else p.step_real)(20)
+        got = p.get_state(device=False).astype(np.complex128)
+        ref = O.run(gr, phi0, imag, 20)
+        if np.linalg.norm(ref) == 0:
+            assert np.linalg.norm(got) == 0
+        else:
+            assert rel_l2(got, ref) <= tol, (imag, rel_l2(got, ref))
+        p.close()
