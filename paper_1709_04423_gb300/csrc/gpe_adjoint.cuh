@@ -49,10 +49,9 @@ __global__ void __launch_bounds__(256) adjoint_phase_kernel(AdjPhaseArgs<T> A) {
     }
     const T dens = p.x * p.x + p.y * p.y;
     const T th = A.dt * (Vq + A.g * dens);
-    // rotations in the forward's form (rot_neg): cos th = 1 + cm1, cm1 = -2 sin^2(th/2)
-    T sh, ch;
-    sincos(T(0.5) * th, &sh, &ch);
-    const T sn = T(2) * (sh * ch), cm1 = T(-2) * (sh * sh);
+    // rotations with the forward's coefficients (rot_coefs): cos th = 1 + cm1
+    T sn, cm1;
+    rot_coefs<T>(th, sn, cm1);
     const c2_t<T> u = rot_neg<T>(p, th);                                // exp(-i th) p
     const T s = l.x * u.y - l.y * u.x;                                  // Im(conj(lam) u)
     const T ds = A.dt * s;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "gpe_df.cuh"
@@ -29,16 +30,32 @@ template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T>
 }
 
 // exp(-i th) p (FP32 and FP64 states), as p + ((c - 1) p + s (p.y, -p.x))
-// with c - 1 = -2 sin^2(th/2) and s = 2 sin(th/2) cos(th/2).  The rounded
+// with c - 1 = -2 sin^2(th/2) and s = 2 sin(th/2) cos(th/2) (or their series
+// for small FP32 angles, rot_coefs).  The rounded
 // pair (1 + (c - 1), s) has modulus 1 + O(th^2 eps); a rounded cos(th) next
 // to 1 would instead carry an error of up to half an ulp of 1 in the
 // modulus, the same at a point step after step (th changes slowly), so that
 // |phi| would drift linearly with the number of steps.  What remains is the
 // rounding of the final sums, which is unbiased.
+// s = sin th and cm1 = cos th - 1 (the coefficients of rot_neg).  FP32 with
+// |th| < 1/8: their Taylor series (s to th^7, cm1 to th^8; the first omitted
+// terms are below 1e-13 relative), else from the half angle.
+template <typename T> __device__ __forceinline__ void rot_coefs(T th, T& s, T& cm1) {
+  if (std::is_same<T, float>::value && fabs(th) < T(0.125)) {
+    const T t2 = th * th;
+    s = th * fma(t2, fma(t2, fma(t2, T(-1.0 / 5040), T(1.0 / 120)), T(-1.0 / 6)), T(1));
+    cm1 = t2 * fma(t2, fma(t2, fma(t2, T(1.0 / 40320), T(-1.0 / 720)), T(1.0 / 24)), T(-0.5));
+  } else {
+    T sh, ch;
+    sincos(T(0.5) * th, &sh, &ch);
+    s = T(2) * (sh * ch);
+    cm1 = T(-2) * (sh * sh);
+  }
+}
+
 template <typename T> __device__ __forceinline__ c2_t<T> rot_neg(c2_t<T> p, T th) {
-  T sh, ch;
-  sincos(T(0.5) * th, &sh, &ch);
-  const T s = T(2) * (sh * ch), cm1 = T(-2) * (sh * sh);
+  T s, cm1;
+  rot_coefs<T>(th, s, cm1);
   return mk<T>(p.x + fma(cm1, p.x, s * p.y), p.y + fma(cm1, p.y, -(s * p.x)));
 }
 
