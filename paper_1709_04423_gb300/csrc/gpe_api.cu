@@ -93,9 +93,10 @@ double axis_coord(int geom, int d, int n, double dx, int i) {
 // (-(1 - h_k), 2, -(1 + h_k)) with h_k = drho/(2 rho_k) = 1/(2k - 1) on
 // rho_k = (k - 1/2) drho.  Thomas factors of (1 + rT): m_k = 1/(b - a_k
 // c'_{k-1}) with a_k = -r(1 - h_k), c_k = -r(1 + h_k), c'_k = c_k m_k; the
-// increment form's forward recurrence e_k = af_k e_{k-1} + bf_k lapv_k and
+// increment form's forward recurrence e_k = af_k e_{k-1} + 2 r m_k lapv_k and
 // backward recurrence z_k = e_k + ab_k z_{k+1} have af_k = r(1 - h_k) m_k,
-// bf_k = 2 r m_k, ab_k = r(1 + h_k) m_k; hh_k = (1 - h_k, 1 + h_k).
+// ab_k = r(1 + h_k) m_k; the sweeps carry them at half scale, so bf_k =
+// r m_k (half of 2 r m_k, exactly); hh_k = (1 - h_k, 1 + h_k).
 static void rho_factors(int n, double beta, bool imag, std::vector<cd>& af, std::vector<cd>& ab, std::vector<cd>& bf,
                  std::vector<cd>& hh) {
   af.assign(n, cd(0, 0));
@@ -111,7 +112,7 @@ static void rho_factors(int n, double beta, bool imag, std::vector<cd>& af, std:
     const cd m = 1.0 / (b - a * cprev);
     af[k] = r * (1.0 - h) * m;
     ab[k] = r * (1.0 + h) * m;
-    bf[k] = 2.0 * r * m;
+    bf[k] = r * m;
     hh[k] = cd(1.0 - h, 1.0 + h);
     cprev = c * m;
   }

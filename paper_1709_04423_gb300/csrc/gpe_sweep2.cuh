@@ -14,7 +14,13 @@
 // first-order recurrences
 //     forward   e_k = alpha_k (e_{k-1} - 2 lap_k),        e_0 = 0
 //     backward  z_k = e_k + alpha_k z_{k+1},              z_{M+1} = 0
-// over the interior points k = 1..M = n-2.
+// over the interior points k = 1..M = n-2.  The kernels carry both at half
+// scale, e~ = e/2 and z~ = z/2:
+//     e~_k = alpha_k (e~_{k-1} + 2 p_k - p_{k-1} - p_{k+1}),   u_k = p_k - 2 z~_k,
+// which saves a multiplication per point and component; scaling by 2
+// commutes with rounding in binary floating point (away from overflow and
+// subnormals), so every value is exactly half the full-scale one and u is
+// bit for bit the same.
 //
 // Both recurrences are linear with time-invariant coefficients, so a line is
 // split into segments of SEG points, each run by its own thread with a zero
@@ -94,11 +100,12 @@ struct Sweep2Args {
   double* parts_out;
   // rho axis of a circular or axial trap (x sweeps with VAR): the matrix is
   // not symmetric -- row k of T is (-(1 - h_k), 2, -(1 + h_k)) -- so the
-  // forward recurrence is e_k = alpha_k e_{k-1} + vbf_k lapv_k with alpha_k =
-  // r (1 - h_k) m_k, vbf_k = 2 r m_k and lapv_k = 2 p_k - (1 - h_k) p_{k-1} -
-  // (1 + h_k) p_{k+1} (vh_k = (1 - h_k, 1 + h_k)), and the backward one is
-  // z_k = e_k + vab_k z_{k+1} with vab_k = r (1 + h_k) m_k; gf / gb and the
-  // carry tables are the segment products of alpha / vab.
+  // forward recurrence is e_k = alpha_k e_{k-1} + 2 r m_k lapv_k with alpha_k
+  // = r (1 - h_k) m_k and lapv_k = 2 p_k - (1 - h_k) p_{k-1} - (1 + h_k)
+  // p_{k+1} (vh_k = (1 - h_k, 1 + h_k)), carried at half scale like the
+  // symmetric one (vbf_k = r m_k), and the backward one is z_k = e_k + vab_k
+  // z_{k+1} with vab_k = r (1 + h_k) m_k; gf / gb and the carry tables are the
+  // segment products of alpha / vab.
   const c2_t<T>* vab;
   const c2_t<T>* vbf;
   const c2_t<T>* vh;
@@ -313,12 +320,19 @@ __device__ __forceinline__ c2_t<T> shfl_down2(c2_t<T> v, int o) {
   return mk<T>(shfl_down_t(v.x, o), shfl_down_t(v.y, o));
 }
 
-// 4 p - 2 (l + r) = -2 lap, the part of the forward step that does not
-// depend on the recurrence (the scalings by 2 and 4 are exact)
+// 2 p - (l + r) = -lap, the part of the half-scale forward step that does not
+// depend on the recurrence (exactly half of 4 p - 2 (l + r))
 template <typename T>
-__device__ __forceinline__ T neg2lap(T l, T r, T p) {
-  if constexpr (is_df<T>::value) return df_scale(p, 4.f) - df_scale(l + r, 2.f);
-  else return fma(T(4), p, T(-2) * (l + r));
+__device__ __forceinline__ T neg_lap(T l, T r, T p) {
+  if constexpr (is_df<T>::value) return df_scale(p, 2.f) - (l + r);
+  else return fma(T(2), p, -(l + r));
+}
+
+// u = p - 2 z~ (one rounding, the same as p - z at full scale)
+template <typename T>
+__device__ __forceinline__ c2_t<T> sub2(c2_t<T> p, c2_t<T> zh) {
+  if constexpr (is_df<T>::value) return mk<T>(p.x - df_scale(zh.x, 2.f), p.y - df_scale(zh.y, 2.f));
+  else return mk<T>(fma(T(-2), zh.x, p.x), fma(T(-2), zh.y, p.y));
 }
 
 // 2 p - hl l - hr r, the stencil of a rho row (VAR)
@@ -353,8 +367,8 @@ __device__ __forceinline__ void local_forward(const c2_t<T> (&p)[SEG], c2_t<T> (
     if constexpr (VAR) {
       if (k <= M) v = var_forward<T, IMAG>(prev, left, p[j], right, alpha, vbf, vh, k);
     } else {
-      // t = e_{k-1} - 2 lap_k,  lap_k = left - 2 p_k + right
-      const c2_t<T> t = mk<T>(prev.x + neg2lap(left.x, right.x, p[j].x), prev.y + neg2lap(left.y, right.y, p[j].y));
+      // t = e~_{k-1} - lap_k,  lap_k = left - 2 p_k + right
+      const c2_t<T> t = mk<T>(prev.x + neg_lap(left.x, right.x, p[j].x), prev.y + neg_lap(left.y, right.y, p[j].y));
       if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
     }
     e[j] = v;
@@ -400,7 +414,7 @@ __device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], con
     if constexpr (VAR) {
       if (k <= M) v = var_forward<T, IMAG>(prev, pm, pc, pn, alpha, vbf, vh, k);
     } else {
-      const c2 t = mk<T>(prev.x + neg2lap(pm.x, pn.x, pc.x), prev.y + neg2lap(pm.y, pn.y, pc.y));
+      const c2 t = mk<T>(prev.x + neg_lap(pm.x, pn.x, pc.x), prev.y + neg_lap(pm.y, pn.y, pc.y));
       if (k <= M) v = cf_mul<T, IMAG>(alpha[k], t);
     }
     e[j] = v;
@@ -564,7 +578,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
         c2 pk;
         if constexpr (KEEP) pk = p[j];
         else pk = __ldcg(&line[k * st]);
-        c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
+        c2 u = sub2<T>(pk, z[j]);
         if constexpr (CLOSE) {
           const int jy = G.axis == 2 ? cf2 : k, kz = G.axis == 2 ? k : cf2;
           u = half_phase<T, IMAG>(A, u, qb + (long)k * st, ci, jy, kz);
@@ -773,7 +787,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     const int k = k0 + j;
     if (k <= M) {
       const c2 pk = tile[k * kTilePitch + lane];
-      const c2 u = mk<T>(pk.x - z[j].x, pk.y - z[j].y);
+      const c2 u = sub2<T>(pk, z[j]);
       tile[k * kTilePitch + lane] = u;
       if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
     }
@@ -906,7 +920,7 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       const int k = k0 + j;
       if (k <= M) {
         const c2 z = cf_fma<T, IMAG>(__ldg(&A.gb[k]), Zin, e[j]);
-        const c2 u = mk<T>(p[j].x - z.x, p[j].y - z.y);
+        const c2 u = sub2<T>(p[j], z);
         line[k] = u;
         if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
       }
@@ -1052,7 +1066,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
         const int k = k0 + j;
         if (k <= M) {
           const c2 p = at(k);
-          const c2 u = mk<T>(p.x - z[j].x, p.y - z[j].y);
+          const c2 u = sub2<T>(p, z[j]);
           at(k) = u;
           if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
         }
@@ -1071,7 +1085,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
         const int k = k0 + j;
         if (k <= M) {
           const c2 p = at(k);
-          const c2 u = mk<T>(p.x - z[j].x, p.y - z[j].y);
+          const c2 u = sub2<T>(p, z[j]);
           line[k * st] = u;
           if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
         }
