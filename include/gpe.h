@@ -336,11 +336,17 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
  * grid, precision and mode applies it without timing unless best_ms != NULL,
  * which receives the best mean x-sweep and y+z-sweep times in ms).  Uses one
  * temporary state-sized device buffer.  gp_set_shapes applies shapes (e.g.
- * from a cache file); GP_ERR_INVALID if they do not fit the grid. */
+ * from a cache file); GP_ERR_INVALID if they do not fit the grid.
+ * GP_SHAPE_FUSE_XY (3d GP_F32 grids with nx, ny <= 128 and seg_x 8, 16 or 32
+ * for both x and y): the x and y sweeps run as one kernel per xy plane held in
+ * shared memory -- one read and one write of the state instead of two -- with
+ * the same per-line arithmetic (bit-identical results); the tuner keeps it
+ * where it is faster. */
 enum {
   GP_SHAPE_KEEP_YZ = 1, /* y/z sweeps keep their input segment in registers */
   GP_SHAPE_PIPE_X = 2,  /* x sweep: persistent double-buffered tile kernel (needs tile_x) */
-  GP_SHAPE_PIPE_YZ = 4  /* y/z sweeps: persistent double-buffered kernel */
+  GP_SHAPE_PIPE_YZ = 4, /* y/z sweeps: persistent double-buffered kernel */
+  GP_SHAPE_FUSE_XY = 8  /* x and y sweeps fused, one block per xy plane (3d FP32) */
 };
 int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms);
 int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags);

@@ -266,6 +266,19 @@ bool pipe_fits(const gp_handle* h, int n, bool axis0) {
   return (3L * n + 512 + 2 * stage) * (long)h->esize <= 200L * 1024;
 }
 
+// The fused x + y sweeps (one block per xy plane): FP32 3d Cartesian grids
+// with nx, ny <= 128 (four 32-line groups), a segment length of 8, 16 or 32
+// for both axes, at most 32 warps, and the plane in dynamic shared memory.
+bool plane_fits(const gp_handle* h, int seg) {
+  if (h->prec != GP_F32 || h->dim != 3 || h->geom != 0) return false;
+  const int nx = h->n[0], ny = h->n[1];
+  if (nx > 128 || ny > 128 || (seg != 8 && seg != 16 && seg != 32)) return false;
+  const int sx = (nx - 2 + seg - 1) / seg, sy = (ny - 2 + seg - 1) / seg;
+  if (sx > 16 || sy > 16) return false;
+  if (sx * ((ny + 31) / 32) > 32 || sy * ((nx + 31) / 32) > 32) return false;
+  return (3L * nx + 512 + 3L * ny + 512 + (long)ny * (nx + 1)) * 8 <= 180L * 1024;
+}
+
 int tile_seg(int M) {
   for (int s : {4, 8, 16, 32})
     if ((M + s - 1) / s <= 16) return s;
@@ -304,6 +317,7 @@ void choose_shapes(gp_handle* h) {
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
   const bool pipe = env_int("GPE_PIPE", 0) != 0 && h->prec != GP_DF64;
   h->pipe_x = pipe && h->tile_x && h->geom != 2 && pipe_fits(h, h->n[0], true);  // (no rho-axis pipelined sweep)
+  h->xyfuse = env_int("GPE_FUSE_XY", 0) != 0 && plane_fits(h, sx);
   h->pipe_c = pipe && h->dim > 1 && sc > 0 && pipe_fits(h, nmax, false);
 }
 
@@ -914,6 +928,10 @@ int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
   if (h->real_mode && (!tile_x || seg_x == 0 || seg_c == 0))
     return fail(GP_ERR_STATE, "gp_set_shapes: a real state needs the x tile and segmented y/z sweeps");
+  const bool fxy = (flags & GP_SHAPE_FUSE_XY) != 0;
+  if (fxy && (!plane_fits(h, seg_x) || (flags & GP_SHAPE_PIPE_X)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: the fused x + y sweeps take 3d FP32 grids with nx, ny <= 128 and "
+                                "seg_x 8, 16 or 32 for both axes, without the pipelined x sweep");
   if (h->geom == 2 && (seg_x == 0 || (h->dim > 1 && seg_c == 0) || (flags & GP_SHAPE_PIPE_X)))
     return fail(GP_ERR_INVALID, "gp_set_shapes: the rho axis takes the segmented, non-pipelined x sweeps");
   const bool px = (flags & GP_SHAPE_PIPE_X) != 0, pc = (flags & GP_SHAPE_PIPE_YZ) != 0;
@@ -932,6 +950,7 @@ int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   h->keep_c = (flags & GP_SHAPE_KEEP_YZ) != 0;
   h->pipe_x = px;
   h->pipe_c = pc;
+  h->xyfuse = fxy;
   return GP_OK;
 }
 
@@ -941,7 +960,8 @@ int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* 
   if (seg_x) *seg_x = h->seg_x;
   if (seg_c) *seg_c = h->seg_c;
   if (flags)
-    *flags = (h->keep_c ? GP_SHAPE_KEEP_YZ : 0) | (h->pipe_x ? GP_SHAPE_PIPE_X : 0) | (h->pipe_c ? GP_SHAPE_PIPE_YZ : 0);
+    *flags = (h->keep_c ? GP_SHAPE_KEEP_YZ : 0) | (h->pipe_x ? GP_SHAPE_PIPE_X : 0) |
+             (h->pipe_c ? GP_SHAPE_PIPE_YZ : 0) | (h->xyfuse ? GP_SHAPE_FUSE_XY : 0);
   return GP_OK;
 }
 
@@ -978,7 +998,8 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
         if (h->prec != GP_DF64 && !real && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
       }
   const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
-  const bool keep_px = h->pipe_x, keep_pc = h->pipe_c;
+  const bool keep_px = h->pipe_x, keep_pc = h->pipe_c, keep_fxy = h->xyfuse;
+  h->xyfuse = false;  // the separate sweeps first
   void* saved = nullptr;
   void* const state = real ? h->rpsi : h->psi;
   const size_t sbytes = (size_t)h->np * (real ? h->esize / 2 : h->esize);
@@ -1015,6 +1036,24 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     const double t = ms[1] + ms[2];
     if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; }
   }
+  // the fused x + y sweeps, with the best z shape, against the best separate ones
+  bool best_fxy = false;
+  if (!real)
+    for (int sg : {8, 16, 32}) {
+      if (rc || !plane_fits(h, sg) || !shapes_valid(h, 1, sg, best_c)) continue;
+      double ms[3];
+      h->xyfuse = true;
+      rc = time_shape(1, sg, 0, best_c, best_k, best_pc, ms);
+      h->xyfuse = false;
+      if (!rc && ms[0] + ms[1] + ms[2] < bx + bc) {
+        bx = ms[0] + ms[1];
+        bc = ms[2];
+        best_fxy = true;
+        best_t = 1;
+        best_x = sg;
+        best_px = 0;
+      }
+    }
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(state, saved, sbytes, cudaMemcpyDeviceToDevice, h->work);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->work);
@@ -1022,10 +1061,10 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   }
   cudaFree(saved);
   const int best_flags = (best_k ? GP_SHAPE_KEEP_YZ : 0) | (best_px ? GP_SHAPE_PIPE_X : 0) |
-                         (best_pc ? GP_SHAPE_PIPE_YZ : 0);
+                         (best_pc ? GP_SHAPE_PIPE_YZ : 0) | (best_fxy ? GP_SHAPE_FUSE_XY : 0);
   if (rc) {
     h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c; h->keep_c = keep_k;
-    h->pipe_x = keep_px; h->pipe_c = keep_pc;
+    h->pipe_x = keep_px; h->pipe_c = keep_pc; h->xyfuse = keep_fxy;
     return rc;
   }
   {

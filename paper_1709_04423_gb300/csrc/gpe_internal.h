@@ -125,6 +125,7 @@ struct gp_handle {
   int geom = 0;
   // a real imaginary-time state (gp_set_real_state): np values of the state
   // precision in rpsi; psi then serves as the complex staging copy
+  bool xyfuse = false;  // 3d FP32: the x and y sweeps as one kernel per xy plane
   bool real_mode = false;
   void* rpsi = nullptr;
   int* real_flag = nullptr;  // device flag: a nonzero imaginary part was seen
@@ -180,6 +181,7 @@ void segment_products(const std::vector<std::complex<double>>& af, const std::ve
 void carry_tables(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
                   int sg, std::complex<double>* out);
 int tile_seg(int M);
+bool plane_fits(const gp_handle* h, int seg);  // the fused x + y sweep kernel takes this grid and segment length
 
 int dev_alloc(gp_handle* h, void** p, size_t bytes);
 int join_in(gp_handle* h);

@@ -98,6 +98,39 @@ unsigned launch_c_seg(int seg, int keep, const Sweep2Args<T>& a, cudaStream_t s,
   }
 }
 
+// ---- fused x + y sweeps of a 3d FP32 grid (one block per xy plane)
+template <bool IMAG, int SEG>
+unsigned launch_xy(const Sweep2Args<float>& ax, const Sweep2Args<float>& ay, cudaStream_t s, bool pdl) {
+  const int nx = ax.geom.nx, ny = ax.geom.ny;
+  const int wx = ((nx - 2 + SEG - 1) / SEG) * ((ny + 31) / 32), wy = ((ny - 2 + SEG - 1) / SEG) * ((nx + 31) / 32);
+  const int threads = 32 * std::max(wx, wy);
+  const size_t smem = (size_t)(3 * nx + 512 + 3 * ny + 512 + ny * (nx + 1)) * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(xyplane_kernel<IMAG, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    attr_set = true;
+  }
+  launch_k(pdl, xyplane_kernel<IMAG, SEG>, dim3(ax.geom.nz), dim3(threads), smem, s, ax, ay);
+  count_launch();
+  return (unsigned)ax.geom.nz;
+}
+
+template <bool IMAG>
+unsigned launch_xy_seg(int seg, const Sweep2Args<float>& ax, const Sweep2Args<float>& ay, cudaStream_t s, bool pdl) {
+  switch (seg) {
+    case 8: return launch_xy<IMAG, 8>(ax, ay, s, pdl);
+    case 16: return launch_xy<IMAG, 16>(ax, ay, s, pdl);
+    default: return launch_xy<IMAG, 32>(ax, ay, s, pdl);
+  }
+}
+
+// Whether the x and y sweeps of this handle run as one kernel (the complex
+// state of a 3d FP32 grid whose planes fit; the adjoint's sweeps, which read
+// the step's input from another buffer, run apart).
+inline bool xy_fused(const gp_handle* h) {
+  return h->xyfuse && h->prec == GP_F32 && h->dim == 3 && !h->real_mode;
+}
+
 // ---- shared-memory tile x sweep
 // (RL: a.geom.nlines real lines, two per tile column; VAR: a rho axis)
 template <typename T, bool IMAG, bool FIRST, bool LAST, int SEG, bool RL = false, bool VAR = false>
@@ -242,6 +275,8 @@ bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
   const double* parts_in = read ? h->parts[ns.rd] : nullptr;
   double* parts_out = write ? h->parts[ns.wr] : nullptr;
   unsigned blocks = 0;
+  const bool fuse_xy = xy_fused(h) && src == nullptr && (d == 0 || d == 1);
+  if (fuse_xy && d == 1) return false;  // done by the fused x + y kernel
   if (seg > 0) {
     Sweep2Args<T> a;
     std::memset(&a, 0, sizeof(a));
@@ -270,6 +305,20 @@ bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
       a.vh = cv + 2 * h->n[0];
     }
     bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (fuse_xy) {  // d == 0: the y axis' coefficients beside the x sweep's arguments
+        Sweep2Args<float> ay;
+        std::memset(&ay, 0, sizeof(ay));
+        ay.geom = geom_of(h, 1);
+        ay.alpha = coef_ptr<float>(h, mode, 1, 0);
+        ay.gf = coef_ptr<float>(h, mode, 1, 1 + 2 * si);
+        ay.gb = coef_ptr<float>(h, mode, 1, 2 + 2 * si);
+        ay.ptab = (const float2*)h->ctab[mode][1] + (size_t)si * 512;
+        blocks = imag ? launch_xy_seg<true>(seg, a, ay, h->work, h->pdl_now)
+                      : launch_xy_seg<false>(seg, a, ay, h->work, h->pdl_now);
+        done = true;
+      }
+    }
     if (var) {
       if (h->tile_x) {  // axial trap: x is not the last axis
         blocks = imag ? launch_t_seg<T, true, true, false, false, true>(seg, a, h->work, h->pdl_now)
@@ -520,8 +569,8 @@ int run_steps_t(gp_handle* h, bool imag, long nsteps) {
     }
     for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
       GP_CUDA(cudaGraphLaunch(ge, h->work));
-      count_launch((unsigned long long)kGraphSteps *
-                   (h->dim + (next_f.close && h->strang && !strang_close_fused(h, imag) ? 1 : 0)));
+      count_launch((unsigned long long)kGraphSteps * (h->dim - (xy_fused(h) ? 1 : 0) +
+                                                      (next_f.close && h->strang && !strang_close_fused(h, imag) ? 1 : 0)));
     }
   }
   for (; t < nsteps; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t), nullptr, nullptr, next_f);

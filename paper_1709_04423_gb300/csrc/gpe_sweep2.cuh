@@ -823,6 +823,130 @@ __global__ void __launch_bounds__(512) tsweep_kernel(Sweep2Args<T> A) {
                                          red_smem);
 }
 
+// ---------------------------------------------------------------- fused x + y sweeps (3d, FP32)
+// One block per xy plane (fixed z index): the plane is loaded once into
+// shared memory (rows along x, pitch nx + 1), the pending renormalisation
+// factor and the sub-step N are applied as in the tile x sweep, then the x
+// sweep runs on its rows (lane = row, warp = segment, up to four 32-row groups
+// at once) and the y sweep on its columns (lane = column), both in place, and
+// the plane is stored once: one read and one write of the state instead of
+// two each, and one launch instead of two.  The per-line arithmetic is that
+// of tsweep_body (x) and colsweep_body (y) with the same segment length.
+// Ax: the x sweep's arguments (FIRST: sub-step fields, pending factor); Ay:
+// the y axis' coefficients.  Needs nx, ny <= 128 so that the groups fit, and
+// the plane in shared memory (checked by plane_fits on the host).
+constexpr int kPlaneGroups = 4;
+
+template <bool IMAG, int SEG>
+__global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Sweep2Args<float> Ay) {
+  using T = float;
+  using c2 = float2;
+  extern __shared__ __align__(16) unsigned char plane_smem_raw[];
+  __shared__ c2 cf[kPlaneGroups + 1][16][33], cb[kPlaneGroups + 1][16][33];
+  __shared__ double red_smem[32];
+  const int nx = Ax.geom.nx, ny = Ax.geom.ny;
+  const int PX = nx + 1;
+  c2* scx = reinterpret_cast<c2*>(plane_smem_raw);
+  c2* scy = scx + 3 * nx + 512;
+  c2* P = scy + 3 * ny + 512;
+  const int kz = blockIdx.x;
+  const long base = (long)kz * nx * ny;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  load_coefs<T>(Ax, scx, nx);
+  load_coefs<T>(Ay, scy, ny);
+  pdl_wait();  // the state and the norm sums are the previous kernels' output
+  pdl_release();
+  const int Mx = nx - 2, My = ny - 2;
+  const c2* in = Ax.psi + base;
+  // per-row part of N (row j of plane kz is x line j + ny kz)
+  auto row_v = [&](int j) -> T { return Ax.V ? T(0) : Ax.vy[j] + Ax.vz[kz]; };
+  auto apply = [&](c2 w, int j, int i, T vline, T scl) -> c2 {
+    w.x *= scl;
+    w.y *= scl;
+    return phase_direct<T, IMAG>(w, Ax.V ? Ax.V[base + (long)j * nx + i] : Ax.vx[i] + vline, Ax.dt, Ax.g);
+  };
+  const bool pend = Ax.parts_in != nullptr;
+  if (pend && warp == 0) {
+    const double f = pending_factor_warp(Ax.parts_in, Ax.nparts_in, Ax.parts_wscale);
+    if (lane == 0) red_smem[0] = f;
+  }
+  // ---- load (N on the way in, or raw while warp 0 forms the pending factor)
+  const int w0 = (pend && nwarps > 1) ? 1 : 0;
+  if (warp >= w0) {
+    for (int j = warp - w0; j < ny; j += nwarps - w0) {
+      const T vline = pend ? T(0) : row_v(j);
+      for (int i = lane; i < nx; i += 32) {
+        c2 v = mk<T>(0, 0);
+        if (i >= 1 && i <= Mx) {
+          v = in[(long)j * nx + i];
+          if (!pend) v = apply(v, j, i, vline, T(1));
+        }
+        P[j * PX + i] = v;
+      }
+    }
+  }
+  if (pend) {
+    __syncthreads();
+    const T scl = (T)red_smem[0];
+    for (int j = warp; j < ny; j += nwarps) {
+      const T vline = row_v(j);
+      for (int i = lane; i < nx; i += 32)
+        if (i >= 1 && i <= Mx) P[j * PX + i] = apply(P[j * PX + i], j, i, vline, scl);
+    }
+  }
+  __syncthreads();
+  // ---- x sweep: row j = 32 g + lane, segment s of x
+  {
+    const int nseg = (Mx + SEG - 1) / SEG, ng = (ny + 31) >> 5;
+    int g = warp / nseg, s = warp % nseg;
+    if (g > ng) g = ng;  // spare warps: a zero group, they only join the barriers
+    const int j = 32 * g + lane;
+    const bool row_ok = g < ng && j < ny;
+    const int k0 = 1 + s * SEG;
+    c2 z[SEG];
+    stream_forward<T, IMAG, SEG>(
+        [&](int k) { return (row_ok && k >= 1 && k <= Mx) ? P[j * PX + k] : mk<T>(0, 0); }, z, scx, k0, Mx);
+    seg_carries<T, IMAG, SEG>(z, scx, nx, cf[g], cb[g], s, nseg, lane);
+    if (row_ok) {
+#pragma unroll
+      for (int q = 0; q < SEG; ++q) {
+        const int k = k0 + q;
+        if (k <= Mx) P[j * PX + k] = sub2<T>(P[j * PX + k], z[q]);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- y sweep: column i = 32 g + lane, segment s of y
+  {
+    const int nseg = (My + SEG - 1) / SEG, ng = (nx + 31) >> 5;
+    int g = warp / nseg, s = warp % nseg;
+    if (g > ng) g = ng;
+    const int i = 32 * g + lane;
+    const bool col_ok = g < ng && i < nx;
+    const int k0 = 1 + s * SEG;
+    c2 z[SEG];
+    stream_forward<T, IMAG, SEG>(
+        [&](int k) { return (col_ok && k >= 1 && k <= My) ? P[k * PX + i] : mk<T>(0, 0); }, z, scy, k0, My);
+    seg_carries<T, IMAG, SEG>(z, scy, ny, cf[g], cb[g], s, nseg, lane);
+    if (col_ok) {
+#pragma unroll
+      for (int q = 0; q < SEG; ++q) {
+        const int k = k0 + q;
+        if (k <= My) P[k * PX + i] = sub2<T>(P[k * PX + i], z[q]);
+      }
+      if (s == 0) {  // the y ends are held at zero
+        P[i] = mk<T>(0, 0);
+        P[(ny - 1) * PX + i] = mk<T>(0, 0);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- store (x ends are zero)
+  c2* out = Ax.psi + base;
+  for (int j = warp; j < ny; j += nwarps)
+    for (int i = lane; i < nx; i += 32) out[(long)j * nx + i] = P[j * PX + i];
+}
+
 // ---------------------------------------------------------------- x sweep (1d)
 // One warp per line; lane j owns interior points k = 1 + j*SEG .. (j+1)*SEG;
 // carries by a Kogge-Stone affine scan over shuffles.

@@ -31,6 +31,7 @@ PRECISIONS = {"f64": GP_F64, "f32": GP_F32, "df64": GP_DF64}
 GP_SHAPE_KEEP_YZ = 1
 GP_SHAPE_PIPE_X = 2
 GP_SHAPE_PIPE_YZ = 4
+GP_SHAPE_FUSE_XY = 8
 
 # every entry point declared in include/gpe.h
 ABI_SYMBOLS = (

@@ -336,3 +336,46 @@ def test_degenerate_and_boundary_sizes(G, dim, n, dx, prec):
         else:
             assert rel_l2(got, ref) <= tol, (imag, rel_l2(got, ref))
         p.close()
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_fused_xy_sweeps(G, imag):
+    """GP_SHAPE_FUSE_XY (x and y sweeps in one kernel per xy plane): bit for
+    bit the tile and column sweeps with the same 16-point segments at 128^3,
+    and the oracle on a ragged grid, with the Lie and the Strang splitting."""
+    n, dx, nkl = [128] * 3, [0.1] * 3, [1.0, 1.4, 1.8]
+    phi0 = I.gaussian_state(3, n, dx, nkl, seed=1710, noise=1e-3)
+    dt = 1e-3 if imag else 2e-4
+    states = []
+    for flags in (G.GP_SHAPE_KEEP_YZ, G.GP_SHAPE_KEEP_YZ | G.GP_SHAPE_FUSE_XY):
+        p = G.Propagator(3, n, dx, dt, nkl, 50.0, precision="f32")
+        G.gp_set_shapes(p.h, 1, 16, 16, flags)
+        assert p.shapes()["flags"] == flags
+        p.set_state(phi0)
+        l0 = G.gp_kernel_launches()
+        (p.step_imag if imag else p.step_real)(40)
+        launches = G.gp_kernel_launches() - l0
+        assert launches == 40 * (2 if flags & G.GP_SHAPE_FUSE_XY else 3) + (1 if imag else 0)
+        states.append(p.get_state(device=False))
+        p.close()
+    assert np.array_equal(states[0], states[1])
+    n, dx, nkl = [100, 90, 50], [0.12, 0.13, 0.2], [1.0, 1.3, 1.7]
+    phi0 = I.gaussian_state(3, n, dx, nkl, seed=1711, noise=1e-3)
+    for split in (0, 1):
+        p = G.Propagator(3, n, dx, dt, nkl, 50.0, precision="f32")
+        G.gp_set_shapes(p.h, 1, 16, 16, G.GP_SHAPE_KEEP_YZ | G.GP_SHAPE_FUSE_XY)
+        if split:
+            p.set_splitting("strang")
+        p.set_state(phi0)
+        (p.step_imag if imag else p.step_real)(60)
+        ref = O.run(O.Grid(3, n, dx, dt, nkl, 50.0, split=split), phi0, imag, 60)
+        assert rel_l2(p.get_state(device=False).astype(np.complex128), ref) <= 3e-6, split
+        p.close()
+
+
+def test_fused_xy_rejections(G):
+    for prec, dim, n in (("f64", 3, [64, 64, 64]), ("f32", 2, [64, 64]), ("f32", 3, [160, 64, 32])):
+        p = G.Propagator(dim, n, [0.2] * dim, 1e-3, [1.0] * dim, 1.0, precision=prec)
+        with pytest.raises(G.GPError):
+            G.gp_set_shapes(p.h, 1, 16, 16, G.GP_SHAPE_FUSE_XY)
+        p.close()
