@@ -1037,9 +1037,11 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; }
   }
   // the fused x + y sweeps, with the best z shape, against the best separate ones
+  // (8- and 16-point segments: 32-point ones spill under the 64 registers a
+  // thread of a 1024-thread block may hold)
   bool best_fxy = false;
   if (!real)
-    for (int sg : {8, 16, 32}) {
+    for (int sg : {8, 16}) {
       if (rc || !plane_fits(h, sg) || !shapes_valid(h, 1, sg, best_c)) continue;
       double ms[3];
       h->xyfuse = true;
