@@ -870,18 +870,26 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
     const double f = pending_factor_warp(Ax.parts_in, Ax.nparts_in, Ax.parts_wscale);
     if (lane == 0) red_smem[0] = f;
   }
-  // ---- load (N on the way in, or raw while warp 0 forms the pending factor)
+  // ---- load (N on the way in, or raw while warp 0 forms the pending factor);
+  // four points of a row per lane at a time, their loads issued first
   const int w0 = (pend && nwarps > 1) ? 1 : 0;
+  const int per_row = (nx + 31) >> 5;
   if (warp >= w0) {
     for (int j = warp - w0; j < ny; j += nwarps - w0) {
       const T vline = pend ? T(0) : row_v(j);
-      for (int i = lane; i < nx; i += 32) {
-        c2 v = mk<T>(0, 0);
-        if (i >= 1 && i <= Mx) {
-          v = in[(long)j * nx + i];
-          if (!pend) v = apply(v, j, i, vline, T(1));
+      for (int q0 = 0; q0 < per_row; q0 += 4) {
+        c2 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = (q0 + t) * 32 + lane;
+          v[t] = (i >= 1 && i <= Mx) ? in[(long)j * nx + i] : mk<T>(0, 0);
         }
-        P[j * PX + i] = v;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = (q0 + t) * 32 + lane;
+          if (i >= nx) break;
+          P[j * PX + i] = (!pend && i >= 1 && i <= Mx) ? apply(v[t], j, i, vline, T(1)) : v[t];
+        }
       }
     }
   }
@@ -890,8 +898,19 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
     const T scl = (T)red_smem[0];
     for (int j = warp; j < ny; j += nwarps) {
       const T vline = row_v(j);
-      for (int i = lane; i < nx; i += 32)
-        if (i >= 1 && i <= Mx) P[j * PX + i] = apply(P[j * PX + i], j, i, vline, scl);
+      for (int q0 = 0; q0 < per_row; q0 += 4) {
+        c2 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = (q0 + t) * 32 + lane;
+          if (i >= 1 && i <= Mx) v[t] = P[j * PX + i];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = (q0 + t) * 32 + lane;
+          if (i >= 1 && i <= Mx) P[j * PX + i] = apply(v[t], j, i, vline, scl);
+        }
+      }
     }
   }
   __syncthreads();
@@ -941,10 +960,22 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
     }
   }
   __syncthreads();
-  // ---- store (x ends are zero)
+  // ---- store (x ends are zero), four points of a row per lane at a time
   c2* out = Ax.psi + base;
   for (int j = warp; j < ny; j += nwarps)
-    for (int i = lane; i < nx; i += 32) out[(long)j * nx + i] = P[j * PX + i];
+    for (int q0 = 0; q0 < per_row; q0 += 4) {
+      c2 v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = (q0 + t) * 32 + lane;
+        if (i < nx) v[t] = P[j * PX + i];
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = (q0 + t) * 32 + lane;
+        if (i < nx) out[(long)j * nx + i] = v[t];
+      }
+    }
 }
 
 // ---------------------------------------------------------------- x sweep (1d)
