@@ -379,3 +379,28 @@ def test_fused_xy_rejections(G):
         with pytest.raises(G.GPError):
             G.gp_set_shapes(p.h, 1, 16, 16, G.GP_SHAPE_FUSE_XY)
         p.close()
+
+
+def test_fused_xy_sweeps_with_a_user_potential(G):
+    """The fused x + y kernel's per-point potential path: bit for bit the
+    separate sweeps, imaginary then real time, and the oracle."""
+    n, dx, nkl = [96, 80, 40], [0.15, 0.15, 0.2], [1.0, 1.3, 1.6]
+    gr = O.Grid(3, n, dx, 1e-3, nkl, 30.0)
+    dV, _ = I.gaussian_bumps(3, n, dx, seed=1714)
+    V = O.potential(gr) + dV
+    phi0 = I.gaussian_state(3, n, dx, nkl, seed=1715, noise=1e-3)
+    states = []
+    for flags in (G.GP_SHAPE_KEEP_YZ, G.GP_SHAPE_KEEP_YZ | G.GP_SHAPE_FUSE_XY):
+        p = G.Propagator(3, n, dx, 1e-3, nkl, 30.0, precision="f32")
+        G.gp_set_shapes(p.h, 1, 16, 16, flags)
+        p.set_potential(V)
+        p.set_state(phi0)
+        p.step_imag(30)
+        p.set_dt(2e-4)
+        p.step_real(30)
+        states.append(p.get_state(device=False))
+        p.close()
+    assert np.array_equal(states[0], states[1])
+    ref = O.run(gr.with_(V=V), phi0, True, 30)
+    ref = O.run(gr.with_(V=V, dt=2e-4), ref, False, 30)
+    assert rel_l2(states[1].astype(np.complex128), ref) <= 3e-6
