@@ -81,3 +81,11 @@ def test_batch_init_rejects_bad_arguments(lib):
         rc, b = init(**kw)
         assert rc == gpe.GP_ERR_INVALID, kw
         assert not b.value
+
+
+def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
+    """No CPU fallback: without libgpe.so the binding raises instead of
+    running anything else."""
+    monkeypatch.setattr(gpe, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        gpe.load(str(tmp_path / "libgpe.so"))
