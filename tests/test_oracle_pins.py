@@ -305,6 +305,68 @@ def test_observables_on_analytic_gaussian(dim):
     assert ob["rms_r"] == pytest.approx(np.sqrt(sum(1 / (2 * v) for v in nkl)), rel=1e-8)
 
 
+def _poly_line(n, dx, coef):
+    """A polynomial f (degree <= 4, complex coefficients) sampled on the R1
+    grid, and the derivative the R8 stencils give for it, in closed form from
+    the analytic derivatives (no finite differences): the 4th-order central
+    difference is exact on quartics; the 2nd-order one at i = 1 and n - 2 is
+    f' + h^2 f'''/6 exactly (its error series stops there on quartics); the
+    end points carry 0."""
+    P = np.polynomial.polynomial
+    x = O.coords(n, dx)
+    f = P.polyval(x, coef)
+    d = P.polyval(x, P.polyder(coef))
+    d3 = P.polyval(x, P.polyder(coef, 3))
+    d[[1, n - 2]] += dx * dx / 6.0 * d3[[1, n - 2]]
+    d[[0, n - 1]] = 0.0
+    return f, d
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_kinetic_term_boundary_stencils_on_polynomials(dim):
+    """R8's derivative branches pinned where they matter: a product of
+    quartics with nonzero values at every index (including i = 0, 1, n-2,
+    n-1).  With V = 0 and g = 0, E = mu = sum_q w_q |grad phi|_q^2 / 2 over
+    sum_q w_q |phi_q|^2, the gradient from the closed form of _poly_line.  A
+    wrong stencil, order or index at i = 1 / n - 2, or a nonzero end value,
+    changes the sum."""
+    n = [9, 12, 7][:dim]          # odd and even n (even: Simpson on n - 1 points)
+    dx = [0.3, 0.25, 0.4][:dim]
+    coefs = [np.array([0.7 + 0.2j, -0.4 + 0.9j, 0.35 - 0.1j, 0.08 + 0.05j, -0.03 + 0.02j]),
+             np.array([1.1 - 0.3j, 0.5 + 0.2j, -0.6 + 0.4j, 0.1 - 0.07j, 0.04]),
+             np.array([0.9, -0.2 - 0.5j, 0.3 + 0.3j, -0.05j, 0.02 - 0.01j])]
+    lines = [_poly_line(n[d], dx[d], coefs[d]) for d in range(dim)]
+    w = [O.simpson_weights(n[d], dx[d]) for d in range(dim)]
+    # arrays in (z, y, x) order: axis d of the grid is array axis dim-1-d
+    def outer(vs):
+        out = np.ones((), dtype=np.complex128)
+        for v in reversed(vs):
+            out = np.multiply.outer(out, v)
+        return out
+    phi = outer([l[0] for l in lines])
+    W = np.real(outer([wd.astype(np.complex128) for wd in w]))
+    grad2 = np.zeros(phi.shape)
+    for d in range(dim):
+        comp = outer([lines[e][1] if e == d else lines[e][0] for e in range(dim)])
+        grad2 += np.abs(comp) ** 2
+    kin = 0.5 * np.sum(W * grad2)
+    nrm = np.sum(W * np.abs(phi) ** 2)
+    gr = O.Grid(dim, n, dx, 1e-3, [0.0] * dim, 0.0)
+    ob = O.observables(gr, phi)
+    assert ob["norm"] == pytest.approx(nrm, rel=1e-13)
+    assert ob["energy"] == pytest.approx(kin / nrm, rel=1e-12)
+    assert ob["mu"] == pytest.approx(kin / nrm, rel=1e-12)
+    # the same state read with the 2nd-order stencil everywhere, or with the
+    # boundary branch dropped (0 at i = 1, n - 2), gives a different kinetic
+    # term: the pin separates the readings
+    x0 = O.coords(n[0], dx[0])
+    f0 = lines[0][0]
+    alt = np.zeros(n[0], dtype=np.complex128)
+    alt[1:-1] = (f0[2:] - f0[:-2]) / (2 * dx[0])
+    assert not np.allclose(alt, lines[0][1], rtol=1e-6, atol=0)
+    assert abs(lines[0][1][1]) > 1e-3 and abs(lines[0][1][n[0] - 2]) > 1e-3 and abs(x0[0]) > 0
+
+
 def test_kinetic_term_is_fourth_order():
     """Halving dx divides the kinetic-energy error of a Gaussian by ~16."""
     errs = []
