@@ -298,14 +298,15 @@ int gp_batch_destroy(gp_batch* b);
 
 /* Observables without a handle and without allocating.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory at the moment they need the observables -- code running
- * while a stream is captured into a CUDA graph, code inside an application
- * that owns the whole device-memory budget, code that must not synchronise
- * (cudaMalloc/cudaFree may).  It computes what gp_observables computes, for
- * a state the caller passes, and calls no cudaMalloc, cudaFree or other
- * allocating routine.
- *   dim, n, dx, nkl, g, prec  as for gp_init; at most 4096 points per axis
- *                             (GP_ERR_INVALID beyond that).
+ * device memory at the moment they need the observables -- an application
+ * that owns the whole device-memory budget and forbids allocations after
+ * start-up, or a loop that must not synchronise the device (cudaMalloc and
+ * cudaFree may).  It computes what gp_observables computes, for a state the
+ * caller passes, and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   dim, n, dx, nkl, g  as for gp_init; at most 4096 points per axis
+ *                       (GP_ERR_INVALID beyond that).
+ *   prec     GP_F64 or GP_F32 only (GP_DF64 states: GP_ERR_INVALID).
  *   psi      device state (npoints complex values in precision prec).
  *   V        device potential (npoints doubles), or NULL for the harmonic trap.
  *   out      device buffer of 7 doubles, written in stream order with
@@ -316,8 +317,11 @@ int gp_batch_destroy(gp_batch* b);
  * and it keeps the last call's contents (each call clears what must start at
  * zero), so calls that overlap on the GPU -- on different streams, or from
  * different host threads -- race and must be serialised by the caller.  The
- * first call on a device looks up the array's device address, so make that
- * first call before any stream capture begins. */
+ * array's device address is looked up on each call whose stream is not being
+ * captured (so it follows a device reset); a call during a stream capture
+ * reuses the address found by the last call outside one, so the first call on
+ * a device must come before any stream capture begins (GP_ERR_STATE
+ * otherwise). */
 int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const double nkl[3], double g,
                            gp_precision prec, const void* psi, const double* V, double* out, void* stream);
 

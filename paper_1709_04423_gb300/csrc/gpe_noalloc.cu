@@ -2,15 +2,14 @@
 // callers that cannot allocate device memory (declared in include/gpe.h).
 //
 // Some callers cannot call cudaMalloc when they need the observables of a
-// state: code that runs while a stream is being captured into a CUDA graph
-// (allocation calls are not allowed inside a capture), code embedded in a
-// host application that owns the whole device-memory budget and forbids
-// allocations after start-up, and code that must never synchronise the
-// device (cudaMalloc and cudaFree may synchronise).  For them this entry point
-// computes the same quantities as gp_observables without a handle and
-// without allocating: its scratch space (per-axis tables, per-block partial
-// sums, the raw sums and the completion counter) is the file-scope array
-// below, which every GPU that loads the library holds until the process ends.
+// state: a host application that owns the whole device-memory budget and
+// forbids allocations after start-up (its own pool holds every byte), and a
+// loop that must never synchronise the device (cudaMalloc and cudaFree may
+// synchronise).  For them this entry point computes the same quantities as
+// gp_observables without a handle and without allocating: its scratch space
+// (per-axis tables, per-block partial sums, the raw sums and the completion
+// counter) is the file-scope array below, which every GPU that loads the
+// library holds until the process ends.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,18 +90,28 @@ __global__ void noalloc_finish_kernel(const double* S, double g, double* out) {
   out[6] = sqrt(r2);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device.
-int scratch_address(double** out) {
+// Device address of the scratch array on the current device.  Host code only
+// holds a host-side stand-in for the array's name, so the address is looked
+// up with cudaGetSymbolAddress with the device current.  It is looked up
+// again on every call made while the stream is not being captured (a device
+// reset, or a released and re-created primary context, may move the array);
+// a call made during a capture takes the address found by the last call
+// outside one, so the first call on a device must come before any capture.
+int scratch_address(cudaStream_t s, double** out) {
   int dev = 0;
   GP_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: device ordinal too large");
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(s, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (!capturing) {
     void* p = nullptr;
     GP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_scratch_addr[dev] = p;
   }
+  if (!g_scratch_addr[dev])
+    return gpe::fail(GP_ERR_STATE,
+                     "gp_observables_noalloc: the first call on a device must come before any stream capture");
   *out = (double*)g_scratch_addr[dev];
   return GP_OK;
 }
@@ -146,6 +155,8 @@ extern "C" int gp_observables_noalloc(int dim, const int n[3], const double dx[3
                                       void* stream) {
   if (!n || !dx || !nkl || !psi || !out) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: NULL argument");
   if (dim < 1 || dim > 3) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: dim must be 1, 2 or 3");
+  if (prec == GP_DF64)
+    return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: GP_DF64 is not supported here (GP_F64 or GP_F32 states only)");
   if (prec != GP_F64 && prec != GP_F32) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: unknown precision");
   int n3[3] = {1, 1, 1};
   double dx3[3] = {1.0, 1.0, 1.0};
@@ -163,9 +174,9 @@ extern "C" int gp_observables_noalloc(int dim, const int n[3], const double dx[3
     return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: more than 2^31-1 grid points");
   if (!std::isfinite(g)) return gpe::fail(GP_ERR_INVALID, "gp_observables_noalloc: g must be finite");
   double* scratch = nullptr;
-  int rc = scratch_address(&scratch);
-  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = scratch_address(s, &scratch);
+  if (rc) return rc;
   noalloc_setup_kernel<<<36, 256, 0, s>>>(scratch, dim, n3[0], n3[1], n3[2], dx3[0], dx3[1], dx3[2],
                                           nkl[0], dim > 1 ? nkl[1] : 0.0, dim > 2 ? nkl[2] : 0.0);
   gpe::count_launch();

@@ -1,9 +1,9 @@
 """gp_observables_noalloc -- the allocation-free observables entry point.
 
 Callers that cannot allocate device memory when they need the observables
-(code inside a CUDA-graph stream capture, applications that own the whole
-device-memory budget, code that must not synchronise) use this entry point;
-it must give what gp_observables gives for the same state.  This file is
+(an application that owns the whole device-memory budget, a loop that must
+not synchronise the device) use this entry point; it must give what
+gp_observables gives for the same state.  This file is
 collected last so that a stop-at-first-failure run has already run every
 other test; it also passes on its own in a fresh process.
 """
@@ -26,6 +26,7 @@ def test_noalloc_matches_handle_observables_on_two_calls(prec):
     cases = [
         (3, [40, 33, 24], [0.25, 0.3, 0.35], [1.0, 1.4, 1.8], 20.0, 31, False),
         (2, [64, 48], [0.2, 0.25], [1.0, 1.3], 7.5, 32, True),
+        (1, [257], [0.05], [1.0], 10.0, 33, False),   # both absent axes on one-point tables
     ]
     for dim, n, dx, nkl, g, seed, with_v in cases:   # two calls in a row
         p = gpe.Propagator(dim, n, dx, 1e-3, nkl, g, precision=prec)
@@ -34,6 +35,7 @@ def test_noalloc_matches_handle_observables_on_two_calls(prec):
         if with_v:
             dV, _ = inputs.gaussian_bumps(dim, n, dx, seed=seed)
             x = [inputs.axis_coords(n[d], dx[d]) for d in range(dim)]
+            assert dim == 2
             harm = 0.5 * (nkl[1] ** 2 * x[1][:, None] ** 2 + nkl[0] ** 2 * x[0][None, :] ** 2)
             V = torch.tensor(harm + dV, dtype=torch.float64, device="cuda")
             p.set_potential(V)
@@ -57,3 +59,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         gpe.gp_observables_noalloc(1, [5000], [0.1], [1.0], 1.0, gpe.GP_F64, 1, None, 1, None)
     assert e.value.code == gpe.GP_ERR_INVALID
     assert "4096" in str(e.value)
+    with pytest.raises(gpe.GPError) as e:
+        gpe.gp_observables_noalloc(1, [64], [0.1], [1.0], 1.0, gpe.GP_DF64, 1, None, 1, None)
+    assert e.value.code == gpe.GP_ERR_INVALID
+    assert "GP_DF64" in str(e.value)
