@@ -202,11 +202,22 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
 // mu further from FP64 -- the FP32 iteration stops at an exact fixed point of
 // the rounded map, whose mu depends on how each sub-step rounds, and that
 // form stops 1.3e-6 away against 8e-9 for the product.)
+// The FP32 factor e^{-th} is 1 + expm1(-th) rounded once: for the small th of a
+// time step this is the correctly rounded factor except within a small
+// fraction of an ulp of a rounding boundary, whereas the library expf (up to
+// 2 ulp) carries an error that varies smoothly with th.  A smooth error is
+// smooth in space and, th changing slowly, the same at a point step after
+// step, so it acts as a small perturbation of the potential that the state
+// follows: the 128^3 imaginary-time workload stood 2.2e-6 off in mu after 100
+// steps with expf against 4e-8 for an FP32 emulation with correctly rounded
+// factors.
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
   const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
   if (IMAG) {
-    const T f = exp(-th);
+    T f;
+    if constexpr (std::is_same<T, float>::value) f = 1.0f + expm1f(-th);
+    else f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
   }
   return rot_neg<T>(p, th);
