@@ -238,6 +238,21 @@ int gp_reduced_density(gp_handle* h, int keep_mask, double* out, int out_on_devi
  * Synchronises the stream. */
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch);
 
+/* The same per-axis durations as the kernels run inside a step's CUDA graph:
+ * for each axis, reps (1..1024) launches of that axis' sweep back to back in a
+ * captured graph, with the programmatic-dependent-launch edges of the step
+ * graph, one warm-up replay and one timed replay (events on the library's
+ * stream); ms_per_launch[d] = mean per launch (0 for y when the fused x + y
+ * kernel runs both).  Uses one temporary state-sized device buffer; the state
+ * is restored.  For instrumentation. */
+int gp_time_sweeps_graph(gp_handle* h, int imag, int reps, double* ms_per_launch);
+
+/* Measured arithmetic rates of this GPU (the current device): FP64 and FP32
+ * fused multiply-adds per second (thread instructions), from a kernel of
+ * independent FMA chains on every SM timed with events.  The denominators of
+ * an ALU roofline; synchronises the device.  For instrumentation. */
+int gp_fp_fma_rates(double* dfma_per_s, double* ffma_per_s);
+
 /* ---- Differentiation form: adjoint of real-time propagation.
  * Objective J(phi(T)) of the state after nsteps real-time steps; gradients
  * with respect to the potential values V (per grid point), g and phi(0).
@@ -345,12 +360,27 @@ int gp_observables_noalloc(int dim, const int n[3], const double dx[3], const do
  * for both x and y): the x and y sweeps run as one kernel per xy plane held in
  * shared memory -- one read and one write of the state instead of two -- with
  * the same per-line arithmetic (bit-identical results); the tuner keeps it
- * where it is faster. */
+ * where it is faster.
+ * GP_SHAPE_TMA_YZ (GP_F32 complex states of 2d/3d grids with nx even, y/z
+ * lines of at most 256 points, seg_c 8, 16 or 32 with at most 16 segments):
+ * the y/z sweeps run as persistent kernels that move 32-line tiles between
+ * global and shared memory with the TMA unit, three stages deep, and solve
+ * them in place with the same per-line arithmetic as the other y/z sweeps.
+ * Their waits for a tile give up after a limit (1 s, or GPE_WAIT_LIMIT_MS
+ * milliseconds at gp_init); the next synchronising call (gp_observables) then
+ * returns GP_ERR_TIMEOUT.
+ * GP_SHAPE_TMA_X (GP_F32 complex states of Cartesian 2d/3d grids with nx a
+ * multiple of 16 and at most 256, the x tile with seg_x 8 or 16): the x sweep,
+ * with the sub-step N and the pending renormalisation, runs the same way, its
+ * segments aligned to even points; not with GP_SHAPE_PIPE_X or
+ * GP_SHAPE_FUSE_XY. */
 enum {
   GP_SHAPE_KEEP_YZ = 1, /* y/z sweeps keep their input segment in registers */
   GP_SHAPE_PIPE_X = 2,  /* x sweep: persistent double-buffered tile kernel (needs tile_x) */
   GP_SHAPE_PIPE_YZ = 4, /* y/z sweeps: persistent double-buffered kernel */
-  GP_SHAPE_FUSE_XY = 8  /* x and y sweeps fused, one block per xy plane (3d FP32) */
+  GP_SHAPE_FUSE_XY = 8, /* x and y sweeps fused, one block per xy plane (3d FP32) */
+  GP_SHAPE_TMA_YZ = 16, /* y/z sweeps: persistent kernel, tiles moved by TMA (FP32) */
+  GP_SHAPE_TMA_X = 32   /* x sweep (with N): persistent kernel, tiles moved by TMA (FP32) */
 };
 int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms);
 int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags);
@@ -369,6 +399,17 @@ const char* gp_last_error(void);
 /* Number of kernels this library has launched in this process (graph
  * replays count every kernel node); for instrumentation. */
 unsigned long long gp_kernel_launches(void);
+
+/* Test hook of the bounded device-side waits (the paper has no counterpart).
+ * With extra_bytes > 0 every TMA tile load of this handle's sweeps
+ * (GP_SHAPE_TMA_X / GP_SHAPE_TMA_YZ) announces extra_bytes more than it
+ * moves, so its wait on the tile can never complete: each such sweep gives up
+ * after the wait limit (GPE_WAIT_LIMIT_MS at gp_init, default 1000 ms), and
+ * the next gp_observables returns GP_ERR_TIMEOUT -- the way the tests check
+ * that a wait that runs out ends the kernel and leaves the context usable.
+ * 0 restores normal operation; the state is not valid after a timeout
+ * (set it again).  0 <= extra_bytes <= 1024, else GP_ERR_INVALID. */
+int gp_test_stall_transfers(gp_handle* h, int extra_bytes);
 
 #ifdef __cplusplus
 }

@@ -125,12 +125,12 @@ void segment_products(const std::vector<cd>& alpha, int n, int seg, std::vector<
 }
 
 void segment_products(const std::vector<cd>& af, const std::vector<cd>& ab, int n, int seg, std::vector<cd>& gf,
-                      std::vector<cd>& gb) {
-  const int M = n - 2;
+                      std::vector<cd>& gb, int first) {
+  const int last = first == 0 ? n - 1 : n - 2;  // even-aligned segments also cover the two end points
   gf.assign(n, cd(0, 0));
   gb.assign(n, cd(0, 0));
-  for (int k0 = 1; k0 <= M; k0 += seg) {
-    const int k1 = std::min(M, k0 + seg - 1);
+  for (int k0 = first; k0 <= last; k0 += seg) {
+    const int k1 = std::min(last, k0 + seg - 1);
     cd acc(1, 0);
     for (int k = k0; k <= k1; ++k) {
       acc *= af[k];
@@ -151,12 +151,12 @@ void carry_tables(const std::vector<cd>& alpha, int n, int sg, cd* out /* 512 */
   carry_tables(alpha, alpha, n, sg, out);
 }
 
-void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, int sg, cd* out /* 512 */) {
-  const int M = n - 2;
+void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, int sg, cd* out /* 512 */, int first) {
+  const int last = first == 0 ? n - 1 : n - 2;
   cd Aseg[16], Bseg[16];
   for (int q = 0; q < 16; ++q) {
     cd acc(1, 0), bcc(1, 0);
-    for (int k = 1 + q * sg; k <= std::min(M, (q + 1) * sg); ++k) {
+    for (int k = first + q * sg; k <= std::min(last, first + (q + 1) * sg - 1); ++k) {
       acc *= af[k];
       bcc *= ab[k];
     }
@@ -237,6 +237,19 @@ int upload_coefs_t(gp_handle* h) {
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
       if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;
+      if (d == 0 && h->coef_even[mode]) {
+        // segments aligned to even points (q SEG .. q SEG + SEG - 1, alpha = 0 at both
+        // ends) for SEG = 8 and 16: gf, gb, then the carry tables of each
+        std::vector<cd> ev((size_t)4 * n + 1024, cd(0, 0));
+        for (int si = 0; si < 2; ++si) {
+          const int sg = si == 0 ? 8 : 16;
+          segment_products(af, ab, n, sg, gf, gb, 0);
+          std::copy(gf.begin(), gf.end(), ev.begin() + (size_t)(2 * si) * n);
+          std::copy(gb.begin(), gb.end(), ev.begin() + (size_t)(2 * si + 1) * n);
+          carry_tables(af, ab, n, sg, ev.data() + (size_t)4 * n + 512 * si, 0);
+        }
+        if ((rc = upload_c2<T>(h, h->coef_even[mode], ev))) return rc;
+      }
       if (mode < 2) {
         if ((rc = upload_c2<T>(h, h->cm[mode == MODE_IMAG][d], f.m))) return rc;
         if ((rc = upload_c2<T>(h, h->ccp[mode == MODE_IMAG][d], f.cp))) return rc;
@@ -277,6 +290,47 @@ bool plane_fits(const gp_handle* h, int seg) {
   if (sx > 16 || sy > 16) return false;
   if (sx * ((ny + 31) / 32) > 32 || sy * ((nx + 31) / 32) > 32) return false;
   return (3L * nx + 512 + 3L * ny + 512 + (long)ny * (nx + 1)) * 8 <= 180L * 1024;
+}
+
+// The TMA y/z sweeps (gpe_tma.cuh): FP32 complex states of 2d/3d grids with
+// nx even (the tensor map's row strides are multiples of 16 bytes), y/z lines
+// of at most 256 points (a box dimension's limit), a segment length of 8, 16
+// or 32 with at most 16 segments per line, and three 32-line stages plus the
+// coefficients in shared memory.
+bool tma_fits(const gp_handle* h, int seg) {
+  if (h->prec != GP_F32 || h->dim < 2 || h->real_mode || (h->n[0] & 1)) return false;
+  if (seg != 8 && seg != 16 && seg != 32) return false;
+  int nmax = 0;
+  for (int d = 1; d < h->dim; ++d) {
+    if (h->n[d] > 256 || (h->n[d] - 2 + seg - 1) / seg > 16) return false;
+    nmax = std::max(nmax, h->n[d]);
+  }
+  const long coef = (3L * nmax + 512) * 8;
+  const long smem = (coef + 1023) / 1024 * 1024 + 1024 + 3L * 32 * nmax * 8;
+  return smem + 9 * 1024 <= 227L * 1024;  // + the static carries and barriers
+}
+
+// The TMA x sweep: FP32 complex states of 2d/3d Cartesian grids with nx a
+// multiple of 16 (whole 16-point chunks per box) and at most 256, segments of
+// 8 or 16 points aligned to even points with at most 16 per line.
+bool tma_x_fits(const gp_handle* h, int seg) {
+  if (h->prec != GP_F32 || h->dim < 2 || h->real_mode || h->geom != 0 || !h->coef_even[0]) return false;
+  const int nx = h->n[0];
+  if ((nx & 15) || nx > 256 || (seg != 8 && seg != 16) || nx / seg > 16) return false;
+  const long coef = (3L * nx + 512) * 8 + 4L * nx;
+  const long smem = (coef + 1023) / 1024 * 1024 + 1024 + 3L * 32 * nx * 8;
+  return smem + 9 * 1024 <= 227L * 1024;
+}
+
+int read_dev_err(gp_handle* h, const char* who) {
+  int e = 0;
+  GP_CUDA(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+  GP_CUDA(cudaStreamSynchronize(h->work));
+  if (e == 0) return GP_OK;
+  GP_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->work));
+  GP_CUDA(cudaStreamSynchronize(h->work));
+  return fail(GP_ERR_TIMEOUT, std::string(who) + ": a device-side wait gave up (a sweep's tile transfer did not "
+                                                  "complete within the wait limit); the state is not valid");
 }
 
 int tile_seg(int M) {
@@ -576,6 +630,9 @@ int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double
       if ((rc = dev_alloc(h, &h->coef[mode][d], (size_t)(1 + 2 * kNumSegs) * h->n[d] * h->esize))) return bail(rc);
       if ((rc = dev_alloc(h, &h->ctab[mode][d], (size_t)kNumSegs * 512 * h->esize))) return bail(rc);
     }
+    if (d == 0 && prec == GP_F32 && dim > 1 && geom == 0)
+      for (int mode = 0; mode < 2; ++mode)
+        if ((rc = dev_alloc(h, &h->coef_even[mode], ((size_t)4 * h->n[0] + 1024) * h->esize))) return bail(rc);
     for (int im = 0; im < 2; ++im) {
       if ((rc = dev_alloc(h, &h->cm[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
       if ((rc = dev_alloc(h, &h->ccp[im][d], (size_t)h->n[d] * h->esize))) return bail(rc);
@@ -615,6 +672,8 @@ int init_handle(gp_handle** out, int geom, int dim, const int n[3], const double
   for (int d = 0; d < dim; ++d) maxblocks = std::max(maxblocks, h->np / h->n[d] / 4 + 1);
   if ((rc = dev_alloc(h, (void**)&h->partials, (size_t)maxblocks * 8 * sizeof(double)))) return bail(rc);
   if ((rc = dev_alloc(h, (void**)&h->counter, 64))) return bail(rc);
+  if ((rc = dev_alloc(h, (void**)&h->dev_err, 64))) return bail(rc);
+  h->tma_limit_ns = (unsigned long long)env_int("GPE_WAIT_LIMIT_MS", 1000) * 1000000ull;
   {
     // one norm sum per block of any last sweep: 32 lines per block (tiles and
     // y/z sweeps), 4 (one-warp x lines), 128 (long lines), or a persistent grid
@@ -801,6 +860,32 @@ int gp_step_real(gp_handle* h, long nsteps) {
   return run_steps_any(h, false, nsteps);
 }
 
+int gp_time_sweeps_graph(gp_handle* h, int imag, int reps, double* ms_per_launch) {
+  if (!h || !ms_per_launch) return fail(GP_ERR_INVALID, "gp_time_sweeps_graph: NULL argument");
+  if (reps < 1 || reps > 1024) return fail(GP_ERR_INVALID, "gp_time_sweeps_graph: reps must be in [1, 1024]");
+  if (h->real_mode && !imag) return fail(GP_ERR_STATE, "gp_time_sweeps_graph: a real state takes imaginary time only");
+  void* const state = h->real_mode ? h->rpsi : h->psi;
+  const size_t sbytes = (size_t)h->np * (h->real_mode ? h->esize / 2 : h->esize);
+  void* saved = nullptr;
+  GP_CUDA(cudaMalloc(&saved, sbytes));
+  int rc = join_in(h);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(saved, state, sbytes, cudaMemcpyDeviceToDevice, h->work);
+    if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (!rc) {
+    rc = h->prec == GP_DF64 ? time_graph_df(h, imag != 0, reps, ms_per_launch)
+         : h->prec == GP_F64 ? time_graph_f64(h, imag != 0, reps, ms_per_launch)
+                             : time_graph_f32(h, imag != 0, reps, ms_per_launch);
+  }
+  cudaError_t e = cudaMemcpyAsync(state, saved, sbytes, cudaMemcpyDeviceToDevice, h->work);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->work);
+  cudaFree(saved);
+  if (!rc && e != cudaSuccess) rc = fail(GP_ERR_CUDA, std::string("gp_time_sweeps_graph: ") + cudaGetErrorString(e));
+  if (!rc) rc = read_dev_err(h, "gp_time_sweeps_graph");
+  return rc;
+}
+
 int gp_time_sweeps(gp_handle* h, int imag, long nsteps, double* ms_per_launch) {
   if (!h || !ms_per_launch) return fail(GP_ERR_INVALID, "gp_time_sweeps: NULL argument");
   if (nsteps < 0 || nsteps > 4096) return fail(GP_ERR_INVALID, "gp_time_sweeps: nsteps must be in [0, 4096]");
@@ -923,6 +1008,15 @@ std::mutex g_tune_mutex;
 
 }  // namespace
 
+int gp_test_stall_transfers(gp_handle* h, int extra_bytes) {
+  if (!h) return fail(GP_ERR_INVALID, "gp_test_stall_transfers: NULL handle");
+  if (extra_bytes < 0 || extra_bytes > 1024)
+    return fail(GP_ERR_INVALID, "gp_test_stall_transfers: extra_bytes must be in [0, 1024]");
+  drop_graphs(h);  // captured launches carry the old value
+  h->tma_expect_extra = extra_bytes;
+  return GP_OK;
+}
+
 int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   if (!h) return fail(GP_ERR_INVALID, "gp_set_shapes: NULL handle");
   if (!shapes_valid(h, tile_x, seg_x, seg_c)) return fail(GP_ERR_INVALID, "gp_set_shapes: invalid shapes for this grid");
@@ -943,7 +1037,19 @@ int gp_set_shapes(gp_handle* h, int tile_x, int seg_x, int seg_c, int flags) {
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
   if (pc && (h->dim < 2 || seg_c == 0 || !pipe_fits(h, nmax, false)))
     return fail(GP_ERR_INVALID, "gp_set_shapes: pipelined y/z sweeps need two stages in shared memory");
+  const bool tx = (flags & GP_SHAPE_TMA_X) != 0;
+  if (tx && (px || fxy || !tile_x || !tma_x_fits(h, seg_x)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: the TMA x sweep takes GP_F32 complex states of Cartesian 2d/3d grids "
+                                "with nx a multiple of 16 and at most 256, the x tile with seg_x 8 or 16, without the "
+                                "pipelined or fused x sweeps");
+  const bool tc = (flags & GP_SHAPE_TMA_YZ) != 0;
+  if (tc && (pc || !tma_fits(h, seg_c)))
+    return fail(GP_ERR_INVALID, "gp_set_shapes: the TMA y/z sweeps take GP_F32 complex states with nx even, y/z lines of "
+                                "at most 256 points and seg_c 8, 16 or 32 (at most 16 segments), without the "
+                                "pipelined y/z sweeps");
   drop_graphs(h);
+  h->tma_c = tc;
+  h->tma_x = tx;
   h->tile_x = tile_x != 0;
   h->seg_x = seg_x;
   h->seg_c = seg_c;
@@ -961,7 +1067,8 @@ int gp_get_shapes(const gp_handle* h, int* tile_x, int* seg_x, int* seg_c, int* 
   if (seg_c) *seg_c = h->seg_c;
   if (flags)
     *flags = (h->keep_c ? GP_SHAPE_KEEP_YZ : 0) | (h->pipe_x ? GP_SHAPE_PIPE_X : 0) |
-             (h->pipe_c ? GP_SHAPE_PIPE_YZ : 0) | (h->xyfuse ? GP_SHAPE_FUSE_XY : 0);
+             (h->pipe_c ? GP_SHAPE_PIPE_YZ : 0) | (h->xyfuse ? GP_SHAPE_FUSE_XY : 0) |
+             (h->tma_c ? GP_SHAPE_TMA_YZ : 0) | (h->tma_x ? GP_SHAPE_TMA_X : 0);
   return GP_OK;
 }
 
@@ -979,26 +1086,29 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     }
   }
   // candidate shapes for the x sweep and for the y/z sweeps (timed separately)
-  std::vector<std::array<int, 3>> xs;  // (tile, seg, pipelined)
+  std::vector<std::array<int, 4>> xs;  // (tile, seg, pipelined, TMA)
   for (int sg : {4, 8, 16, 32})
     if (shapes_valid(h, 1, sg, h->seg_c)) {
-      xs.push_back({1, sg, 0});
-      if (h->prec != GP_DF64 && !real && h->geom != 2 && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1});
+      xs.push_back({1, sg, 0, 0});
+      if (h->prec != GP_DF64 && !real && h->geom != 2 && pipe_fits(h, h->n[0], true)) xs.push_back({1, sg, 1, 0});
+      if (!real && tma_x_fits(h, sg)) xs.push_back({1, sg, 0, 1});
     }
   for (int sg : {1, 2, 4, 8, 16})
-    if (!real && shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0}); break; }
-  std::vector<std::array<int, 3>> cs;  // (seg, keep input in registers, pipelined)
+    if (!real && shapes_valid(h, 0, sg, h->seg_c)) { xs.push_back({0, sg, 0, 0}); break; }
+  std::vector<std::array<int, 4>> cs;  // (seg, keep input in registers, pipelined, TMA)
   int nmax = 0;
   for (int d = 1; d < h->dim; ++d) nmax = std::max(nmax, h->n[d]);
   if (h->dim > 1)
     for (int sg : {4, 8, 16, 32})
       if (shapes_valid(h, h->tile_x, h->seg_x, sg)) {
-        if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1, 0});
-        cs.push_back({sg, 0, 0});
-        if (h->prec != GP_DF64 && !real && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1});
+        if (sg * (int)h->esize / 2 <= 64) cs.push_back({sg, 1, 0, 0});
+        cs.push_back({sg, 0, 0, 0});
+        if (h->prec != GP_DF64 && !real && pipe_fits(h, nmax, false)) cs.push_back({sg, 0, 1, 0});
+        if (!real && tma_fits(h, sg)) cs.push_back({sg, 0, 0, 1});
       }
   const int keep_t = h->tile_x, keep_x = h->seg_x, keep_c = h->seg_c, keep_k = h->keep_c;
-  const bool keep_px = h->pipe_x, keep_pc = h->pipe_c, keep_fxy = h->xyfuse;
+  const bool keep_px = h->pipe_x, keep_pc = h->pipe_c, keep_fxy = h->xyfuse, keep_tc = h->tma_c;
+  const bool keep_tx = h->tma_x;
   h->xyfuse = false;  // the separate sweeps first
   void* saved = nullptr;
   void* const state = real ? h->rpsi : h->psi;
@@ -1009,13 +1119,15 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
     cudaError_t e = cudaMemcpyAsync(saved, state, sbytes, cudaMemcpyDeviceToDevice, h->work);
     if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, cudaGetErrorString(e));
   }
-  auto time_shape = [&](int t, int sx, int px, int sc, int kc, int pc, double* ms3) -> int {
+  auto time_shape = [&](int t, int sx, int px, int tx, int sc, int kc, int pc, int tc, double* ms3) -> int {
     h->tile_x = t != 0;
     h->seg_x = sx;
     h->pipe_x = px != 0;
+    h->tma_x = tx != 0;
     h->seg_c = sc;
     h->keep_c = kc;
     h->pipe_c = pc != 0;
+    h->tma_c = tc != 0;
     double warm[3];
     int r = time_steps_any(h, imag != 0, 2, warm);
     if (r) return r;
@@ -1023,18 +1135,19 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   };
   double bx = 1e30, bc = 1e30;
   int best_t = keep_t, best_x = keep_x, best_c = keep_c, best_k = keep_k, best_px = keep_px, best_pc = keep_pc;
+  int best_tc = keep_tc, best_tx = keep_tx;
   for (const auto& c : xs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(c[0], c[1], c[2], keep_c, keep_k, keep_pc, ms);
-    if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; best_px = c[2]; }
+    rc = time_shape(c[0], c[1], c[2], c[3], keep_c, keep_k, keep_pc, keep_tc, ms);
+    if (!rc && ms[0] < bx) { bx = ms[0]; best_t = c[0]; best_x = c[1]; best_px = c[2]; best_tx = c[3]; }
   }
   for (const auto& c : cs) {
     if (rc) break;
     double ms[3];
-    rc = time_shape(best_t, best_x, best_px, c[0], c[1], c[2], ms);
+    rc = time_shape(best_t, best_x, best_px, best_tx, c[0], c[1], c[2], c[3], ms);
     const double t = ms[1] + ms[2];
-    if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; }
+    if (!rc && t < bc) { bc = t; best_c = c[0]; best_k = c[1]; best_pc = c[2]; best_tc = c[3]; }
   }
   // the fused x + y sweeps, with the best z shape, against the best separate ones
   // (8- and 16-point segments: 32-point ones spill under the 64 registers a
@@ -1045,7 +1158,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
       if (rc || !plane_fits(h, sg) || !shapes_valid(h, 1, sg, best_c)) continue;
       double ms[3];
       h->xyfuse = true;
-      rc = time_shape(1, sg, 0, best_c, best_k, best_pc, ms);
+      rc = time_shape(1, sg, 0, 0, best_c, best_k, best_pc, best_tc, ms);
       h->xyfuse = false;
       if (!rc && ms[0] + ms[1] + ms[2] < bx + bc) {
         bx = ms[0] + ms[1];
@@ -1054,6 +1167,7 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
         best_t = 1;
         best_x = sg;
         best_px = 0;
+        best_tx = 0;
       }
     }
   if (!rc) {
@@ -1063,10 +1177,11 @@ int gp_autotune(gp_handle* h, int imag, int nsteps, double* best_ms) {
   }
   cudaFree(saved);
   const int best_flags = (best_k ? GP_SHAPE_KEEP_YZ : 0) | (best_px ? GP_SHAPE_PIPE_X : 0) |
-                         (best_pc ? GP_SHAPE_PIPE_YZ : 0) | (best_fxy ? GP_SHAPE_FUSE_XY : 0);
+                         (best_pc ? GP_SHAPE_PIPE_YZ : 0) | (best_fxy ? GP_SHAPE_FUSE_XY : 0) |
+                         (best_tc ? GP_SHAPE_TMA_YZ : 0) | (best_tx ? GP_SHAPE_TMA_X : 0);
   if (rc) {
     h->tile_x = keep_t; h->seg_x = keep_x; h->seg_c = keep_c; h->keep_c = keep_k;
-    h->pipe_x = keep_px; h->pipe_c = keep_pc; h->xyfuse = keep_fxy;
+    h->pipe_x = keep_px; h->pipe_c = keep_pc; h->xyfuse = keep_fxy; h->tma_c = keep_tc; h->tma_x = keep_tx;
     return rc;
   }
   {
@@ -1141,6 +1256,7 @@ int gp_observables(gp_handle* h, gp_obs* out, double* density, int density_on_de
   }
   rc = run_observables_any(h, ddev);
   if (rc) return rc;
+  if ((rc = read_dev_err(h, "gp_observables"))) return rc;
   GP_CUDA(cudaMemcpyAsync(h->obs_host, h->obs_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->work));
   if (density && !density_on_device)
     GP_CUDA(cudaMemcpyAsync(density, ddev, (size_t)h->np * sizeof(double), cudaMemcpyDeviceToHost, h->work));

@@ -96,6 +96,10 @@ struct gp_handle {
   // per (mode, axis): for each segment length, the carry tables Pf and Pb
   // (16 x 16 complex each) of the segment scans
   void* ctab[gpe::NUM_MODES][3] = {{nullptr}};
+  // FP32 2d/3d grids, x axis, real and imaginary time: the tables of segments
+  // aligned to even points (TMA x sweep): gf, gb for SEG 8 then 16 (n complex
+  // values each), then the carry tables (512) for SEG 8 and 16
+  void* coef_even[gpe::NUM_MODES] = {nullptr};
   // circular / axial traps (geom 2): per mode, the rho axis' backward
   // coefficients, forward right-hand-side factors and stencil factors
   // (vab, vbf, vh of Sweep2Args; 3 n[0] complex values)
@@ -112,6 +116,14 @@ struct gp_handle {
   // persistent double-buffered sweeps (x needs tile_x); only where two
   // shared-memory stages of 32 lines fit
   bool pipe_x = false, pipe_c = false;
+  // y/z sweeps of an FP32 state as persistent TMA-pipelined kernels
+  // (gpe_tma.cuh); their mbarrier waits give up after tma_limit_ns and then
+  // set *dev_err, which the next synchronising call turns into GP_ERR_TIMEOUT
+  bool tma_c = false;
+  bool tma_x = false;  // the x sweep too (FP32, nx a multiple of 16, at most 256)
+  int* dev_err = nullptr;
+  unsigned long long tma_limit_ns = 1000000000ull;
+  int tma_expect_extra = 0;  // bytes added to every expected TMA transaction (a test's way to make a wait run out)
   // imaginary time: per-block norm sums of a step's last sweep, two slots
   // alternating with the step parity, their count and grid factor
   double* parts[2] = {nullptr, nullptr};
@@ -176,12 +188,19 @@ void segment_products(const std::vector<std::complex<double>>& alpha, int n, int
 void carry_tables(const std::vector<std::complex<double>>& alpha, int n, int sg, std::complex<double>* out);
 // the same with separate forward (af) and backward (ab) coefficients
 double axis_coord(int geom, int d, int n, double dx, int i);  // grid coordinate (Cartesian, r, or rho)
+// first: the first point of segment 0 -- 1 (segments over the interior points
+// 1..n-2) or 0 (segments aligned to even points, over 0..n-1; alpha is 0 at
+// both end points, so they take part in the recurrences as zeros)
 void segment_products(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
-                      int seg, std::vector<std::complex<double>>& gf, std::vector<std::complex<double>>& gb);
+                      int seg, std::vector<std::complex<double>>& gf, std::vector<std::complex<double>>& gb,
+                      int first = 1);
 void carry_tables(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
-                  int sg, std::complex<double>* out);
+                  int sg, std::complex<double>* out, int first = 1);
 int tile_seg(int M);
 bool plane_fits(const gp_handle* h, int seg);  // the fused x + y sweep kernel takes this grid and segment length
+bool tma_fits(const gp_handle* h, int seg);    // the TMA y/z sweeps take this grid and segment length
+bool tma_x_fits(const gp_handle* h, int seg);  // the TMA x sweep takes this grid and segment length
+int read_dev_err(gp_handle* h, const char* who);  // GP_ERR_TIMEOUT (and clears it) if a device wait gave up
 
 int dev_alloc(gp_handle* h, void** p, size_t bytes);
 int join_in(gp_handle* h);
@@ -196,6 +215,9 @@ int run_steps_any(gp_handle* h, bool imag, long nsteps);  // dispatch on h->prec
 int time_steps_any(gp_handle* h, bool imag, long nsteps, double* ms_out);
 // sums_out: where the seven FP64 sums go (default: the handle's slot)
 int run_observables_any(gp_handle* h, double* dens_dev, double* sums_out = nullptr);
+int time_graph_f32(gp_handle* h, bool imag, int reps, double* ms_out);
+int time_graph_f64(gp_handle* h, bool imag, int reps, double* ms_out);
+int time_graph_df(gp_handle* h, bool imag, int reps, double* ms_out);
 int run_steps_df(gp_handle* h, bool imag, long nsteps);
 int time_steps_df(gp_handle* h, bool imag, long nsteps, double* ms_out);
 int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out = nullptr);

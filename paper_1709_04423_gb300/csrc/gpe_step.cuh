@@ -16,6 +16,9 @@
 #include "gpe_obs.cuh"
 #include "gpe_sweep.cuh"
 #include "gpe_sweep2.cuh"
+#include "gpe_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace gpe {
 
@@ -201,6 +204,142 @@ unsigned launch_p_seg(int seg, const Sweep2Args<T>& a, cudaStream_t s, bool pdl)
   }
 }
 
+// ---- TMA-pipelined persistent y/z sweeps (FP32 state; gpe_tma.cuh)
+// The tensor-map encoder is a driver entry point, looked up through the
+// runtime (no link against the driver library).
+inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The FP32 state (nx, ny, nz complex values of 8 bytes, x fastest) as a 3d
+// tensor whose box is 32 x positions times a whole y line (axis 1) or z line
+// (axis 2).  Needs nx even (row strides a multiple of 16 bytes) and the line
+// length <= 256 (a box dimension's limit); false if the driver refuses.
+inline bool encode_line_map(CUtensorMap* m, void* psi, const LineGeom& g) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.nx * g.ny * 8};
+  const cuuint32_t box[3] = {32u, g.axis == 1 ? (cuuint32_t)g.ny : 1u, g.axis == 2 ? (cuuint32_t)g.nz : 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, psi, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline size_t tmacol_smem(int n) {
+  const size_t coef = (size_t)(3 * n + 512) * 8;
+  return ((coef + 1023) / 1024) * 1024 + 1024 + (size_t)kTmaStages * 32 * n * 8;
+}
+
+template <bool IMAG, bool LAST, int SEG, bool CLOSE>
+unsigned launch_tc(gp_handle* h, const Sweep2Args<float>& a, cudaStream_t s, bool pdl) {
+  const LineGeom& g = a.geom;
+  const int nseg = (g.n - 2 + SEG - 1) / SEG;
+  const size_t smem = tmacol_smem(g.n);
+  auto kern = tmacol_kernel<IMAG, LAST, SEG, CLOSE>;
+  static size_t attr_set = 0;  // largest dynamic shared memory opted in so far
+  if (smem > attr_set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = smem;
+  }
+  CUtensorMap map;
+  if (!encode_line_map(&map, a.psi, g)) {
+    g_err = "cuTensorMapEncodeTiled refused the state's tensor map";
+    return 0;
+  }
+  TmaTiles T;
+  T.nxt = (g.nx + 31) / 32;
+  T.ntiles = T.nxt * (g.axis == 1 ? g.nz : g.ny);
+  T.limit_ns = h->tma_limit_ns;
+  T.expect_extra = h->tma_expect_extra;
+  T.err = h->dev_err;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (nseg + 1), smem);
+  const int blocks = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * std::max(1, sms)));
+  launch_k(pdl, kern, dim3(blocks), dim3(32 * (nseg + 1)), smem, s, map, a, T);
+  count_launch();
+  return (unsigned)blocks;
+}
+
+// The FP32 state as (16, nx/16, nlines) 8-byte elements -- 16-point chunks of
+// the x lines -- with the box (16, 1, 32) and the 128-byte swizzle (the TMA x
+// sweep's tiles).  Needs nx a multiple of 16.
+inline bool encode_row_map(CUtensorMap* m, void* psi, const LineGeom& g) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {16u, (cuuint64_t)(g.nx / 16), (cuuint64_t)g.nlines};
+  const cuuint64_t strides[2] = {128u, (cuuint64_t)g.nx * 8};
+  const cuuint32_t box[3] = {16u, 1u, 32u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, psi, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline size_t tmarow_smem(int n) {
+  const size_t coef = (size_t)(3 * n + 512) * 8 + (size_t)n * 4;
+  return ((coef + 1023) / 1024) * 1024 + 1024 + (size_t)kTmaStages * 32 * n * 8;
+}
+
+template <bool IMAG, int SEG>
+unsigned launch_tx(gp_handle* h, Sweep2Args<float> a, int mode, cudaStream_t s, bool pdl) {
+  const LineGeom& g = a.geom;
+  const int nseg = g.n / SEG;
+  const size_t smem = tmarow_smem(g.n);
+  auto kern = tmarow_kernel<IMAG, SEG>;
+  static size_t attr_set = 0;
+  if (smem > attr_set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = smem;
+  }
+  // the tables of segments aligned to even points
+  const float2* ev = (const float2*)h->coef_even[mode];
+  const int si = SEG == 8 ? 0 : 1;
+  a.gf = ev + (size_t)(2 * si) * g.n;
+  a.gb = ev + (size_t)(2 * si + 1) * g.n;
+  a.ptab = ev + (size_t)4 * g.n + 512 * si;
+  CUtensorMap map;
+  if (!encode_row_map(&map, a.psi, g)) {
+    g_err = "cuTensorMapEncodeTiled refused the state's tensor map";
+    return 0;
+  }
+  TmaTiles T;
+  T.nxt = 1;
+  T.ntiles = (int)((g.nlines + 31) / 32);
+  T.limit_ns = h->tma_limit_ns;
+  T.expect_extra = h->tma_expect_extra;
+  T.err = h->dev_err;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (nseg + 1), smem);
+  const int blocks = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * std::max(1, sms)));
+  // nseg consumer warps (one per segment) and one producer warp
+  launch_k(pdl, kern, dim3(blocks), dim3(32 * (nseg + 1)), smem, s, map, a, T);
+  count_launch();
+  return (unsigned)blocks;
+}
+
+template <bool IMAG, bool LAST, bool CLOSE = false>
+unsigned launch_tc_seg(gp_handle* h, int seg, const Sweep2Args<float>& a, cudaStream_t s, bool pdl) {
+  switch (seg) {
+    case 8: return launch_tc<IMAG, LAST, 8, CLOSE>(h, a, s, pdl);
+    case 16: return launch_tc<IMAG, LAST, 16, CLOSE>(h, a, s, pdl);
+    default: return launch_tc<IMAG, LAST, 32, CLOSE>(h, a, s, pdl);
+  }
+}
+
 // ---- thread-per-line fallback (lines longer than the segmented kernels take)
 template <typename T, bool IMAG, bool FIRST, bool LAST>
 unsigned launch_legacy(const SweepArgs<T>& a, cudaStream_t s) {
@@ -330,6 +469,22 @@ bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
         blocks = launch_x_seg<T, false, true, false, true>(seg, a, h->work, h->pdl_now);
       }
       done = true;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (!done && d == 0 && h->tma_x && src == nullptr && !var) {
+        blocks = seg == 8 ? (imag ? launch_tx<true, 8>(h, a, mode, h->work, h->pdl_now)
+                                  : launch_tx<false, 8>(h, a, mode, h->work, h->pdl_now))
+                          : (imag ? launch_tx<true, 16>(h, a, mode, h->work, h->pdl_now)
+                                  : launch_tx<false, 16>(h, a, mode, h->work, h->pdl_now));
+        done = true;
+      }
+      if (!done && d > 0 && h->tma_c) {
+        if (fuse_close) blocks = launch_tc_seg<true, true, true>(h, seg, a, h->work, h->pdl_now);
+        else if (imag) blocks = write ? launch_tc_seg<true, true>(h, seg, a, h->work, h->pdl_now)
+                                      : launch_tc_seg<true, false>(h, seg, a, h->work, h->pdl_now);
+        else blocks = launch_tc_seg<false, false>(h, seg, a, h->work, h->pdl_now);
+        done = true;
+      }
     }
     if constexpr (!is_df<T>::value) {  // pipelined shapes: FP32 and FP64 states only
       if (done) {
@@ -603,6 +758,69 @@ int time_steps_t(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   for (auto& ee : ev) cudaEventDestroy(ee);
   if (rc) return rc;
   for (int d = 0; d < 3; ++d) ms_out[d] = (d < h->dim && nsteps > 0) ? acc[d] / nsteps : 0.0;
+  GP_CUDA(cudaGetLastError());
+  return join_out(h);
+}
+
+// Each axis' sweep (the x sweep with N, or the fused x + y kernel; the y/z
+// sweeps, the last with its norm) launched reps times back to back inside a
+// captured graph -- programmatic edges as in the step graph -- and the
+// replay timed with events on the library's stream: ms_out[d] = mean
+// duration per launch as the kernel runs inside a step's graph (0 for an axis
+// that has no launch of its own).  Two eager steps first give the norm slots
+// valid contents; the caller restores the state.
+template <typename T>
+int time_sweeps_graph_t(gp_handle* h, bool imag, int reps, double* ms_out) {
+  int rc = join_in(h);
+  if (rc) return rc;
+  for (int d = 0; d < 3; ++d) ms_out[d] = 0.0;
+  struct PdlScope {
+    gp_handle* h;
+    explicit PdlScope(gp_handle* hh) : h(hh) { h->pdl_now = pdl_enabled() && h->prec != GP_F64; }
+    ~PdlScope() { h->pdl_now = false; }
+  } pdl_scope(h);
+  for (long t = 0; t < 2; ++t) enqueue_step<T>(h, imag, slots_of_step(imag, t));
+  NormSlots ns;
+  if (imag) {
+    ns.rd = 1;  // written by step 1 above
+    ns.wr = 0;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GP_CUDA(cudaEventCreate(&e0));
+  GP_CUDA(cudaEventCreate(&e1));
+  for (int d = 0; d < h->dim && !rc; ++d) {
+    if (xy_fused(h) && d == 1) continue;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    const int nparts = h->parts_n;
+    const double pws = h->parts_ws;
+    cudaError_t e = cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal);
+    const unsigned long long before = g_launches.load();
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      if (h->real_mode) enqueue_sweep_real<T>(h, ns, d);
+      else enqueue_sweep<T>(h, imag, ns, d);
+      h->parts_n = nparts;  // every x launch reads the slot step 1 wrote
+      h->parts_ws = pws;
+    }
+    g_launches.store(before);
+    if (e == cudaSuccess) e = cudaStreamEndCapture(h->work, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->work);  // warm-up replay
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->work);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->work);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->work);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) rc = fail(GP_ERR_CUDA, std::string("gp_time_sweeps_graph: ") + cudaGetErrorString(e));
+    else ms_out[d] = ms / reps;
+    count_launch(2ull * reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
   GP_CUDA(cudaGetLastError());
   return join_out(h);
 }

@@ -55,6 +55,10 @@ int time_steps_df(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   return time_steps_t<df64>(h, imag, nsteps, ms_out);
 }
 
+int time_graph_df(gp_handle* h, bool imag, int reps, double* ms_out) {
+  return time_sweeps_graph_t<df64>(h, imag, reps, ms_out);
+}
+
 // The observables take the state rounded to complex128 (the sums are FP64).
 int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out) {
   df_to_c128(h, h->df_stage);

@@ -9,6 +9,10 @@ int time_steps_f64(gp_handle* h, bool imag, long nsteps, double* ms_out) {
   return time_steps_t<double>(h, imag, nsteps, ms_out);
 }
 
+int time_graph_f64(gp_handle* h, bool imag, int reps, double* ms_out) {
+  return time_sweeps_graph_t<double>(h, imag, reps, ms_out);
+}
+
 int run_observables_f64(gp_handle* h, double* dens_dev, double* sums_out) {
   return run_observables_t<double>(h, dens_dev, sums_out);
 }

@@ -31,6 +31,8 @@ PRECISIONS = {"f64": GP_F64, "f32": GP_F32, "df64": GP_DF64}
 GP_SHAPE_KEEP_YZ = 1
 GP_SHAPE_PIPE_X = 2
 GP_SHAPE_PIPE_YZ = 4
+GP_SHAPE_TMA_YZ = 16
+GP_SHAPE_TMA_X = 32
 GP_SHAPE_FUSE_XY = 8
 
 # every entry point declared in include/gpe.h
@@ -42,6 +44,7 @@ ABI_SYMBOLS = (
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
     "gp_init_spherical", "gp_set_splitting", "gp_set_real_state", "gp_init_circular", "gp_init_axial",
+    "gp_test_stall_transfers", "gp_time_sweeps_graph", "gp_fp_fma_rates",
 )
 
 
@@ -82,6 +85,9 @@ def load(path: str = LIB_PATH):
     lib.gp_step_real.argtypes = [_vp, L]
     lib.gp_observables.argtypes = [_vp, ctypes.POINTER(GpObs), _vp, I]
     lib.gp_time_sweeps.argtypes = [_vp, I, L, ctypes.POINTER(D)]
+    lib.gp_time_sweeps_graph.argtypes = [_vp, I, I, ctypes.POINTER(D)]
+    lib.gp_fp_fma_rates.argtypes = [ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.gp_test_stall_transfers.argtypes = [_vp, I]
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
     lib.gp_autotune.argtypes = [_vp, I, I, ctypes.POINTER(D)]
@@ -218,6 +224,21 @@ def gp_time_sweeps(h, imag, nsteps):
     return list(ms)
 
 
+def gp_time_sweeps_graph(h, imag, reps):
+    """Mean per-launch duration (ms) of each axis' sweep kernel launched reps
+    times back to back inside a CUDA graph (as in a step's graph)."""
+    ms = (ctypes.c_double * 3)()
+    _check(load().gp_time_sweeps_graph(h, int(bool(imag)), int(reps), ms))
+    return list(ms)
+
+
+def gp_fp_fma_rates():
+    """Measured FP64 and FP32 FMA thread-instruction rates (per second) of the device."""
+    d, f = ctypes.c_double(), ctypes.c_double()
+    _check(load().gp_fp_fma_rates(ctypes.byref(d), ctypes.byref(f)))
+    return d.value, f.value
+
+
 def gp_observables_noalloc(dim, n, dx, nkl, g, prec, psi_ptr, V_ptr, out_ptr, stream=None):
     """Observables of a device state into a device buffer of 7 doubles, with
     no handle and no allocation (see include/gpe.h); asynchronous on stream."""
@@ -316,6 +337,12 @@ def gp_last_error():
 
 def gp_kernel_launches():
     return int(load().gp_kernel_launches())
+
+
+def gp_test_stall_transfers(h, extra_bytes):
+    """Test hook: TMA tile loads announce extra bytes, so their bounded waits
+    run out (see include/gpe.h)."""
+    return _check(load().gp_test_stall_transfers(h, int(extra_bytes)))
 
 
 # ----------------------------------------------------------------- wrapper
@@ -440,6 +467,9 @@ class Propagator:
 
     def time_sweeps(self, imag, nsteps):
         return gp_time_sweeps(self.h, imag, nsteps)
+
+    def time_sweeps_graph(self, imag, reps=32):
+        return gp_time_sweeps_graph(self.h, imag, reps)
 
     def shapes(self):
         return gp_get_shapes(self.h)
