@@ -1,34 +1,42 @@
 """Benchmark of the split-step Crank-Nicolson GP propagator on GB300.
 
-Workload (default): the 3d imaginary-time anisotropic trap -- 128^3 grid,
+Headline workload: the 3d imaginary-time anisotropic trap -- 128^3 grid,
 dx = 0.1, dt = 1e-3, V = (nu^2 x^2 + kappa^2 y^2 + lambda^2 z^2)/2 with
-nu, kappa, lambda = 1, 1.4, 1.8, g = 50, seeded-noise Gaussian initial state.
-One bench step = ``--inner`` imaginary-time steps (renormalised every step)
-followed by one evaluation of the observables (norm, energy, mu, rms), i.e.
-one pass of the whole hot path.  The metric is grid-point-steps per second.
+nu, kappa, lambda = 1, 1.4, 1.8, g = 50, seeded-noise Gaussian initial state
+(the 5000-step job).  One bench step = ``--inner`` imaginary-time steps
+(renormalised every step) followed by one evaluation of the observables, i.e.
+one pass of the whole hot path; the metric is grid-point-steps per second.
 
-Two forms are timed: the plain FP64 path and the chosen FP32 form (FP32 state
-and sweeps, FP64 norm/energy/mu reductions and renormalisation).  ``value`` is
-the FP32 form's throughput; its mu error is measured against the FP64 path
-over the full 5000-step job (the FP64 path itself is held to the CPU oracle
-by the parity tests).
+Forms: the plain FP64 path, the chosen FP32 form (FP32 state and sweeps, FP64
+norm/energy/mu reductions and renormalisation; ``value``) and the
+double-float form (FP64-class accuracy on the FP32 pipes).  Each form's
+observables are compared with the FP64 path's after the full job and when
+converged (the FP64 path itself is held to the CPU oracle by the parity
+tests).  The 128^3 FP32 state fits in the 129 MB L2, so L2 is flushed (a
+256 MB write) before every timed bench step.
 
-The state (16.8 MB FP32, 33.5 MB FP64) fits in the 129 MB L2, so L2 is
-flushed (a 256 MB write) before every timed bench step; within a bench step
-the state stays resident across time steps, as it does in a real run.
+Also measured, in the same run: the 256^3 real-time quench (the state is
+larger than L2, so its sweeps stream from HBM: the HBM roofline is measured
+there), the 64-run batched form, the 128^3 adjoint, and the symmetric-trap,
+Strang and real-state forms.  Kernel durations for the rooflines are those of
+the kernels launched back to back inside a CUDA graph (as in the step graph).
+The FP64 sweeps are bound by the FP64 pipe, so they are also held to the
+measured FP64 FMA rate.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
-bounded sample of the same workload per step).
+bounded sample of the same workload per step), on the same config.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -40,8 +48,10 @@ WORKLOAD = {
     "dim": 3, "n": [128, 128, 128], "dx": [0.1, 0.1, 0.1], "dt": 1e-3,
     "nkl": [1.0, 1.4, 1.8], "g": 50.0, "seed": 1710, "job_steps": 5000,
 }
+QUENCH = "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, ground state at g=20 then g=40"
 METRIC = "3d split-step CN grid-point-steps/s: FP32/batched vs FP64 at fixed mu error"
 UNIT = "grid-point-steps/s"
+OBS = ("norm", "energy", "mu", "rms_x", "rms_y", "rms_z", "rms_r")
 
 
 def parse():
@@ -53,17 +63,13 @@ def parse():
     ap.add_argument("--inner", type=int, default=100, help="time steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mu-check", action="store_true")
-    ap.add_argument("--no-quench", action="store_true", help="skip the 256^3 real-time form")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint form")
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
-    ap.add_argument("--no-spherical", action="store_true", help="skip the spherical-trap form")
-    ap.add_argument("--no-strang", action="store_true", help="skip the Strang-splitting form")
-    ap.add_argument("--no-real", action="store_true", help="skip the real-state form")
     ap.add_argument("--forms", default="f64,f32,df64",
-                    help="precision forms of the headline workload to time (the line needs f32; f64 for ratios)")
-    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical", "strang", "real"],
-                    help="time one form only (for profiling); the other forms are reported as null")
+                    help="precision forms to time (the line needs f32; f64 for ratios and errors)")
+    ap.add_argument("--only", choices=["headline", "quench256", "batched", "adjoint", "spherical", "strang", "real",
+                                       "dp-peak"],
+                    help="time one part only (for profiling); the others are skipped")
+    ap.add_argument("--details", default=None, help="also write every measured number to this JSON file")
     args = ap.parse_args()
     if "f32" not in args.forms.split(","):
         ap.error("--forms must include f32 (the headline form)")
@@ -97,7 +103,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-SWEEP_SOURCES = ("gpe_common.cuh", "gpe_df.cuh", "gpe_sweep2.cuh", "gpe_step.cuh")
+SWEEP_SOURCES = ("gpe_common.cuh", "gpe_df.cuh", "gpe_sweep2.cuh", "gpe_step.cuh", "gpe_tma.cuh")
 
 
 def src_hash():
@@ -111,64 +117,106 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel_key):
-    """DRAM bytes per launch from a committed ncu capture, if the kernels have
-    not changed since it was taken (else None)."""
+def profile_record(name, key):
+    """A per-launch counter (DRAM bytes, FP64 instructions) from a committed ncu
+    summary under profiles/, if the sweep sources have not changed since it was
+    taken (else None)."""
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
     except Exception:
         return None
-    r = rec.get(kernel_key)
+    r = rec.get(key)
     if not r or r.get("src_hash") != src_hash():
         return None
-    return r.get("bytes_per_launch")
+    return r
 
+
+# ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons of the GPU, sampled every 10 ms by a
+    thread through NVML (ctypes; nvidia-smi as a fallback); summary() keeps
+    the samples between mark_start() and mark_end()."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
-        self.p = None
+        self.samples = []
+        self.t0 = self.t1 = None
+        self.stop = threading.Event()
+        self.nvml = None
+        self.smi = None
+        self.max_mhz = None
 
     def __enter__(self):
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            h = ctypes.c_void_p()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            idx = int(vis.split(",")[self.idx]) if vis and vis.split(",")[0].isdigit() else self.idx
+            if nv.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) != 0:
+                raise OSError("handle")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.nvml, self.h = nv, h
+            self.thr = threading.Thread(target=self._poll, daemon=True)
+            self.thr.start()
         except Exception:
-            self.p = None
+            self.nvml = None
+            try:
+                self.smi = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.idx), "--query-gpu=timestamp,clocks.sm,clocks.max.sm,"
+                     "clocks_event_reasons.active", "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.smi = None
         return self
 
+    def _poll(self):
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            t = time.perf_counter()
+            a = self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk))
+            b = self.nvml.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs))
+            if a == 0 and b == 0:
+                self.samples.append((t, float(clk.value), int(rs.value)))
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
+
     def __exit__(self, *a):
-        self.rows = []
-        if self.p is None:
-            return
-        self.p.terminate()
-        try:
-            out, _ = self.p.communicate(timeout=5)
-        except Exception:
-            self.p.kill()
-            out = ""
-        for line in out.strip().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+        self.stop.set()
+        if self.nvml is not None:
+            self.thr.join(timeout=2)
+        if self.smi is not None:
+            self.smi.terminate()
+            try:
+                out, _ = self.smi.communicate(timeout=5)
+            except Exception:
+                self.smi.kill()
+                out = ""
+            # no usable timestamps against perf_counter: keep every sample
+            for line in out.strip().splitlines():
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 4 and p[1].replace(".", "").isdigit():
+                    self.max_mhz = float(p[2]) if p[2].replace(".", "").isdigit() else self.max_mhz
+                    self.samples.append((None, float(p[1]), int(p[3], 16) if p[3].startswith("0x") else 0))
 
     def summary(self):
-        if not getattr(self, "rows", None):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
-        loaded = sorted(sm)[len(sm) // 4:] if sm else []
-        return {"sm_mhz": statistics.median(loaded) if loaded else None,
-                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        s = [x for x in self.samples if x[0] is None or (self.t0 is not None and self.t0 <= x[0] <= (self.t1 or 1e30))]
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        reasons = sorted({name for _, _, r in s for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(x[1] for x in s), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(s), "source": "nvml" if self.nvml is not None else "nvidia-smi"}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -193,7 +241,14 @@ def oracle_rate(target_s=12.0, max_steps=2000):
     np_ = int(np.prod(w["n"]))
     return {"value": k * np_ / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": f"{k} imaginary-time steps of the 128^3 workload (FP64, OpenMP over lines)",
-            "seconds": dt}
+            "seconds": round(dt, 2)}
+
+
+def line_config(world):
+    """The config both arms print (the workload, not how a bench step samples it)."""
+    w = WORKLOAD
+    return {"workload": w["name"], "global_batch": 1, "points": w["n"][0] * w["n"][1] * w["n"][2],
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def run_reference(args):
@@ -222,8 +277,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": w["name"], "inner_steps_per_step": per, "l2": "n/a (CPU)"},
+        "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
+        "config": line_config(1),
+        "timing": {"inner_steps_per_step": per, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{per} imaginary-time steps + observables of the 128^3 workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -246,11 +302,18 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    peak_note = "measured hbm_gbs" if peak_src == "measured" else "fallback 6.8 TB/s"
     w = WORKLOAD
     np_ = int(np.prod(w["n"]))
     phi0 = inputs.gaussian_state(w["dim"], w["n"], w["dx"], w["nkl"], seed=w["seed"], noise=1e-3)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    only = args.only
+    run = (lambda part: only is None or only == part)
+    forms_sel = [f for f in ("f64", "f32", "df64") if f in args.forms.split(",")]
+    R = {}  # everything measured (written with --details)
 
     def barrier():
         torch.cuda.synchronize()
@@ -264,43 +327,63 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    def make(prec):
+    def errs(a, b, keys=OBS):
+        return {k: abs(a[k] - b[k]) for k in keys}
+
+    # ---- FP64 / FP32 FMA rates of this GPU (the FP64 sweeps' ALU roof)
+    dfma, ffma = gpe.gp_fp_fma_rates()
+    R["fp_rates"] = {"dfma_per_s": dfma, "ffma_per_s": ffma}
+    if only == "dp-peak":
+        if rank == 0:
+            print(json.dumps({"only": "dp-peak", **R["fp_rates"]}), flush=True)
+        return
+
+    def make(prec, n=w["n"], dx=w["dx"], dt=w["dt"], nkl=w["nkl"], g=w["g"], phi=phi0, imag=True):
         with torch.cuda.stream(stream):
-            p = gpe.Propagator(w["dim"], w["n"], w["dx"], w["dt"], w["nkl"], w["g"], precision=prec,
-                               stream=stream)
-            p.autotune(imag=True, cache=False)   # kernel shapes for this grid (untimed)
-            p.set_state(torch.tensor(phi0, device="cuda"))
+            p = gpe.Propagator(w["dim"], n, dx, dt, nkl, g, precision=prec, stream=stream)
+            p.autotune(imag=imag, cache=False)   # kernel shapes for this grid (untimed)
+            p.set_state(torch.tensor(phi, device="cuda") if isinstance(phi, np.ndarray) else phi)
         return p
 
-    results = {}
-    # ---- mu accuracy of the FP32 form over the full job (untimed)
-    mu = {}
-    forms_sel = [f for f in ("f64", "f32", "df64") if f in args.forms.split(",")]
-    mu_conv = {}
-    if not args.no_mu_check:
+    def fp64_alu(kms, key_fmt, npts):
+        """FP64 sweeps against the measured DFMA rate: DP thread instructions
+        per point from a committed ncu capture of the same kernels."""
+        out = []
+        for d, t in enumerate(kms):
+            rec = profile_record("fp64_dp_ops.json", key_fmt.format(d))
+            if not t or not rec:
+                out.append(None)
+                continue
+            rate = rec["dp_inst_per_point"] * npts / (t * 1e-3)
+            out.append({"dp_inst_per_point": rec["dp_inst_per_point"], "achieved": rate, "frac": rate / dfma})
+        return out
+
+    # ---- headline: 128^3 imaginary time, every form
+    head = {}
+    if run("headline"):
+        mu_job, mu_conv = {}, {}
+        if not args.no_mu_check:
+            for prec in forms_sel:
+                p = make(prec)
+                with torch.cuda.stream(stream):
+                    p.step_imag(w["job_steps"])
+                    mu_job[prec] = p.observables()
+                    # continued to 20000 steps: converged (FP32: an exact fixed point of the rounded step)
+                    p.step_imag(20000 - w["job_steps"])
+                    mu_conv[prec] = p.observables()
+                p.close()
         for prec in forms_sel:
             p = make(prec)
-            with torch.cuda.stream(stream):
-                p.step_imag(w["job_steps"])
-                mu[prec] = p.observables()
-                # continued to 20000 steps: the state no longer changes (FP32: an
-                # exact fixed point of the rounded step), mu is the converged one
-                p.step_imag(20000 - w["job_steps"])
-                mu_conv[prec] = p.observables()
-            p.close()
-    # ---- timed forms
-    for prec in (forms_sel if not args.no_headline else ()):
-        p = make(prec)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                p.step_imag(args.inner)
-                p.observables()
-            barrier()
-            l0 = gpe.gp_kernel_launches()
-            torch.cuda.nvtx.range_push(f"timed_{prec}")   # profilers can select the timed launches
-            with ClockSampler(local) as clk:
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            with torch.cuda.stream(stream), ClockSampler(local) as clk:
+                for _ in range(args.warmup):
+                    p.step_imag(args.inner)
+                    p.observables()
+                barrier()
+                l0 = gpe.gp_kernel_launches()
+                torch.cuda.nvtx.range_push(f"timed_{prec}")   # profilers can select the timed launches
+                clk.mark_start()
                 for s in range(args.steps):
                     flush.fill_(float(s))                 # evict the state from L2
                     ev[s][0].record(stream)
@@ -308,101 +391,25 @@ def run_ours(args):
                     p.observables()
                     ev[s][1].record(stream)
                 barrier()
-            torch.cuda.nvtx.range_pop()
+                clk.mark_end()
+                torch.cuda.nvtx.range_pop()
             launches = gpe.gp_kernel_launches() - l0
             ms = [a.elapsed_time(b) for a, b in ev]
-            # whole-job throughput over replicas: all ranks' points / slowest rank's time
             value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
-            # per-kernel durations, same state and sizes, right after the timed region
-            kms = p.time_sweeps(True, 64)
-            ob = p.observables()
+            kms = p.time_sweeps_graph(True, 32)       # in-graph per-launch durations, same state and sizes
             shp = p.shapes()
-            # reduced densities of the final state (1d along x, 2d in x-y), device outputs
-            red = {}
-            for keep in ((0,), (0, 1)):
-                for _ in range(3):
-                    p.reduced_density(keep)
-                r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                r0.record(stream)
-                for _ in range(20):
-                    p.reduced_density(keep)
-                r1.record(stream)
-                r1.synchronize()
-                us = r0.elapsed_time(r1) / 20 * 1e3
-                red["keep_" + "".join("xyz"[d] for d in keep)] = {
-                    "us": us, "state_read_gbs": np_ * (8 if prec == "f32" else 16) / (us * 1e-6) / 1e9}
-        p.close()
-        results[prec] = {"total_s": total_s, "value": value, "ms": ms, "launches": launches,
-                         "clocks": clk.summary(), "kernel_ms": kms, "obs": ob, "shapes": shp,
-                         "reduced_density": red}
-    # ---- batched form: 64 independent 2d real-time runs (sizes from
-    # {128..512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1, kappa ~ U[1, 2]),
-    # each from its g = 0 trap ground state (an interaction quench)
-    P = inputs.batch_runs(seed=1712, nruns=64)
-    bsizes = [(int(v), int(v)) for v in P["n"]]
-    bnk = [(1.0, float(k)) for k in P["kappa"]]
-    bg = [float(v) for v in P["g"]]
-    bpts = sum(a * b for a, b in bsizes)
-    bphi = [torch.tensor(inputs.gaussian_state(2, list(sz), [0.1, 0.1], list(k)), device="cuda")
-            for sz, k in zip(bsizes, bnk)]
+            p.close()
+            head[prec] = {"value": value, "ms_per_step": 1e3 * total_s / args.steps, "launches": launches,
+                          "clocks": clk.summary(), "kernel_ms": kms, "shapes": shp}
+        R["headline"] = head
+        R["headline_mu"] = {"job_end": mu_job, "converged_20000": mu_conv}
 
-    def make_batch(prec):
-        with torch.cuda.stream(stream):
-            bb = gpe.Batch(bsizes, [(0.1, 0.1)] * 64, 5e-4, bnk, bg, precision=prec, stream=stream)
-            for i, ph in enumerate(bphi):
-                bb.set_state(i, ph)
-        return bb
-
-    bres = {}
-    bmu = {}
-    for prec in (("f64", "f32") if not args.no_batched else ()):
-        bb = make_batch(prec)
-        with torch.cuda.stream(stream):
-            if not args.no_mu_check:
-                bb.step_real(400)
-                bmu[prec] = [o["mu"] for o in bb.observables()]
-                for i, ph in enumerate(bphi):
-                    bb.set_state(i, ph)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-            for _ in range(args.warmup):
-                bb.step_real(args.inner)
-                bb.observables()
-            barrier()
-            l0 = gpe.gp_kernel_launches()
-            torch.cuda.nvtx.range_push(f"timed_batched_{prec}")
-            for s in range(args.steps):
-                flush.fill_(float(s))
-                ev[s][0].record(stream)
-                bb.step_real(args.inner)
-                bb.observables()
-                ev[s][1].record(stream)
-            barrier()
-            torch.cuda.nvtx.range_pop()
-            blaunch = gpe.gp_kernel_launches() - l0
-            bt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
-        bb.close()
-        bres[prec] = {"value": world * args.steps * args.inner * bpts / bt, "ms_per_step": 1e3 * bt / args.steps,
-                      "gpu_launches": blaunch}
-    bmu_err = bmu_rel = bmu_worst = None
-    if bmu:
-        diffs = [(abs(a - b_), abs(a - b_) / abs(b_), b_, i) for i, (a, b_) in enumerate(zip(bmu["f32"], bmu["f64"]))]
-        bmu_err = max(d[0] for d in diffs)
-        bmu_rel = max(d[1] for d in diffs)
-        w_ = max(diffs)
-        # an FP32 state's own rounding (~6e-8 relative) bounds |dmu| at ~6e-8 mu
-        bmu_worst = {"run": w_[3], "mu_f64": w_[2], "abs_diff": w_[0], "rel_diff": w_[1],
-                     "mu_range_f64": [min(bmu["f64"]), max(bmu["f64"])]}
-
-    # ---- 3d real-time quench at 256^3 (dx = 0.08, dt = 2e-4, isotropic trap):
-    # imaginary-time ground state at g = 20, then real time at g = 40.  The
-    # state (134 MB FP32, 268 MB FP64) is larger than L2, so these sweeps run
-    # from HBM; timed per kernel like the headline form.
-    qres = {}
-    if not args.no_quench:
-        qn, qdx = [256] * 3, [0.08] * 3
-        qnp = 256 ** 3
+    # ---- 256^3 real-time quench: HBM-resident sweeps
+    quench = {}
+    if run("quench256"):
+        qn, qdx, qnp = [256] * 3, [0.08] * 3, 256 ** 3
         qphi = torch.tensor(inputs.gaussian_state(3, qn, qdx, [1.0] * 3, seed=1711, noise=1e-3), device="cuda")
+        qsteps, qwarm = min(args.steps, 5), min(args.warmup, 3)
         for prec in forms_sel:
             with torch.cuda.stream(stream):
                 q = gpe.Propagator(3, qn, qdx, 1e-3, [1.0] * 3, 20.0, precision=prec, stream=stream)
@@ -413,88 +420,148 @@ def run_ours(args):
                 q.autotune(imag=False, cache=False)
                 ob0 = q.observables()
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(args.steps)]
-                for _ in range(args.warmup):
+                      for _ in range(qsteps)]
+                for _ in range(qwarm):
                     q.step_real(args.inner)
                 barrier()
                 torch.cuda.nvtx.range_push(f"timed_quench_{prec}")
                 recs = []
-                for s_ in range(args.steps):
+                for s_ in range(qsteps):
                     ev[s_][0].record(stream)
                     # inner steps + the observables at their end, recorded on the device
                     recs.append(q.step_series(False, args.inner, args.inner, device=True))
                     ev[s_][1].record(stream)
                 barrier()
                 torch.cuda.nvtx.range_pop()
-                rms_t = [[args.warmup * args.inner + (i + 1) * args.inner, float(r_[0, 6])]
-                         for i, r_ in enumerate(recs)]
                 qt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
-                kms = q.time_sweeps(False, 16)
+                kms = q.time_sweeps_graph(False, 16)
                 ob1 = q.observables()
+                shp = q.shapes()
                 q.close()
             esize = 8 if prec == "f32" else 16
-            axis = max(range(3), key=lambda d: kms[d])
-            ach = 2 * esize * qnp / (kms[axis] * 1e-3) / 1e9
-            qres[prec] = {"value": world * args.steps * args.inner * qnp / qt, "ms_per_step": 1e3 * qt / args.steps,
-                          "kernel_ms": kms, "dominant_sweep_axis": axis, "achieved_gbs": ach,
-                          "frac_of_measured_hbm": ach / float(measured_peaks()[0]["hbm_gbs"]),
-                          "energy_drift_rel": abs(ob1["energy"] / ob0["energy"] - 1),
-                          "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1),
-                          "rms_r_t": rms_t}
+            step_us = 1e6 * qt / (qsteps * args.inner)
+            quench[prec] = {"value": world * qsteps * args.inner * qnp / qt, "us_per_time_step": step_us,
+                            "sweep_us": [1e3 * t for t in kms],
+                            "sweep_frac_hbm": [(2 * esize * qnp / (t * 1e-3) / 1e9 / hbm) if t else None for t in kms],
+                            "step_frac_hbm": 6 * esize * qnp / (step_us * 1e-6) / 1e9 / hbm,
+                            "energy_drift_rel": abs(ob1["energy"] / ob0["energy"] - 1),
+                            "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1), "obs_end": ob1,
+                            "rms_r_t": [float(r_[0, 6]) for r_ in recs], "shapes": shp}
+            if prec == "f64":
+                quench[prec]["alu"] = fp64_alu(kms, "sweep{}_f64_real_256", qnp)
+        R["quench256"] = quench
 
-    # ---- spherically symmetric trap (radial problem for u = sqrt(4 pi) r phi):
-    # n = 513 points on [0, 10.24], dt = 1e-4, nu = 1, g = 100, imaginary time
-    # (a 1d line: launch-latency bound, one sweep kernel per step)
-    sres = {}
-    if not args.no_spherical:
-        sn, sdr = 513, 0.02
-        sr = np.arange(sn) * sdr
-        su = torch.tensor((np.sqrt(4 * np.pi) * sr * np.exp(-0.6 * sr ** 2)).astype(np.complex128), device="cuda")
-        smu = {}
-        for prec in forms_sel:
+    # ---- batched form: 64 independent 2d real-time runs
+    bres, bmu = {}, {}
+    if run("batched"):
+        P = inputs.batch_runs(seed=1712, nruns=64)
+        bsizes = [(int(v), int(v)) for v in P["n"]]
+        bnk = [(1.0, float(k)) for k in P["kappa"]]
+        bg = [float(v) for v in P["g"]]
+        bpts = sum(a * b for a, b in bsizes)
+        bphi = [torch.tensor(inputs.gaussian_state(2, list(sz), [0.1, 0.1], list(k)), device="cuda")
+                for sz, k in zip(bsizes, bnk)]
+        for prec in ("f64", "f32"):
             with torch.cuda.stream(stream):
-                q = gpe.Propagator(1, [sn], [sdr], 1e-4, [1.0], 100.0, precision=prec, stream=stream, spherical=True)
-                q.set_state(su)
-                q.step_imag(20000)
-                smu[prec] = q.observables()
-                q.set_state(su)
+                bb = gpe.Batch(bsizes, [(0.1, 0.1)] * 64, 5e-4, bnk, bg, precision=prec, stream=stream)
+                for i, ph in enumerate(bphi):
+                    bb.set_state(i, ph)
+                if not args.no_mu_check:
+                    bb.step_real(400)
+                    bmu[prec] = bb.observables()
+                    for i, ph in enumerate(bphi):
+                        bb.set_state(i, ph)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
                 for _ in range(args.warmup):
-                    q.step_imag(2000)
+                    bb.step_real(args.inner)
+                    bb.observables()
                 barrier()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for _ in range(args.steps):
-                    q.step_imag(2000)
-                e1.record(stream)
+                l0 = gpe.gp_kernel_launches()
+                torch.cuda.nvtx.range_push(f"timed_batched_{prec}")
+                for s in range(args.steps):
+                    flush.fill_(float(s))
+                    ev[s][0].record(stream)
+                    bb.step_real(args.inner)
+                    bb.observables()
+                    ev[s][1].record(stream)
                 barrier()
-                st = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-                q.close()
-            sres[prec] = {"value": world * args.steps * 2000 * sn / st, "us_per_step": 1e6 * st / (args.steps * 2000),
-                          "mu_after_20000_steps": smu[prec]["mu"], "rms_radius": smu[prec]["rms_x"]}
-        if "f64" in smu:
-            for prec in sres:
-                sres[prec]["mu_diff_vs_f64"] = abs(smu[prec]["mu"] - smu["f64"]["mu"])
+                torch.cuda.nvtx.range_pop()
+                blaunch = gpe.gp_kernel_launches() - l0
+                bt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
+                bb.close()
+            bres[prec] = {"value": world * args.steps * args.inner * bpts / bt, "ms_per_step": 1e3 * bt / args.steps,
+                          "gpu_launches": blaunch}
+        R["batched"] = {"points": bpts, **bres}
+        if bmu:
+            worst = {k: max(abs(a[k] - b[k]) for a, b in zip(bmu["f32"], bmu["f64"])) for k in OBS}
+            run_w = max(range(64), key=lambda i: abs(bmu["f32"][i]["mu"] - bmu["f64"][i]["mu"]))
+            R["batched"]["f32_err_vs_f64_400_steps"] = {"worst_per_observable": worst, "worst_mu_run": run_w,
+                                                         "mu_f64_of_that_run": bmu["f64"][run_w]["mu"]}
 
-    # ---- circularly symmetric 2d trap (513 rho points, drho = 0.02, g = 100,
-    # dt = 1e-4) and axially symmetric 3d trap (rho x z = 256 x 512, drho = dz
-    # = 0.04, nu = 1, lambda = 2, g = 100, dt = 5e-4), imaginary time, every
-    # form; mu after 20000 / 4000 steps against the FP64 form's
-    ares_sym = {}
-    if not args.no_spherical:
-        cases = {"circular": (1, [513], [0.02], [1.0], 1e-4, 20000, 2000),
-                 "axial": (2, [256, 512], [0.04, 0.04], [1.0, 2.0], 5e-4, 4000, 200)}
-        for name, (cd, cn, cdx, cnkl, cdt, cmu_steps, cblock) in cases.items():
-            rho = np.arange(cn[0]) * cdx[0] - 0.5 * cdx[0]
-            if cd == 1:
-                cphi = np.exp(-0.3 * rho ** 2)
-            else:
-                zz = inputs.axis_coords(cn[1], cdx[1])
-                cphi = np.exp(-0.3 * (rho[None, :] ** 2 + 2.0 * zz[:, None] ** 2))
-            cphi = torch.tensor(cphi.astype(np.complex128), device="cuda")
-            cmu, cres = {}, {}
+    # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V and g
+    ares = {}
+    if run("adjoint"):
+        an, adx = [128] * 3, [0.1] * 3
+        anp = 128 ** 3
+        dV, _bp = inputs.gaussian_bumps(3, an, adx, seed=1713, count=8, amp=0.5, center=3.0)
+        xs = inputs.axis_coords(128, 0.1)
+        harm = 0.5 * (xs[:, None, None] ** 2 + xs[None, :, None] ** 2 + xs[None, None, :] ** 2)
+        AV = torch.tensor(harm + dV, device="cuda")
+        aphi = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3), device="cuda")
+        atgt = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3, shift=(0.5, 0.0, 0.0)), device="cuda")
+        with torch.cuda.stream(stream):
+            q = gpe.Propagator(3, an, adx, 5e-4, [1.0] * 3, 30.0, precision="f32", stream=stream)
+            q.set_potential(AV)
+            times = []
+            for rep in range(1 + 2):
+                q.set_state(aphi)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                barrier()
+                e0.record(stream)
+                gpe.gp_adjoint_forward(q.h, 1000, 50)
+                e1.record(stream)
+                phiT = q.get_state(device=True).to(torch.complex128)
+                c = torch.sum(torch.conj(atgt) * phiT) * 1e-3
+                lam = (2 * c * atgt * 1e-3).to(q.ctype).contiguous()
+                dJdV = torch.empty(tuple(an), dtype=torch.float64, device="cuda")
+                e_b = torch.cuda.Event(enable_timing=True)
+                e_b.record(stream)
+                dJdg = gpe.gp_adjoint_backward(q.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1)
+                e2.record(stream)
+                barrier()
+                if rep:
+                    times.append((e0.elapsed_time(e1), e_b.elapsed_time(e2)))
+            q.close()
+        tf = sum(t[0] for t in times) / len(times)
+        tb = sum(t[1] for t in times) / len(times)
+        ares = {"forward_ms": tf, "backward_ms": tb, "value": world * 1000 * anp / ((tf + tb) * 1e-3),
+                "backward_over_forward": tb / tf, "dJdg": dJdg}
+        R["adjoint_f32"] = ares
+
+    # ---- symmetric traps: spherical (513 radial points), circular (513 rho
+    # points), axial (rho x z = 256 x 512); imaginary time, every form
+    sym = {}
+    if run("spherical"):
+        sr = np.arange(513) * 0.02
+        cases = {"spherical": (1, [513], [0.02], [1.0], 1e-4, 20000, 2000, dict(spherical=True),
+                               (np.sqrt(4 * np.pi) * sr * np.exp(-0.6 * sr ** 2)).astype(np.complex128)),
+                 "circular": (1, [513], [0.02], [1.0], 1e-4, 20000, 2000, dict(axisym=True), None),
+                 "axial": (2, [256, 512], [0.04, 0.04], [1.0, 2.0], 5e-4, 4000, 200, dict(axisym=True), None)}
+        for name, (cd, cn, cdx, cnkl, cdt, cmu_steps, cblock, kw, cphi) in cases.items():
+            if cphi is None:
+                rho = np.arange(cn[0]) * cdx[0] - 0.5 * cdx[0]
+                if cd == 1:
+                    cphi = np.exp(-0.3 * rho ** 2)
+                else:
+                    zz = inputs.axis_coords(cn[1], cdx[1])
+                    cphi = np.exp(-0.3 * (rho[None, :] ** 2 + 2.0 * zz[:, None] ** 2))
+                cphi = cphi.astype(np.complex128)
+            cphi = torch.tensor(cphi, device="cuda")
+            cres, cmu = {}, {}
             for prec in forms_sel:
                 with torch.cuda.stream(stream):
-                    q = gpe.Propagator(cd, cn, cdx, cdt, cnkl, 100.0, precision=prec, stream=stream, axisym=True)
+                    q = gpe.Propagator(cd, cn, cdx, cdt, cnkl, 100.0, precision=prec, stream=stream, **kw)
                     q.set_state(cphi)
                     q.step_imag(cmu_steps)
                     cmu[prec] = q.observables()
@@ -512,95 +579,69 @@ def run_ours(args):
                     q.close()
                 npts = int(np.prod(cn))
                 cres[prec] = {"value": world * args.steps * cblock * npts / st,
-                              "us_per_step": 1e6 * st / (args.steps * cblock),
-                              "mu": cmu[prec]["mu"], "rms_rho": cmu[prec]["rms_x"]}
+                              "us_per_step": 1e6 * st / (args.steps * cblock), "mu": cmu[prec]["mu"]}
             if "f64" in cmu:
                 for prec in cres:
                     cres[prec]["mu_diff_vs_f64"] = abs(cmu[prec]["mu"] - cmu["f64"]["mu"])
-            ares_sym[name] = cres
+            sym[name] = cres
+        R["symmetric_traps"] = sym
 
-    # ---- real state (imaginary-time maps keep the real input real): the
-    # headline workload and loop with the state held as np real values;
-    # mu after the full job against the complex FP64 form's
+    # ---- real state: the headline workload held as np real values
     rres = {}
-    if not args.no_real:
+    if run("real"):
         for prec in [f for f in forms_sel if f != "df64"]:
             p = make(prec)
             p.set_real_state(True)
-            p.autotune(imag=True, cache=False)   # shapes for the real state (untimed)
+            p.autotune(imag=True, cache=False)
             with torch.cuda.stream(stream):
                 p.step_imag(w["job_steps"])
                 rmu = p.observables()["mu"]
                 p.set_state(torch.tensor(phi0, device="cuda"))
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-            with torch.cuda.stream(stream):
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
                 for _ in range(args.warmup):
                     p.step_imag(args.inner)
                     p.observables()
                 barrier()
-                l0 = gpe.gp_kernel_launches()
-                torch.cuda.nvtx.range_push(f"timed_real_{prec}")
-                with ClockSampler(local) as rclk:
-                    for s in range(args.steps):
-                        flush.fill_(float(s))
-                        ev[s][0].record(stream)
-                        p.step_imag(args.inner)
-                        p.observables()
-                        ev[s][1].record(stream)
-                    barrier()
-                torch.cuda.nvtx.range_pop()
-                launches = gpe.gp_kernel_launches() - l0
+                for s in range(args.steps):
+                    flush.fill_(float(s))
+                    ev[s][0].record(stream)
+                    p.step_imag(args.inner)
+                    p.observables()
+                    ev[s][1].record(stream)
+                barrier()
             ms = [a.elapsed_time(b) for a, b in ev]
             value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
-            kms = p.time_sweeps(True, 64)
             p.close()
-            esz = 4 if prec == "f32" else 8
-            rres[prec] = {"value": value, "ms_per_step": 1e3 * total_s / args.steps, "gpu_launches": launches,
-                          "clocks": rclk.summary(), "kernel_ms": kms,
-                          "sweep_state_gbs": [2 * esz * np_ / (t * 1e-3) / 1e9 for t in kms],
-                          "mu_after_job": rmu,
-                          "mu_err_vs_complex_f64": abs(rmu - mu["f64"]["mu"]) if "f64" in mu else None,
-                          "speedup_vs_complex": (value / results[prec]["value"]) if prec in results else None}
+            rres[prec] = {"value": value, "ms_per_step": 1e3 * total_s / args.steps, "mu_after_job": rmu}
+        R["real_state"] = rres
 
-    # ---- Strang splitting (N(dt/2), the sweeps, N(dt/2)) on the headline
-    # workload, timed like the Lie step; and its accuracy: real-time runs of a
-    # 64^3 grid (dx = 0.2, trap (1, 1.4, 1.8), g = 50) to t = 0.1 with dt =
-    # 2e-3, 1e-3, 5e-4 against a Strang run with dt = 6.25e-5, FP64, for both
-    # splittings (relative L2 error of phi(t), observed order)
+    # ---- Strang splitting on the headline grid; accuracy study at 64^3
     stres = {}
-    if not args.no_strang:
+    if run("strang"):
         for prec in forms_sel:
             p = make(prec)
             stres[prec] = {}
             for mode in ("imag", "real"):
                 for split in ("lie", "strang"):
                     p.set_splitting(split)
-                    run = p.step_imag if mode == "imag" else p.step_real
+                    stepper = p.step_imag if mode == "imag" else p.step_real
                     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                           for _ in range(args.steps)]
                     with torch.cuda.stream(stream):
                         p.set_state(torch.tensor(phi0, device="cuda"))
                         for _ in range(args.warmup):
-                            run(args.inner)
+                            stepper(args.inner)
                         barrier()
-                        l0 = gpe.gp_kernel_launches()
-                        torch.cuda.nvtx.range_push(f"timed_{split}_{mode}_{prec}")
                         for s in range(args.steps):
                             flush.fill_(float(s))
                             ev[s][0].record(stream)
-                            run(args.inner)
+                            stepper(args.inner)
                             ev[s][1].record(stream)
                         barrier()
-                        torch.cuda.nvtx.range_pop()
-                        launches = gpe.gp_kernel_launches() - l0
                     ms = [a.elapsed_time(b) for a, b in ev]
-                    value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
-                    stres[prec][f"{split}_{mode}"] = {"value": value, "us_per_time_step": 1e6 * total_s / (
-                        args.steps * args.inner), "gpu_launches": launches}
-            for mode in ("imag", "real"):
-                stres[prec][f"strang_time_over_lie_{mode}"] = (stres[prec][f"lie_{mode}"]["value"] /
-                                                                stres[prec][f"strang_{mode}"]["value"])
+                    value, _ = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
+                    stres[prec][f"{split}_{mode}"] = value
             p.close()
         sn_, sdx, snkl, sT = [64] * 3, [0.2] * 3, [1.0, 1.4, 1.8], 0.1
         sphi = torch.tensor(inputs.gaussian_state(3, sn_, sdx, snkl, seed=1715, noise=0.0), device="cuda")
@@ -617,72 +658,20 @@ def run_ours(args):
             return out
         sdts = [2e-3, 1e-3, 5e-4]
         fine = run_rt(sdts[-1] / 8, "strang")
-        acc = {}
         for split in ("lie", "strang"):
-            errs = [float(torch.linalg.norm(run_rt(dt, split) - fine) / torch.linalg.norm(fine)) for dt in sdts]
-            acc[split] = {"rel_l2_err": errs,
-                          "observed_order": [float(np.log2(errs[i] / errs[i + 1])) for i in range(len(sdts) - 1)]}
-        stres["accuracy"] = {"dt": sdts, **acc}
+            e_ = [float(torch.linalg.norm(run_rt(dt, split) - fine) / torch.linalg.norm(fine)) for dt in sdts]
+            stres[f"{split}_order"] = [float(np.log2(e_[i] / e_[i + 1])) for i in range(len(sdts) - 1)]
+        R["strang"] = stres
 
-    # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V
-    # and g at 128^3 (dx = 0.1, dt = 5e-4, 1000 steps, g = 30, isotropic trap +
-    # 8 Gaussian bumps, checkpoints every 50 steps); FP32 forward, FP64
-    # accumulation of the gradients.  One timed unit = forward + backward.
-    ares = {}
-    if not args.no_adjoint:
-        an, adx = [128] * 3, [0.1] * 3
-        anp = 128 ** 3
-        dV, _bp = inputs.gaussian_bumps(3, an, adx, seed=1713, count=8, amp=0.5, center=3.0)
-        xs = inputs.axis_coords(128, 0.1)
-        harm = 0.5 * (xs[:, None, None] ** 2 + xs[None, :, None] ** 2 + xs[None, None, :] ** 2)
-        AV = torch.tensor(harm + dV, device="cuda")
-        aphi = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3), device="cuda")
-        atgt = torch.tensor(inputs.gaussian_state(3, an, adx, [1.0] * 3, shift=(0.5, 0.0, 0.0)), device="cuda")
-        for prec in ("f32",):
-            with torch.cuda.stream(stream):
-                q = gpe.Propagator(3, an, adx, 5e-4, [1.0] * 3, 30.0, precision=prec, stream=stream)
-                q.set_potential(AV)
-                times = []
-                for rep in range(1 + 2):
-                    q.set_state(aphi)
-                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-                    barrier()
-                    e0.record(stream)
-                    gpe.gp_adjoint_forward(q.h, 1000, 50)
-                    e1.record(stream)
-                    phiT = q.get_state(device=True).to(torch.complex128)
-                    c = torch.sum(torch.conj(atgt) * phiT) * 1e-3
-                    lam = (2 * c * atgt * 1e-3).to(q.ctype).contiguous()
-                    dJdV = torch.empty(tuple(an), dtype=torch.float64, device="cuda")
-                    e_b = torch.cuda.Event(enable_timing=True)
-                    e_b.record(stream)
-                    torch.cuda.nvtx.range_push(f"adjoint_backward_{prec}")
-                    dJdg = gpe.gp_adjoint_backward(q.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1)
-                    torch.cuda.nvtx.range_pop()
-                    e2.record(stream)
-                    barrier()
-                    if rep:
-                        times.append((e0.elapsed_time(e1), e_b.elapsed_time(e2)))
-                q.close()
-            tf = sum(t[0] for t in times) / len(times)
-            tb = sum(t[1] for t in times) / len(times)
-            ares[prec] = {"forward_ms": tf, "backward_ms": tb,
-                          "value": world * 1000 * anp / ((tf + tb) * 1e-3),
-                          "backward_over_forward": tb / tf, "dJdg": dJdg}
-
-    if args.only and args.only != "headline":
-        # profiling run of a single form: report it and stop
+    if only is not None:
         if rank == 0:
-            print(json.dumps({"only": args.only, "quench256": qres or None, "adjoint": ares or None,
-                              "batched": bres or None, "spherical": sres or None,
-                              "axisym": ares_sym or None, "strang": stres or None, "real": rres or None}),
+            print(json.dumps({"only": only, **{k: v for k, v in R.items() if k != "headline_mu"}}, default=str),
                   flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
     # ---- end to end through the public API with host buffers (FP32 form)
-    e2e = None
     p = make("f32")
     host = torch.tensor(phi0.astype(np.complex64)).pin_memory()
     hnp = host.numpy()
@@ -696,7 +685,7 @@ def run_ours(args):
         for s in range(args.steps):
             p.set_state(hnp)                       # H2D of the state from pinned host memory
             p.step_imag(args.inner)
-            ob = p.observables()                   # D2H of the observables
+            p.observables()                        # D2H of the observables
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
     p.close()
@@ -707,137 +696,105 @@ def run_ours(args):
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    peaks, peak_src = measured_peaks()
-    hbm = float(peaks["hbm_gbs"])
+    cpu = None if args.no_cpu_baseline else oracle_rate()
 
-    def roofline(prec):
-        r = results[prec]
-        kms = r["kernel_ms"]
-        axis = max(range(3), key=lambda d: kms[d])
-        esize = 8 if prec == "f32" else 16
-        # algorithmic bytes: one read + one write of the state per sweep; the
-        # fused x + y kernel (shape flag 8) does the x and the y sweep in one
-        # launch, so it carries two sweeps' bytes (its DRAM traffic is one
-        # read + one write: the intermediate round trip is what fusion saves)
-        fused = axis == 0 and bool(r["shapes"]["flags"] & gpe.GP_SHAPE_FUSE_XY)
-        algo = (2 if fused else 1) * 2 * esize * np_
-        achieved = algo / (kms[axis] * 1e-3) / 1e9
-        key = f"sweep_xy_{prec}_imag_128cube" if fused else f"sweep_axis{axis}_{prec}_imag_128cube"
-        tr = traffic_record(key)
-        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": tr, "kernel": key, "sweeps_per_launch": 2 if fused else 1,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                "kernel_ms": kms}
+    # ---- the headline's roofline: its dominant kernel as it runs in the step graph
+    h32 = head["f32"]
+    kms = h32["kernel_ms"]
+    axis = max(range(3), key=lambda d: kms[d])
+    fused = axis == 0 and bool(h32["shapes"]["flags"] & gpe.GP_SHAPE_FUSE_XY)
+    algo = (2 if fused else 1) * 2 * 8 * np_   # one read + one write of the state per sweep
+    achieved = algo / (kms[axis] * 1e-3) / 1e9
+    key = f"sweep_xy_f32_imag_128cube" if fused else f"sweep_axis{axis}_f32_imag_128cube"
+    tr = profile_record("traffic.json", key)
+    step_ms = h32["ms_per_step"] / args.inner
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": tr["bytes_per_launch"] if tr else None, "algorithmic_bytes": algo,
+            "kernel": key, "peak_source": peak_note,
+            "regime": "L2-resident state (16.8 MB): latency-bound; HBM roofline at 256^3 in hbm256",
+            "kernel_ms_in_graph": kms, "kernel_sum_over_time_step": sum(kms) / step_ms}
+    mu = R["headline_mu"]
 
-    forms = {}
-    for prec in forms_sel:
-        r = results[prec]
-        v = r["value"]
-        forms[prec] = {"value": v, "ms_per_step": 1e3 * r["total_s"] / args.steps,
-                       "mu": r["obs"]["mu"], "roofline": roofline(prec)}
-    mu_err = abs(mu["f32"]["mu"] - mu["f64"]["mu"]) if "f32" in mu and "f64" in mu else None
-    mu_err_df = abs(mu["df64"]["mu"] - mu["f64"]["mu"]) if "df64" in mu and "f64" in mu else None
+    LINE_OBS = ("norm", "energy", "mu", "rms_r")
 
-    def conv_err(prec):
-        return abs(mu_conv[prec]["mu"] - mu_conv["f64"]["mu"]) if prec in mu_conv and "f64" in mu_conv else None
+    def form_err(prec, which):
+        d = mu[which]
+        return errs(d[prec], d["f64"], LINE_OBS) if prec in d and "f64" in d else None
+
+    q = R.get("quench256", {})
+
+    def qform(prec):
+        r = q.get(prec)
+        if not r:
+            return None
+        out = {"value": r["value"], "step_frac_hbm": r["step_frac_hbm"], "sweep_frac_hbm": r["sweep_frac_hbm"]}
+        if prec == "f32":
+            out.update({"us_step": r["us_per_time_step"], "sweep_us": r["sweep_us"],
+                        "dE_rel": r["energy_drift_rel"], "dnorm_rel": r["norm_drift_rel"]})
+        if r.get("alu"):
+            out["sweep_frac_fp64_fma"] = [a["frac"] if a else None for a in r["alu"]]
+        return out
 
     def ratio(a, b):
-        return forms[a]["value"] / forms[b]["value"] if a in forms and b in forms else None
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = oracle_rate()
-    head = forms["f32"]
-    r32 = results["f32"]
+        return a / b if a and b else None
+    hv = {p_: head[p_]["value"] for p_ in head}
+    qv = {p_: q[p_]["value"] for p_ in q}
+    bat = R.get("batched", {})
     line = {
-        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "metric": METRIC, "value": h32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h32["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state+sweeps, f64 reductions",
         "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
-        "config": {"workload": w["name"], "global_batch": 1, "inner_steps_per_step": args.inner,
-                   "points": np_, "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": head["roofline"],
+        "config": line_config(world),
+        "timing": {"inner_steps_per_step": args.inner, "l2": "flushed (256 MB write) before every timed step"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": r32["launches"],
-        "clocks": r32["clocks"],
-        "forms": {
-            "f64": ({"value": forms["f64"]["value"], "ms_per_step": forms["f64"]["ms_per_step"],
-                     "roofline": forms["f64"]["roofline"], "gpu_launches": results["f64"]["launches"],
-                     "clocks": results["f64"]["clocks"]} if "f64" in forms else None),
-            "f32": {"value": forms["f32"]["value"], "speedup_vs_f64": ratio("f32", "f64"),
-                    "reduced_density": results["f32"]["reduced_density"],
-                    "mu_err_vs_f64_full_job": mu_err, "mu_err_vs_f64_converged_20000_steps": conv_err("f32"),
-                    "mu_f32": mu["f32"]["mu"] if "f32" in mu else None,
-                    "mu_f64": mu["f64"]["mu"] if "f64" in mu else None},
-            "df64": ({"value": forms["df64"]["value"], "ms_per_step": forms["df64"]["ms_per_step"],
-                      "speedup_vs_f64": ratio("df64", "f64"),
-                      "mu_err_vs_f64_full_job": mu_err_df,
-                      "mu_err_vs_f64_converged_20000_steps": conv_err("df64"), "roofline": forms["df64"]["roofline"],
-                      "note": "double-float state and sweeps on the FP32 pipes (~48-bit), exact triple-float "
-                              "potential factors, FP64 reductions; FP32-ALU bound"} if "df64" in forms else None),
-            "quench256": ({"workload": "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, imaginary-time "
-                                       f"ground state at g=20 ({args.quench_imag_steps} steps) then g=40; L2 not flushed "
-                                       "(state larger than L2)",
-                           "f64": qres.get("f64"), "f32": qres.get("f32"), "df64": qres.get("df64"),
-                           "speedup_f32_vs_f64": (qres["f32"]["value"] / qres["f64"]["value"]
-                                                  if "f64" in qres else None),
-                           "speedup_df64_vs_f64": (qres["df64"]["value"] / qres["f64"]["value"]
-                                                   if "df64" in qres and "f64" in qres else None)} if qres else None),
-            "adjoint": ({"workload": "gradient of |<phi_target|phi(T)>|^2 w.r.t. V (per grid value) and g: 128^3, "
-                                     "dx=0.1, dt=5e-4, 1000 real-time steps, g=30, isotropic trap + 8 Gaussian bumps "
-                                     "(amplitude <= 0.5), checkpoints every 50 steps; value = forward+backward "
-                                     "point-steps/s; FP32 forward, FP64 gradient accumulation",
-                         "f32": ares.get("f32")} if ares else None),
-            "spherical": ({"workload": "spherically symmetric 3d trap as the radial problem for u = sqrt(4 pi) r phi: "
-                                       "513 points on [0, 10.24], dt=1e-4, nu=1, g=100, imaginary time; one 1d line, "
-                                       "launch-latency bound", **sres} if sres else None),
-            "axisym": ({"workload": "circularly symmetric 2d trap (513 rho points, drho=0.02, nu=1, g=100, "
-                                    "dt=1e-4) and axially symmetric 3d trap (rho x z = 256 x 512, drho=dz=0.04, nu=1, "
-                                    "lambda=2, g=100, dt=5e-4), imaginary time; rho_i = (i - 1/2) drho",
-                        **ares_sym} if ares_sym else None),
-            "real_state": ({"workload": "the headline workload (its input is real) with the state held as np real "
-                                        "values: imaginary-time maps keep it real; same loop, observables per step, "
-                                        "L2 flushed", **rres} if rres else None),
-            "strang": ({"workload": "the headline grid (128^3, dt=1e-3, g=50) stepped with the Lie and the Strang "
-                                    "splitting N(dt/2), sweeps, N(dt/2), imaginary time (renormalised after the "
-                                    "closing half) and real time (halves between steps merged), no observables, L2 "
-                                    "flushed before every timed step; accuracy: 64^3 real time to t=0.1 against a "
-                                    "dt=6.25e-5 Strang run, FP64",
-                        **stres} if stres else None),
-            "batched": ({"workload": "64 independent 2d real-time runs, sizes from {128,192,256,384,512}^2 "
-                                    "(SplitMix64 seed 1712), dx=0.1, dt=5e-4, g~U[0,50], nu=1, kappa~U[1,2], "
-                                    "g=0 trap ground state quenched; one launch per sweep and segment class, "
-                                    "graph-captured; L2 flushed before every timed step",
-                        "points": bpts,
-                        "value_f32": bres["f32"]["value"], "value_f64": bres["f64"]["value"],
-                        "speedup_f32_vs_f64": bres["f32"]["value"] / bres["f64"]["value"],
-                        "ms_per_step_f32": bres["f32"]["ms_per_step"], "gpu_launches_f32": bres["f32"]["gpu_launches"],
-                        "max_abs_mu_diff_f32_vs_f64_after_400_steps": bmu_err,
-                        "max_rel_mu_diff_f32_vs_f64_after_400_steps": bmu_rel,
-                        "largest_abs_mu_diff_run": bmu_worst} if bres else None),
-        },
+        "gpu_launches": h32["launches"],
+        "clocks": h32["clocks"],
+        "f32_err_vs_f64": {"job_end_5000": form_err("f32", "job_end"), "converged_20000": form_err("f32", "converged_20000"),
+                           "quench256_end": errs(q["f32"]["obs_end"], q["f64"]["obs_end"], LINE_OBS)
+                           if "f32" in q and "f64" in q else None,
+                           "batched_worst_run_400": {k: v for k, v in bat.get("f32_err_vs_f64_400_steps", {})
+                                                     .get("worst_per_observable", {}).items() if k in LINE_OBS}},
+        "df64_mu_err_vs_f64": {"job_end_5000": (form_err("df64", "job_end") or {}).get("mu"),
+                               "converged_20000": (form_err("df64", "converged_20000") or {}).get("mu")},
+        "hbm256": {"workload": QUENCH, "f32": qform("f32"), "f64": qform("f64"), "df64": qform("df64")},
+        "speedups": {"f32_vs_f64_128": ratio(hv.get("f32"), hv.get("f64")),
+                     "df64_vs_f64_128": ratio(hv.get("df64"), hv.get("f64")),
+                     "f32_vs_f64_256": ratio(qv.get("f32"), qv.get("f64")),
+                     "df64_vs_f64_256": ratio(qv.get("df64"), qv.get("f64")),
+                     "batched_f32_vs_f64": ratio(bat.get("f32", {}).get("value"), bat.get("f64", {}).get("value"))},
+        "values": {"f64_128": hv.get("f64"), "df64_128": hv.get("df64"),
+                   "batched_f32": bat.get("f32", {}).get("value"), "batched_f64": bat.get("f64", {}).get("value"),
+                   "adjoint_f32_fwd_bwd": R.get("adjoint_f32", {}).get("value")},
+        "fp_rates": R["fp_rates"],
     }
-    print(json.dumps(line), flush=True)
+    for k in ("f32_err_vs_f64", "df64_mu_err_vs_f64", "hbm256", "speedups", "values", "fp_rates"):
+        line[k] = compact(line[k], 3)
+    line = compact(line)
+    print(json.dumps(line, separators=(",", ":")), flush=True)
+    if args.details:
+        with open(args.details, "w") as f:
+            json.dump({"line": line, "all": R}, f, indent=1, default=str)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+def compact(obj, sig=4):
+    """Floats to `sig` significant digits (the line stays within the few KB
+    of output a driver keeps)."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{sig}g}")
+    if isinstance(obj, dict):
+        return {k: compact(v, sig) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [compact(v, sig) for v in obj]
+    return obj
+
+
 def main():
     args = parse()
-    if args.only:
-        args.no_quench = args.only != "quench256"
-        args.no_adjoint = args.only != "adjoint"
-        args.no_batched = args.only != "batched"
-        args.no_spherical = args.only != "spherical"
-        args.no_strang = args.only != "strang"
-        args.no_real = args.only != "real"
-        args.no_headline = args.only != "headline"
-        if args.only != "headline":
-            args.no_cpu_baseline = True
-            args.no_mu_check = True
-    else:
-        args.no_headline = False
     if args.impl == "reference":
         run_reference(args)
     else:
