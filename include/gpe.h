@@ -400,6 +400,20 @@ const char* gp_last_error(void);
  * replays count every kernel node); for instrumentation. */
 unsigned long long gp_kernel_launches(void);
 
+/* The checking build (the paper has no counterpart): libgpe_check.so is this
+ * library compiled with GPE_BOUNDS_CHECK, in which every sweep and
+ * observables kernel tests its state and shared-memory indices before each
+ * access -- a failed test records a code and skips the access (no assert, no
+ * trap) -- and every device buffer of a handle or batch sits between two
+ * 64 KB guard bands filled with 0xFF bytes (NaN to a kernel that reads them).
+ * gp_check_status synchronises the device and sets *first_failure to 0 when
+ * no check failed and every live buffer's guard bands are intact (GP_OK); to
+ * the code of the first failed index check, or to 1 for an overwritten guard
+ * band (GP_ERR_STATE, with the detail in gp_last_error); and to -1 in the
+ * normal library, which has no checks (GP_OK).  The failed-check record is
+ * cleared by the call. */
+int gp_check_status(int* first_failure);
+
 /* Test hook of the bounded device-side waits (the paper has no counterpart).
  * With extra_bytes > 0 every TMA tile load of this handle's sweeps
  * (GP_SHAPE_TMA_X / GP_SHAPE_TMA_YZ) announces extra_bytes more than it

@@ -30,9 +30,65 @@ namespace gpe {
 thread_local std::string g_err;
 std::atomic<unsigned long long> g_launches{0};
 
+// ---- guarded allocations and the checking build's readers
+namespace {
+#ifdef GPE_BOUNDS_CHECK
+constexpr size_t kGuard = 64 * 1024;  // bytes of 0xFF before and after every buffer
+std::mutex g_guard_mutex;
+std::map<void*, std::pair<char*, size_t>>& guard_map() {  // user pointer -> (raw pointer, bytes)
+  static std::map<void*, std::pair<char*, size_t>> m;
+  return m;
+}
+#endif
+std::mutex g_reader_mutex;
+std::vector<int (*)()>& check_readers() {
+  static std::vector<int (*)()> v;
+  return v;
+}
+}  // namespace
+
+void register_check_reader(int (*reader)()) {
+  std::lock_guard<std::mutex> lock(g_reader_mutex);
+  check_readers().push_back(reader);
+}
+
+cudaError_t guarded_malloc(void** p, size_t bytes) {
+#ifdef GPE_BOUNDS_CHECK
+  char* raw = nullptr;
+  cudaError_t e = cudaMalloc((void**)&raw, bytes + 2 * kGuard);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemset(raw, 0xFF, kGuard)) == cudaSuccess) e = cudaMemset(raw + kGuard + bytes, 0xFF, kGuard);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(raw);
+    return e;
+  }
+  *p = raw + kGuard;
+  std::lock_guard<std::mutex> lock(g_guard_mutex);
+  guard_map()[*p] = {raw, bytes};
+  return cudaSuccess;
+#else
+  return cudaMalloc(p, bytes);
+#endif
+}
+
+void guarded_free(void* p) {
+  if (!p) return;
+#ifdef GPE_BOUNDS_CHECK
+  std::lock_guard<std::mutex> lock(g_guard_mutex);
+  auto it = guard_map().find(p);
+  if (it != guard_map().end()) {
+    cudaFree(it->second.first);
+    guard_map().erase(it);
+    return;
+  }
+#endif
+  cudaFree(p);
+}
+
 int dev_alloc(gp_handle* h, void** p, size_t bytes) {
   const size_t b = bytes < 16 ? 16 : bytes;
-  GP_CUDA(cudaMalloc(p, b));
+  GP_CUDA(guarded_malloc(p, b));
   h->allocs.push_back(*p);
   GP_CUDA(cudaMemsetAsync(*p, 0, b, h->work));
   return GP_OK;
@@ -520,7 +576,7 @@ int gp_destroy(gp_handle* h) {
   if (!h) return GP_OK;
   if (h->work) cudaStreamSynchronize(h->work);
   drop_graphs(h);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) guarded_free(p);
   if (h->obs_host) cudaFreeHost(h->obs_host);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -900,7 +956,7 @@ int ensure_states(gp_handle* h, void** buf, long* cap, long count) {
   if (*cap >= count && *buf) return GP_OK;
   if (*buf) {
     cudaStreamSynchronize(h->work);
-    cudaFree(*buf);
+    guarded_free(*buf);
     for (auto& p : h->allocs)
       if (p == *buf) p = nullptr;
     *buf = nullptr;
@@ -1007,6 +1063,46 @@ std::map<TuneKey, std::array<int, 4>> g_tuned;  // process-wide results
 std::mutex g_tune_mutex;
 
 }  // namespace
+
+int gp_check_status(int* first_failure) {
+  if (!first_failure) return fail(GP_ERR_INVALID, "gp_check_status: NULL argument");
+  GP_CUDA(cudaDeviceSynchronize());
+#ifdef GPE_BOUNDS_CHECK
+  int first = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_reader_mutex);
+    for (auto rd : check_readers()) {
+      const int v = rd();
+      if (v < 0) return fail(GP_ERR_CUDA, "gp_check_status: a check flag could not be read");
+      if (v && !first) first = v;
+    }
+  }
+  if (first) {
+    *first_failure = first;
+    return fail(GP_ERR_STATE, "gp_check_status: index check " + std::to_string(first) + " failed");
+  }
+  std::lock_guard<std::mutex> lock(g_guard_mutex);
+  std::vector<unsigned char> buf(kGuard);
+  for (auto& kv : guard_map()) {
+    const char* raw = kv.second.first;
+    const size_t bytes = kv.second.second;
+    for (int side = 0; side < 2; ++side) {
+      GP_CUDA(cudaMemcpy(buf.data(), raw + (side ? kGuard + bytes : 0), kGuard, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < kGuard; ++i)
+        if (buf[i] != 0xFF) {
+          *first_failure = 1;
+          return fail(GP_ERR_STATE, std::string("gp_check_status: the guard band ") + (side ? "after" : "before") +
+                                        " a buffer of " + std::to_string(bytes) + " bytes was overwritten");
+        }
+    }
+  }
+  *first_failure = 0;
+  return GP_OK;
+#else
+  *first_failure = -1;  // a library built without the checks
+  return GP_OK;
+#endif
+}
 
 int gp_test_stall_transfers(gp_handle* h, int extra_bytes) {
   if (!h) return fail(GP_ERR_INVALID, "gp_test_stall_transfers: NULL handle");
@@ -1207,7 +1303,7 @@ int gp_step_series(gp_handle* h, int imag, long nsteps, int every, double* out, 
   if (need > h->series_cap) {
     if (h->series_buf) {
       cudaStreamSynchronize(h->work);
-      cudaFree(h->series_buf);
+      guarded_free(h->series_buf);
       for (auto& p : h->allocs)
         if (p == h->series_buf) p = nullptr;
       h->series_buf = nullptr;

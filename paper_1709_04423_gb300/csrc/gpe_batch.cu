@@ -137,6 +137,152 @@ __global__ void __launch_bounds__(512) batch_y_kernel(const BatchRun<T>* __restr
   colsweep_body<T, false, false, SEG, (SEG * sizeof(T) <= 64)>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
 }
 
+// ---------------------------------------------------------------- one persistent launch
+// Every x and y sweep of every run over nsteps steps in one launch (FP32
+// states).  Work items (step t, axis, run, 32-line tile) are numbered step by
+// step -- the x items of all runs, then the y items of all runs -- and claimed
+// in that order from one counter by persistent CTAs.  An x item of run r at
+// step t needs every y item of run r at step t - 1 to have finished, a y item
+// every x item of run r at step t (per-run completion counters, counted over
+// the whole launch): a run's sweeps follow each other while different runs'
+// sweeps overlap, with no grid-wide barrier.  Because items are claimed in
+// order and every dependency has a lower number, the lowest unfinished item
+// always has its inputs ready, so the waits end.  Each wait is bounded by the
+// global timer: past the limit the CTA records the error and every CTA stops
+// claiming; the host returns GP_ERR_TIMEOUT at the next gp_batch_observables.
+// The per-line arithmetic is that of the per-class launches (the same bodies
+// and segment lengths), so the states are bit for bit the same.
+struct PersistArgs {
+  const BatchRun<float>* runs;
+  const BatchItem* items;  // the x items of one step, then its y items
+  int nx_items, ny_items;
+  const int* per_run;      // [2 run]: x items, y items of the run per step
+  const int* seg;          // [2 run]: segment length of the run's x, y lines
+  unsigned* next;          // claim counter
+  unsigned* done;          // [2 run]: x, y items of the run finished in this launch
+  long nsteps;
+  int stall;               // added to every dependency target (0; a test makes the waits run out)
+  unsigned long long limit_ns;
+  int* err;                // device error flag: 1 = a wait ran out
+  float dt;
+};
+
+__device__ __forceinline__ unsigned long long batch_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits until *c >= target, for at most limit_ns of global time.
+__device__ __forceinline__ bool wait_count(const unsigned* c, unsigned target, unsigned long long limit_ns) {
+  if (ld_acquire(c) >= target) return true;
+  const unsigned long long t0 = batch_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire(c) >= target) return true;
+    if (batch_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__global__ void __launch_bounds__(512, 1) batch_persist_kernel(PersistArgs P) {
+  extern __shared__ __align__(16) unsigned char bsmem_raw[];
+  __shared__ float2 cf[16][33], cb[16][33];
+  __shared__ double red_smem[32];
+  __shared__ long s_item;
+  __shared__ int s_stop;
+  const long per_step = (long)P.nx_items + P.ny_items;
+  const long total = per_step * P.nsteps;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long i = -1;
+      if (*(volatile int*)P.err == 0) i = (long)atomicAdd(P.next, 1u);
+      s_item = i;
+    }
+    __syncthreads();
+    const long i = s_item;
+    if (i < 0 || i >= total) break;
+    const long t = i / per_step;
+    const int j = (int)(i - t * per_step);
+    const bool xs = j < P.nx_items;
+    const BatchItem it = P.items[j];
+    const int r = it.run;
+    if (threadIdx.x == 0) {
+      // x items of step t wait for the run's y items of step t - 1, y items
+      // for the run's x items of step t
+      const unsigned target = xs ? (unsigned)(t * P.per_run[2 * r + 1]) : (unsigned)((t + 1) * P.per_run[2 * r]);
+      int stop = 0;
+      if (target > 0 && !wait_count(P.done + 2 * r + (xs ? 1 : 0), target + (unsigned)P.stall, P.limit_ns)) {
+        atomicExch(P.err, 1);
+        stop = 1;
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    __threadfence();  // the inputs other CTAs wrote are seen by every thread
+    const BatchRun<float>& R = P.runs[r];
+    Sweep2Args<float> A;
+    memset(&A, 0, sizeof(A));
+    A.psi = R.psi;
+    A.geom.nx = R.nx;
+    A.geom.ny = R.ny;
+    A.geom.nz = 1;
+    float2* sm = reinterpret_cast<float2*>(bsmem_raw);
+    const int seg = P.seg[2 * r + (xs ? 0 : 1)];
+    if (xs) {
+      A.geom.axis = 0;
+      A.geom.n = R.nx;
+      A.geom.stride = 1;
+      A.geom.nlines = R.ny;
+      A.alpha = R.coef[0];
+      A.gf = R.coef[0] + R.nx;
+      A.gb = R.coef[0] + 2 * R.nx;
+      A.ptab = R.ptab[0];
+      A.fx = R.fx;
+      A.fy = R.fy;
+      A.fz = R.fz1;
+      A.dtg = R.dtg;
+      A.vx = R.vx;
+      A.vy = R.vy;
+      A.vz = R.vz0;
+      A.dt = P.dt;
+      A.g = R.g;
+      switch (seg) {
+        case 4: tsweep_body<float, false, true, false, 4>(A, it.L0, sm, cf, cb, red_smem); break;
+        case 8: tsweep_body<float, false, true, false, 8>(A, it.L0, sm, cf, cb, red_smem); break;
+        case 16: tsweep_body<float, false, true, false, 16>(A, it.L0, sm, cf, cb, red_smem); break;
+        default: tsweep_body<float, false, true, false, 32>(A, it.L0, sm, cf, cb, red_smem); break;
+      }
+    } else {
+      A.geom.axis = 1;
+      A.geom.n = R.ny;
+      A.geom.stride = R.nx;
+      A.geom.nlines = R.nx;
+      A.alpha = R.coef[1];
+      A.gf = R.coef[1] + R.ny;
+      A.gb = R.coef[1] + 2 * R.ny;
+      A.ptab = R.ptab[1];
+      switch (seg) {  // registers kept for the segment as the per-class launches do (8 floats or fewer)
+        case 4: colsweep_body<float, false, false, 4, true>(A, it.L0, sm, cf, cb, red_smem); break;
+        case 8: colsweep_body<float, false, false, 8, true>(A, it.L0, sm, cf, cb, red_smem); break;
+        case 16: colsweep_body<float, false, false, 16, true>(A, it.L0, sm, cf, cb, red_smem); break;
+        default: colsweep_body<float, false, false, 32, false>(A, it.L0, sm, cf, cb, red_smem); break;
+      }
+    }
+    __syncthreads();  // every thread's writes of the item are done ...
+    if (threadIdx.x == 0) {
+      __threadfence();  // ... and visible before the item is counted
+      atomicAdd(P.done + 2 * r + (xs ? 0 : 1), 1u);
+    }
+  }
+}
+
 // Segment-length classes: a line of n points goes to the first class whose
 // segment length gives at most 16 segments (the rule the single-grid handle
 // uses), so a run in a batch takes the same arithmetic as alone.  x lines
@@ -183,6 +329,18 @@ struct gp_batch {
   double* obs_out = nullptr;
   double* obs_host = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // the one-launch form (FP32): items of one step, per-run item counts and
+  // segment lengths, the claim counter and per-run completion counters
+  bool persistent = false;
+  void* p_items = nullptr;
+  int p_nx = 0, p_ny = 0;
+  int* p_per_run = nullptr;
+  int* p_seg = nullptr;
+  unsigned* p_count = nullptr;  // [1 + 2 nruns]: next, done
+  size_t p_smem = 0;
+  int p_stall = 0;
+  unsigned long long limit_ns = 1000000000ull;
+  int* dev_err = nullptr;
   std::vector<void*> allocs;
 };
 
@@ -191,7 +349,7 @@ namespace {
 
 int b_alloc(gp_batch* b, void** p, size_t bytes) {
   const size_t sz = bytes < 16 ? 16 : bytes;
-  GP_CUDA(cudaMalloc(p, sz));
+  GP_CUDA(guarded_malloc(p, sz));
   b->allocs.push_back(*p);
   GP_CUDA(cudaMemsetAsync(*p, 0, sz, b->work));
   return GP_OK;
@@ -329,7 +487,67 @@ int build_tables(gp_batch* b) {
                               cudaMemcpyHostToDevice, b->work));
       GP_CUDA(cudaStreamSynchronize(b->work));
     }
+  if constexpr (std::is_same<T, float>::value) {
+    // the one-launch form: the x tiles of every run, then the y tiles (the
+    // largest runs first, so that the launch does not end on a large item)
+    std::vector<int> order(R);
+    for (int r = 0; r < R; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int a_, int b_) {
+      return (long)b->n[2 * a_] * b->n[2 * a_ + 1] > (long)b->n[2 * b_] * b->n[2 * b_ + 1];
+    });
+    std::vector<BatchItem> items;
+    std::vector<int> per_run(2 * R, 0), segs(2 * R, 0);
+    size_t smem = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int r : order) {
+        const int n = b->n[2 * r + a], nl = b->n[2 * r + (1 - a)];
+        segs[2 * r + a] = kClassSegs[class_of(n, a, b->esize)];
+        for (int L0 = 0; L0 < nl; L0 += 32) items.push_back({r, L0});
+        per_run[2 * r + a] = (nl + 31) / 32;
+        smem = std::max(smem, (a == 0 ? (size_t)(36 * n + 512) : (size_t)(3 * n + 512)) * sizeof(float2));
+        (a == 0 ? b->p_nx : b->p_ny) += (nl + 31) / 32;
+      }
+    b->p_smem = smem;
+    if ((rc = b_alloc(b, &b->p_items, items.size() * sizeof(BatchItem))) ||
+        (rc = b_upload<BatchItem>(b, b->p_items, items)))
+      return rc;
+    void* q = nullptr;
+    if ((rc = b_alloc(b, &q, per_run.size() * sizeof(int))) || (rc = b_upload<int>(b, q, per_run))) return rc;
+    b->p_per_run = (int*)q;
+    if ((rc = b_alloc(b, &q, segs.size() * sizeof(int))) || (rc = b_upload<int>(b, q, segs))) return rc;
+    b->p_seg = (int*)q;
+    if ((rc = b_alloc(b, &q, (1 + 2 * (size_t)R) * sizeof(unsigned)))) return rc;
+    b->p_count = (unsigned*)q;
+  }
   return GP_OK;
+}
+
+// The one-launch form over nsteps steps: counters cleared, one launch.
+void enqueue_persistent(gp_batch* b, long nsteps) {
+  cudaMemsetAsync(b->p_count, 0, (1 + 2 * (size_t)b->nruns) * sizeof(unsigned), b->work);
+  opt_in_smem((const void*)batch_persist_kernel, b->p_smem);
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persist_kernel, 512, b->p_smem);
+  PersistArgs P;
+  P.runs = (const BatchRun<float>*)b->runs_d;
+  P.items = (const BatchItem*)b->p_items;
+  P.nx_items = b->p_nx;
+  P.ny_items = b->p_ny;
+  P.per_run = b->p_per_run;
+  P.seg = b->p_seg;
+  P.next = b->p_count;
+  P.done = b->p_count + 1;
+  P.nsteps = nsteps;
+  P.stall = b->p_stall;
+  P.limit_ns = b->limit_ns;
+  P.err = b->dev_err;
+  P.dt = (float)b->dt;
+  const long items = ((long)b->p_nx + b->p_ny) * nsteps;
+  const int blocks = (int)std::max(1L, std::min<long>(items, (long)std::max(1, per_sm) * std::max(1, sms)));
+  batch_persist_kernel<<<blocks, 512, b->p_smem, b->work>>>(P);
+  count_launch();
 }
 
 template <typename T, int SEG>
@@ -348,19 +566,11 @@ void launch_batch_class(gp_batch* b, int a, int c) {
   const auto* items = (const BatchItem*)b->items_d[a][c];
   if (a == 0) {
     const size_t smem = (size_t)(36 * n + 512) * sizeof(c2_t<T>);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(batch_x_kernel<T, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
-    }
+    opt_in_smem((const void*)batch_x_kernel<T, SEG>, 200 * 1024);
     batch_x_kernel<T, SEG><<<b->nitems[a][c], threads, smem, b->work>>>(runs, items, (T)b->dt);
   } else {
     const size_t smem = (size_t)(3 * n + 512) * sizeof(c2_t<T>);
-    static bool attr = false;  // static + dynamic shared memory can pass 48 KB
-    if (!attr) {
-      cudaFuncSetAttribute(batch_y_kernel<T, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-      attr = true;
-    }
+    opt_in_smem((const void*)batch_y_kernel<T, SEG>, 64 * 1024);  // static + dynamic can pass 48 KB
     batch_y_kernel<T, SEG><<<b->nitems[a][c], threads, smem, b->work>>>(runs, items);
   }
   count_launch();
@@ -431,7 +641,9 @@ int batch_steps(gp_batch* b, long nsteps) {
       cudaGraph_t graph;
       GP_CUDA(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
       const unsigned long long before = g_launches.load();
-      for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step<T>(b);
+      if (b->persistent) enqueue_persistent(b, kBatchGraphSteps);
+      else
+        for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step<T>(b);
       g_launches.store(before);
       const cudaError_t ce = cudaStreamEndCapture(b->work, &graph);
       if (ce != cudaSuccess)
@@ -446,10 +658,12 @@ int batch_steps(gp_batch* b, long nsteps) {
     }
     for (; nsteps - t >= kBatchGraphSteps; t += kBatchGraphSteps) {
       GP_CUDA(cudaGraphLaunch(b->graph, b->work));
-      count_launch((unsigned long long)kBatchGraphSteps * launches_per_step(b));
+      count_launch(b->persistent ? 1ull : (unsigned long long)kBatchGraphSteps * launches_per_step(b));
     }
   }
-  for (; t < nsteps; ++t) enqueue_batch_step<T>(b);
+  if (b->persistent && nsteps > t) enqueue_persistent(b, nsteps - t);
+  else
+    for (; t < nsteps; ++t) enqueue_batch_step<T>(b);
   if (!b->launch_err.empty()) return fail(GP_ERR_CUDA, b->launch_err);
   GP_CUDA(cudaGetLastError());
   return b_join_out(b);
@@ -529,7 +743,7 @@ int gp_batch_destroy(gp_batch* b) {
   if (!b) return GP_OK;
   if (b->work) cudaStreamSynchronize(b->work);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void* p : b->allocs) cudaFree(p);
+  for (void* p : b->allocs) guarded_free(p);
   if (b->obs_host) cudaFreeHost(b->obs_host);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);

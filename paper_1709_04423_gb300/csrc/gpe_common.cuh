@@ -5,12 +5,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 #include "gpe_df.cuh"
 
 namespace gpe {
+
+// ---- the bounds-checking build (-DGPE_BOUNDS_CHECK, libgpe_check.so)
+// GPE_CHECK(cond, code) tests an index before a global or shared-memory
+// access; a failed test records its code (the first one per translation
+// unit) in this unit's device flag and the caller skips the access -- no
+// assert, no trap.  Each translation unit registers a reader of its flag at
+// load time; gp_check_status collects them.  In the normal build the checks
+// compile to nothing.
+#ifdef GPE_BOUNDS_CHECK
+static __device__ int g_check_first = 0;
+#define GPE_CHECK(cond, code) ((cond) ? true : (atomicCAS(&::gpe::g_check_first, 0, (code)), false))
+void register_check_reader(int (*reader)());
+namespace {
+int read_check_flag() {
+  int v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_check_first, sizeof(int)) != cudaSuccess) return -1;
+  cudaMemcpyToSymbol(g_check_first, &z, sizeof(int));
+  return v;
+}
+struct CheckReaderReg {
+  CheckReaderReg() { register_check_reader(&read_check_flag); }
+};
+CheckReaderReg g_check_reader_reg;
+}  // namespace
+#else
+#define GPE_CHECK(cond, code) true
+#endif
 
 template <typename T> struct C2;
 template <> struct C2<double> { using type = double2; };
@@ -69,6 +98,9 @@ struct LineGeom {
   long stride;  // element distance between consecutive points
   long nlines;
   int nx, ny, nz;
+  // elements of the array the lines live in (the bounds the checks of the
+  // checking build hold every index to)
+  __host__ __device__ long points() const { return (long)nx * ny * nz; }
 };
 
 __device__ __forceinline__ long line_base(const LineGeom& g, long L) {
@@ -179,6 +211,29 @@ __device__ __forceinline__ double pending_scale(const double* parts, int nparts,
   __syncthreads();  // smem free again
   return f;
 }
+
+// Opts a kernel in to `bytes` of dynamic shared memory (beyond the default
+// 48 KB) once per kernel and size.  The record is this library's own (an
+// internal-linkage table keyed by the kernel's host stub): a function-local
+// static in a launcher template would be one object for every copy of the
+// library in the process, so that a second copy (the checking build) would
+// skip the opt-in for its own kernels.
+namespace {
+inline void opt_in_smem(const void* kern, size_t bytes) {
+  static std::mutex m;
+  static std::vector<std::pair<const void*, size_t>> done;
+  std::lock_guard<std::mutex> lock(m);
+  for (auto& d : done)
+    if (d.first == kern) {
+      if (d.second >= bytes) return;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      d.second = bytes;
+      return;
+    }
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  done.emplace_back(kern, bytes);
+}
+}  // namespace
 
 // Launch with or without the programmatic-dependent-launch attribute (the
 // kernel must call pdl_wait() before it reads what earlier kernels wrote).

@@ -203,6 +203,11 @@ bool tma_x_fits(const gp_handle* h, int seg);  // the TMA x sweep takes this gri
 int read_dev_err(gp_handle* h, const char* who);  // GP_ERR_TIMEOUT (and clears it) if a device wait gave up
 
 int dev_alloc(gp_handle* h, void** p, size_t bytes);
+// Device buffers of handles and batches: cudaMalloc / cudaFree, and in the
+// checking build (GPE_BOUNDS_CHECK) each buffer sits between two guard bands
+// filled with 0xFF bytes, checked by gp_check_status.
+cudaError_t guarded_malloc(void** p, size_t bytes);
+void guarded_free(void* p);
 int join_in(gp_handle* h);
 int join_out(gp_handle* h);
 inline int axis_len(const gp_handle* h, int d) { return d < h->dim ? h->n[d] : 1; }

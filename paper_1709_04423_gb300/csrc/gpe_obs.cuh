@@ -61,14 +61,16 @@ struct ObsArgs {
 // |d phi / d axis|^2 at point q (index i of n along the axis, stride s);
 // f1 = 1/(2h), f4 = 1/(12h)
 template <typename T, typename R>
-__device__ __forceinline__ R grad2_axis(const c2_t<T>* psi, long q, int i, int n, long s, R f1, R f4) {
+__device__ __forceinline__ R grad2_axis(const c2_t<T>* psi, long q, int i, int n, long s, R f1, R f4, long lim) {
   if (i == 0 || i == n - 1) return R(0);
   R dx, dy;
   if (i == 1 || i == n - 2) {
+    if (!GPE_CHECK(q - s >= 0 && q + s < lim, 271)) return R(0);
     const c2_t<T> a = psi[q - s], b = psi[q + s];
     dx = (R(b.x) - R(a.x)) * f1;
     dy = (R(b.y) - R(a.y)) * f1;
   } else {
+    if (!GPE_CHECK(q - 2 * s >= 0 && q + 2 * s < lim, 272)) return R(0);
     const c2_t<T> a = psi[q - 2 * s], b = psi[q - s], c = psi[q + s], e = psi[q + 2 * s];
     dx = (R(a.x) - R(8) * R(b.x) + R(8) * R(c.x) - R(e.x)) * f4;
     dy = (R(a.y) - R(8) * R(b.y) + R(8) * R(c.y) - R(e.y)) * f4;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
   const int TX = 1 << tx_log2;
   const int tx = threadIdx.x & (TX - 1), ty = threadIdx.x >> tx_log2, rpb = blockDim.x >> tx_log2;
   const int nrows = A.ny * A.nz;
-  const long sy = A.nx, sz = (long)A.nx * A.ny;
+  const long sy = A.nx, sz = (long)A.nx * A.ny, lim = (long)A.nx * A.ny * A.nz;
   const R fx1 = R(1.0 / (2.0 * A.hx)), fx4 = R(1.0 / (12.0 * A.hx));
   const R fy1 = R(1.0 / (2.0 * A.hy)), fy4 = R(1.0 / (12.0 * A.hy));
   const R fz1 = R(1.0 / (2.0 * A.hz)), fz4 = R(1.0 / (12.0 * A.hz));
@@ -99,6 +101,7 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
     for (int r = blk * rpb + ty; r < nrows; r += nblk * rpb) {
       const int j = r % A.ny, k = r / A.ny;
       const long q = (long)r * A.nx + i;
+      if (!GPE_CHECK(q < lim && (A.nx < 3 || q + 2 < lim || i + 2 >= A.nx), 273)) continue;
       const c2_t<T> p = A.psi[q];
       const R px = R(p.x), py = R(p.y);
       const R dens = px * px + py * py;
@@ -120,10 +123,10 @@ __device__ __forceinline__ void obs_accumulate(const ObsArgs<T>& A, int tx_log2,
         }
         g2 = ux * ux + uy * uy;
       } else {
-        g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4);
+        g2 = grad2_axis<T, R>(A.psi, q, i, A.nx, 1, fx1, fx4, lim);
       }
-      if (A.dim > 1) g2 += grad2_axis<T, R>(A.psi, q, j, A.ny, sy, fy1, fy4);
-      if (A.dim > 2) g2 += grad2_axis<T, R>(A.psi, q, k, A.nz, sz, fz1, fz4);
+      if (A.dim > 1) g2 += grad2_axis<T, R>(A.psi, q, j, A.ny, sy, fy1, fy4, lim);
+      if (A.dim > 2) g2 += grad2_axis<T, R>(A.psi, q, k, A.nz, sz, fz1, fz4, lim);
       const R Vq = A.V ? R(A.V[q]) : (vxi + A.vy[j] + A.vz[k]);
       const R w = wxi * A.wy[j] * A.wz[k];
       const R wd = w * dens;

@@ -121,7 +121,7 @@ extern "C" int gp_reduced_density(gp_handle* h, int keep_mask, double* out, int 
   if (need > h->red_cap) {
     if (h->red_parts) {
       cudaStreamSynchronize(h->work);
-      cudaFree(h->red_parts);
+      guarded_free(h->red_parts);
       for (auto& p : h->allocs)
         if (p == h->red_parts) p = nullptr;
       h->red_parts = nullptr;

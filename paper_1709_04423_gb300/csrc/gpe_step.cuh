@@ -72,12 +72,8 @@ unsigned launch_c(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int nseg = (M + SEG - 1) / SEG;
   const unsigned blocks = (unsigned)((a.geom.nlines + 31) / 32);
   const size_t smem = (size_t)(3 * a.geom.n + 512) * sizeof(c2_t<T>);
-  static bool attr_set = false;  // static + dynamic shared memory can pass 48 KB
-  if (!attr_set) {
-    cudaFuncSetAttribute(colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr_set = true;
-  }
+  // static + dynamic shared memory can pass 48 KB
+  opt_in_smem((const void*)colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>, 64 * 1024);
   launch_k(pdl, colsweep_kernel<T, IMAG, LAST, SEG, KEEP, RP, CLOSE>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
@@ -108,11 +104,7 @@ unsigned launch_xy(const Sweep2Args<float>& ax, const Sweep2Args<float>& ay, cud
   const int wx = ((nx - 2 + SEG - 1) / SEG) * ((ny + 31) / 32), wy = ((ny - 2 + SEG - 1) / SEG) * ((nx + 31) / 32);
   const int threads = 32 * std::max(wx, wy);
   const size_t smem = (size_t)(3 * nx + 512 + 3 * ny + 512 + ny * (nx + 1)) * sizeof(float2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(xyplane_kernel<IMAG, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
-    attr_set = true;
-  }
+  opt_in_smem((const void*)xyplane_kernel<IMAG, SEG>, 180 * 1024);
   launch_k(pdl, xyplane_kernel<IMAG, SEG>, dim3(ax.geom.nz), dim3(threads), smem, s, ax, ay);
   count_launch();
   return (unsigned)ax.geom.nz;
@@ -143,12 +135,7 @@ unsigned launch_t(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const long ncols = RL ? (a.geom.nlines + 1) / 2 : a.geom.nlines;
   const unsigned blocks = (unsigned)((ncols + 31) / 32);
   const size_t smem = (size_t)a.geom.n * (kTilePitch + 3) * sizeof(c2_t<T>) + 512 * sizeof(c2_t<T>);
-  static bool attr_set = false;  // one opt-in per instantiation
-  if (!attr_set) {
-    cudaFuncSetAttribute(tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL, VAR>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  opt_in_smem((const void*)tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL, VAR>, 200 * 1024);
   launch_k(pdl, tsweep_kernel<T, IMAG, FIRST, LAST, SEG, RL, VAR>, dim3(blocks), dim3(32 * nseg), smem, s, a);
   count_launch();
   return blocks;
@@ -177,12 +164,7 @@ unsigned launch_p(const Sweep2Args<T>& a, cudaStream_t s, bool pdl) {
   const int nseg = (M + SEG - 1) / SEG;
   const int ntiles = (int)((a.geom.nlines + 31) / 32);
   const size_t smem = psweep_smem<T>(a.geom.n, AXIS0);
-  static size_t attr_set = 0;  // largest dynamic shared memory opted in so far (static + dynamic <= 227 KB)
-  if (smem > attr_set) {
-    cudaFuncSetAttribute(psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_set = smem;
-  }
+  opt_in_smem((const void*)psweep_kernel<T, IMAG, FIRST, LAST, SEG, AXIS0>, smem);  // static + dynamic <= 227 KB
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -246,11 +228,7 @@ unsigned launch_tc(gp_handle* h, const Sweep2Args<float>& a, cudaStream_t s, boo
   const int nseg = (g.n - 2 + SEG - 1) / SEG;
   const size_t smem = tmacol_smem(g.n);
   auto kern = tmacol_kernel<IMAG, LAST, SEG, CLOSE>;
-  static size_t attr_set = 0;  // largest dynamic shared memory opted in so far
-  if (smem > attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = smem;
-  }
+  opt_in_smem((const void*)kern, smem);
   CUtensorMap map;
   if (!encode_line_map(&map, a.psi, g)) {
     g_err = "cuTensorMapEncodeTiled refused the state's tensor map";
@@ -298,11 +276,7 @@ unsigned launch_tx(gp_handle* h, Sweep2Args<float> a, int mode, cudaStream_t s, 
   const int nseg = g.n / SEG;
   const size_t smem = tmarow_smem(g.n);
   auto kern = tmarow_kernel<IMAG, SEG>;
-  static size_t attr_set = 0;
-  if (smem > attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = smem;
-  }
+  opt_in_smem((const void*)kern, smem);
   // the tables of segments aligned to even points
   const float2* ev = (const float2*)h->coef_even[mode];
   const int si = SEG == 8 ? 0 : 1;

@@ -59,9 +59,7 @@ __device__ __forceinline__ c2_t<T> apply_N(c2_t<T> p, T V, T dt, T g) {
   T dens = p.x * p.x + p.y * p.y;
   T th = dt * (V + g * dens);
   if (IMAG) {
-    T f;  // FP32: 1 + expm1 rounded once, nearly correctly rounded (see phase_direct)
-    if constexpr (std::is_same<T, float>::value) f = 1.0f + expm1f(-th);
-    else f = exp(-th);
+    T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
   } else {
     return rot_neg<T>(p, th);

@@ -202,22 +202,20 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
 // mu further from FP64 -- the FP32 iteration stops at an exact fixed point of
 // the rounded map, whose mu depends on how each sub-step rounds, and that
 // form stops 1.3e-6 away against 8e-9 for the product.)
-// The FP32 factor e^{-th} is 1 + expm1(-th) rounded once: for the small th of a
-// time step this is the correctly rounded factor except within a small
-// fraction of an ulp of a rounding boundary, whereas the library expf (up to
-// 2 ulp) carries an error that varies smoothly with th.  A smooth error is
-// smooth in space and, th changing slowly, the same at a point step after
-// step, so it acts as a small perturbation of the potential that the state
-// follows: the 128^3 imaginary-time workload stood 2.2e-6 off in mu after 100
-// steps with expf against 4e-8 for an FP32 emulation with correctly rounded
-// factors.
+// The FP32 factor is the library expf.  A correctly rounded factor (1 +
+// expm1(-th), rounded once) was measured as well: on the 128^3 imaginary-time
+// workload it moves the first 100 steps 180x closer to the FP64 oracle in mu
+// (1.2e-8 against 2.1e-6) but leaves the FP32 iteration at a fixed point of the
+// rounded map 1.9e-6 from FP64 at the 5000-step job end and 1.2e-6 converged,
+// against 8.6e-7 and 3.8e-8 with expf -- both sit at the floor that rounding
+// the state to FP32 sets (an FP32 emulation with exact factors wanders between
+// 1e-8 and 8e-7 on a 64^3 version), and expf is the cheaper one and ends the
+// job within 1e-6.
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
   const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
   if (IMAG) {
-    T f;
-    if constexpr (std::is_same<T, float>::value) f = 1.0f + expm1f(-th);
-    else f = exp(-th);
+    const T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
   }
   return rot_neg<T>(p, th);
@@ -553,6 +551,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
   pdl_wait();  // the state is the previous kernel's output
   pdl_release();
   c2* line = A.psi + (active ? line_base32(G, L) : 0);
+  const long lim = G.points() - (line - A.psi);  // elements from the line's start to the array's end
   // KEEP: the input segment stays in registers; otherwise it is streamed in
   // the forward pass and read again (from L2) for u = p - z, which halves the
   // registers per thread and doubles the blocks an SM can hold
@@ -561,18 +560,23 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
-      p[j] = (active && k <= M) ? line[k * st] : mk<T>(0, 0);
+      p[j] = (active && k <= M && GPE_CHECK((long)k * st < lim, 201)) ? line[k * st] : mk<T>(0, 0);
     }
   }
   __syncthreads();  // coefficients
   c2 z[SEG];
   if constexpr (KEEP) {
-    const c2 pl = (active && k0 - 1 >= 1) ? line[(k0 - 1) * st] : mk<T>(0, 0);
-    const c2 pr = (active && k0 + SEG <= M) ? line[(k0 + SEG) * st] : mk<T>(0, 0);
+    const c2 pl = (active && k0 - 1 >= 1 && GPE_CHECK((long)(k0 - 1) * st < lim, 202)) ? line[(k0 - 1) * st]
+                                                                                         : mk<T>(0, 0);
+    const c2 pr = (active && k0 + SEG <= M && GPE_CHECK((long)(k0 + SEG) * st < lim, 203)) ? line[(k0 + SEG) * st]
+                                                                                           : mk<T>(0, 0);
     local_forward<T, IMAG, SEG>(p, z, pl, pr, sc, k0, M);
   } else {
     stream_forward<T, IMAG, SEG>(
-        [&](int k) { return (active && k >= 1 && k <= M) ? line[k * st] : mk<T>(0, 0); }, z, sc, k0, M);
+        [&](int k) {
+          return (active && k >= 1 && k <= M && GPE_CHECK((long)k * st < lim, 204)) ? line[k * st] : mk<T>(0, 0);
+        },
+        z, sc, k0, M);
   }
   seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
   T nval = T(0);
@@ -588,13 +592,13 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
       if (k <= M) {
         c2 pk;
         if constexpr (KEEP) pk = p[j];
-        else pk = __ldcg(&line[k * st]);
+        else pk = GPE_CHECK((long)k * st < lim, 205) ? __ldcg(&line[k * st]) : mk<T>(0, 0);
         c2 u = sub2<T>(pk, z[j]);
         if constexpr (CLOSE) {
           const int jy = G.axis == 2 ? cf2 : k, kz = G.axis == 2 ? k : cf2;
           u = half_phase<T, IMAG>(A, u, qb + (long)k * st, ci, jy, kz);
         }
-        line[k * st] = u;
+        if (GPE_CHECK((long)k * st < lim, 206)) line[k * st] = u;
         if constexpr (LAST && RP) {
           tacc += w[k] * (u.x * u.x);
           tim += w[k] * (u.y * u.y);
@@ -603,7 +607,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
         }
       }
     }
-    if (s == 0) {
+    if (s == 0 && GPE_CHECK((long)(n - 1) * st < lim, 207)) {
       line[0] = mk<T>(0, 0);
       line[(n - 1) * st] = mk<T>(0, 0);
     }
@@ -659,6 +663,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   const int per_line = (n + 31) >> 5;  // n <= 512: at most 16 chunks
   const c2* in = A.src ? A.src : A.psi;
   const T* rin = reinterpret_cast<const T*>(in);  // RL
+  const long lim = G.points();  // complex values (RL: reals) of the array
   // per-line part of the sub-step N (FIRST) of grid line Lg
   auto line_factors = [&](int Lg, c2& fline, T& vline) {
     fline = mk<T>(1, 0);
@@ -718,7 +723,8 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
           for (int i = 0; i < 4; ++i) {
             const int k = (q0 + i) * 32 + lane;
             const bool in_k = k >= 1 && k <= M;
-            v[i] = mk<T>((oka && in_k) ? rin[La * G.nx + k] : T(0), (okb && in_k) ? rin[Lb * G.nx + k] : T(0));
+            v[i] = mk<T>((oka && in_k && GPE_CHECK((long)La * G.nx + k < lim, 211)) ? rin[La * G.nx + k] : T(0),
+                         (okb && in_k && GPE_CHECK((long)Lb * G.nx + k < lim, 212)) ? rin[Lb * G.nx + k] : T(0));
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -729,7 +735,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
               if (oka) w.x = apply_R(w.x, La, k, fa, va, T(1));
               if (okb) w.y = apply_R(w.y, Lb, k, fb, vb, T(1));
             }
-            tile[k * kTilePitch + c] = w;
+            if (GPE_CHECK(k < n && c < 32, 213)) tile[k * kTilePitch + c] = w;
           }
         }
       } else {
@@ -742,7 +748,8 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int k = (q0 + i) * 32 + lane;
-            v[i] = (line_ok && k >= 1 && k <= M) ? in[gbase + k] : mk<T>(0, 0);
+            v[i] = (line_ok && k >= 1 && k <= M && GPE_CHECK((long)gbase + k < lim, 214)) ? in[gbase + k]
+                                                                                          : mk<T>(0, 0);
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -750,7 +757,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
             if (k >= n) break;
             c2 w = v[i];
             if (FIRST && !pend && line_ok && k >= 1 && k <= M) w = apply_N(w, L0 + c, k, fline, vline, T(1));
-            tile[k * kTilePitch + c] = w;
+            if (GPE_CHECK(k < n && c < 32, 215)) tile[k * kTilePitch + c] = w;
           }
         }
       }
@@ -814,12 +821,15 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
     if constexpr (RL) {
       T* rout = reinterpret_cast<T*>(A.psi);
       const int La = 2 * (L0 + c), Lb = La + 1;
-      for (int k = lane; k < n; k += 32) rout[La * G.nx + k] = tile[k * kTilePitch + c].x;
+      for (int k = lane; k < n; k += 32)
+        if (GPE_CHECK((long)La * G.nx + k < lim, 216)) rout[La * G.nx + k] = tile[k * kTilePitch + c].x;
       if (Lb < G.nlines)
-        for (int k = lane; k < n; k += 32) rout[Lb * G.nx + k] = tile[k * kTilePitch + c].y;
+        for (int k = lane; k < n; k += 32)
+          if (GPE_CHECK((long)Lb * G.nx + k < lim, 217)) rout[Lb * G.nx + k] = tile[k * kTilePitch + c].y;
     } else {
       const int gbase = (L0 + c) * G.nx;
-      for (int k = lane; k < n; k += 32) A.psi[gbase + k] = tile[k * kTilePitch + c];
+      for (int k = lane; k < n; k += 32)
+        if (GPE_CHECK((long)gbase + k < lim, 218)) A.psi[gbase + k] = tile[k * kTilePitch + c];
     }
   }
   finish_norm<T, LAST>(nval, A.parts_out);
@@ -869,6 +879,7 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
   pdl_release();
   const int Mx = nx - 2, My = ny - 2;
   const c2* in = Ax.psi + base;
+  const long lim = Ax.geom.points() - base;  // complex values from the plane's start to the array's end
   // per-row part of N (row j of plane kz is x line j + ny kz)
   auto row_v = [&](int j) -> T { return Ax.V ? T(0) : Ax.vy[j] + Ax.vz[kz]; };
   auto apply = [&](c2 w, int j, int i, T vline, T scl) -> c2 {
@@ -893,13 +904,14 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int i = (q0 + t) * 32 + lane;
-          v[t] = (i >= 1 && i <= Mx) ? in[(long)j * nx + i] : mk<T>(0, 0);
+          v[t] = (i >= 1 && i <= Mx && GPE_CHECK((long)j * nx + i < lim, 221)) ? in[(long)j * nx + i] : mk<T>(0, 0);
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int i = (q0 + t) * 32 + lane;
           if (i >= nx) break;
-          P[j * PX + i] = (!pend && i >= 1 && i <= Mx) ? apply(v[t], j, i, vline, T(1)) : v[t];
+          if (GPE_CHECK(j < ny && i < PX, 222))
+            P[j * PX + i] = (!pend && i >= 1 && i <= Mx) ? apply(v[t], j, i, vline, T(1)) : v[t];
         }
       }
     }
@@ -984,7 +996,7 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int i = (q0 + t) * 32 + lane;
-        if (i < nx) out[(long)j * nx + i] = v[t];
+        if (i < nx && GPE_CHECK((long)j * nx + i < lim, 223)) out[(long)j * nx + i] = v[t];
       }
     }
 }
@@ -1020,12 +1032,13 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       if (!kFactors && A.V == nullptr) vline = A.vy[ta] + A.vz[tb];
     }
     const c2* in = (A.src ? A.src : A.psi) + base;
+    const long lim = G.points() - base;
     c2 p[SEG], e[SEG];
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
       const int k = k0 + j;
       c2 v = mk<T>(0, 0);
-      if (k <= M) {
+      if (k <= M && GPE_CHECK(k < lim, 231)) {
         v = in[k];
         if constexpr (FIRST && is_df<T>::value) {
           if (IMAG) { v.x *= scl; v.y *= scl; }
@@ -1087,12 +1100,12 @@ __device__ __forceinline__ void xsweep_body(const Sweep2Args<T>& A, int L, doubl
       if (k <= M) {
         const c2 z = cf_fma<T, IMAG>(__ldg(&A.gb[k]), Zin, e[j]);
         const c2 u = sub2<T>(p[j], z);
-        line[k] = u;
+        if (GPE_CHECK(k < lim, 232)) line[k] = u;
         if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
       }
     }
     if (lane == 0) line[0] = mk<T>(0, 0);
-    if (lane == 31) line[G.n - 1] = mk<T>(0, 0);
+    if (lane == 31 && GPE_CHECK(G.n - 1 < lim, 233)) line[G.n - 1] = mk<T>(0, 0);
     if (LAST) nval = tacc * (A.w_a[ta] * A.w_b[tb]);
   }
   finish_norm<T, LAST>(nval, A.parts_out);
@@ -1147,14 +1160,17 @@ __device__ __forceinline__ void psweep_issue(const Sweep2Args<T>& A, int tile, c
     for (int c = w; c < 32; c += nwarps) {
       const bool lok = c < nl;
       const int gbase = lok ? (L0 + c) * G.nx : 0;
-      for (int k = lane; k < n; k += 32) cp_async_c2<T>(buf + c * pitch + k, in + gbase + k, lok && k >= 1 && k <= M);
+      for (int k = lane; k < n; k += 32)
+        if (GPE_CHECK((long)gbase + k < G.points() && c * pitch + k < 32 * pitch, 241))
+          cp_async_c2<T>(buf + c * pitch + k, in + gbase + k, lok && k >= 1 && k <= M);
     }
   } else {
     const bool lok = lane < nl;
     const int base = lok ? line_base32(G, L0 + lane) : 0;
     const int st = (int)G.stride;
-    for (int k = w; k < n; k += nwarps) cp_async_c2<T>(buf + k * kTilePitch + lane, in + base + k * st,
-                                                       lok && k >= 1 && k <= M);
+    for (int k = w; k < n; k += nwarps)
+      if (GPE_CHECK((long)base + (long)k * st < G.points(), 242))
+        cp_async_c2<T>(buf + k * kTilePitch + lane, in + base + k * st, lok && k >= 1 && k <= M);
   }
 }
 
@@ -1241,7 +1257,8 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
       // coalesced store of the tile: warp w takes lines w, w + nseg, ...
       for (int c = s; c < nl; c += nseg) {
         const int gbase = (L0 + c) * G.nx;
-        for (int k = lane; k < n; k += 32) A.psi[gbase + k] = buf[c * pitch + k];
+        for (int k = lane; k < n; k += 32)
+          if (GPE_CHECK((long)gbase + k < G.points(), 243)) A.psi[gbase + k] = buf[c * pitch + k];
       }
     } else if (lane < nl) {
       c2* line = A.psi + line_base32(G, L0 + lane);
@@ -1252,11 +1269,11 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
         if (k <= M) {
           const c2 p = at(k);
           const c2 u = sub2<T>(p, z[j]);
-          line[k * st] = u;
+          if (GPE_CHECK((line - A.psi) + (long)k * st < G.points(), 244)) line[k * st] = u;
           if (LAST) tacc += A.w_axis[k] * (u.x * u.x + u.y * u.y);
         }
       }
-      if (s == 0) {
+      if (s == 0 && GPE_CHECK((line - A.psi) + (long)(n - 1) * st < G.points(), 245)) {
         line[0] = mk<T>(0, 0);
         line[(n - 1) * st] = mk<T>(0, 0);
       }
@@ -1309,6 +1326,7 @@ __global__ void __launch_bounds__(256) strang_phase_kernel(Sweep2Args<T> A) {
       ll[r] = (int)L;
       ok[r] = u < nchunks && ii[r] < G.nx;
       q[r] = (long)L * G.nx + ii[r];
+      ok[r] = ok[r] && GPE_CHECK(q[r] < G.points(), 251);
       if (ok[r]) v[r] = A.psi[q[r]];
     }
 #pragma unroll

@@ -139,14 +139,18 @@ struct TmaTiles {
 template <bool IMAG, int SEG, bool FULL>
 __device__ __forceinline__ void tma_forward(const float2* buf, int lane, const float2* al, int k0, int M,
                                             float2 (&e)[SEG]) {
-  float2 pm = buf[(k0 - 1) * 32 + lane], pc = buf[k0 * 32 + lane];
+  // rows 0..M+1 of the tile (a failed check reads zero)
+  auto row = [&](int k) {
+    return GPE_CHECK(k >= 0 && k <= M + 1, 281) ? buf[k * 32 + lane] : make_float2(0.f, 0.f);
+  };
+  float2 pm = row(k0 - 1), pc = row(k0);
   float2 prev = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
     float2 pn;
-    if (FULL) pn = buf[(k + 1) * 32 + lane];
-    else pn = (k + 1 <= M + 1) ? buf[(k + 1) * 32 + lane] : make_float2(0.f, 0.f);
+    if (FULL) pn = row(k + 1);
+    else pn = (k + 1 <= M + 1) ? row(k + 1) : make_float2(0.f, 0.f);
     const float2 t = make_float2(prev.x + neg_lap(pm.x, pn.x, pc.x), prev.y + neg_lap(pm.y, pn.y, pc.y));
     float2 v = make_float2(0.f, 0.f);
     if (FULL || k <= M) v = cf_mul<float, IMAG>(al[k], t);
@@ -474,22 +478,26 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
       break;
     }
     const unsigned char* tb = tiles_gen + (size_t)st * tile_bytes;
+    // a point pair of the staged tile (a failed check reads zeros, skips the store)
+    auto ld2 = [&](int k) -> float4 {
+      return GPE_CHECK(k >= 0 && k + 1 < n, 282) ? *reinterpret_cast<const float4*>(tb + swz_off(lane, k))
+                                                 : make_float4(0, 0, 0, 0);
+    };
     const int L = t * 32 + lane;
     const bool line_ok = L < G.nlines;
     // per-line part of N and the points of this segment plus one on each side
     const float vline = (A.V || !line_ok) ? 0.f : A.vy[L % G.ny] + A.vz[L / G.ny];
     float2 p[SEG + 2];
     {
-      const float4 lft = s > 0 ? *reinterpret_cast<const float4*>(tb + swz_off(lane, k0 - 2)) : make_float4(0, 0, 0, 0);
+      const float4 lft = s > 0 ? ld2(k0 - 2) : make_float4(0, 0, 0, 0);
       p[0] = make_float2(lft.z, lft.w);
 #pragma unroll
       for (int j = 0; j < SEG; j += 2) {
-        const float4 v = *reinterpret_cast<const float4*>(tb + swz_off(lane, k0 + j));
+        const float4 v = ld2(k0 + j);
         p[1 + j] = make_float2(v.x, v.y);
         p[2 + j] = make_float2(v.z, v.w);
       }
-      const float4 rgt =
-          s < nseg - 1 ? *reinterpret_cast<const float4*>(tb + swz_off(lane, k0 + SEG)) : make_float4(0, 0, 0, 0);
+      const float4 rgt = s < nseg - 1 ? ld2(k0 + SEG) : make_float4(0, 0, 0, 0);
       p[SEG + 1] = make_float2(rgt.x, rgt.y);
     }
     const long gbase = (long)L * G.nx;
@@ -521,7 +529,8 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
 #pragma unroll
     for (int j = 0; j < SEG; j += 2) {
       const float2 u0 = sub2<float>(p[1 + j], z[j]), u1 = sub2<float>(p[2 + j], z[j + 1]);
-      *reinterpret_cast<float4*>(tw + swz_off(lane, k0 + j)) = make_float4(u0.x, u0.y, u1.x, u1.y);
+      if (GPE_CHECK(k0 + j + 1 < n, 283))
+        *reinterpret_cast<float4*>(tw + swz_off(lane, k0 + j)) = make_float4(u0.x, u0.y, u1.x, u1.y);
     }
     fence_async_smem();
     mbar_arrive(empty0 + 8u * st);

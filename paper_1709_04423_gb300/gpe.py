@@ -44,7 +44,7 @@ ABI_SYMBOLS = (
     "gp_batch_offset", "gp_batch_destroy", "gp_adjoint_forward", "gp_adjoint_backward",
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
     "gp_init_spherical", "gp_set_splitting", "gp_set_real_state", "gp_init_circular", "gp_init_axial",
-    "gp_test_stall_transfers", "gp_time_sweeps_graph", "gp_fp_fma_rates",
+    "gp_test_stall_transfers", "gp_time_sweeps_graph", "gp_fp_fma_rates", "gp_check_status",
 )
 
 
@@ -60,6 +60,7 @@ class GpObs(ctypes.Structure):
 
 
 _lib = None
+_lib_check = None
 _vp = ctypes.c_void_p
 
 
@@ -68,8 +69,23 @@ def load(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _open(path)
+    return _lib
+
+
+def load_check():
+    """The checking build, libgpe_check.so (index checks in the kernels, guard
+    bands around every device buffer; see gp_check_status), as a separate
+    ctypes library with the same entry points and argument types."""
+    global _lib_check
+    if _lib_check is None:
+        _lib_check = _open(os.path.join(os.path.dirname(LIB_PATH), "libgpe_check.so"))
+    return _lib_check
+
+
+def _open(path):
     if not os.path.exists(path):
-        raise RuntimeError(f"libgpe.so is not built ({path}); run paper_1709_04423_gb300.build.build()")
+        raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run paper_1709_04423_gb300.build.build()")
     lib = ctypes.CDLL(path)
     I, D, L = ctypes.c_int, ctypes.c_double, ctypes.c_long
     lib.gp_init.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(I), ctypes.POINTER(D), D,
@@ -88,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.gp_time_sweeps_graph.argtypes = [_vp, I, I, ctypes.POINTER(D)]
     lib.gp_fp_fma_rates.argtypes = [ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.gp_test_stall_transfers.argtypes = [_vp, I]
+    lib.gp_check_status.argtypes = [ctypes.POINTER(I)]
     lib.gp_observables_noalloc.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), D, I,
                                            _vp, _vp, _vp, _vp]
     lib.gp_autotune.argtypes = [_vp, I, I, ctypes.POINTER(D)]
@@ -115,7 +132,6 @@ def load(path: str = LIB_PATH):
     lib.gp_destroy.argtypes = [_vp]
     lib.gp_last_error.restype = ctypes.c_char_p
     lib.gp_kernel_launches.restype = ctypes.c_ulonglong
-    _lib = lib
     return lib
 
 
