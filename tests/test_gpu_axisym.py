@@ -4,13 +4,13 @@ rho) against the FP64 oracle.
 
 Tolerances as for the Cartesian grids: FP64 relative L2 <= 1e-12 after 1000
 steps and |d mu| <= 1e-10; FP32 relative L2 2e-5 (imaginary) / 1e-4 (real)
-and |d mu| <= 1e-6 (absolute; on 1d lines the FP32 storage bound of
-mu_tol_f32); double-float 1e-12.
+and |d mu| within the FP32 bound of tests/tolerances.py; double-float 1e-12.
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from tolerances import mu_tol_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -26,17 +26,6 @@ def G():
 
 def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
-
-
-def mu_tol_f32(dim, mu):
-    """|d mu| bound of the FP32 form: 1e-6 absolute, except on a single line
-    (dim 1, a few hundred points), where rounding the state to FP32 after
-    every sub-step -- with all arithmetic exact -- already moves mu by about
-    1e-7 of mu: an FP32 emulation of a 257-point line over 300 real-time
-    steps gives 7.7e-7 at mu = 14 from the storage rounding alone, because
-    the rounding noise averages over only ~sqrt(257) independent points.
-    There the bound is 4e-7 |mu| (about seven FP32 ulps of mu)."""
-    return 1e-6 if dim > 1 else max(1e-6, 4e-7 * abs(mu))
 
 
 def start(dim, n, dx, nkl, seed=0.0):
@@ -108,7 +97,7 @@ def test_axisym_other_precisions(G, case, prec, imag):
     else:
         assert rel_l2(got, ref) <= 1e-12
     mu, mur = p.observables()["mu"], O.observables(gr, ref)["mu"]
-    assert abs(mu - mur) <= (mu_tol_f32(dim, mur) if prec == "f32" else 1e-10)
+    assert abs(mu - mur) <= (mu_tol_f32(mur) if prec == "f32" else 1e-10)
     p.close()
 
 

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tolerances import mu_tol_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +55,8 @@ def test_spherical_other_precisions(G, prec, tol):
     p.step_imag(1000)
     ref = O.run(gr, u0, True, 1000)
     assert rel_l2(p.get_state(device=False).astype(np.complex128), ref) <= tol
-    assert abs(p.observables()["mu"] - O.observables(gr, ref)["mu"]) <= (1e-6 if prec == "f32" else 1e-10)
+    mur = O.observables(gr, ref)["mu"]
+    assert abs(p.observables()["mu"] - mur) <= (mu_tol_f32(mur) if prec == "f32" else 1e-10)
     p.close()
 
 
