@@ -308,6 +308,28 @@ int gp_batch_observables(gp_batch* b, gp_obs* out);
 /* Element offset of run `run` in the back-to-back state, or -1. */
 long gp_batch_offset(const gp_batch* b, int run);
 
+/* How a batch step is launched (the paper has no counterpart: its programs
+ * run one problem at a time).  Mode 0: one launch per sweep direction and
+ * segment-length class per step (every run's x lines, then every run's y
+ * lines).  Mode 1 (FP32 batches only): one persistent launch per block of
+ * steps; CTAs claim (step, axis, run, 32-line tile) items in order and each
+ * item waits, on per-run completion counters, for the sweep it depends on
+ * (a run's x sweep of step t for its y sweep of step t-1, its y sweep for
+ * its x sweep), so different runs' sweeps overlap with no grid-wide barrier.
+ * The per-line arithmetic is the same in both modes: the states agree bit
+ * for bit.  Each wait is bounded (GPE_WAIT_LIMIT_MS at gp_batch_init, default
+ * 1000 ms); a wait that runs out stops the launch and the next
+ * gp_batch_observables returns GP_ERR_TIMEOUT (the states are then not
+ * valid).  gp_batch_set_mode: GP_ERR_INVALID for mode 1 on an FP64 batch.
+ * gp_batch_get_mode returns the mode (-1 for NULL).  gp_batch_autotune times
+ * nsteps >= 1 steps in each mode (after nsteps untimed ones), keeps the faster
+ * and writes the two times in ms to ms_out[0..1] when ms_out is not NULL
+ * (-1 where not timed; FP64 batches keep mode 0 untimed); the states are put
+ * back.  Synchronises the stream. */
+int gp_batch_set_mode(gp_batch* b, int persistent);
+int gp_batch_get_mode(const gp_batch* b);
+int gp_batch_autotune(gp_batch* b, long nsteps, double* ms_out);
+
 /* Frees the batch (NULL is a no-op). */
 int gp_batch_destroy(gp_batch* b);
 
@@ -424,6 +446,15 @@ int gp_check_status(int* first_failure);
  * 0 restores normal operation; the state is not valid after a timeout
  * (set it again).  0 <= extra_bytes <= 1024, else GP_ERR_INVALID. */
 int gp_test_stall_transfers(gp_handle* h, int extra_bytes);
+
+/* Test hook of the one-launch batch form's bounded step waits (the paper has
+ * no counterpart).  With extra > 0 every wait of mode 1 asks for extra more
+ * finished items than the launch will ever count, so the first y sweep's
+ * waits run out after the wait limit and the next gp_batch_observables
+ * returns GP_ERR_TIMEOUT with the context still usable.  0 restores normal
+ * operation (set the states again).  0 <= extra <= 1 << 20, else
+ * GP_ERR_INVALID. */
+int gp_test_batch_stall(gp_batch* b, int extra);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -179,18 +180,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// Waits until *c >= target, for at most limit_ns of global time.
-__device__ __forceinline__ bool wait_count(const unsigned* c, unsigned target, unsigned long long limit_ns) {
+// Waits until *c >= target, for at most limit_ns of global time; gives up at
+// once when another CTA has recorded an error.
+__device__ __forceinline__ bool wait_count(const unsigned* c, unsigned target, unsigned long long limit_ns,
+                                           const int* err) {
   if (ld_acquire(c) >= target) return true;
   const unsigned long long t0 = batch_ns();
   for (;;) {
     __nanosleep(64);
     if (ld_acquire(c) >= target) return true;
-    if (batch_ns() - t0 > limit_ns) return false;
+    if (*(const volatile int*)err != 0 || batch_ns() - t0 > limit_ns) return false;
   }
 }
 
-__global__ void __launch_bounds__(512, 1) batch_persist_kernel(PersistArgs P) {
+__global__ void __launch_bounds__(512) batch_persist_kernel(PersistArgs P) {
   extern __shared__ __align__(16) unsigned char bsmem_raw[];
   __shared__ float2 cf[16][33], cb[16][33];
   __shared__ double red_smem[32];
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(512, 1) batch_persist_kernel(PersistArgs P) {
       // for the run's x items of step t
       const unsigned target = xs ? (unsigned)(t * P.per_run[2 * r + 1]) : (unsigned)((t + 1) * P.per_run[2 * r]);
       int stop = 0;
-      if (target > 0 && !wait_count(P.done + 2 * r + (xs ? 1 : 0), target + (unsigned)P.stall, P.limit_ns)) {
+      if (target > 0 && !wait_count(P.done + 2 * r + (xs ? 1 : 0), target + (unsigned)P.stall, P.limit_ns, P.err)) {
         atomicExch(P.err, 1);
         stop = 1;
       }
@@ -338,6 +341,7 @@ struct gp_batch {
   int* p_seg = nullptr;
   unsigned* p_count = nullptr;  // [1 + 2 nruns]: next, done
   size_t p_smem = 0;
+  int p_threads = 32;           // 32 x the most segments of any line
   int p_stall = 0;
   unsigned long long limit_ns = 1000000000ull;
   int* dev_err = nullptr;
@@ -504,6 +508,7 @@ int build_tables(gp_batch* b) {
         segs[2 * r + a] = kClassSegs[class_of(n, a, b->esize)];
         for (int L0 = 0; L0 < nl; L0 += 32) items.push_back({r, L0});
         per_run[2 * r + a] = (nl + 31) / 32;
+        b->p_threads = std::max(b->p_threads, 32 * ((n - 2 + segs[2 * r + a] - 1) / segs[2 * r + a]));
         smem = std::max(smem, (a == 0 ? (size_t)(36 * n + 512) : (size_t)(3 * n + 512)) * sizeof(float2));
         (a == 0 ? b->p_nx : b->p_ny) += (nl + 31) / 32;
       }
@@ -529,7 +534,7 @@ void enqueue_persistent(gp_batch* b, long nsteps) {
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persist_kernel, 512, b->p_smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persist_kernel, b->p_threads, b->p_smem);
   PersistArgs P;
   P.runs = (const BatchRun<float>*)b->runs_d;
   P.items = (const BatchItem*)b->p_items;
@@ -546,7 +551,7 @@ void enqueue_persistent(gp_batch* b, long nsteps) {
   P.dt = (float)b->dt;
   const long items = ((long)b->p_nx + b->p_ny) * nsteps;
   const int blocks = (int)std::max(1L, std::min<long>(items, (long)std::max(1, per_sm) * std::max(1, sms)));
-  batch_persist_kernel<<<blocks, 512, b->p_smem, b->work>>>(P);
+  batch_persist_kernel<<<blocks, b->p_threads, b->p_smem, b->work>>>(P);
   count_launch();
 }
 
@@ -795,7 +800,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
     cudaError_t e = cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->obs_host, 8 * sizeof(double) * nruns);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->obs_host, 8 * sizeof(double) * (nruns + 1));
     if (e != cudaSuccess) return bail(fail(GP_ERR_CUDA, std::string("gp_batch_init: ") + cudaGetErrorString(e)));
   }
   int rc;
@@ -841,6 +846,12 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   }
   if ((rc = b_alloc(b, (void**)&b->partials, 152L * 16 * 8 * sizeof(double)))) return bail(rc);
   if ((rc = b_alloc(b, (void**)&b->counter, 64))) return bail(rc);
+  if ((rc = b_alloc(b, (void**)&b->dev_err, 64))) return bail(rc);
+  {
+    const char* lim = std::getenv("GPE_WAIT_LIMIT_MS");
+    const long ms = lim ? std::atol(lim) : 1000;
+    b->limit_ns = (unsigned long long)(ms > 0 ? ms : 1000) * 1000000ull;
+  }
   if ((rc = b_alloc(b, (void**)&b->obs_out, (8L * nruns + 8) * sizeof(double)))) return bail(rc);
   if ((rc = prec == GP_F64 ? build_obs<double>(b) : build_obs<float>(b))) return bail(rc);
   *out = b;
@@ -891,8 +902,17 @@ int gp_batch_observables(gp_batch* b, gp_obs* out) {
   rc = b->prec == GP_F64 ? batch_observables<double>(b) : batch_observables<float>(b);
   if (rc) return rc;
   GP_CUDA(cudaMemcpyAsync(b->obs_host, b->obs_out, 8 * sizeof(double) * b->nruns, cudaMemcpyDeviceToHost, b->work));
+  GP_CUDA(cudaMemcpyAsync(b->obs_host + 8L * b->nruns, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost, b->work));
   GP_CUDA(cudaStreamSynchronize(b->work));
   if ((rc = b_join_out(b))) return rc;
+  int err = 0;
+  std::memcpy(&err, b->obs_host + 8L * b->nruns, sizeof(int));
+  if (err) {
+    GP_CUDA(cudaMemsetAsync(b->dev_err, 0, sizeof(int), b->work));
+    GP_CUDA(cudaStreamSynchronize(b->work));
+    return fail(GP_ERR_TIMEOUT, "gp_batch_observables: a step barrier of the one-launch form ran out of time "
+                                "(GPE_WAIT_LIMIT_MS); the states are not valid");
+  }
   bool finite = true;
   for (int r = 0; r < b->nruns; ++r) {
     const double* S = b->obs_host + 8L * r;
@@ -908,6 +928,83 @@ int gp_batch_observables(gp_batch* b, gp_obs* out) {
     for (int q = 0; q < 7; ++q) finite = finite && std::isfinite(S[q]);
   }
   if (!finite) return fail(GP_ERR_NONFINITE, "gp_batch_observables: a state holds NaN or Inf");
+  return GP_OK;
+}
+
+int gp_batch_set_mode(gp_batch* b, int persistent) {
+  if (!b) return fail(GP_ERR_INVALID, "gp_batch_set_mode: NULL handle");
+  if (persistent != 0 && persistent != 1) return fail(GP_ERR_INVALID, "gp_batch_set_mode: mode must be 0 or 1");
+  if (persistent && b->prec != GP_F32)
+    return fail(GP_ERR_INVALID, "gp_batch_set_mode: the one-launch form takes FP32 states only");
+  if ((bool)persistent != b->persistent) {
+    if (b->work) GP_CUDA(cudaStreamSynchronize(b->work));
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->persistent = persistent;
+  }
+  return GP_OK;
+}
+
+int gp_batch_get_mode(const gp_batch* b) { return b ? (int)b->persistent : -1; }
+
+int gp_batch_autotune(gp_batch* b, long nsteps, double* ms_out) {
+  if (!b) return fail(GP_ERR_INVALID, "gp_batch_autotune: NULL handle");
+  if (nsteps < 1) return fail(GP_ERR_INVALID, "gp_batch_autotune: nsteps < 1");
+  if (ms_out) ms_out[0] = ms_out[1] = -1.0;
+  if (b->prec != GP_F32) return gp_batch_set_mode(b, 0);  // one form only
+  int rc = b_join_in(b);
+  if (rc) return rc;
+  // the states are kept and put back: timing steps the runs
+  void* keep = nullptr;
+  GP_CUDA(cudaMallocAsync(&keep, (size_t)b->total * b->esize, b->work));
+  GP_CUDA(cudaMemcpyAsync(keep, b->psi, (size_t)b->total * b->esize, cudaMemcpyDeviceToDevice, b->work));
+  cudaEvent_t e0, e1;
+  GP_CUDA(cudaEventCreate(&e0));
+  GP_CUDA(cudaEventCreate(&e1));
+  double ms[2] = {0.0, 0.0};
+  const bool was = b->persistent;
+  for (int m = 0; m < 2 && rc == GP_OK; ++m) {
+    if ((rc = gp_batch_set_mode(b, m))) break;
+    if ((rc = batch_steps<float>(b, nsteps))) break;  // warm-up (graph capture included)
+    cudaEventRecord(e0, b->work);
+    if ((rc = batch_steps<float>(b, nsteps))) break;
+    cudaEventRecord(e1, b->work);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(GP_ERR_CUDA, "gp_batch_autotune: timing failed"); break; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms[m] = t;
+  }
+  int err = 0;
+  if (rc == GP_OK) {
+    cudaMemcpy(&err, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) cudaMemset(b->dev_err, 0, sizeof(int));
+  }
+  cudaMemcpyAsync(b->psi, keep, (size_t)b->total * b->esize, cudaMemcpyDeviceToDevice, b->work);
+  cudaFreeAsync(keep, b->work);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    gp_batch_set_mode(b, was);
+    return rc;
+  }
+  if (err) {
+    gp_batch_set_mode(b, 0);
+    return fail(GP_ERR_TIMEOUT, "gp_batch_autotune: a step barrier of the one-launch form ran out of time");
+  }
+  if (ms_out) ms_out[0] = ms[0], ms_out[1] = ms[1];
+  if ((rc = gp_batch_set_mode(b, ms[1] < ms[0] ? 1 : 0))) return rc;
+  return b_join_out(b);
+}
+
+int gp_test_batch_stall(gp_batch* b, int extra) {
+  if (!b) return fail(GP_ERR_INVALID, "gp_test_batch_stall: NULL handle");
+  if (extra < 0 || extra > (1 << 20)) return fail(GP_ERR_INVALID, "gp_test_batch_stall: extra outside [0, 2^20]");
+  if (extra != b->p_stall) {
+    if (b->work) GP_CUDA(cudaStreamSynchronize(b->work));
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->p_stall = extra;
+  }
   return GP_OK;
 }
 

@@ -45,6 +45,7 @@ ABI_SYMBOLS = (
     "gp_autotune", "gp_set_shapes", "gp_get_shapes", "gp_reduced_density", "gp_step_series",
     "gp_init_spherical", "gp_set_splitting", "gp_set_real_state", "gp_init_circular", "gp_init_axial",
     "gp_test_stall_transfers", "gp_time_sweeps_graph", "gp_fp_fma_rates", "gp_check_status",
+    "gp_batch_set_mode", "gp_batch_get_mode", "gp_batch_autotune", "gp_test_batch_stall",
 )
 
 
@@ -126,6 +127,10 @@ def _open(path):
     lib.gp_batch_offset.argtypes = [_vp, I]
     lib.gp_batch_offset.restype = L
     lib.gp_batch_destroy.argtypes = [_vp]
+    lib.gp_batch_set_mode.argtypes = [_vp, I]
+    lib.gp_batch_get_mode.argtypes = [_vp]
+    lib.gp_batch_autotune.argtypes = [_vp, L, ctypes.POINTER(D)]
+    lib.gp_test_batch_stall.argtypes = [_vp, I]
     lib.gp_npoints.argtypes = [_vp]
     lib.gp_npoints.restype = L
     lib.gp_precision_of.argtypes = [_vp]
@@ -333,6 +338,26 @@ def gp_batch_offset(b, run):
 
 def gp_batch_destroy(b):
     return _check(load().gp_batch_destroy(b))
+
+
+def gp_batch_set_mode(b, persistent):
+    return _check(load().gp_batch_set_mode(b, int(persistent)))
+
+
+def gp_batch_get_mode(b):
+    return int(load().gp_batch_get_mode(b))
+
+
+def gp_batch_autotune(b, nsteps):
+    ms = (ctypes.c_double * 2)()
+    _check(load().gp_batch_autotune(b, int(nsteps), ms))
+    return [float(ms[0]), float(ms[1])]
+
+
+def gp_test_batch_stall(b, extra):
+    """Test hook: the one-launch batch form's step waits ask for more items
+    than will finish, so they run out (see include/gpe.h)."""
+    return _check(load().gp_test_batch_stall(b, int(extra)))
 
 
 def gp_npoints(h):
@@ -629,6 +654,18 @@ class Batch:
 
     def observables(self):
         return gp_batch_observables(self.b, self.nruns)
+
+    def set_mode(self, persistent):
+        """0: per-class launches; 1: one persistent launch (FP32)."""
+        gp_batch_set_mode(self.b, persistent)
+
+    def mode(self):
+        return gp_batch_get_mode(self.b)
+
+    def autotune(self, nsteps=32):
+        """Times both launch forms over nsteps steps and keeps the faster;
+        returns their times in ms (-1 where not timed)."""
+        return gp_batch_autotune(self.b, nsteps)
 
 
 def real_time_evolution(prop, phi0, V, g, nsteps, ckpt_every):

@@ -5,7 +5,11 @@ A run in a batch must give exactly what the same run gives in its own handle
 oracle run by run.  The full-size case is the 64-run workload (sizes drawn
 from {128, 192, 256, 384, 512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1,
 kappa ~ U[1, 2]) in the launch configuration the benchmark times, checked on
-sampled runs against the oracle.
+sampled runs against the oracle.  The one-launch form (FP32; per-run step
+waits inside one persistent launch) must give the per-class launches' states
+bit for bit, its bounded waits must come back as GP_ERR_TIMEOUT when made to
+run out, and the autotuner must keep the faster form and leave the states as
+they were.
 """
 import numpy as np
 import pytest
@@ -101,3 +105,103 @@ def test_batch_64_runs_full_size_sampled(G):
         assert rel_l2(b.get_state(i).astype(np.complex128), ref) <= 2e-5, i
         assert ob1[i]["mu"] == pytest.approx(O.observables(gr, ref)["mu"], rel=1e-5)
     b.close()
+
+
+# ---------------------------------------------------------------- one persistent launch
+
+def fp32_batch(G, runs, seed, mode):
+    b = G.Batch([r[0] for r in runs], [r[1] for r in runs], 5e-4, [r[2] for r in runs], [r[3] for r in runs],
+                precision="f32")
+    b.set_mode(mode)
+    assert b.mode() == mode
+    for i, (n, dx, nk, g) in enumerate(runs):
+        b.set_state(i, I.gaussian_state(2, list(n), list(dx), list(nk), seed=seed + i, noise=1e-2))
+    return b
+
+
+@pytest.mark.parametrize("nsteps", [1, 5, 37])
+def test_persistent_batch_bitwise_equals_class_launches(G, nsteps):
+    """Mode 1 (one launch per block of steps, per-run step waits) against mode
+    0 (one launch per sweep and class): the same per-line arithmetic, so the
+    same states bit for bit -- one step, a few, and graph blocks plus a tail."""
+    out = []
+    for mode in (0, 1):
+        b = fp32_batch(G, RUNS, 60, mode)
+        b.step_real(nsteps)
+        out.append([b.get_state(i) for i in range(len(RUNS))])
+        b.close()
+    for i in range(len(RUNS)):
+        assert np.array_equal(out[0][i], out[1][i]), i
+
+
+def test_persistent_batch_64_runs_full_size(G):
+    """The 64-run workload in mode 1 as the benchmark times it (graph blocks of
+    16 steps): bit for bit the per-class launches after 40 steps; one sampled
+    run against the FP64 oracle."""
+    P = I.batch_runs(seed=1712, nruns=64)
+    runs = [((int(n), int(n)), (0.1, 0.1), (1.0, float(k)), float(g)) for n, k, g in zip(P["n"], P["kappa"], P["g"])]
+    out, obs = [], []
+    for mode in (0, 1):
+        b = fp32_batch(G, runs, 70, mode)
+        b.step_real(40)
+        obs.append(b.observables())
+        out.append([b.get_state(i) for i in range(64)])
+        b.close()
+    for i in range(64):
+        assert np.array_equal(out[0][i], out[1][i]), i
+        assert obs[0][i]["mu"] == obs[1][i]["mu"], i
+    i = int(np.argmax(P["n"]))
+    (n, dx, nk, g) = runs[i]
+    gr = O.Grid(2, list(n), list(dx), 5e-4, list(nk), g)
+    ref = O.run(gr, I.gaussian_state(2, list(n), list(dx), list(nk), seed=70 + i, noise=1e-2), False, 40)
+    assert rel_l2(out[1][i].astype(np.complex128), ref) <= 2e-5
+
+
+def test_persistent_batch_refused_for_fp64(G):
+    b = G.Batch([r[0] for r in RUNS[:2]], [r[1] for r in RUNS[:2]], 5e-4, [r[2] for r in RUNS[:2]],
+                [r[3] for r in RUNS[:2]], precision="f64")
+    with pytest.raises(G.GPError):
+        b.set_mode(1)
+    assert b.mode() == 0
+    assert b.autotune(4) == [-1.0, -1.0] and b.mode() == 0
+    b.close()
+
+
+def test_batch_autotune_keeps_the_faster_form_and_the_states(G):
+    b = fp32_batch(G, RUNS, 80, 0)
+    before = [b.get_state(i) for i in range(len(RUNS))]
+    ms = b.autotune(8)
+    assert ms[0] > 0 and ms[1] > 0
+    assert b.mode() == (1 if ms[1] < ms[0] else 0)
+    for i in range(len(RUNS)):
+        assert np.array_equal(b.get_state(i), before[i]), i
+    b.step_real(3)
+    assert all(np.isfinite(o["mu"]) for o in b.observables())
+    b.close()
+
+
+def test_persistent_batch_wait_that_runs_out_returns_gp_err_timeout(G, monkeypatch):
+    """With the test hook every step wait of mode 1 asks for more finished
+    items than the launch counts: the first y sweep's waits give up after the
+    wait limit (50 ms here), the next gp_batch_observables returns
+    GP_ERR_TIMEOUT, and the context stays usable -- the same batch, hook off
+    and states set again, steps bit for bit as the per-class launches."""
+    monkeypatch.setenv("GPE_WAIT_LIMIT_MS", "50")
+    b = fp32_batch(G, RUNS, 90, 1)
+    G.gp_test_batch_stall(b.b, 1000)
+    b.step_real(3)
+    with pytest.raises(G.GPError) as e:
+        b.observables()
+    assert e.value.code == G.GP_ERR_TIMEOUT
+    G.gp_test_batch_stall(b.b, 0)
+    for i, (n, dx, nk, g) in enumerate(RUNS):
+        b.set_state(i, I.gaussian_state(2, list(n), list(dx), list(nk), seed=90 + i, noise=1e-2))
+    b.step_real(3)
+    b.observables()                            # the flag was cleared: no timeout now
+    got = [b.get_state(i) for i in range(len(RUNS))]
+    b.close()
+    c = fp32_batch(G, RUNS, 90, 0)
+    c.step_real(3)
+    for i in range(len(RUNS)):
+        assert np.array_equal(c.get_state(i), got[i]), i
+    c.close()

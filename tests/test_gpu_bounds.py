@@ -9,7 +9,7 @@ point per axis, even and odd sizes from 3 to 17, lines of 514 and 515 points
 (the longest segmented line and the first thread-per-line one) -- in every
 precision and in both time directions, with enough steps for the graph
 replays, in the default kernel shapes and in the fused-plane, pipelined and
-TMA shapes, and a batch of edge sizes.  The two libraries are loaded into the
+TMA shapes, and a batch of edge sizes in both launch forms.  The two libraries are loaded into the
 same process, which the test suite thereby also checks.  After every case gp_check_status must
 report no failed check and intact guard bands; the FP64 runs must also match
 the oracle (1e-12), so that a skipped access would show.
@@ -109,8 +109,8 @@ def test_kernel_shapes_pass_the_checks(lib, shapes, imag):
     assert rc == 0 and code == 0, (code, msg)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_batch_of_edge_sizes_passes_the_checks(lib, prec):
+@pytest.mark.parametrize("prec,mode", [("f64", 0), ("f32", 0), ("f32", 1)])
+def test_batch_of_edge_sizes_passes_the_checks(lib, prec, mode):
     sizes = [(3, 3), (17, 5), (514, 4), (4, 514), (64, 48)]   # a batch takes at most 514 points per axis
     nr = len(sizes)
     n = (ctypes.c_int * (2 * nr))(*[v for s in sizes for v in s])
@@ -120,6 +120,7 @@ def test_batch_of_edge_sizes_passes_the_checks(lib, prec):
     b = ctypes.c_void_p()
     assert lib.gp_batch_init(ctypes.byref(b), nr, n, dxs, 5e-4, nkl, g, PREC[prec], None) == 0, lib.gp_last_error()
     try:
+        assert lib.gp_batch_set_mode(b, mode) == 0, lib.gp_last_error()   # 1: the one-launch form
         for r, (nx, ny) in enumerate(sizes):
             a = np.ascontiguousarray(I.gaussian_state(2, [nx, ny], [0.3, 0.3], [1.0, 1.4]),
                                      dtype=np.complex64 if prec == "f32" else np.complex128)
