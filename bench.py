@@ -533,10 +533,12 @@ def run_ours(args):
                 lam = (2 * c * atgt * 1e-3).to(q.ctype).contiguous()
                 dJdV = torch.empty(tuple(an), dtype=torch.float64, device="cuda")
                 e_b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.nvtx.range_push("timed_adjoint_backward_f32")
                 e_b.record(stream)
                 dJdg = gpe.gp_adjoint_backward(q.h, lam.data_ptr(), 1, dJdV.data_ptr(), 1)
                 e2.record(stream)
                 barrier()
+                torch.cuda.nvtx.range_pop()
                 if rep:
                     times.append((e0.elapsed_time(e1), e_b.elapsed_time(e2)))
             q.close()
@@ -577,11 +579,13 @@ def run_ours(args):
                         q.step_imag(cblock)
                     barrier()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.nvtx.range_push(f"timed_{name}_{prec}")
                     e0.record(stream)
                     for _ in range(args.steps):
                         q.step_imag(cblock)
                     e1.record(stream)
                     barrier()
+                    torch.cuda.nvtx.range_pop()
                     st = max_over_ranks(e0.elapsed_time(e1) / 1e3)
                     q.close()
                 npts = int(np.prod(cn))
@@ -610,6 +614,7 @@ def run_ours(args):
                     p.step_imag(args.inner)
                     p.observables()
                 barrier()
+                torch.cuda.nvtx.range_push(f"timed_real_{prec}")
                 for s in range(args.steps):
                     flush.fill_(float(s))
                     ev[s][0].record(stream)
@@ -617,6 +622,7 @@ def run_ours(args):
                     p.observables()
                     ev[s][1].record(stream)
                 barrier()
+                torch.cuda.nvtx.range_pop()
             ms = [a.elapsed_time(b) for a, b in ev]
             value, total_s = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
             p.close()
@@ -640,12 +646,14 @@ def run_ours(args):
                         for _ in range(args.warmup):
                             stepper(args.inner)
                         barrier()
+                        torch.cuda.nvtx.range_push(f"timed_{split}_{mode}_{prec}")
                         for s in range(args.steps):
                             flush.fill_(float(s))
                             ev[s][0].record(stream)
                             stepper(args.inner)
                             ev[s][1].record(stream)
                         barrier()
+                        torch.cuda.nvtx.range_pop()
                     ms = [a.elapsed_time(b) for a, b in ev]
                     value, _ = replica_throughput(args.steps * args.inner * np_, sum(ms) / 1e3, device="cuda")
                     stres[prec][f"{split}_{mode}"] = value

@@ -303,6 +303,25 @@ int upload_coefs_t(gp_handle* h) {
           std::copy(gf.begin(), gf.end(), ev.begin() + (size_t)(2 * si) * n);
           std::copy(gb.begin(), gb.end(), ev.begin() + (size_t)(2 * si + 1) * n);
           carry_tables(af, ab, n, sg, ev.data() + (size_t)4 * n + 512 * si, 0);
+          // how far a carry reaches above 2^-48 (the TMA x sweep truncates the rest)
+          const double tau = std::ldexp(1.0, -48);
+          const int nseg = n / sg;
+          int nj = 4;
+          for (int q = 0; q < nseg; ++q)
+            for (int j = 0; j < sg; ++j) {
+              const int need = std::max(std::abs(gf[q * sg + j]) > tau ? j + 1 : 0,
+                                        std::abs(gb[q * sg + j]) > tau ? sg - j : 0);
+              nj = std::max(nj, need);
+            }
+          h->even_nj[mode][si] = nj <= 4 ? 4 : (nj <= 8 ? 8 : sg);
+          const cd* P = ev.data() + (size_t)4 * n + 512 * si;
+          int depth = 1;
+          for (int a = 0; a < nseg; ++a)
+            for (int b = 0; b < nseg; ++b) {
+              if (b < a && std::abs(P[b * 16 + a - 1]) > tau) depth = std::max(depth, a - b);        // forward
+              if (b > a && std::abs(P[256 + b * 16 + a + 1]) > tau) depth = std::max(depth, b - a);  // backward
+            }
+          h->even_depth[mode][si] = depth;
         }
         if ((rc = upload_c2<T>(h, h->coef_even[mode], ev))) return rc;
       }

@@ -66,15 +66,25 @@ template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T>
 // modulus, the same at a point step after step (th changes slowly), so that
 // |phi| would drift linearly with the number of steps.  What remains is the
 // rounding of the final sums, which is unbiased.
-// s = sin th and cm1 = cos th - 1 (the coefficients of rot_neg).  FP32 with
-// |th| < 1/8: their Taylor series (s to th^7, cm1 to th^8; the first omitted
-// terms are below 1e-13 relative), else from the half angle.
+// The Taylor series of s = sin th and cm1 = cos th - 1 (s to th^7, cm1 to
+// th^8; for FP32 angles |th| < 1/8 the first omitted terms are below 1e-13
+// relative).
+__device__ __forceinline__ void rot_coefs_series(float th, float& s, float& cm1) {
+  const float t2 = th * th;
+  s = th * fmaf(t2, fmaf(t2, fmaf(t2, float(-1.0 / 5040), float(1.0 / 120)), float(-1.0 / 6)), 1.0f);
+  cm1 = t2 * fmaf(t2, fmaf(t2, fmaf(t2, float(1.0 / 40320), float(-1.0 / 720)), float(1.0 / 24)), -0.5f);
+}
+
+// s = sin th and cm1 = cos th - 1 (the coefficients of rot_neg): FP32 with
+// |th| < 1/8 their series (rot_coefs_series), else from the half angle.
 template <typename T> __device__ __forceinline__ void rot_coefs(T th, T& s, T& cm1) {
-  if (std::is_same<T, float>::value && fabs(th) < T(0.125)) {
-    const T t2 = th * th;
-    s = th * fma(t2, fma(t2, fma(t2, T(-1.0 / 5040), T(1.0 / 120)), T(-1.0 / 6)), T(1));
-    cm1 = t2 * fma(t2, fma(t2, fma(t2, T(1.0 / 40320), T(-1.0 / 720)), T(1.0 / 24)), T(-0.5));
-  } else {
+  if constexpr (std::is_same<T, float>::value) {
+    if (fabsf(th) < 0.125f) {
+      rot_coefs_series(th, s, cm1);
+      return;
+    }
+  }
+  {
     T sh, ch;
     sincos(T(0.5) * th, &sh, &ch);
     s = T(2) * (sh * ch);
@@ -82,10 +92,15 @@ template <typename T> __device__ __forceinline__ void rot_coefs(T th, T& s, T& c
   }
 }
 
+// p + ((c - 1) p + s (p.y, -p.x)) for given coefficients
+template <typename T> __device__ __forceinline__ c2_t<T> rot_apply(c2_t<T> p, T s, T cm1) {
+  return mk<T>(p.x + fma(cm1, p.x, s * p.y), p.y + fma(cm1, p.y, -(s * p.x)));
+}
+
 template <typename T> __device__ __forceinline__ c2_t<T> rot_neg(c2_t<T> p, T th) {
   T s, cm1;
   rot_coefs<T>(th, s, cm1);
-  return mk<T>(p.x + fma(cm1, p.x, s * p.y), p.y + fma(cm1, p.y, -(s * p.x)));
+  return rot_apply<T>(p, s, cm1);
 }
 
 // Geometry of the lines of one sweep.  Line L of axis 0 starts at L*nx

@@ -100,6 +100,10 @@ struct gp_handle {
   // aligned to even points (TMA x sweep): gf, gb for SEG 8 then 16 (n complex
   // values each), then the carry tables (512) for SEG 8 and 16
   void* coef_even[gpe::NUM_MODES] = {nullptr};
+  // per mode and even segment length (8, 16): points at a segment's start (end)
+  // that take a carry, and segments a carry crosses, above 2^-48 (gpe_tma.cuh)
+  int even_nj[gpe::NUM_MODES][2] = {{0}};
+  int even_depth[gpe::NUM_MODES][2] = {{0}};
   // circular / axial traps (geom 2): per mode, the rho axis' backward
   // coefficients, forward right-hand-side factors and stencil factors
   // (vab, vbf, vh of Sweep2Args; 3 n[0] complex values)

@@ -240,6 +240,7 @@ unsigned launch_tc(gp_handle* h, const Sweep2Args<float>& a, cudaStream_t s, boo
   T.limit_ns = h->tma_limit_ns;
   T.expect_extra = h->tma_expect_extra;
   T.err = h->dev_err;
+  T.depth = 0;  // (x sweep only)
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -275,11 +276,13 @@ unsigned launch_tx(gp_handle* h, Sweep2Args<float> a, int mode, cudaStream_t s, 
   const LineGeom& g = a.geom;
   const int nseg = g.n / SEG;
   const size_t smem = tmarow_smem(g.n);
-  auto kern = tmarow_kernel<IMAG, SEG>;
+  const int si = SEG == 8 ? 0 : 1;
+  // the points of a segment that take a carry (the host's bound on the tables)
+  const int nj = h->even_nj[mode][si];
+  auto kern = nj <= 4 ? tmarow_kernel<IMAG, SEG, 4> : (nj <= 8 ? tmarow_kernel<IMAG, SEG, 8> : tmarow_kernel<IMAG, SEG, SEG>);
   opt_in_smem((const void*)kern, smem);
   // the tables of segments aligned to even points
   const float2* ev = (const float2*)h->coef_even[mode];
-  const int si = SEG == 8 ? 0 : 1;
   a.gf = ev + (size_t)(2 * si) * g.n;
   a.gb = ev + (size_t)(2 * si + 1) * g.n;
   a.ptab = ev + (size_t)4 * g.n + 512 * si;
@@ -294,6 +297,7 @@ unsigned launch_tx(gp_handle* h, Sweep2Args<float> a, int mode, cudaStream_t s, 
   T.limit_ns = h->tma_limit_ns;
   T.expect_extra = h->tma_expect_extra;
   T.err = h->dev_err;
+  T.depth = std::max(1, h->even_depth[mode][si]);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

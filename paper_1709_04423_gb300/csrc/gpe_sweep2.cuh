@@ -211,9 +211,15 @@ __device__ __forceinline__ c2_t<T> phase_N(c2_t<T> p, c2_t<T> F, T dtg) {
 // the state to FP32 sets (an FP32 emulation with exact factors wanders between
 // 1e-8 and 8e-7 on a 64^3 version), and expf is the cheaper one and ends the
 // job within 1e-6.
+// th = dt (V + g |p|^2) as every FP32 phase forms it
+template <typename T>
+__device__ __forceinline__ T phase_angle(c2_t<T> p, T V, T dt, T g) {
+  return dt * (V + g * (p.x * p.x + p.y * p.y));
+}
+
 template <typename T, bool IMAG>
 __device__ __forceinline__ c2_t<T> phase_direct(c2_t<T> p, T V, T dt, T g) {
-  const T th = dt * (V + g * (p.x * p.x + p.y * p.y));
+  const T th = phase_angle<T>(p, V, dt, g);
   if (IMAG) {
     const T f = exp(-th);
     return mk<T>(f * p.x, f * p.y);
