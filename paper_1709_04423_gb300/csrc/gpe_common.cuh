@@ -66,20 +66,31 @@ template <typename T> __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T>
 // modulus, the same at a point step after step (th changes slowly), so that
 // |phi| would drift linearly with the number of steps.  What remains is the
 // rounding of the final sums, which is unbiased.
-// The Taylor series of s = sin th and cm1 = cos th - 1 (s to th^7, cm1 to
-// th^8; for FP32 angles |th| < 1/8 the first omitted terms are below 1e-13
-// relative).
+// The Taylor series of s = sin th and cm1 = cos th - 1: for FP32 angles
+// |th| < 1/8 s to th^7 and cm1 to th^8, for |th| < 1/32 s to th^5 and cm1 to
+// th^6; in both ranges the first omitted terms are below 2e-13 relative.
 __device__ __forceinline__ void rot_coefs_series(float th, float& s, float& cm1) {
   const float t2 = th * th;
   s = th * fmaf(t2, fmaf(t2, fmaf(t2, float(-1.0 / 5040), float(1.0 / 120)), float(-1.0 / 6)), 1.0f);
   cm1 = t2 * fmaf(t2, fmaf(t2, fmaf(t2, float(1.0 / 40320), float(-1.0 / 720)), float(1.0 / 24)), -0.5f);
 }
+__device__ __forceinline__ void rot_coefs_series_short(float th, float& s, float& cm1) {
+  const float t2 = th * th;
+  s = th * fmaf(t2, fmaf(t2, float(1.0 / 120), float(-1.0 / 6)), 1.0f);
+  cm1 = t2 * fmaf(t2, fmaf(t2, float(-1.0 / 720), float(1.0 / 24)), -0.5f);
+}
 
 // s = sin th and cm1 = cos th - 1 (the coefficients of rot_neg): FP32 with
-// |th| < 1/8 their series (rot_coefs_series), else from the half angle.
+// |th| < 1/8 their series (rot_coefs_series_short below 1/32), else from the
+// half angle.
 template <typename T> __device__ __forceinline__ void rot_coefs(T th, T& s, T& cm1) {
   if constexpr (std::is_same<T, float>::value) {
-    if (fabsf(th) < 0.125f) {
+    const float a = fabsf(th);
+    if (a < 0.03125f) {
+      rot_coefs_series_short(th, s, cm1);
+      return;
+    }
+    if (a < 0.125f) {
       rot_coefs_series(th, s, cm1);
       return;
     }

@@ -229,16 +229,26 @@ __device__ __forceinline__ void tma_carries_x(float2 (&z)[SEG], const float2* sc
   const float2* gb = sc + 2 * n;
   const float2* Pf = sc + 3 * n;
   const float2* Pb = Pf + 256;
+  // (k0 and NJ are even and the tables start on 16-byte boundaries: the
+  // coefficients of two points come in one 16-byte load)
+  auto pair = [](const float2* t, int k) { return *reinterpret_cast<const float4*>(t + k); };
   cf[s][lane] = z[SEG - 1];
   consumers_sync(32 * nseg);
   float2 Ein = make_float2(0.f, 0.f);
   for (int q = max(0, s - depth); q < s; ++q) Ein = cf_fma<float, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) z[j] = cf_fma<float, IMAG>(gf[k0 + j], Ein, z[j]);
+  for (int j = 0; j < NJ; j += 2) {
+    const float4 g2 = pair(gf, k0 + j);
+    z[j] = cf_fma<float, IMAG>(make_float2(g2.x, g2.y), Ein, z[j]);
+    z[j + 1] = cf_fma<float, IMAG>(make_float2(g2.z, g2.w), Ein, z[j + 1]);
+  }
   float2 next = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int j = SEG - 1; j >= 0; --j) {
-    next = cf_fma<float, IMAG>(al[k0 + j], next, z[j]);
+  for (int j = SEG - 2; j >= 0; j -= 2) {
+    const float4 a2 = pair(al, k0 + j);
+    next = cf_fma<float, IMAG>(make_float2(a2.z, a2.w), next, z[j + 1]);
+    z[j + 1] = next;
+    next = cf_fma<float, IMAG>(make_float2(a2.x, a2.y), next, z[j]);
     z[j] = next;
   }
   cb[s][lane] = z[0];
@@ -247,7 +257,11 @@ __device__ __forceinline__ void tma_carries_x(float2 (&z)[SEG], const float2* sc
   const int qe = min(nseg, s + 1 + depth);
   for (int q = s + 1; q < qe; ++q) Zin = cf_fma<float, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
 #pragma unroll
-  for (int j = SEG - NJ; j < SEG; ++j) z[j] = cf_fma<float, IMAG>(gb[k0 + j], Zin, z[j]);
+  for (int j = SEG - NJ; j < SEG; j += 2) {
+    const float4 g2 = pair(gb, k0 + j);
+    z[j] = cf_fma<float, IMAG>(make_float2(g2.x, g2.y), Zin, z[j]);
+    z[j + 1] = cf_fma<float, IMAG>(make_float2(g2.z, g2.w), Zin, z[j + 1]);
+  }
 }
 
 // Solve of one staged tile in place (every thread of the block); returns this
@@ -564,28 +578,49 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
     const long gbase = (long)L * G.nx;
     // N on every point (the neighbours outside the line are zeros and stay
     // zeros; their potential index is clamped into the line)
+    // the potential at point j of p (the neighbours' indices clamped into the
+    // line); with the harmonic trap four points' vx come in one 16-byte load
+    auto vpt = [&](int j, const float4& v4) -> float {
+      if (A.V) return line_ok ? A.V[gbase + min(max(k0 - 1 + j, 0), n - 1)] : 0.f;
+      if (j == 0) return sv[max(k0 - 1, 0)] + vline;
+      if (j == SEG + 1) return sv[min(k0 + SEG, n - 1)] + vline;
+      const int q = (j - 1) & 3;
+      return (q == 0 ? v4.x : q == 1 ? v4.y : q == 2 ? v4.z : v4.w) + vline;
+    };
+    auto v4at = [&](int j) -> float4 {  // vx of points k0 + 4((j-1)/4) .. +3
+      return (A.V || j == 0 || j == SEG + 1) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                             : *reinterpret_cast<const float4*>(sv + k0 + ((j - 1) & ~3));
+    };
     if (IMAG) {
+      float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < SEG + 2; ++j) {
-        const int k = min(max(k0 - 1 + j, 0), n - 1);
+        if (j >= 1 && j <= SEG && ((j - 1) & 3) == 0) v4 = v4at(j);
         const float2 w = make_float2(p[j].x * scl, p[j].y * scl);  // the pending renormalisation
-        const float Vk = A.V ? (line_ok ? A.V[gbase + k] : 0.f) : sv[k] + vline;
-        p[j] = phase_direct<float, true>(w, Vk, A.dt, A.g);
+        p[j] = phase_direct<float, true>(w, vpt(j, v4), A.dt, A.g);
       }
     } else {
-      // real time: every angle first; when all of the warp's are below 1/8
-      // (the series range of rot_coefs) one branch-free pass rotates them
-      // all, else rot_neg per point -- the same results either way
+      // real time: every angle first; when all of the warp's are below 1/32
+      // (1/8) one branch-free pass rotates them all with the short (long)
+      // series of rot_coefs, else rot_neg per point
       float th[SEG + 2];
-      bool small = true;
+      bool small = true, tiny = true;
+      float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < SEG + 2; ++j) {
-        const int k = min(max(k0 - 1 + j, 0), n - 1);
-        const float Vk = A.V ? (line_ok ? A.V[gbase + k] : 0.f) : sv[k] + vline;
-        th[j] = phase_angle<float>(p[j], Vk, A.dt, A.g);
+        if (j >= 1 && j <= SEG && ((j - 1) & 3) == 0) v4 = v4at(j);
+        th[j] = phase_angle<float>(p[j], vpt(j, v4), A.dt, A.g);
         small = small && fabsf(th[j]) < 0.125f;
+        tiny = tiny && fabsf(th[j]) < 0.03125f;
       }
-      if (__all_sync(0xffffffffu, small)) {
+      if (__all_sync(0xffffffffu, tiny)) {
+#pragma unroll
+        for (int j = 0; j < SEG + 2; ++j) {
+          float sn, cm1;
+          rot_coefs_series_short(th[j], sn, cm1);
+          p[j] = rot_apply<float>(p[j], sn, cm1);
+        }
+      } else if (__all_sync(0xffffffffu, small)) {
 #pragma unroll
         for (int j = 0; j < SEG + 2; ++j) {
           float sn, cm1;
@@ -604,9 +639,10 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
       float2 prev = make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < SEG; ++j) {
+        const float4 a2 = *reinterpret_cast<const float4*>(sc + k0 + (j & ~1));  // alpha of two points
         const float2 t2 = make_float2(prev.x + neg_lap(p[j].x, p[j + 2].x, p[j + 1].x),
                                       prev.y + neg_lap(p[j].y, p[j + 2].y, p[j + 1].y));
-        prev = cf_mul<float, IMAG>(sc[k0 + j], t2);
+        prev = cf_mul<float, IMAG>((j & 1) ? make_float2(a2.z, a2.w) : make_float2(a2.x, a2.y), t2);
         z[j] = prev;
       }
     }
