@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", type=int, default=100, help="time steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mu-check", action="store_true")
+    ap.add_argument("--no-mu-check", action="store_true",
+                    help="skip the untimed accuracy runs (the job's mu, the batch's 400 steps, the Strang study)")
     ap.add_argument("--quench-imag-steps", type=int, default=1500)
     ap.add_argument("--forms", default="f64,f32,df64",
                     help="precision forms to time (the line needs f32; f64 for ratios and errors)")
@@ -571,9 +572,10 @@ def run_ours(args):
             for prec in forms_sel:
                 with torch.cuda.stream(stream):
                     q = gpe.Propagator(cd, cn, cdx, cdt, cnkl, 100.0, precision=prec, stream=stream, **kw)
-                    q.set_state(cphi)
-                    q.step_imag(cmu_steps)
-                    cmu[prec] = q.observables()
+                    if not args.no_mu_check:   # mu after cmu_steps (untimed)
+                        q.set_state(cphi)
+                        q.step_imag(cmu_steps)
+                        cmu[prec] = q.observables()
                     q.set_state(cphi)
                     for _ in range(args.warmup):
                         q.step_imag(cblock)
@@ -590,7 +592,8 @@ def run_ours(args):
                     q.close()
                 npts = int(np.prod(cn))
                 cres[prec] = {"value": world * args.steps * cblock * npts / st,
-                              "us_per_step": 1e6 * st / (args.steps * cblock), "mu": cmu[prec]["mu"]}
+                              "us_per_step": 1e6 * st / (args.steps * cblock),
+                              "mu": cmu[prec]["mu"] if prec in cmu else None}
             if "f64" in cmu:
                 for prec in cres:
                     cres[prec]["mu_diff_vs_f64"] = abs(cmu[prec]["mu"] - cmu["f64"]["mu"])
@@ -605,9 +608,11 @@ def run_ours(args):
             p.set_real_state(True)
             p.autotune(imag=True, cache=False)
             with torch.cuda.stream(stream):
-                p.step_imag(w["job_steps"])
-                rmu = p.observables()["mu"]
-                p.set_state(torch.tensor(phi0, device="cuda"))
+                rmu = None
+                if not args.no_mu_check:   # mu after the job (untimed)
+                    p.step_imag(w["job_steps"])
+                    rmu = p.observables()["mu"]
+                    p.set_state(torch.tensor(phi0, device="cuda"))
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(args.steps)]
                 for _ in range(args.warmup):
@@ -672,10 +677,11 @@ def run_ours(args):
             stream.synchronize()
             return out
         sdts = [2e-3, 1e-3, 5e-4]
-        fine = run_rt(sdts[-1] / 8, "strang")
-        for split in ("lie", "strang"):
-            e_ = [float(torch.linalg.norm(run_rt(dt, split) - fine) / torch.linalg.norm(fine)) for dt in sdts]
-            stres[f"{split}_order"] = [float(np.log2(e_[i] / e_[i + 1])) for i in range(len(sdts) - 1)]
+        if not args.no_mu_check:   # the accuracy study (untimed)
+            fine = run_rt(sdts[-1] / 8, "strang")
+            for split in ("lie", "strang"):
+                e_ = [float(torch.linalg.norm(run_rt(dt, split) - fine) / torch.linalg.norm(fine)) for dt in sdts]
+                stres[f"{split}_order"] = [float(np.log2(e_[i] / e_[i + 1])) for i in range(len(sdts) - 1)]
         R["strang"] = stres
 
     if only is not None:

@@ -394,7 +394,7 @@ bool tma_x_fits(const gp_handle* h, int seg) {
   if ((nx & 15) || nx > 256 || (seg != 8 && seg != 16) || nx / seg > 16) return false;
   const long coef = (3L * nx + 512) * 8 + 4L * nx;
   const long smem = (coef + 1023) / 1024 * 1024 + 1024 + 3L * 32 * nx * 8;
-  return smem + 9 * 1024 <= 227L * 1024;
+  return smem + 17 * 1024 <= 227L * 1024;  // + the static carries, edge points and barriers
 }
 
 int read_dev_err(gp_handle* h, const char* who) {

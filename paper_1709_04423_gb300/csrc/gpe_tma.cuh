@@ -452,9 +452,10 @@ __global__ void __launch_bounds__(544, 1) tmacol_kernel(const __grid_constant__ 
 // coefficients are zero there, and the tables -- gf, gb and the carry tables
 // -- are those of this segmentation), so with nx a multiple of 16 and SEG 8
 // or 16 every segment is full and the solve has no bounds tests.  Each thread
-// applies the pending factor and N to its own points and to the point on
-// either side of its segment (the same arithmetic its neighbours apply), so
-// no pass over the tile and no barrier precede the solve.
+// applies the pending factor and N to its own points in registers (no pass
+// over the tile) and takes the point on either side of its segment, after N,
+// from the neighbouring warps through two small shared arrays (one barrier).
+// (Recomputing those two points instead, with no barrier, was 4 % slower.)
 __device__ __forceinline__ unsigned swz_off(int l, int k) {
   // byte offset of point k of line l in a tile of 16-point chunks (k even: the pair k, k + 1)
   return (unsigned)(k >> 4) * 4096u + (unsigned)l * 128u + ((unsigned)(((k & 15) >> 1) ^ (l & 7)) << 4) +
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
   extern __shared__ __align__(1024) unsigned char tma_smem_raw[];
   __shared__ __align__(8) unsigned long long full[kTmaStages], empty[kTmaStages];
   __shared__ float2 cf[16][33], cb[16][33];
+  __shared__ float2 edge_l[16][32], edge_r[16][32];  // each segment's first and last point after N
   __shared__ float scl_smem;
   __shared__ int abort_flag;
   const LineGeom& G = A.geom;
@@ -561,41 +563,31 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
       }
       vline = A.vy[jr] + A.vz[kq];
     }
-    // the points of this segment plus one on each side
+    // p[1..SEG]: the points of this segment; p[0], p[SEG + 1]: the points on
+    // either side, after N, from the neighbouring segments' warps
     float2 p[SEG + 2];
-    {
-      const float4 lft = s > 0 ? ld2(k0 - 2) : make_float4(0, 0, 0, 0);
-      p[0] = make_float2(lft.z, lft.w);
 #pragma unroll
-      for (int j = 0; j < SEG; j += 2) {
-        const float4 v = ld2(k0 + j);
-        p[1 + j] = make_float2(v.x, v.y);
-        p[2 + j] = make_float2(v.z, v.w);
-      }
-      const float4 rgt = s < nseg - 1 ? ld2(k0 + SEG) : make_float4(0, 0, 0, 0);
-      p[SEG + 1] = make_float2(rgt.x, rgt.y);
+    for (int j = 0; j < SEG; j += 2) {
+      const float4 v = ld2(k0 + j);
+      p[1 + j] = make_float2(v.x, v.y);
+      p[2 + j] = make_float2(v.z, v.w);
     }
     const long gbase = (long)L * G.nx;
-    // N on every point (the neighbours outside the line are zeros and stay
-    // zeros; their potential index is clamped into the line)
-    // the potential at point j of p (the neighbours' indices clamped into the
-    // line); with the harmonic trap four points' vx come in one 16-byte load
+    // the potential at point j of p; with the harmonic trap the vx of four
+    // points come in one 16-byte load
     auto vpt = [&](int j, const float4& v4) -> float {
-      if (A.V) return line_ok ? A.V[gbase + min(max(k0 - 1 + j, 0), n - 1)] : 0.f;
-      if (j == 0) return sv[max(k0 - 1, 0)] + vline;
-      if (j == SEG + 1) return sv[min(k0 + SEG, n - 1)] + vline;
+      if (A.V) return line_ok ? A.V[gbase + k0 - 1 + j] : 0.f;
       const int q = (j - 1) & 3;
       return (q == 0 ? v4.x : q == 1 ? v4.y : q == 2 ? v4.z : v4.w) + vline;
     };
-    auto v4at = [&](int j) -> float4 {  // vx of points k0 + 4((j-1)/4) .. +3
-      return (A.V || j == 0 || j == SEG + 1) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                             : *reinterpret_cast<const float4*>(sv + k0 + ((j - 1) & ~3));
+    auto v4at = [&](int j) -> float4 {  // vx of points k0 + (j - 1) .. + 3, j - 1 a multiple of 4
+      return A.V ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(sv + k0 + j - 1);
     };
     if (IMAG) {
       float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < SEG + 2; ++j) {
-        if (j >= 1 && j <= SEG && ((j - 1) & 3) == 0) v4 = v4at(j);
+      for (int j = 1; j <= SEG; ++j) {
+        if (((j - 1) & 3) == 0) v4 = v4at(j);
         const float2 w = make_float2(p[j].x * scl, p[j].y * scl);  // the pending renormalisation
         p[j] = phase_direct<float, true>(w, vpt(j, v4), A.dt, A.g);
       }
@@ -603,37 +595,44 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
       // real time: every angle first; when all of the warp's are below 1/32
       // (1/8) one branch-free pass rotates them all with the short (long)
       // series of rot_coefs, else rot_neg per point
-      float th[SEG + 2];
+      float th[SEG + 1];
       bool small = true, tiny = true;
       float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < SEG + 2; ++j) {
-        if (j >= 1 && j <= SEG && ((j - 1) & 3) == 0) v4 = v4at(j);
+      for (int j = 1; j <= SEG; ++j) {
+        if (((j - 1) & 3) == 0) v4 = v4at(j);
         th[j] = phase_angle<float>(p[j], vpt(j, v4), A.dt, A.g);
         small = small && fabsf(th[j]) < 0.125f;
         tiny = tiny && fabsf(th[j]) < 0.03125f;
       }
       if (__all_sync(0xffffffffu, tiny)) {
 #pragma unroll
-        for (int j = 0; j < SEG + 2; ++j) {
+        for (int j = 1; j <= SEG; ++j) {
           float sn, cm1;
           rot_coefs_series_short(th[j], sn, cm1);
           p[j] = rot_apply<float>(p[j], sn, cm1);
         }
       } else if (__all_sync(0xffffffffu, small)) {
 #pragma unroll
-        for (int j = 0; j < SEG + 2; ++j) {
+        for (int j = 1; j <= SEG; ++j) {
           float sn, cm1;
           rot_coefs_series(th[j], sn, cm1);
           p[j] = rot_apply<float>(p[j], sn, cm1);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < SEG + 2; ++j) p[j] = rot_neg<float>(p[j], th[j]);
+        for (int j = 1; j <= SEG; ++j) p[j] = rot_neg<float>(p[j], th[j]);
       }
     }
     if (s == 0) p[1] = make_float2(0.f, 0.f);  // the end points are held at zero
     if (s == nseg - 1) p[SEG] = make_float2(0.f, 0.f);
+    // the segment's end points to the neighbours (every warp is past the
+    // previous tile's reads of these arrays: the vote above is a barrier)
+    edge_l[s][lane] = p[1];
+    edge_r[s][lane] = p[SEG];
+    consumers_sync(32 * nseg);
+    p[0] = s > 0 ? edge_r[s - 1][lane] : make_float2(0.f, 0.f);
+    p[SEG + 1] = s < nseg - 1 ? edge_l[s + 1][lane] : make_float2(0.f, 0.f);
     float2 z[SEG];
     {
       float2 prev = make_float2(0.f, 0.f);
