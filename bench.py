@@ -48,7 +48,9 @@ WORKLOAD = {
     "dim": 3, "n": [128, 128, 128], "dx": [0.1, 0.1, 0.1], "dt": 1e-3,
     "nkl": [1.0, 1.4, 1.8], "g": 50.0, "seed": 1710, "job_steps": 5000,
 }
-QUENCH = "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, ground state at g=20 then g=40"
+QUENCH = "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, ground state at g=20 then g=40, 10000 steps"
+QUENCH_STEPS = 10000
+BATCH_STEPS = 4000
 METRIC = "3d split-step CN grid-point-steps/s: FP32/batched vs FP64 at fixed mu error"
 UNIT = "grid-point-steps/s"
 OBS = ("norm", "energy", "mu", "rms_x", "rms_y", "rms_z", "rms_r")
@@ -436,6 +438,10 @@ def run_ours(args):
                 torch.cuda.nvtx.range_pop()
                 qt = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3)
                 kms = q.time_sweeps_graph(False, 16)
+                done = (qwarm + qsteps) * args.inner
+                if not args.no_mu_check and done < QUENCH_STEPS:   # the rest of the 10000-step run, untimed
+                    q.step_real(QUENCH_STEPS - done)
+                    done = QUENCH_STEPS
                 ob1 = q.observables()
                 shp = q.shapes()
                 q.close()
@@ -447,6 +453,7 @@ def run_ours(args):
                             "step_frac_hbm": 6 * esize * qnp / (step_us * 1e-6) / 1e9 / hbm,
                             "energy_drift_rel": abs(ob1["energy"] / ob0["energy"] - 1),
                             "norm_drift_rel": abs(ob1["norm"] / ob0["norm"] - 1), "obs_start": ob0, "obs_end": ob1,
+                            "steps_at_end": done,
                             "rms_r_t": [float(r_[0, 6]) for r_ in recs], "shapes": shp}
             if prec == "f64":
                 quench[prec]["alu"] = fp64_alu(kms, "sweep{}_f64_real_256", qnp)
@@ -472,7 +479,7 @@ def run_ours(args):
                     bres["autotune_choice"] = "one_launch" if bb.mode() == 1 else "class"
                 bb.set_mode(mode)
                 if not args.no_mu_check and mode == 0:
-                    bb.step_real(400)
+                    bb.step_real(BATCH_STEPS)
                     bmu[prec] = bb.observables()
                     for i, ph in enumerate(bphi):
                         bb.set_state(i, ph)
@@ -504,7 +511,7 @@ def run_ours(args):
         if bmu:
             worst = {k: max(abs(a[k] - b[k]) for a, b in zip(bmu["f32"], bmu["f64"])) for k in OBS}
             run_w = max(range(64), key=lambda i: abs(bmu["f32"][i]["mu"] - bmu["f64"][i]["mu"]))
-            R["batched"]["f32_err_vs_f64_400_steps"] = {"worst_per_observable": worst, "worst_mu_run": run_w,
+            R["batched"]["f32_err_vs_f64_4000_steps"] = {"worst_per_observable": worst, "worst_mu_run": run_w,
                                                          "mu_f64_of_that_run": bmu["f64"][run_w]["mu"]}
 
     # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V and g
@@ -752,6 +759,9 @@ def run_ours(args):
         if prec == "f32":
             out.update({"us_step": r["us_per_time_step"], "sweep_us": r["sweep_us"],
                         "dE_rel": r["energy_drift_rel"], "dnorm_rel": r["norm_drift_rel"]})
+            # DRAM bytes per sweep launch (committed ncu capture) over one read + one write of the state
+            trs = [profile_record("traffic.json", f"sweep_axis{d}_f32_real_256cube") for d in range(3)]
+            out["sweep_dram_over_algo"] = [t_["bytes_per_launch"] / (2 * 8 * 256 ** 3) if t_ else None for t_ in trs]
         if r.get("alu"):
             out["sweep_frac_fp64_fma"] = [a["frac"] if a else None for a in r["alu"]]
         return out
@@ -779,7 +789,7 @@ def run_ours(args):
                            if "f32" in q and "f64" in q else None,
                            "quench256_end": errs(q["f32"]["obs_end"], q["f64"]["obs_end"], LINE_OBS)
                            if "f32" in q and "f64" in q else None,
-                           "batched_worst_run_400": {k: v for k, v in bat.get("f32_err_vs_f64_400_steps", {})
+                           "batched_worst_run_4000": {k: v for k, v in bat.get("f32_err_vs_f64_4000_steps", {})
                                                      .get("worst_per_observable", {}).items() if k in LINE_OBS}},
         "df64_mu_err_vs_f64": {"job_end_5000": (form_err("df64", "job_end") or {}).get("mu"),
                                "converged_20000": (form_err("df64", "converged_20000") or {}).get("mu")},
