@@ -48,7 +48,7 @@ WORKLOAD = {
     "dim": 3, "n": [128, 128, 128], "dx": [0.1, 0.1, 0.1], "dt": 1e-3,
     "nkl": [1.0, 1.4, 1.8], "g": 50.0, "seed": 1710, "job_steps": 5000,
 }
-QUENCH = "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, ground state at g=20 then g=40, 10000 steps"
+QUENCH = "3d real-time quench, 256^3, dx=0.08, dt=2e-4, isotropic trap, g=20 ground state -> g=40, 10000 steps"
 QUENCH_STEPS = 10000
 BATCH_STEPS = 4000
 METRIC = "3d split-step CN grid-point-steps/s: FP32/batched vs FP64 at fixed mu error"
@@ -739,7 +739,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": tr["bytes_per_launch"] if tr else None, "algorithmic_bytes": algo,
             "kernel": key, "peak_source": peak_note,
-            "regime": "L2-resident state (16.8 MB): latency-bound; HBM roofline at 256^3 in hbm256",
+            "regime": "L2-resident 16.8 MB state, latency-bound; HBM roofline: hbm256",
             "kernel_ms_in_graph": kms, "kernel_sum_over_time_step": sum(kms) / step_ms}
     mu = R["headline_mu"]
 
