@@ -469,7 +469,8 @@ def run_ours(args):
         bpts = sum(a * b for a, b in bsizes)
         bphi = [torch.tensor(inputs.gaussian_state(2, list(sz), [0.1, 0.1], list(k)), device="cuda")
                 for sz, k in zip(bsizes, bnk)]
-        for key, prec, mode in (("f64", "f64", 0), ("f32_class", "f32", 0), ("f32_one_launch", "f32", 1)):
+        for key, prec, mode in (("f64", "f64", 0), ("f32_class", "f32", 0), ("f32_one_launch", "f32", 1),
+                                ("df64", "df64", 0)):
             with torch.cuda.stream(stream):
                 bb = gpe.Batch(bsizes, [(0.1, 0.1)] * 64, 5e-4, bnk, bg, precision=prec, stream=stream)
                 for i, ph in enumerate(bphi):
@@ -513,6 +514,10 @@ def run_ours(args):
             run_w = max(range(64), key=lambda i: abs(bmu["f32"][i]["mu"] - bmu["f64"][i]["mu"]))
             R["batched"]["f32_err_vs_f64_4000_steps"] = {"worst_per_observable": worst, "worst_mu_run": run_w,
                                                          "mu_f64_of_that_run": bmu["f64"][run_w]["mu"]}
+            if "df64" in bmu:
+                R["batched"]["df64_err_vs_f64_4000_steps"] = {
+                    "worst_per_observable": {k: max(abs(a[k] - b[k]) for a, b in zip(bmu["df64"], bmu["f64"]))
+                                             for k in OBS}}
 
     # ---- differentiation form: gradient of |<phi_target|phi(T)>|^2 w.r.t. V and g
     ares = {}
@@ -777,7 +782,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state+sweeps, f64 reductions",
         "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
         "config": line_config(world),
-        "timing": {"inner_steps_per_step": args.inner, "l2": "flushed (256 MB write) before every timed step"},
+        "timing": {"inner_steps_per_step": args.inner, "l2": "flushed before every timed step"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -792,13 +797,16 @@ def run_ours(args):
                            "batched_worst_run_4000": {k: v for k, v in bat.get("f32_err_vs_f64_4000_steps", {})
                                                      .get("worst_per_observable", {}).items() if k in LINE_OBS}},
         "df64_mu_err_vs_f64": {"job_end_5000": (form_err("df64", "job_end") or {}).get("mu"),
-                               "converged_20000": (form_err("df64", "converged_20000") or {}).get("mu")},
+                               "converged_20000": (form_err("df64", "converged_20000") or {}).get("mu"),
+                               "batched_worst_run_4000": bat.get("df64_err_vs_f64_4000_steps", {})
+                               .get("worst_per_observable", {}).get("mu")},
         "hbm256": {"workload": QUENCH, "f32": qform("f32"), "f64": qform("f64"), "df64": qform("df64")},
         "speedups": {"f32_vs_f64_128": ratio(hv.get("f32"), hv.get("f64")),
                      "df64_vs_f64_128": ratio(hv.get("df64"), hv.get("f64")),
                      "f32_vs_f64_256": ratio(qv.get("f32"), qv.get("f64")),
                      "df64_vs_f64_256": ratio(qv.get("df64"), qv.get("f64")),
-                     "batched_f32_vs_f64": ratio(bat.get("f32", {}).get("value"), bat.get("f64", {}).get("value"))},
+                     "batched_f32_vs_f64": ratio(bat.get("f32", {}).get("value"), bat.get("f64", {}).get("value")),
+                     "batched_df64_vs_f64": ratio(bat.get("df64", {}).get("value"), bat.get("f64", {}).get("value"))},
         "values": {"f64_128": hv.get("f64"), "df64_128": hv.get("df64"),
                    "batched_f32": bat.get("f32", {}).get("value"), "batched_f64": bat.get("f64", {}).get("value"),
                    "batched_f32_class": bat.get("f32_class", {}).get("value"),

@@ -287,6 +287,9 @@ int gp_adjoint_backward(gp_handle* h, const void* lambda_T, int lambda_on_device
  * split-step Crank-Nicolson step with the same discretisation as gp_step_real
  * (a run in a batch gives the same result as the same run in its own handle).
  * Runs are stored back to back: run r starts at element gp_batch_offset(r).
+ * Precisions: GP_F64, GP_F32 (FP64 reductions) and GP_DF64 (double-float
+ * state, FP64-class results on the FP32 pipes; its observables are those of
+ * the states rounded to complex128).
  * Limits: 1 <= nruns <= 65536, 3 <= n <= 514 per axis, < 2^31 points in all. */
 typedef struct gp_batch gp_batch;
 
@@ -294,7 +297,9 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
                   const double* g, gp_precision prec, void* stream);
 
 /* Copies run `run`'s state in or out (run = -1: all runs, back to back), in
- * the batch's precision; host copies synchronise the stream. */
+ * the batch's precision -- complex128 for GP_DF64, split into double-floats
+ * on the way in and rounded on the way out; host copies synchronise the
+ * stream. */
 int gp_batch_set_state(gp_batch* b, int run, const void* psi, int on_device);
 int gp_batch_get_state(gp_batch* b, int run, void* psi, int on_device);
 

@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "gpe_internal.h"
@@ -40,6 +41,7 @@ struct BatchRun {
   T dtg;                                                   // dt g (FP64)
   const T* vx; const T* vy; const T* vz0;                  // nu^2 x^2/2, kappa^2 y^2/2, a single 0 (FP32)
   T g;
+  const tf3c* tfx; const tf3c* tfy;  // the factors fx, fy as exact triple-floats (double-float state)
 };
 
 struct BatchItem {
@@ -77,6 +79,8 @@ __global__ void __launch_bounds__(512) batch_x_kernel(const BatchRun<T>* __restr
   A.vz = R.vz0;
   A.dt = dt;
   A.g = R.g;
+  A.tfx = R.tfx;
+  A.tfyz = R.tfy;  // fz = 1 in 2d: the line factor is fy
   tsweep_body<T, false, true, false, SEG>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
 }
 
@@ -110,6 +114,8 @@ __global__ void __launch_bounds__(128) batch_xw_kernel(const BatchRun<T>* __rest
   A.vz = R.vz0;
   A.dt = dt;
   A.g = R.g;
+  A.tfx = R.tfx;
+  A.tfyz = R.tfy;
   xsweep_body<T, false, true, false, SEG>(A, it.L0 + (threadIdx.x >> 5), red_smem);
 }
 
@@ -331,6 +337,7 @@ struct gp_batch {
   int nobs_items = 0;
   double* obs_out = nullptr;
   double* obs_host = nullptr;
+  void* stage = nullptr;  // double-float state: the states as complex128 (exchange, observables)
   cudaGraphExec_t graph = nullptr;
   // the one-launch form (FP32): items of one step, per-run item counts and
   // segment lengths, the claim counter and per-run completion counters
@@ -440,8 +447,26 @@ int build_tables(gp_batch* b) {
         pbuf[voff[2 * r + a] + i] = (T)v;
       }
     }
-  void *cdev = nullptr, *vdev = nullptr, *pdev = nullptr;
+  void *cdev = nullptr, *vdev = nullptr, *pdev = nullptr, *tdev = nullptr;
   int rc;
+  if constexpr (std::is_same<T, df64>::value) {
+    // the double-float state takes the FP64 factors as exact triple-floats,
+    // split from the same doubles as the single-grid handle's
+    std::vector<tf3c> tbuf(vtot);
+    for (int r = 0; r < R; ++r)
+      for (int a = 0; a < 2; ++a) {
+        const int n = b->n[2 * r + a];
+        const double h = b->dx[2 * r + a], w = b->nk[2 * r + a];
+        for (int i = 0; i < n; ++i) {
+          const double x = axis_coord(0, a, n, h, i);
+          const double v = 0.5 * w * w * x * x;
+          tf3c& f = tbuf[voff[2 * r + a] + i];
+          tf_split(std::cos(b->dt * v), f.re);
+          tf_split(-std::sin(b->dt * v), f.im);
+        }
+      }
+    if ((rc = b_alloc(b, &tdev, tbuf.size() * sizeof(tf3c))) || (rc = b_upload<tf3c>(b, tdev, tbuf))) return rc;
+  }
   if ((rc = b_alloc(b, &pdev, pbuf.size() * sizeof(T)))) return rc;
   if ((rc = b_upload<T>(b, pdev, pbuf))) return rc;
   if ((rc = b_alloc(b, &cdev, cbuf.size() * sizeof(T)))) return rc;
@@ -466,6 +491,8 @@ int build_tables(gp_batch* b) {
     q.vy = (const T*)pdev + voff[2 * r + 1];
     q.vz0 = (const T*)pdev + vtot;
     q.g = (T)b->g[r];
+    q.tfx = tdev ? (const tf3c*)tdev + voff[2 * r] : nullptr;
+    q.tfy = tdev ? (const tf3c*)tdev + voff[2 * r + 1] : nullptr;
   }
   if ((rc = b_alloc(b, &b->runs_d, R * sizeof(BatchRun<T>)))) return rc;
   GP_CUDA(cudaMemcpyAsync(b->runs_d, runs.data(), R * sizeof(BatchRun<T>), cudaMemcpyHostToDevice, b->work));
@@ -684,7 +711,7 @@ int build_obs(gp_batch* b) {
   for (int r = 0; r < b->nruns; ++r) {
     ObsArgs<T>& a = runs[r];
     std::memset(&a, 0, sizeof(a));
-    a.psi = (const c2_t<T>*)b->psi + b->off[r];
+    a.psi = (const c2_t<T>*)(b->stage ? b->stage : b->psi) + b->off[r];  // double-float: its complex128 copy
     a.dim = 2;
     a.nx = b->n[2 * r];
     a.ny = b->n[2 * r + 1];
@@ -763,7 +790,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   if (!out || !n || !dx || !nkl || !g) return fail(GP_ERR_INVALID, "gp_batch_init: NULL argument");
   *out = nullptr;
   if (nruns < 1 || nruns > 65536) return fail(GP_ERR_INVALID, "gp_batch_init: nruns must be in [1, 65536]");
-  if (prec != GP_F64 && prec != GP_F32) return fail(GP_ERR_INVALID, "gp_batch_init: unknown precision");
+  if (prec != GP_F64 && prec != GP_F32 && prec != GP_DF64) return fail(GP_ERR_INVALID, "gp_batch_init: unknown precision");
   if (!std::isfinite(dt) || dt == 0.0) return fail(GP_ERR_INVALID, "gp_batch_init: dt must be finite and nonzero");
   long total = 0;
   for (int r = 0; r < nruns; ++r) {
@@ -781,7 +808,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   gp_batch* b = new gp_batch();
   b->nruns = nruns;
   b->prec = prec;
-  b->esize = prec == GP_F64 ? sizeof(double2) : sizeof(float2);
+  b->esize = prec == GP_F64 ? sizeof(double2) : prec == GP_DF64 ? sizeof(df64x2) : sizeof(float2);
   b->dt = dt;
   b->n.assign(n, n + 2 * nruns);
   b->dx.assign(dx, dx + 2 * nruns);
@@ -805,8 +832,10 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   }
   int rc;
   if ((rc = b_alloc(b, &b->psi, (size_t)acc * b->esize))) return bail(rc);
-  rc = prec == GP_F64 ? build_tables<double>(b) : build_tables<float>(b);
+  if (prec == GP_DF64 && (rc = b_alloc(b, &b->stage, (size_t)acc * sizeof(double2)))) return bail(rc);
+  rc = prec == GP_F64 ? build_tables<double>(b) : prec == GP_DF64 ? build_tables<df64>(b) : build_tables<float>(b);
   if (rc) return bail(rc);
+  const bool obs64 = prec != GP_F32;  // the observables' arithmetic (double-float: on the complex128 copy)
   // tables of the observables, per run and axis, in their arithmetic type
   b->vd.resize(2 * nruns);
   b->cdx.resize(2 * nruns);
@@ -825,10 +854,10 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
         wt[i] = c;  // exact; the factor h/3 per axis is applied to the FP64 totals
       }
       void *pv, *pc, *pw;
-      const size_t rs = prec == GP_F64 ? sizeof(double) : sizeof(float);
+      const size_t rs = obs64 ? sizeof(double) : sizeof(float);
       auto up = [&](void* dst, const std::vector<double>& src) {
-        return prec == GP_F64 ? b_upload<double>(b, dst, src)
-                              : b_upload<float>(b, dst, std::vector<float>(src.begin(), src.end()));
+        return obs64 ? b_upload<double>(b, dst, src)
+                     : b_upload<float>(b, dst, std::vector<float>(src.begin(), src.end()));
       };
       if ((rc = b_alloc(b, &pv, na * rs)) || (rc = up(pv, v))) return bail(rc);
       if ((rc = b_alloc(b, &pc, na * rs)) || (rc = up(pc, x))) return bail(rc);
@@ -840,8 +869,8 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
   {
     const std::vector<double> zw = {0.0, 1.0};
     if ((rc = b_alloc(b, &b->ztab, 2 * sizeof(double)))) return bail(rc);
-    if ((rc = prec == GP_F64 ? b_upload<double>(b, b->ztab, zw)
-                             : b_upload<float>(b, b->ztab, std::vector<float>(zw.begin(), zw.end()))))
+    if ((rc = obs64 ? b_upload<double>(b, b->ztab, zw)
+                    : b_upload<float>(b, b->ztab, std::vector<float>(zw.begin(), zw.end()))))
       return bail(rc);
   }
   if ((rc = b_alloc(b, (void**)&b->partials, 152L * 16 * 8 * sizeof(double)))) return bail(rc);
@@ -853,7 +882,7 @@ int gp_batch_init(gp_batch** out, int nruns, const int* n, const double* dx, dou
     b->limit_ns = (unsigned long long)(ms > 0 ? ms : 1000) * 1000000ull;
   }
   if ((rc = b_alloc(b, (void**)&b->obs_out, (8L * nruns + 8) * sizeof(double)))) return bail(rc);
-  if ((rc = prec == GP_F64 ? build_obs<double>(b) : build_obs<float>(b))) return bail(rc);
+  if ((rc = obs64 ? build_obs<double>(b) : build_obs<float>(b))) return bail(rc);
   *out = b;
   return GP_OK;
 }
@@ -870,8 +899,19 @@ int gp_batch_set_state(gp_batch* b, int run, const void* psi, int on_device) {
   if (rc) return rc;
   const long off = run < 0 ? 0 : b->off[run];
   const long cnt = run < 0 ? b->total : (long)b->n[2 * run] * b->n[2 * run + 1];
-  GP_CUDA(cudaMemcpyAsync((char*)b->psi + off * b->esize, psi, (size_t)cnt * b->esize,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->work));
+  if (b->prec == GP_DF64) {  // complex128 in, split on the device
+    const void* src = psi;
+    if (!on_device) {
+      GP_CUDA(cudaMemcpyAsync((double2*)b->stage + off, psi, (size_t)cnt * sizeof(double2), cudaMemcpyHostToDevice,
+                              b->work));
+      src = (const double2*)b->stage + off;
+    }
+    launch_c128_to_df((df64x2*)b->psi + off, src, cnt, b->work);
+    GP_CUDA(cudaGetLastError());
+  } else {
+    GP_CUDA(cudaMemcpyAsync((char*)b->psi + off * b->esize, psi, (size_t)cnt * b->esize,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->work));
+  }
   if (!on_device) GP_CUDA(cudaStreamSynchronize(b->work));
   return b_join_out(b);
 }
@@ -883,8 +923,16 @@ int gp_batch_get_state(gp_batch* b, int run, void* psi, int on_device) {
   if (rc) return rc;
   const long off = run < 0 ? 0 : b->off[run];
   const long cnt = run < 0 ? b->total : (long)b->n[2 * run] * b->n[2 * run + 1];
-  GP_CUDA(cudaMemcpyAsync(psi, (const char*)b->psi + off * b->esize, (size_t)cnt * b->esize,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->work));
+  if (b->prec == GP_DF64) {  // rounded to complex128
+    void* dst = on_device ? psi : (void*)((double2*)b->stage + off);
+    launch_df_to_c128(dst, (const df64x2*)b->psi + off, cnt, b->work);
+    GP_CUDA(cudaGetLastError());
+    if (!on_device)
+      GP_CUDA(cudaMemcpyAsync(psi, dst, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToHost, b->work));
+  } else {
+    GP_CUDA(cudaMemcpyAsync(psi, (const char*)b->psi + off * b->esize, (size_t)cnt * b->esize,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->work));
+  }
   if (!on_device) GP_CUDA(cudaStreamSynchronize(b->work));
   return b_join_out(b);
 }
@@ -892,14 +940,20 @@ int gp_batch_get_state(gp_batch* b, int run, void* psi, int on_device) {
 int gp_batch_step_real(gp_batch* b, long nsteps) {
   if (!b) return fail(GP_ERR_INVALID, "gp_batch_step_real: NULL handle");
   if (nsteps < 0) return fail(GP_ERR_INVALID, "gp_batch_step_real: nsteps < 0");
-  return b->prec == GP_F64 ? batch_steps<double>(b, nsteps) : batch_steps<float>(b, nsteps);
+  return b->prec == GP_F64    ? batch_steps<double>(b, nsteps)
+         : b->prec == GP_DF64 ? batch_steps<df64>(b, nsteps)
+                              : batch_steps<float>(b, nsteps);
 }
 
 int gp_batch_observables(gp_batch* b, gp_obs* out) {
   if (!b || !out) return fail(GP_ERR_INVALID, "gp_batch_observables: NULL argument");
   int rc = b_join_in(b);
   if (rc) return rc;
-  rc = b->prec == GP_F64 ? batch_observables<double>(b) : batch_observables<float>(b);
+  if (b->prec == GP_DF64) {
+    launch_df_to_c128(b->stage, b->psi, b->total, b->work);  // the observables of the rounded states
+    GP_CUDA(cudaGetLastError());
+  }
+  rc = b->prec != GP_F32 ? batch_observables<double>(b) : batch_observables<float>(b);
   if (rc) return rc;
   GP_CUDA(cudaMemcpyAsync(b->obs_host, b->obs_out, 8 * sizeof(double) * b->nruns, cudaMemcpyDeviceToHost, b->work));
   GP_CUDA(cudaMemcpyAsync(b->obs_host + 8L * b->nruns, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost, b->work));

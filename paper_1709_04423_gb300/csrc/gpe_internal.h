@@ -233,6 +233,8 @@ int run_observables_df(gp_handle* h, double* dens_dev, double* sums_out = nullpt
 // double-float state <-> complex128 (device buffers, on the library stream)
 void df_from_c128(gp_handle* h, const void* src);
 void df_to_c128(gp_handle* h, void* dst);
+void launch_c128_to_df(void* dst, const void* src, long n, cudaStream_t s);
+void launch_df_to_c128(void* dst, const void* src, long n, cudaStream_t s);
 // real imaginary-time state: its complex copy into psi (no-op for a complex
 // state); the real state from psi (synchronises; GP_ERR_STATE if an
 // imaginary part is nonzero)

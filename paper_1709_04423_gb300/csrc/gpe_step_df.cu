@@ -34,6 +34,16 @@ int grid_for(long n) { return (int)std::min<long>((n + 255) / 256, 152L * 8); }
 
 }  // namespace
 
+// complex128 <-> double-float states of n points on stream s (the batch's)
+void launch_c128_to_df(void* dst, const void* src, long n, cudaStream_t s) {
+  c128_to_df_kernel<<<grid_for(n), 256, 0, s>>>((df64x2*)dst, (const double2*)src, n);
+  count_launch();
+}
+void launch_df_to_c128(void* dst, const void* src, long n, cudaStream_t s) {
+  df_to_c128_kernel<<<grid_for(n), 256, 0, s>>>((double2*)dst, (const df64x2*)src, n);
+  count_launch();
+}
+
 void df_from_c128(gp_handle* h, const void* src) {
   c128_to_df_kernel<<<grid_for(h->np), 256, 0, h->work>>>((df64x2*)h->psi, (const double2*)src, h->np);
   count_launch();

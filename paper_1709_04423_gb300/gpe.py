@@ -601,15 +601,16 @@ class Batch:
         self.torch = torch
         self.sizes = [tuple(int(v) for v in s) for s in sizes]
         self.nruns = len(self.sizes)
-        if precision not in ("f64", "f32"):
-            raise ValueError("batched runs take precision 'f64' or 'f32'")
+        if precision not in ("f64", "f32", "df64"):
+            raise ValueError("batched runs take precision 'f64', 'f32' or 'df64'")
         self.precision = precision
-        self.ctype = torch.complex128 if precision == "f64" else torch.complex64
+        wide = precision != "f32"   # double-float states are exchanged as complex128
+        self.ctype = torch.complex128 if wide else torch.complex64
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
         self.b = gp_batch_init(self.nruns, self.sizes, dx, dt, nkl, g,
-                               GP_F64 if precision == "f64" else GP_F32, stream.cuda_stream)
+                               {"f64": GP_F64, "f32": GP_F32, "df64": GP_DF64}[precision], stream.cuda_stream)
 
     def close(self):
         if self.b is not None:
@@ -626,7 +627,7 @@ class Batch:
         nx, ny = self.sizes[run]
         if isinstance(psi, np.ndarray):
             a = np.ascontiguousarray(psi.reshape(ny, nx),
-                                     dtype=np.complex128 if self.precision == "f64" else np.complex64)
+                                     dtype=np.complex64 if self.precision == "f32" else np.complex128)
             gp_batch_set_state(self.b, run, a.ctypes.data, 0)
             return
         t = psi.reshape(ny, nx).to(dtype=self.ctype).contiguous()
@@ -645,7 +646,7 @@ class Batch:
             out = self.torch.empty((ny, nx), dtype=self.ctype, device="cuda")
             gp_batch_get_state(self.b, run, out.data_ptr(), 1)
             return out
-        out = np.empty((ny, nx), dtype=np.complex128 if self.precision == "f64" else np.complex64)
+        out = np.empty((ny, nx), dtype=np.complex64 if self.precision == "f32" else np.complex128)
         gp_batch_get_state(self.b, run, out.ctypes.data, 0)
         return out
 

@@ -5,7 +5,8 @@ A run in a batch must give exactly what the same run gives in its own handle
 oracle run by run.  The full-size case is the 64-run workload (sizes drawn
 from {128, 192, 256, 384, 512}^2, dx = 0.1, dt = 5e-4, g ~ U[0, 50], nu = 1,
 kappa ~ U[1, 2]) in the launch configuration the benchmark times, checked on
-sampled runs against the oracle.  The one-launch form (FP32; per-run step
+sampled runs against the oracle; so must the double-float batch (FP64-class
+results on the FP32 pipes), which must also equal each run alone.  The one-launch form (FP32; per-run step
 waits inside one persistent launch) must give the per-class launches' states
 bit for bit, its bounded waits must come back as GP_ERR_TIMEOUT when made to
 run out, and the autotuner must keep the faster form and leave the states as
@@ -41,7 +42,7 @@ RUNS = [  # (nx, ny), (dx, dy), (nu, kappa), g -- one per segment class and ragg
 ]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_batch_equals_each_run_alone(G, prec):
     sizes = [r[0] for r in RUNS]
     b = G.Batch(sizes, [r[1] for r in RUNS], 5e-4, [r[2] for r in RUNS], [r[3] for r in RUNS], precision=prec)
@@ -61,9 +62,12 @@ def test_batch_equals_each_run_alone(G, prec):
     b.close()
 
 
-def test_batch_f64_matches_oracle(G):
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_batch_f64_matches_oracle(G, prec):
+    """The FP64 and double-float batches against the oracle run by run (the
+    double-float states rounded to complex128)."""
     sizes = [r[0] for r in RUNS]
-    b = G.Batch(sizes, [r[1] for r in RUNS], 5e-4, [r[2] for r in RUNS], [r[3] for r in RUNS], precision="f64")
+    b = G.Batch(sizes, [r[1] for r in RUNS], 5e-4, [r[2] for r in RUNS], [r[3] for r in RUNS], precision=prec)
     refs = []
     for i, (n, dx, nk, g) in enumerate(RUNS):
         phi = I.gaussian_state(2, list(n), list(dx), list(nk), seed=50 + i, noise=1e-2)

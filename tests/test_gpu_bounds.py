@@ -109,7 +109,7 @@ def test_kernel_shapes_pass_the_checks(lib, shapes, imag):
     assert rc == 0 and code == 0, (code, msg)
 
 
-@pytest.mark.parametrize("prec,mode", [("f64", 0), ("f32", 0), ("f32", 1)])
+@pytest.mark.parametrize("prec,mode", [("f64", 0), ("f32", 0), ("f32", 1), ("df64", 0)])
 def test_batch_of_edge_sizes_passes_the_checks(lib, prec, mode):
     sizes = [(3, 3), (17, 5), (514, 4), (4, 514), (64, 48)]   # a batch takes at most 514 points per axis
     nr = len(sizes)
