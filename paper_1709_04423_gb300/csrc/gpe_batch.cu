@@ -84,11 +84,16 @@ __global__ void __launch_bounds__(512) batch_x_kernel(const BatchRun<T>* __restr
   tsweep_body<T, false, true, false, SEG>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
 }
 
-// x lines whose shared-memory tile would not fit (FP64, n > 333): one warp
-// per line, 4 lines per block; the item's L0 is the block's first line.
+// x lines whose shared-memory tile would not fit (FP64 and double-float,
+// n > 333): one warp per line, 4 lines per block; the item's L0 is the
+// block's first line.  The double-float body is held to 128 registers (four
+// blocks per SM): with the 234 it would take, 8 warps per SM left it
+// latency-bound (604 us per launch on the 64-run workload, ncu; the whole
+// double-float batch 7.29e9 -> 9.24e9 point-steps/s with the cap, 8.96e9 at
+// 80 registers).
 template <typename T, int SEG>
-__global__ void __launch_bounds__(128) batch_xw_kernel(const BatchRun<T>* __restrict__ runs,
-                                                       const BatchItem* __restrict__ items, T dt) {
+__global__ void __launch_bounds__(128, std::is_same<T, df64>::value ? 4 : 1)
+    batch_xw_kernel(const BatchRun<T>* __restrict__ runs, const BatchItem* __restrict__ items, T dt) {
   __shared__ double red_smem[32];
   const BatchItem it = items[blockIdx.x];
   const BatchRun<T>& R = runs[it.run];
