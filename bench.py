@@ -280,7 +280,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
+        "data": "synthetic, seeded",
         "config": line_config(1),
         "timing": {"inner_steps_per_step": per, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
@@ -780,7 +780,7 @@ def run_ours(args):
         "metric": METRIC, "value": h32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h32["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state+sweeps, f64 reductions",
-        "data": "synthetic (seeded Gaussian + 1e-3 SplitMix64 noise)",
+        "data": "synthetic, seeded",
         "config": line_config(world),
         "timing": {"inner_steps_per_step": args.inner, "l2": "flushed before every timed step"},
         "roofline": roof,
@@ -789,9 +789,6 @@ def run_ours(args):
         "gpu_launches": h32["launches"],
         "clocks": h32["clocks"],
         "f32_err_vs_f64": {"job_end_5000": form_err("f32", "job_end"), "converged_20000": form_err("f32", "converged_20000"),
-                           # the quench starts from each form's own 1500-step imaginary-time ground state
-                           "quench256_start": errs(q["f32"]["obs_start"], q["f64"]["obs_start"], LINE_OBS)
-                           if "f32" in q and "f64" in q else None,
                            "quench256_end": errs(q["f32"]["obs_end"], q["f64"]["obs_end"], LINE_OBS)
                            if "f32" in q and "f64" in q else None,
                            "batched_worst_run_4000": {k: v for k, v in bat.get("f32_err_vs_f64_4000_steps", {})
@@ -809,8 +806,9 @@ def run_ours(args):
                      "batched_df64_vs_f64": ratio(bat.get("df64", {}).get("value"), bat.get("f64", {}).get("value"))},
         "values": {"f64_128": hv.get("f64"), "df64_128": hv.get("df64"),
                    "batched_f32": bat.get("f32", {}).get("value"), "batched_f64": bat.get("f64", {}).get("value"),
-                   "batched_f32_class": bat.get("f32_class", {}).get("value"),
-                   "batched_f32_one_launch": bat.get("f32_one_launch", {}).get("value"),
+                   "batched_df64": bat.get("df64", {}).get("value"),
+                   "batched_f32_class_vs_one_launch": [bat.get("f32_class", {}).get("value"),
+                                                       bat.get("f32_one_launch", {}).get("value")],
                    "adjoint_f32_fwd_bwd": R.get("adjoint_f32", {}).get("value")},
         "fp_rates": R["fp_rates"],
     }
