@@ -140,6 +140,7 @@ def test_tma_shape_refused_where_it_does_not_fit(G):
 XGRIDS = [
     (2, [64, 48], [0.2, 0.25]),
     (2, [256, 34], [0.05, 0.3]),
+    (2, [256, 40], [0.02, 0.3]),   # |alpha| ~ 0.4 along x: carries cross several segments (depth > 1)
     (3, [48, 33, 24], [0.25, 0.3, 0.35]),
     (3, [128, 40, 30], [0.1, 0.3, 0.35]),
 ]
