@@ -238,6 +238,29 @@ void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, i
     }
 }
 
+void carry_reach(const cd* gf, const cd* gb, const cd* tabs, int n, int sg, int first, double tau, int& depth,
+                 int& pts) {
+  const int last = first == 0 ? n - 1 : n - 2;
+  const int nseg = std::min(16, (last - first + 1 + sg - 1) / sg);
+  pts = 1;
+  for (int q = 0; q < nseg; ++q) {
+    const int k0 = first + q * sg, kend = std::min(last, k0 + sg - 1), jend = kend - k0 + 1;
+    for (int k = k0; k <= kend; ++k) {
+      const int j = k - k0;
+      if (std::abs(gf[k]) > tau) pts = std::max(pts, j + 1);
+      if (std::abs(gb[k]) > tau) pts = std::max(pts, jend - j);
+    }
+  }
+  const cd* Pf = tabs;
+  const cd* Pb = tabs + 256;
+  depth = 1;
+  for (int a = 0; a < nseg; ++a)
+    for (int b = 0; b < nseg; ++b) {
+      if (b < a && std::abs(Pf[b * 16 + a - 1]) > tau) depth = std::max(depth, a - b);
+      if (b > a && a + 1 < 16 && std::abs(Pb[b * 16 + a + 1]) > tau) depth = std::max(depth, b - a);
+    }
+}
+
 namespace {
 
 template <typename T>
@@ -290,6 +313,11 @@ int upload_coefs_t(gp_handle* h) {
       }
       std::vector<cd> tabs((size_t)kNumSegs * 512, cd(0, 0));
       for (int si = 0; si < kNumSegs; ++si) carry_tables(af, ab, n, kSegs[si], tabs.data() + (size_t)si * 512);
+      // how far the carries reach above the state precision's threshold
+      const double tau = std::ldexp(1.0, h->prec == GP_F32 ? -48 : -64);
+      for (int si = 0; si < kNumSegs; ++si)
+        carry_reach(all.data() + (size_t)(1 + 2 * si) * n, all.data() + (size_t)(2 + 2 * si) * n,
+                    tabs.data() + (size_t)si * 512, n, kSegs[si], 1, tau, h->cdepth[mode][d][si], h->cpts[mode][d][si]);
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
       if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;
@@ -304,23 +332,10 @@ int upload_coefs_t(gp_handle* h) {
           std::copy(gb.begin(), gb.end(), ev.begin() + (size_t)(2 * si + 1) * n);
           carry_tables(af, ab, n, sg, ev.data() + (size_t)4 * n + 512 * si, 0);
           // how far a carry reaches above 2^-48 (the TMA x sweep truncates the rest)
-          const double tau = std::ldexp(1.0, -48);
-          const int nseg = n / sg;
-          int nj = 4;
-          for (int q = 0; q < nseg; ++q)
-            for (int j = 0; j < sg; ++j) {
-              const int need = std::max(std::abs(gf[q * sg + j]) > tau ? j + 1 : 0,
-                                        std::abs(gb[q * sg + j]) > tau ? sg - j : 0);
-              nj = std::max(nj, need);
-            }
+          int depth = 1, nj = 1;
+          carry_reach(gf.data(), gb.data(), ev.data() + (size_t)4 * n + 512 * si, n, sg, 0, std::ldexp(1.0, -48),
+                      depth, nj);
           h->even_nj[mode][si] = nj <= 4 ? 4 : (nj <= 8 ? 8 : sg);
-          const cd* P = ev.data() + (size_t)4 * n + 512 * si;
-          int depth = 1;
-          for (int a = 0; a < nseg; ++a)
-            for (int b = 0; b < nseg; ++b) {
-              if (b < a && std::abs(P[b * 16 + a - 1]) > tau) depth = std::max(depth, a - b);        // forward
-              if (b > a && std::abs(P[256 + b * 16 + a + 1]) > tau) depth = std::max(depth, b - a);  // backward
-            }
           h->even_depth[mode][si] = depth;
         }
         if ((rc = upload_c2<T>(h, h->coef_even[mode], ev))) return rc;

@@ -42,6 +42,7 @@ struct BatchRun {
   const T* vx; const T* vy; const T* vz0;                  // nu^2 x^2/2, kappa^2 y^2/2, a single 0 (FP32)
   T g;
   const tf3c* tfx; const tf3c* tfy;  // the factors fx, fy as exact triple-floats (double-float state)
+  int cdepth[2], cpts[2];            // per axis: the segment carries' reach (as the single-grid handle's)
 };
 
 struct BatchItem {
@@ -70,6 +71,8 @@ __global__ void __launch_bounds__(512) batch_x_kernel(const BatchRun<T>* __restr
   A.gf = R.coef[0] + R.nx;
   A.gb = R.coef[0] + 2 * R.nx;
   A.ptab = R.ptab[0];
+  A.cdepth = R.cdepth[0];
+  A.cpts = R.cpts[0];
   A.fx = R.fx;
   A.fy = R.fy;
   A.fz = R.fz1;
@@ -146,6 +149,8 @@ __global__ void __launch_bounds__(512) batch_y_kernel(const BatchRun<T>* __restr
   A.gf = R.coef[1] + R.ny;
   A.gb = R.coef[1] + 2 * R.ny;
   A.ptab = R.ptab[1];
+  A.cdepth = R.cdepth[1];
+  A.cpts = R.cpts[1];
   colsweep_body<T, false, false, SEG, (SEG * sizeof(T) <= 64)>(A, it.L0, reinterpret_cast<c2_t<T>*>(bsmem_raw), cf, cb, red_smem);
 }
 
@@ -258,6 +263,8 @@ __global__ void __launch_bounds__(512) batch_persist_kernel(PersistArgs P) {
       A.gf = R.coef[0] + R.nx;
       A.gb = R.coef[0] + 2 * R.nx;
       A.ptab = R.ptab[0];
+      A.cdepth = R.cdepth[0];
+      A.cpts = R.cpts[0];
       A.fx = R.fx;
       A.fy = R.fy;
       A.fz = R.fz1;
@@ -282,6 +289,8 @@ __global__ void __launch_bounds__(512) batch_persist_kernel(PersistArgs P) {
       A.gf = R.coef[1] + R.ny;
       A.gb = R.coef[1] + 2 * R.ny;
       A.ptab = R.ptab[1];
+      A.cdepth = R.cdepth[1];
+      A.cpts = R.cpts[1];
       switch (seg) {  // registers kept for the segment as the per-class launches do (8 floats or fewer)
         case 4: colsweep_body<float, false, false, 4, true>(A, it.L0, sm, cf, cb, red_smem); break;
         case 8: colsweep_body<float, false, false, 8, true>(A, it.L0, sm, cf, cb, red_smem); break;
@@ -424,6 +433,7 @@ int build_tables(gp_batch* b) {
   std::vector<T> vbuf(2 * (vtot + 1), T(0));  // complex factors; last entry: the shared 1 for the absent z axis
   vbuf[2 * vtot] = T(1);
   std::vector<T> pbuf(vtot + 1, T(0));        // potentials; last entry: the shared 0 for the absent z axis
+  std::vector<int> reach_d(2 * R, 0), reach_p(2 * R, 0);
   for (int r = 0; r < R; ++r)
     for (int a = 0; a < 2; ++a) {
       const int n = b->n[2 * r + a];
@@ -435,6 +445,8 @@ int build_tables(gp_batch* b) {
       segment_products(f.alpha, n, seg, gf, gb);
       cd tabs[512];
       carry_tables(f.alpha, n, seg, tabs);
+      carry_reach(gf.data(), gb.data(), tabs, n, seg, 1, std::ldexp(1.0, std::is_same<T, float>::value ? -48 : -64),
+                  reach_d[2 * r + a], reach_p[2 * r + a]);
       T* c = cbuf.data() + 2 * coff[2 * r + a];
       for (int k = 0; k < n; ++k) {
         c[2 * k] = (T)f.alpha[k].real(); c[2 * k + 1] = (T)f.alpha[k].imag();
@@ -498,6 +510,10 @@ int build_tables(gp_batch* b) {
     q.g = (T)b->g[r];
     q.tfx = tdev ? (const tf3c*)tdev + voff[2 * r] : nullptr;
     q.tfy = tdev ? (const tf3c*)tdev + voff[2 * r + 1] : nullptr;
+    for (int a = 0; a < 2; ++a) {
+      q.cdepth[a] = reach_d[2 * r + a];
+      q.cpts[a] = reach_p[2 * r + a];
+    }
   }
   if ((rc = b_alloc(b, &b->runs_d, R * sizeof(BatchRun<T>)))) return rc;
   GP_CUDA(cudaMemcpyAsync(b->runs_d, runs.data(), R * sizeof(BatchRun<T>), cudaMemcpyHostToDevice, b->work));

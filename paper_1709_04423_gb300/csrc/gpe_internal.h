@@ -104,6 +104,9 @@ struct gp_handle {
   // that take a carry, and segments a carry crosses, above 2^-48 (gpe_tma.cuh)
   int even_nj[gpe::NUM_MODES][2] = {{0}};
   int even_depth[gpe::NUM_MODES][2] = {{0}};
+  // per mode, axis and segment length: the segment carries' reach (Sweep2Args cdepth, cpts)
+  int cdepth[gpe::NUM_MODES][3][gpe::kNumSegs] = {};
+  int cpts[gpe::NUM_MODES][3][gpe::kNumSegs] = {};
   // circular / axial traps (geom 2): per mode, the rho axis' backward
   // coefficients, forward right-hand-side factors and stencil factors
   // (vab, vbf, vh of Sweep2Args; 3 n[0] complex values)
@@ -200,6 +203,12 @@ void segment_products(const std::vector<std::complex<double>>& af, const std::ve
                       int first = 1);
 void carry_tables(const std::vector<std::complex<double>>& af, const std::vector<std::complex<double>>& ab, int n,
                   int sg, std::complex<double>* out, int first = 1);
+// How far the segment carries reach above tau, read off one segmentation's
+// tables (gf, gb: n values; tabs: its 512 carry-table values): depth =
+// segments a carry crosses, pts = points at a segment's start (end) that take
+// one (both >= 1).
+void carry_reach(const std::complex<double>* gf, const std::complex<double>* gb, const std::complex<double>* tabs,
+                 int n, int sg, int first, double tau, int& depth, int& pts);
 int tile_seg(int M);
 bool plane_fits(const gp_handle* h, int seg);  // the fused x + y sweep kernel takes this grid and segment length
 bool tma_fits(const gp_handle* h, int seg);    // the TMA y/z sweeps take this grid and segment length

@@ -405,6 +405,8 @@ bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
     a.gf = coef_ptr<T>(h, mode, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, mode, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[mode][d] + (size_t)si * 512;
+    a.cdepth = h->cdepth[mode][d][si];
+    a.cpts = h->cpts[mode][d][si];
     set_phase_args<T>(h, imag, (h->strang && half_open) || fuse_close, a);
     a.parts_in = parts_in;
     a.nparts_in = h->parts_n;
@@ -431,6 +433,8 @@ bool enqueue_sweep(gp_handle* h, bool imag, NormSlots ns, int d, const void* src
         ay.gf = coef_ptr<float>(h, mode, 1, 1 + 2 * si);
         ay.gb = coef_ptr<float>(h, mode, 1, 2 + 2 * si);
         ay.ptab = (const float2*)h->ctab[mode][1] + (size_t)si * 512;
+        ay.cdepth = h->cdepth[mode][1][si];
+        ay.cpts = h->cpts[mode][1][si];
         blocks = imag ? launch_xy_seg<true>(seg, a, ay, h->work, h->pdl_now)
                       : launch_xy_seg<false>(seg, a, ay, h->work, h->pdl_now);
         done = true;
@@ -576,6 +580,8 @@ void enqueue_sweep_real(gp_handle* h, NormSlots ns, int d) {
     a.gf = coef_ptr<T>(h, MODE_IMAG, d, 1 + 2 * si);
     a.gb = coef_ptr<T>(h, MODE_IMAG, d, 2 + 2 * si);
     a.ptab = (const c2_t<T>*)h->ctab[MODE_IMAG][d] + (size_t)si * 512;
+    a.cdepth = h->cdepth[MODE_IMAG][d][si];
+    a.cpts = h->cpts[MODE_IMAG][d][si];
     set_phase_args<T>(h, true, false, a);
     a.parts_in = read ? h->parts[ns.rd] : nullptr;
     a.nparts_in = h->parts_n;
@@ -859,6 +865,8 @@ void enqueue_adj_sweep(gp_handle* h, int d) {
   a.gf = coef_ptr<T>(h, MODE_REAL_ADJ, d, 1 + 2 * si);
   a.gb = coef_ptr<T>(h, MODE_REAL_ADJ, d, 2 + 2 * si);
   a.ptab = (const c2_t<T>*)h->ctab[MODE_REAL_ADJ][d] + (size_t)si * 512;
+  a.cdepth = h->cdepth[MODE_REAL_ADJ][d][si];
+  a.cpts = h->cpts[MODE_REAL_ADJ][d][si];
   if (d == 0 && h->tile_x && h->pipe_x) launch_p_seg<T, false, false, false, true>(seg, a, h->work, h->pdl_now);
   else if (d == 0 && h->tile_x) launch_t_seg<T, false, false, false>(seg, a, h->work, h->pdl_now);
   else if (d == 0) launch_x_seg<T, false, false, false>(seg, a, h->work, h->pdl_now);

@@ -109,6 +109,11 @@ struct Sweep2Args {
   const c2_t<T>* vab;
   const c2_t<T>* vbf;
   const c2_t<T>* vh;
+  // how far the segment carries reach above the precision's threshold (the
+  // host reads them off gf, gb and the carry tables): carries cross at most
+  // cdepth segments and reach the first (last) cpts points of a segment; 0 =
+  // every segment and point
+  int cdepth, cpts;
 };
 
 // Sub-step N at one point: p <- F exp(-i a) p (real time) or F exp(-a) p
@@ -443,13 +448,18 @@ __device__ __forceinline__ void stream_forward(GetP getp, c2_t<T> (&e)[SEG], con
 // one per lane and whose segments run one per warp: on entry z holds the
 // segment-local forward values e^ (zero carry-in); on exit the increment z_k.
 // Two block barriers; every thread of the block must call it.  vab: the
-// backward coefficients of a rho axis (VAR), else those of sc.
+// backward coefficients of a rho axis (VAR), else those of sc.  cdepth, cpts
+// (Sweep2Args): the carries' reach; the terms left out are products of the
+// recurrence coefficients below the host's threshold (2^-48 for an FP32
+// state, 2^-64 otherwise), far below a rounding of the carried value.
 template <typename T, bool IMAG, int SEG>
 __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc, int n, c2_t<T> (*cf)[33],
                                             c2_t<T> (*cb)[33], int s, int nseg, int lane,
-                                            const c2_t<T>* vab = nullptr) {
+                                            const c2_t<T>* vab = nullptr, int cdepth = 0, int cpts = 0) {
   using c2 = c2_t<T>;
   const int M = n - 2, k0 = 1 + s * SEG;
+  const int dep = cdepth > 0 ? cdepth : 16, np_ = cpts > 0 ? cpts : SEG;
+  const int jend = min(SEG, M - k0 + 1);  // points of this segment (the last one may be partial)
   const c2* al = sc;
   const c2* gf = sc + n;
   const c2* gb = sc + 2 * n;
@@ -463,21 +473,22 @@ __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc
   }
   __syncthreads();
   c2 Ein = mk<T>(0, 0);
-  for (int q = 0; q < s; ++q) Ein = cf_fma<T, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
+  for (int q = max(0, s - dep); q < s; ++q) Ein = cf_fma<T, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
-    if (k <= M) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
+    if (k <= M && j < np_) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
   }
   local_backward<T, IMAG, SEG>(z, vab ? vab : al, k0, M);
   cb[s][lane] = z[0];
   __syncthreads();
   c2 Zin = mk<T>(0, 0);
-  for (int q = s + 1; q < nseg; ++q) Zin = cf_fma<T, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
+  const int qe = min(nseg, s + 1 + dep);
+  for (int q = s + 1; q < qe; ++q) Zin = cf_fma<T, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
-    if (k <= M) z[j] = cf_fma<T, IMAG>(gb[k], Zin, z[j]);
+    if (k <= M && j >= jend - np_) z[j] = cf_fma<T, IMAG>(gb[k], Zin, z[j]);
   }
 }
 
@@ -584,7 +595,7 @@ __device__ __forceinline__ void colsweep_body(const Sweep2Args<T>& A, int L0, c2
         },
         z, sc, k0, M);
   }
-  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
+  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane, nullptr, A.cdepth, A.cpts);
   T nval = T(0);
   if (active) {
     const T* w = A.w_axis;
@@ -804,7 +815,7 @@ __device__ __forceinline__ void tsweep_body(const Sweep2Args<T>& A, int L0, c2_t
   stream_forward<T, IMAG, SEG, VAR>(
       [&](int k) { return (k >= 1 && k <= M) ? tile[k * kTilePitch + lane] : mk<T>(0, 0); }, z, sc, k0, M, A.vbf,
       A.vh);
-  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane, VAR ? A.vab : nullptr);
+  seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane, VAR ? A.vab : nullptr, A.cdepth, A.cpts);
   T tacc = T(0);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
@@ -954,7 +965,7 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
     c2 z[SEG];
     stream_forward<T, IMAG, SEG>(
         [&](int k) { return (row_ok && k >= 1 && k <= Mx) ? P[j * PX + k] : mk<T>(0, 0); }, z, scx, k0, Mx);
-    seg_carries<T, IMAG, SEG>(z, scx, nx, cf[g], cb[g], s, nseg, lane);
+    seg_carries<T, IMAG, SEG>(z, scx, nx, cf[g], cb[g], s, nseg, lane, nullptr, Ax.cdepth, Ax.cpts);
     if (row_ok) {
 #pragma unroll
       for (int q = 0; q < SEG; ++q) {
@@ -975,7 +986,7 @@ __global__ void __launch_bounds__(1024) xyplane_kernel(Sweep2Args<float> Ax, Swe
     c2 z[SEG];
     stream_forward<T, IMAG, SEG>(
         [&](int k) { return (col_ok && k >= 1 && k <= My) ? P[k * PX + i] : mk<T>(0, 0); }, z, scy, k0, My);
-    seg_carries<T, IMAG, SEG>(z, scy, ny, cf[g], cb[g], s, nseg, lane);
+    seg_carries<T, IMAG, SEG>(z, scy, ny, cf[g], cb[g], s, nseg, lane, nullptr, Ay.cdepth, Ay.cpts);
     if (col_ok) {
 #pragma unroll
       for (int q = 0; q < SEG; ++q) {
@@ -1246,7 +1257,7 @@ __global__ void __launch_bounds__(512) psweep_kernel(Sweep2Args<T> A) {
     }
     c2 z[SEG];
     stream_forward<T, IMAG, SEG>([&](int k) { return (k >= 1 && k <= M) ? at(k) : mk<T>(0, 0); }, z, sc, k0, M);
-    seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane);
+    seg_carries<T, IMAG, SEG>(z, sc, n, cf, cb, s, nseg, lane, nullptr, A.cdepth, A.cpts);
     T tacc = T(0);
     if (AXIS0) {
 #pragma unroll

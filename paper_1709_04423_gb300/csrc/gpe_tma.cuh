@@ -169,7 +169,10 @@ __device__ __forceinline__ void tma_forward(const float2* buf, int lane, const f
 // The consumer warps (32 nseg threads) synchronise on barrier 1.
 template <bool IMAG, int SEG, bool FULL>
 __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, int n, float2 (*cf)[33],
-                                            float2 (*cb)[33], int s, int nseg, int lane, int k0, int M) {
+                                            float2 (*cb)[33], int s, int nseg, int lane, int k0, int M,
+                                            int cdepth, int cpts) {
+  const int dep = cdepth > 0 ? cdepth : 16, np_ = cpts > 0 ? cpts : SEG;
+  const int jend = min(SEG, M - k0 + 1);
   const float2* al = sc;
   const float2* gf = sc + n;
   const float2* gb = sc + 2 * n;
@@ -186,11 +189,11 @@ __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, 
   }
   consumers_sync(32 * nseg);
   float2 Ein = make_float2(0.f, 0.f);
-  for (int q = 0; q < s; ++q) Ein = cf_fma<float, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
+  for (int q = max(0, s - dep); q < s; ++q) Ein = cf_fma<float, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
-    if (FULL || k <= M) z[j] = cf_fma<float, IMAG>(gf[k], Ein, z[j]);
+    if ((FULL || k <= M) && j < np_) z[j] = cf_fma<float, IMAG>(gf[k], Ein, z[j]);
   }
   float2 next = make_float2(0.f, 0.f);
 #pragma unroll
@@ -203,11 +206,12 @@ __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, 
   cb[s][lane] = z[0];
   consumers_sync(32 * nseg);
   float2 Zin = make_float2(0.f, 0.f);
-  for (int q = s + 1; q < nseg; ++q) Zin = cf_fma<float, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
+  const int qe = min(nseg, s + 1 + dep);
+  for (int q = s + 1; q < qe; ++q) Zin = cf_fma<float, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
-    if (FULL || k <= M) z[j] = cf_fma<float, IMAG>(gb[k], Zin, z[j]);
+    if ((FULL || k <= M) && j >= jend - np_) z[j] = cf_fma<float, IMAG>(gb[k], Zin, z[j]);
   }
 }
 
@@ -276,7 +280,7 @@ __device__ __forceinline__ float tma_solve_tile(const Sweep2Args<float>& A, floa
   const int k0 = 1 + s * SEG;
   float2 z[SEG];
   tma_forward<IMAG, SEG, FULL>(buf, lane, sc, k0, M, z);
-  tma_carries<IMAG, SEG, FULL>(z, sc, n, cf, cb, s, nseg, lane, k0, M);
+  tma_carries<IMAG, SEG, FULL>(z, sc, n, cf, cb, s, nseg, lane, k0, M, A.cdepth, A.cpts);
   float tacc = 0.f;
   const long st = G.stride;
   const long qb = G.axis == 1 ? (long)i + (long)G.nx * G.ny * c : (long)i + (long)G.nx * c;

@@ -169,5 +169,7 @@ def test_df64_limits(G):
     with pytest.raises(G.GPError):
         G.gp_adjoint_forward(p.h, 4, 2)
     p.close()
-    with pytest.raises(ValueError):
-        G.Batch([(16, 16)], [(0.1, 0.1)], 1e-3, [(1.0, 1.0)], [1.0], precision="df64")
+    b = G.Batch([(16, 16)], [(0.1, 0.1)], 1e-3, [(1.0, 1.0)], [1.0], precision="df64")   # the batch takes it
+    with pytest.raises(G.GPError):
+        b.set_mode(1)                                     # but not its one-launch form (FP32 only)
+    b.close()
