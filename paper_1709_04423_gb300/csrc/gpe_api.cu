@@ -241,9 +241,10 @@ void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, i
 void carry_reach(const cd* gf, const cd* gb, const cd* tabs, int n, int sg, int first, double tau, int& depth,
                  int& pts) {
   const int last = first == 0 ? n - 1 : n - 2;
-  const int nseg = std::min(16, (last - first + 1 + sg - 1) / sg);
+  const int nall = (last - first + 1 + sg - 1) / sg;  // every segment (a warp-per-line sweep has up to 32)
+  const int nseg = std::min(16, nall);                // those of the 16 x 16 carry tables
   pts = 1;
-  for (int q = 0; q < nseg; ++q) {
+  for (int q = 0; q < nall; ++q) {
     const int k0 = first + q * sg, kend = std::min(last, k0 + sg - 1), jend = kend - k0 + 1;
     for (int k = k0; k <= kend; ++k) {
       const int j = k - k0;

@@ -113,6 +113,8 @@ __global__ void __launch_bounds__(128, std::is_same<T, df64>::value ? 4 : 1)
   A.alpha = R.coef[0];
   A.gf = R.coef[0] + R.nx;
   A.gb = R.coef[0] + 2 * R.nx;
+  A.cdepth = R.cdepth[0];
+  A.cpts = R.cpts[0];
   A.fx = R.fx;
   A.fy = R.fy;
   A.fz = R.fz1;
