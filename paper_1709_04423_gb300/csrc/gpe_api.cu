@@ -238,6 +238,8 @@ void carry_tables(const std::vector<cd>& af, const std::vector<cd>& ab, int n, i
     }
 }
 
+int carry_pts_class(int pts) { return pts <= 4 ? 4 : pts <= 8 ? 8 : pts <= 12 ? 12 : 0; }
+
 void carry_reach(const cd* gf, const cd* gb, const cd* tabs, int n, int sg, int first, double tau, int& depth,
                  int& pts) {
   const int last = first == 0 ? n - 1 : n - 2;
@@ -316,9 +318,12 @@ int upload_coefs_t(gp_handle* h) {
       for (int si = 0; si < kNumSegs; ++si) carry_tables(af, ab, n, kSegs[si], tabs.data() + (size_t)si * 512);
       // how far the carries reach above the state precision's threshold
       const double tau = std::ldexp(1.0, h->prec == GP_F32 ? -48 : -64);
-      for (int si = 0; si < kNumSegs; ++si)
+      for (int si = 0; si < kNumSegs; ++si) {
+        int pts = 0;
         carry_reach(all.data() + (size_t)(1 + 2 * si) * n, all.data() + (size_t)(2 + 2 * si) * n,
-                    tabs.data() + (size_t)si * 512, n, kSegs[si], 1, tau, h->cdepth[mode][d][si], h->cpts[mode][d][si]);
+                    tabs.data() + (size_t)si * 512, n, kSegs[si], 1, tau, h->cdepth[mode][d][si], pts);
+        h->cpts[mode][d][si] = carry_pts_class(pts);
+      }
       int rc = upload_c2<T>(h, h->coef[mode][d], all);
       if (rc) return rc;
       if ((rc = upload_c2<T>(h, h->ctab[mode][d], tabs))) return rc;

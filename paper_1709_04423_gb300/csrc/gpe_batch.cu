@@ -514,7 +514,7 @@ int build_tables(gp_batch* b) {
     q.tfy = tdev ? (const tf3c*)tdev + voff[2 * r + 1] : nullptr;
     for (int a = 0; a < 2; ++a) {
       q.cdepth[a] = reach_d[2 * r + a];
-      q.cpts[a] = reach_p[2 * r + a];
+      q.cpts[a] = carry_pts_class(reach_p[2 * r + a]);
     }
   }
   if ((rc = b_alloc(b, &b->runs_d, R * sizeof(BatchRun<T>)))) return rc;

@@ -209,6 +209,8 @@ void carry_tables(const std::vector<std::complex<double>>& af, const std::vector
 // one (both >= 1).
 void carry_reach(const std::complex<double>* gf, const std::complex<double>* gb, const std::complex<double>* tabs,
                  int n, int sg, int first, double tau, int& depth, int& pts);
+// The class of carried points the block-wide sweeps are unrolled for: 4, 8, 12 or 0 (every point).
+int carry_pts_class(int pts);
 int tile_seg(int M);
 bool plane_fits(const gp_handle* h, int seg);  // the fused x + y sweep kernel takes this grid and segment length
 bool tma_fits(const gp_handle* h, int seg);    // the TMA y/z sweeps take this grid and segment length

@@ -111,8 +111,8 @@ struct Sweep2Args {
   const c2_t<T>* vh;
   // how far the segment carries reach above the precision's threshold (the
   // host reads them off gf, gb and the carry tables): carries cross at most
-  // cdepth segments and reach the first (last) cpts points of a segment; 0 =
-  // every segment and point
+  // cdepth segments and reach the first (last) cpts points of a segment, cpts
+  // one of 4, 8, 12; 0 = every segment and point
   int cdepth, cpts;
 };
 
@@ -458,8 +458,11 @@ __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc
                                             const c2_t<T>* vab = nullptr, int cdepth = 0, int cpts = 0) {
   using c2 = c2_t<T>;
   const int M = n - 2, k0 = 1 + s * SEG;
-  const int dep = cdepth > 0 ? cdepth : 16, np_ = cpts > 0 ? cpts : SEG;
-  const int jend = min(SEG, M - k0 + 1);  // points of this segment (the last one may be partial)
+  const int dep = cdepth > 0 ? cdepth : 16;
+  // cpts is 4, 8, 12 or 0 (every point): the carry loops below are unrolled for
+  // each class, so that no per-point test is added; a partial last segment
+  // takes every point
+  const bool whole = k0 + SEG - 1 <= M;
   const c2* al = sc;
   const c2* gf = sc + n;
   const c2* gb = sc + 2 * n;
@@ -474,22 +477,34 @@ __device__ __forceinline__ void seg_carries(c2_t<T> (&z)[SEG], const c2_t<T>* sc
   __syncthreads();
   c2 Ein = mk<T>(0, 0);
   for (int q = max(0, s - dep); q < s; ++q) Ein = cf_fma<T, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
+  auto fwd = [&](auto nj) {
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    if (k <= M && j < np_) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
-  }
+    for (int j = 0; j < decltype(nj)::value; ++j) {
+      const int k = k0 + j;
+      if (k <= M) z[j] = cf_fma<T, IMAG>(gf[k], Ein, z[j]);
+    }
+  };
+  if (SEG > 4 && cpts == 4) fwd(std::integral_constant<int, (SEG > 4 ? 4 : SEG)>());
+  else if (SEG > 8 && cpts == 8) fwd(std::integral_constant<int, (SEG > 8 ? 8 : SEG)>());
+  else if (SEG > 12 && cpts == 12) fwd(std::integral_constant<int, (SEG > 12 ? 12 : SEG)>());
+  else fwd(std::integral_constant<int, SEG>());
   local_backward<T, IMAG, SEG>(z, vab ? vab : al, k0, M);
   cb[s][lane] = z[0];
   __syncthreads();
   c2 Zin = mk<T>(0, 0);
   const int qe = min(nseg, s + 1 + dep);
   for (int q = s + 1; q < qe; ++q) Zin = cf_fma<T, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
+  auto bwd = [&](auto nj) {
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    if (k <= M && j >= jend - np_) z[j] = cf_fma<T, IMAG>(gb[k], Zin, z[j]);
-  }
+    for (int j = SEG - decltype(nj)::value; j < SEG; ++j) {
+      const int k = k0 + j;
+      if (k <= M) z[j] = cf_fma<T, IMAG>(gb[k], Zin, z[j]);
+    }
+  };
+  if (SEG > 4 && whole && cpts == 4) bwd(std::integral_constant<int, (SEG > 4 ? 4 : SEG)>());
+  else if (SEG > 8 && whole && cpts == 8) bwd(std::integral_constant<int, (SEG > 8 ? 8 : SEG)>());
+  else if (SEG > 12 && whole && cpts == 12) bwd(std::integral_constant<int, (SEG > 12 ? 12 : SEG)>());
+  else bwd(std::integral_constant<int, SEG>());
 }
 
 __device__ __forceinline__ int line_base32(const LineGeom& g, int L) {

@@ -171,8 +171,8 @@ template <bool IMAG, int SEG, bool FULL>
 __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, int n, float2 (*cf)[33],
                                             float2 (*cb)[33], int s, int nseg, int lane, int k0, int M,
                                             int cdepth, int cpts) {
-  const int dep = cdepth > 0 ? cdepth : 16, np_ = cpts > 0 ? cpts : SEG;
-  const int jend = min(SEG, M - k0 + 1);
+  const int dep = cdepth > 0 ? cdepth : 16;
+  const bool whole = FULL || k0 + SEG - 1 <= M;  // (cpts: 4, 8, 12 or 0 = every point, as in seg_carries)
   const float2* al = sc;
   const float2* gf = sc + n;
   const float2* gb = sc + 2 * n;
@@ -190,11 +190,17 @@ __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, 
   consumers_sync(32 * nseg);
   float2 Ein = make_float2(0.f, 0.f);
   for (int q = max(0, s - dep); q < s; ++q) Ein = cf_fma<float, IMAG>(Pf[q * 16 + s - 1], cf[q][lane], Ein);
+  auto fwd = [&](auto nj) {
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    if ((FULL || k <= M) && j < np_) z[j] = cf_fma<float, IMAG>(gf[k], Ein, z[j]);
-  }
+    for (int j = 0; j < decltype(nj)::value; ++j) {
+      const int k = k0 + j;
+      if (FULL || k <= M) z[j] = cf_fma<float, IMAG>(gf[k], Ein, z[j]);
+    }
+  };
+  if (SEG > 4 && cpts == 4) fwd(std::integral_constant<int, (SEG > 4 ? 4 : SEG)>());
+  else if (SEG > 8 && cpts == 8) fwd(std::integral_constant<int, (SEG > 8 ? 8 : SEG)>());
+  else if (SEG > 12 && cpts == 12) fwd(std::integral_constant<int, (SEG > 12 ? 12 : SEG)>());
+  else fwd(std::integral_constant<int, SEG>());
   float2 next = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = SEG - 1; j >= 0; --j) {
@@ -208,11 +214,17 @@ __device__ __forceinline__ void tma_carries(float2 (&z)[SEG], const float2* sc, 
   float2 Zin = make_float2(0.f, 0.f);
   const int qe = min(nseg, s + 1 + dep);
   for (int q = s + 1; q < qe; ++q) Zin = cf_fma<float, IMAG>(Pb[q * 16 + s + 1], cb[q][lane], Zin);
+  auto bwd = [&](auto nj) {
 #pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    if ((FULL || k <= M) && j >= jend - np_) z[j] = cf_fma<float, IMAG>(gb[k], Zin, z[j]);
-  }
+    for (int j = SEG - decltype(nj)::value; j < SEG; ++j) {
+      const int k = k0 + j;
+      if (FULL || k <= M) z[j] = cf_fma<float, IMAG>(gb[k], Zin, z[j]);
+    }
+  };
+  if (SEG > 4 && whole && cpts == 4) bwd(std::integral_constant<int, (SEG > 4 ? 4 : SEG)>());
+  else if (SEG > 8 && whole && cpts == 8) bwd(std::integral_constant<int, (SEG > 8 ? 8 : SEG)>());
+  else if (SEG > 12 && whole && cpts == 12) bwd(std::integral_constant<int, (SEG > 12 ? 12 : SEG)>());
+  else bwd(std::integral_constant<int, SEG>());
 }
 
 // The carries of the even-aligned x sweep (every segment full), truncated to
