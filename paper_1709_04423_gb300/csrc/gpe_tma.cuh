@@ -538,6 +538,30 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
   // ---- consumer warps: warp = segment, lane = line
   const float scl = scl_smem;
   const float inv_ny = 1.0f / (float)G.ny;
+  // per-line part of N of this lane's line in tile t, vy[j] + vz[k] for the
+  // line L = j + ny k: k from a float estimate of L / ny (exact to within one
+  // for L < 2^24), corrected
+  auto line_potential = [&](int t) -> float {
+    const int L = t * 32 + lane;
+    if (A.V || t >= T.ntiles || L >= G.nlines) return 0.f;
+    int kq, jr;
+    if (G.nlines < (1L << 24)) {
+      kq = (int)((float)L * inv_ny);
+      jr = L - kq * G.ny;
+      if (jr < 0) {
+        --kq;
+        jr += G.ny;
+      } else if (jr >= G.ny) {
+        ++kq;
+        jr -= G.ny;
+      }
+    } else {
+      kq = L / G.ny;
+      jr = L - kq * G.ny;
+    }
+    return A.vy[jr] + A.vz[kq];
+  };
+  float vnext = line_potential(blockIdx.x);
   const int k0 = s * SEG;
   int it = 0;
   for (int t = blockIdx.x; t < T.ntiles; t += gridDim.x, ++it) {
@@ -558,27 +582,9 @@ __global__ void __launch_bounds__(544, 1) tmarow_kernel(const __grid_constant__ 
     };
     const int L = t * 32 + lane;
     const bool line_ok = L < G.nlines;
-    // per-line part of N, vy[j] + vz[k] for the line L = j + ny k: k from a
-    // float estimate of L / ny (exact to within one for L < 2^24), corrected
-    float vline = 0.f;
-    if (!A.V && line_ok) {
-      int kq, jr;
-      if (G.nlines < (1L << 24)) {
-        kq = (int)((float)L * inv_ny);
-        jr = L - kq * G.ny;
-        if (jr < 0) {
-          --kq;
-          jr += G.ny;
-        } else if (jr >= G.ny) {
-          ++kq;
-          jr -= G.ny;
-        }
-      } else {
-        kq = L / G.ny;
-        jr = L - kq * G.ny;
-      }
-      vline = A.vy[jr] + A.vz[kq];
-    }
+    // this tile's per-line potential (loaded one tile ahead), the next tile's issued now
+    const float vline = vnext;
+    vnext = line_potential(t + gridDim.x);
     // p[1..SEG]: the points of this segment; p[0], p[SEG + 1]: the points on
     // either side, after N, from the neighbouring segments' warps
     float2 p[SEG + 2];
