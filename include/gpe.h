@@ -325,11 +325,11 @@ long gp_batch_offset(const gp_batch* b, int run);
  * for bit.  Each wait is bounded (GPE_WAIT_LIMIT_MS at gp_batch_init, default
  * 1000 ms); a wait that runs out stops the launch and the next
  * gp_batch_observables returns GP_ERR_TIMEOUT (the states are then not
- * valid).  gp_batch_set_mode: GP_ERR_INVALID for mode 1 on an FP64 batch.
+ * valid).  gp_batch_set_mode: GP_ERR_INVALID for mode 1 on an FP64 or double-float batch.
  * gp_batch_get_mode returns the mode (-1 for NULL).  gp_batch_autotune times
  * nsteps >= 1 steps in each mode (after nsteps untimed ones), keeps the faster
  * and writes the two times in ms to ms_out[0..1] when ms_out is not NULL
- * (-1 where not timed; FP64 batches keep mode 0 untimed); the states are put
+ * (-1 where not timed; FP64 and double-float batches keep mode 0 untimed); the states are put
  * back.  Synchronises the stream. */
 int gp_batch_set_mode(gp_batch* b, int persistent);
 int gp_batch_get_mode(const gp_batch* b);
